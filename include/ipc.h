@@ -1,0 +1,144 @@
+/*
+ * ipc.h -- C ABI of libipcomp, a GB300 (sm_103a) implementation of IPComp,
+ * the interpolation-based progressive lossy compressor of arXiv 2502.04093.
+ *
+ * Compression (Sec. 3.2, Fig. 2): a coarse-to-fine multi-level interpolation
+ * predictor (Sec. 4.1, Eq. 1 linear / Eq. 2 cubic) with error-bounded
+ * quantization of the residuals (Sec. 4.2.2), then the per-level bitplane
+ * split of the 32-bit codes (Sec. 4.3) with negabinary sign coding and 2-bit
+ * prefix predictive XOR (Sec. 4.4). Retrieval: the optimized loader
+ * (Sec. 5.2 error-bound mode, Sec. 5.3 bitrate mode) picks per level how many
+ * low planes to drop, then reconstruction (Algorithm 1) decodes the selected
+ * planes and rebuilds the field by interpolation. Refinement (Algorithm 2)
+ * adds planes to an earlier retrieval.
+ *
+ * Conventions (all entry points):
+ *  - Pointers named d_* are CUDA device pointers owned by the caller; other
+ *    pointers are host pointers. Arrays are dense row-major, last dimension
+ *    fastest, 1 <= ndim <= 3.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is
+ *    ordered on that stream. ipc_compress and ipc_import synchronise with it
+ *    before returning; ipc_retrieve / ipc_refine return as soon as their
+ *    kernels are queued (d_out is valid once the stream reaches that point).
+ *  - ipc_field and ipc_view objects are owned by the library until
+ *    ipc_free. A view refers to its field: free views before their field.
+ *  - Every function returns IPC_OK (0) or a negative status; on error no
+ *    output argument is written and no object is leaked. ipc_last_error()
+ *    returns a short description of the calling thread's last failure.
+ *  - Calls on one field or view must not overlap; different fields may be
+ *    used from different threads. Compressions on one device are serialised
+ *    internally (they share a scratch workspace).
+ */
+#ifndef IPCOMP_IPC_H
+#define IPCOMP_IPC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+enum {
+  IPC_OK = 0,
+  IPC_EINVAL = -1,   /* bad shape / dtype / error bound / argument           */
+  IPC_EBOUND = -2,   /* requested error bound below the compression bound    */
+  IPC_EBUDGET = -3,  /* bitrate below the mandatory (header + tables) bytes  */
+  IPC_ENOMEM = -4,   /* host or device allocation failed                     */
+  IPC_ECORRUPT = -5, /* container failed validation on import                */
+  IPC_ECUDA = -6,    /* a CUDA call failed (see ipc_last_error)              */
+  IPC_ETIMEOUT = -7, /* a bounded wait ran out                               */
+  IPC_EBUSY = -8     /* resource in use (server slots, pending work)         */
+};
+
+typedef enum { IPC_F32 = 0, IPC_F64 = 1 } ipc_dtype;
+/* Eq. 1 (linear, p = 1) or Eq. 2 (cubic, p = 1.25), Sec. 4.1. */
+typedef enum { IPC_LINEAR = 0, IPC_CUBIC = 1 } ipc_interp;
+/* Error bound absolute, or relative to the value range (max - min). */
+typedef enum { IPC_EB_ABS = 0, IPC_EB_REL = 1 } ipc_eb_mode;
+/* Error model of the loader (Sec. 5.1, Theorem 1): STRICT amplifies every
+ * sweep by p and adds a floating-point rounding margin (a rigorous bound);
+ * PAPER applies p once per level as Theorem 1 states. */
+typedef enum { IPC_BOUND_STRICT = 0, IPC_BOUND_PAPER = 1 } ipc_bound;
+/* Retrieval target: kind 0 = L-inf error bound (in the field's eb mode,
+ * Sec. 5.2), kind 1 = bitrate in bits per value (Sec. 5.3). */
+typedef struct {
+  int kind;
+  double value;
+} ipc_target;
+enum { IPC_TARGET_EB = 0, IPC_TARGET_BITRATE = 1 };
+
+typedef struct ipc_field ipc_field; /* compressed field: device streams + host tables */
+typedef struct ipc_view ipc_view;   /* a retrieval: per-level selection (for refine) */
+
+/* ipc_compress -- Sec. 4.1-4.4 (compression workflow of Sec. 3.2).
+ *  d_in   : device array of prod(dims) elements of `dtype` (not modified).
+ *  dims   : host array of ndim extents, each >= 1.
+ *  eb     : error bound (> 0, finite) in `eb_mode` units. Every
+ *           reconstructed value with all planes loaded is within eb of the
+ *           input (Eq. 4); non-finite inputs and values whose residual
+ *           exceeds the code range are stored exactly.
+ *  out    : receives the new field.
+ * Errors: IPC_EINVAL (shape, dtype, eb, relative eb on an all-non-finite
+ * input), IPC_ENOMEM, IPC_ECUDA. Synchronises `stream`. */
+int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims,
+                 int eb_mode, double eb, int interp, int bound, void* stream,
+                 ipc_field** out);
+
+/* ipc_retrieve -- Sec. 5.2/5.3 selection + Algorithm 1 reconstruction.
+ *  d_out : device array of prod(dims) elements of the field's dtype,
+ *          overwritten with the reconstruction.
+ *  out   : receives a view (NULL allowed when no refinement will follow).
+ * The result satisfies max|x - x_out| <= the guaranteed bound reported by
+ * ipc_selection (<= target in eb mode). Errors: IPC_EINVAL, IPC_EBOUND
+ * (target below the compression eb), IPC_EBUDGET (bitrate below the
+ * mandatory bytes), IPC_ENOMEM, IPC_ECUDA. Asynchronous on `stream`. */
+int ipc_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream,
+                 ipc_view** out);
+
+/* ipc_refine -- Algorithm 2 (incremental reconstruction). The new selection
+ * only adds planes (b'_l <= b_l at every level) and minimises the added
+ * bytes; d_out (normally the array of the earlier retrieve) is rewritten with
+ * a reconstruction bitwise equal to a fresh retrieval of the same planes. A
+ * target the view already meets (or, in bitrate mode, a budget below what is
+ * loaded) leaves the view and d_out unchanged and returns IPC_OK. */
+int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream);
+
+/* ipc_free -- frees a field or a view (NULL is accepted). */
+int ipc_free(void* handle);
+
+/* ipc_selection -- the view's per-level selection b_per_level[l-1] = planes
+ * dropped at level l (host array of at least 64 ints, may be NULL), level
+ * count, loaded bytes (mandatory + selected streams) and the guaranteed
+ * absolute L-inf bound (Sec. 5.1). Any output pointer may be NULL. */
+int ipc_selection(const ipc_view* v, int* b_per_level, int* nlevels,
+                  uint64_t* bytes, double* guaranteed_bound);
+
+/* ipc_compressed_size -- bytes of the exported container. */
+int ipc_compressed_size(const ipc_field* f, uint64_t* bytes);
+
+/* ipc_export -- writes the container to host memory. host_buf == NULL:
+ * *len receives the size. Otherwise *len is the capacity on entry (must be
+ * >= size) and the size on return. Synchronous. */
+int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len);
+
+/* ipc_import -- builds a device-resident field from container bytes (host
+ * memory). Errors: IPC_ECORRUPT (bad magic/version/tables/stream layout),
+ * IPC_ENOMEM, IPC_ECUDA. Synchronises `stream`. */
+int ipc_import(const void* host_buf, uint64_t len, void* stream,
+               ipc_field** out);
+
+/* ---- introspection ------------------------------------------------------- */
+/* ipc_field_info -- dtype, ndim, dims (host array of 3), K (levels), S
+ * (non-empty sweeps), absolute eb, and the value range over finite inputs.
+ * Any output pointer may be NULL. */
+int ipc_field_info(const ipc_field* f, int* dtype, int* ndim, int64_t* dims,
+                   int* K, int* S, double* eb, double* xmin, double* xmax);
+
+/* ipc_last_error -- NUL-terminated description of the calling thread's last
+ * failure (empty string if none). Owned by the library. */
+const char* ipc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,240 @@
+"""Thin Python binding of libipcomp's C ABI (include/ipc.h).
+
+Argument marshalling only: every step of compression and retrieval runs in
+the library's CUDA kernels. Function names are the C names. Device buffers
+are torch CUDA tensors (PyTorch provides device memory and streams); the
+stream defaults to torch's current stream.
+
+The library must be built (``paper_2502_04093_gb300.build.build()``); this
+module raises ImportError-derived errors if it is missing - there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libipcomp.so")
+
+IPC_OK, IPC_EINVAL, IPC_EBOUND, IPC_EBUDGET = 0, -1, -2, -3
+IPC_ENOMEM, IPC_ECORRUPT, IPC_ECUDA, IPC_ETIMEOUT, IPC_EBUSY = -4, -5, -6, -7, -8
+IPC_F32, IPC_F64 = 0, 1
+IPC_LINEAR, IPC_CUBIC = 0, 1
+IPC_EB_ABS, IPC_EB_REL = 0, 1
+IPC_BOUND_STRICT, IPC_BOUND_PAPER = 0, 1
+IPC_TARGET_EB, IPC_TARGET_BITRATE = 0, 1
+
+
+class ipc_target(C.Structure):
+    _fields_ = [("kind", C.c_int), ("value", C.c_double)]
+
+
+class IpcError(RuntimeError):
+    def __init__(self, rc: int, what: str, detail: str):
+        super().__init__("%s failed with status %d: %s" % (what, rc, detail))
+        self.rc = rc
+
+
+class LibraryMissing(ImportError):
+    pass
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libipcomp.so from the package directory (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise LibraryMissing("libipcomp.so is not built: run paper_2502_04093_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, u64p = C.c_void_p, C.POINTER(C.c_uint64)
+    i64p = C.POINTER(C.c_int64)
+    L.ipc_compress.argtypes = [vp, C.c_int, C.c_int, i64p, C.c_int, C.c_double, C.c_int,
+                               C.c_int, vp, C.POINTER(vp)]
+    L.ipc_retrieve.argtypes = [vp, ipc_target, vp, vp, C.POINTER(vp)]
+    L.ipc_refine.argtypes = [vp, ipc_target, vp, vp]
+    L.ipc_free.argtypes = [vp]
+    L.ipc_selection.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
+                                C.POINTER(C.c_double)]
+    L.ipc_compressed_size.argtypes = [vp, u64p]
+    L.ipc_export.argtypes = [vp, vp, u64p]
+    L.ipc_import.argtypes = [vp, C.c_uint64, vp, C.POINTER(vp)]
+    L.ipc_field_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p,
+                                 C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.ipc_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != IPC_OK:
+        raise IpcError(rc, what, lib().ipc_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return IPC_F32
+    if t.dtype == torch.float64:
+        return IPC_F64
+    raise TypeError("ipc takes float32 or float64 tensors")
+
+
+def _require_cuda(t, name):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+
+
+def ipc_compress(x, eb: float, eb_mode: int = IPC_EB_ABS, interp: int = IPC_CUBIC,
+                 bound: int = IPC_BOUND_STRICT, stream=None, dims=None) -> C.c_void_p:
+    """Compress the CUDA tensor x; returns an ipc_field handle."""
+    _require_cuda(x, "x")
+    shape = tuple(x.shape) if dims is None else tuple(dims)
+    arr = (C.c_int64 * max(len(shape), 1))(*[int(s) for s in shape])
+    h = C.c_void_p()
+    _check(lib().ipc_compress(C.c_void_p(x.data_ptr()), _dtype_code(x), len(shape), arr,
+                              int(eb_mode), float(eb), int(interp), int(bound), _stream(stream),
+                              C.byref(h)), "ipc_compress")
+    return h
+
+
+def ipc_retrieve(field, kind: int, value: float, out, stream=None, want_view=True):
+    """Reconstruct into the CUDA tensor `out`; returns an ipc_view handle
+    (or None when want_view is False)."""
+    _require_cuda(out, "out")
+    v = C.c_void_p()
+    _check(lib().ipc_retrieve(field, ipc_target(int(kind), float(value)),
+                              C.c_void_p(out.data_ptr()), _stream(stream),
+                              C.byref(v) if want_view else None), "ipc_retrieve")
+    return v if want_view else None
+
+
+def ipc_refine(view, kind: int, value: float, out, stream=None) -> None:
+    _require_cuda(out, "out")
+    _check(lib().ipc_refine(view, ipc_target(int(kind), float(value)),
+                            C.c_void_p(out.data_ptr()), _stream(stream)), "ipc_refine")
+
+
+def ipc_free(handle) -> None:
+    if handle is not None:
+        _check(lib().ipc_free(handle), "ipc_free")
+
+
+def ipc_selection(view):
+    """(b_per_level list, loaded bytes, guaranteed bound)."""
+    b = (C.c_int * 64)()
+    nl = C.c_int()
+    by = C.c_uint64()
+    bd = C.c_double()
+    _check(lib().ipc_selection(view, b, C.byref(nl), C.byref(by), C.byref(bd)), "ipc_selection")
+    return list(b)[:nl.value], by.value, bd.value
+
+
+def ipc_compressed_size(field) -> int:
+    n = C.c_uint64()
+    _check(lib().ipc_compressed_size(field, C.byref(n)), "ipc_compressed_size")
+    return n.value
+
+
+def ipc_export(field) -> bytes:
+    n = C.c_uint64()
+    _check(lib().ipc_export(field, None, C.byref(n)), "ipc_export")
+    buf = (C.c_uint8 * max(n.value, 1))()
+    _check(lib().ipc_export(field, buf, C.byref(n)), "ipc_export")
+    return bytes(buf)[:n.value]
+
+
+def ipc_import(data: bytes, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    arr = (C.c_uint8 * max(len(data), 1)).from_buffer_copy(data if data else b"\0")
+    _check(lib().ipc_import(arr, len(data), _stream(stream), C.byref(h)), "ipc_import")
+    return h
+
+
+def ipc_field_info(field) -> dict:
+    dt, nd, K, S = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    dims = (C.c_int64 * 3)()
+    eb, mn, mx = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().ipc_field_info(field, C.byref(dt), C.byref(nd), dims, C.byref(K), C.byref(S),
+                                C.byref(eb), C.byref(mn), C.byref(mx)), "ipc_field_info")
+    return dict(dtype=dt.value, ndim=nd.value, dims=tuple(dims)[:nd.value], K=K.value,
+                S=S.value, eb=eb.value, xmin=mn.value, xmax=mx.value)
+
+
+def ipc_last_error() -> str:
+    return lib().ipc_last_error().decode(errors="replace")
+
+
+# -- convenience wrappers (own the handles) ---------------------------------
+class Field:
+    """An ipc_field handle that frees itself."""
+
+    def __init__(self, handle, shape, dtype):
+        self.h = handle
+        self.shape = tuple(shape)
+        self.dtype = dtype
+
+    @classmethod
+    def compress(cls, x, eb, eb_mode=IPC_EB_ABS, interp=IPC_CUBIC, bound=IPC_BOUND_STRICT,
+                 stream=None):
+        return cls(ipc_compress(x, eb, eb_mode, interp, bound, stream), x.shape, x.dtype)
+
+    @classmethod
+    def from_bytes(cls, data, shape, dtype, stream=None):
+        return cls(ipc_import(data, stream), shape, dtype)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.ipc_free(self.h)
+            self.h = None
+
+    def retrieve(self, kind, value, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        v = ipc_retrieve(self.h, kind, value, out, stream)
+        return out, View(v, self, out)
+
+    def export(self) -> bytes:
+        return ipc_export(self.h)
+
+    def size(self) -> int:
+        return ipc_compressed_size(self.h)
+
+    def info(self) -> dict:
+        return ipc_field_info(self.h)
+
+
+class View:
+    def __init__(self, handle, field: Field, out):
+        self.h = handle
+        self.field = field
+        self.out = out
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.ipc_free(self.h)
+            self.h = None
+
+    def refine(self, kind, value, stream=None):
+        ipc_refine(self.h, kind, value, self.out, stream)
+        return self.out
+
+    def selection(self):
+        return ipc_selection(self.h)
