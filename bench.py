@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the IPComp hot path on GB300 (one JSON line on rank 0).
+
+Workload: the 512^3 float32 Gaussian random field with a k^-5/3 power
+spectrum (seeded FFT synthesis, min-max normalised to [0, 1]), compressed at
+an absolute error bound of 1e-6 with cubic interpolation and the strict error
+model. One step = one compression of the field + a progressive retrieval
+sweep: retrieve at eb 1e-1 and refine to 1e-2 ... 1e-6 (Algorithm 2), then
+independent retrievals at 0.5, 1, 2, 4, 8 and 16 bits/value. The metric is
+the bytes of field data the step moves through the codec -- the input of the
+compression plus the output of every reconstruction -- per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank compresses its own field (seed + rank):
+the path shards across fields with no data exchange ("weak" scaling).
+--impl reference times the CPU oracle (the plain single-threaded restatement
+of the method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EB = 1e-6
+EB_SWEEP = [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6]
+BITRATES = [0.5, 1.0, 2.0, 4.0, 8.0, 16.0]
+SEED = 1002
+METRIC = "compress+retrieve GB/s (field bytes through the codec; 512^3 f32 progressive sweep)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--edge", type=int, default=512, help="field edge (default 512)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# The GPU step (through the C ABI)
+# ---------------------------------------------------------------------------
+def gpu_step(ipc, x, out, ev=None):
+    """compress + refine chain + bitrate retrievals; returns the field handle."""
+    f = ipc.ipc_compress(x, EB, ipc.IPC_EB_ABS, ipc.IPC_CUBIC, ipc.IPC_BOUND_STRICT)
+    if ev is not None:
+        ev[1].record()
+    v = ipc.ipc_retrieve(f, ipc.IPC_TARGET_EB, EB_SWEEP[0], out)
+    for E in EB_SWEEP[1:]:
+        ipc.ipc_refine(v, ipc.IPC_TARGET_EB, E, out)
+    ipc.ipc_free(v)
+    for br in BITRATES:
+        ipc.ipc_retrieve(f, ipc.IPC_TARGET_BITRATE, br, out, want_view=False)
+    return f
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_04093_gb300 import ipc, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    edge = args.edge
+    x = synth.grf_k53((edge, edge, edge), seed=SEED + rank, device=dev)
+    out = torch.empty_like(x)
+    torch.cuda.synchronize()
+    nbytes = x.numel() * x.element_size()
+    n_recon = len(EB_SWEEP) + len(BITRATES)
+    step_bytes = nbytes * (1 + n_recon)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        f = gpu_step(ipc, x, out)
+        torch.cuda.synchronize()
+        ipc.ipc_free(f)
+
+    # timed region (device time, CUDA events on the working stream)
+    st = torch.cuda.current_stream()
+    ipc.ipc_profile_enable(True)
+    ipc.ipc_profile_reset()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = ipc.ipc_launch_count()
+    with ClockSampler(local_rank) as clk:
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
+        e_start.record(st)
+        fields = []
+        for _ in range(args.steps):
+            f = gpu_step(ipc, x, out)
+            fields.append((f, None))
+            if len(fields) > 1:
+                # compress of this step synchronised the stream, so the
+                # previous field has no pending work
+                ipc.ipc_free(fields.pop(0)[0])
+        e_end.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    launches = ipc.ipc_launch_count() - launches0
+    elapsed_ms = e_start.elapsed_time(e_end)
+    ipc.ipc_profile_enable(False)
+    prof = {ipc.IPC_KERNEL_NAMES[k]: ipc.ipc_profile_read(k) for k in range(8)}
+    csize = ipc.ipc_compressed_size(fields[-1][0])
+    ipc.ipc_free(fields[-1][0])
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    ms_per_step = elapsed_ms / args.steps
+    value = world * step_bytes * args.steps / (elapsed_ms * 1e-3) / 1e9
+
+    # phase split measured separately (same step, events between phases)
+    cm, rm = [], []
+    for _ in range(3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(st)
+        f = gpu_step(ipc, x, out, ev)
+        ev[2].record(st)
+        torch.cuda.synchronize()
+        cm.append(ev[0].elapsed_time(ev[1]))
+        rm.append(ev[1].elapsed_time(ev[2]) / n_recon)
+        ipc.ipc_free(f)
+    compress_ms, retrieve_ms = statistics.median(cm), statistics.median(rm)
+
+    # roofline of the dominant kernel (by device time in the timed region)
+    dom = max(prof, key=lambda k: prof[k][1])
+    L, ms, alg = prof[dom]
+    peak, peak_src = load_peaks()
+    achieved = alg / (ms * 1e-3) / 1e9 if ms else 0.0
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "launches": L, "avg_launch_us": round(ms * 1e3 / L, 2) if L else None}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3),
+                   "alg_GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None}
+               for k, v in prof.items() if v[0]}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_measure(ipc, x, args, world)
+
+    return dict(value=value, ms_per_step=ms_per_step, compress_ms=compress_ms,
+                retrieve_ms=retrieve_ms, roofline=roof, kernels=kernels, launches=launches,
+                clocks=clk.summary(), csize=csize, nbytes=nbytes, n_recon=n_recon, e2e=e2e,
+                step_bytes=step_bytes)
+
+
+def e2e_measure(ipc, x, args, world):
+    """Same step through the public API with host buffers: pinned input ->
+    device, compress, export of the container to host, every reconstruction
+    copied back to pinned host memory; all inside the timed region."""
+    import torch
+    hx = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    hx.copy_(x.cpu())
+    hout = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    dx = torch.empty_like(x)
+    out = torch.empty_like(x)
+    nbytes = x.numel() * x.element_size()
+    n_recon = len(EB_SWEEP) + len(BITRATES)
+
+    def step():
+        dx.copy_(hx, non_blocking=True)
+        f = ipc.ipc_compress(dx, EB, ipc.IPC_EB_ABS, ipc.IPC_CUBIC, ipc.IPC_BOUND_STRICT)
+        blob = ipc.ipc_export(f)
+        v = ipc.ipc_retrieve(f, ipc.IPC_TARGET_EB, EB_SWEEP[0], out)
+        hout.copy_(out, non_blocking=True)
+        for E in EB_SWEEP[1:]:
+            ipc.ipc_refine(v, ipc.IPC_TARGET_EB, E, out)
+            hout.copy_(out, non_blocking=True)
+        ipc.ipc_free(v)
+        for br in BITRATES:
+            ipc.ipc_retrieve(f, ipc.IPC_TARGET_BITRATE, br, out, want_view=False)
+            hout.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        ipc.ipc_free(f)
+        return len(blob)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        blen = step()
+    t1 = time.perf_counter()
+    sec = (t1 - t0) / steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([sec], device=x.device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    return {"value": round(world * nbytes * (1 + n_recon) / sec / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": blen + n_recon * nbytes}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+SAMPLE_SHAPE = (32, 256, 256)
+
+
+def oracle_step(oracle, xs):
+    t0 = time.perf_counter()
+    f = oracle.compress(xs, EB, oracle.ABS, oracle.CUBIC, oracle.STRICT)
+    y, v = f.retrieve(oracle.EB, EB_SWEEP[0])
+    for E in EB_SWEEP[1:]:
+        v.refine(oracle.EB, E)
+    for br in BITRATES:
+        f.retrieve(oracle.BITRATE, br)
+    return time.perf_counter() - t0
+
+
+def oracle_sample():
+    """The first slab of the bench field (same generator, same seed)."""
+    from paper_2502_04093_gb300 import synth
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    x = synth.grf_k53((512, 512, 512), seed=SEED, device=dev)
+    return x[:SAMPLE_SHAPE[0], :SAMPLE_SHAPE[1], :SAMPLE_SHAPE[2]].contiguous().cpu().numpy()
+
+
+def cpu_baseline(steps=1):
+    from oracle import oracle
+    oracle.build()
+    xs = oracle_sample()
+    secs = [oracle_step(oracle, xs) for _ in range(steps)]
+    sec = statistics.median(secs)
+    n_recon = len(EB_SWEEP) + len(BITRATES)
+    return {"value": round(xs.nbytes * (1 + n_recon) / sec / 1e9, 5), "unit": "GB/s",
+            "cores": 1, "kind": "oracle",
+            "sample": "%dx%dx%d corner slab of the same field, same step (compress + refine "
+                      "chain + 6 bitrate retrievals), %.1f s per step" %
+                      (SAMPLE_SHAPE + (sec,))}
+
+
+def run_reference(args):
+    from oracle import oracle
+    oracle.build()
+    xs = oracle_sample()
+    for _ in range(args.warmup):
+        oracle_step(oracle, xs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(oracle, xs)
+    sec = (time.perf_counter() - t0) / args.steps
+    n_recon = len(EB_SWEEP) + len(BITRATES)
+    value = xs.nbytes * (1 + n_recon) / sec / 1e9
+    sample = "%dx%dx%d corner slab of the 512^3 field, same step" % SAMPLE_SHAPE
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grf_k53 f32 sample %s, eb 1e-6 abs, cubic, strict" %
+                       (SAMPLE_SHAPE,), "parallelism": "single CPU core (oracle)"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "GB/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    r = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline()
+        line = {
+            "metric": METRIC,
+            "value": round(r["value"], 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(r["ms_per_step"], 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": "grf_k53 %d^3 f32 (k^-5/3 GRF, [0,1]), eb 1e-6 abs, cubic, strict; "
+                            "step = compress + retrieve 1e-1 refined to 1e-2..1e-6 + retrieve "
+                            "at 0.5,1,2,4,8,16 bits/value" % args.edge,
+                "l2": "inputs larger than L2 (512 MiB field vs 129 MB L2)",
+                "parallelism": "one field per GPU" if world > 1 else "single GPU"},
+            "compress_gbs": round(r["nbytes"] / (r["compress_ms"] * 1e-3) / 1e9, 1),
+            "retrieve_gbs": round(r["nbytes"] / (r["retrieve_ms"] * 1e-3) / 1e9, 1),
+            "compress_ms": round(r["compress_ms"], 3),
+            "retrieve_ms_avg": round(r["retrieve_ms"], 3),
+            "compression_ratio": round(r["nbytes"] / r["csize"], 3),
+            "roofline": r["roofline"],
+            "kernels": r["kernels"],
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "e2e": r["e2e"],
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

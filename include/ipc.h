@@ -134,6 +134,33 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream,
 int ipc_field_info(const ipc_field* f, int* dtype, int* ndim, int64_t* dims,
                    int* K, int* S, double* eb, double* xmin, double* xmax);
 
+/* ---- kernel profiler (not part of the method; measurement support) ------ */
+/* Kinds of kernels the library launches. */
+enum {
+  IPC_KERNEL_RANGE = 0,           /* min / max / max|x| reduction            */
+  IPC_KERNEL_COMPRESS_SWEEP = 1,  /* one interpolation sweep, compression     */
+  IPC_KERNEL_SCAN = 2,            /* per-plane prefix of tile counts          */
+  IPC_KERNEL_PACK = 3,            /* stream packing                           */
+  IPC_KERNEL_RETRIEVE_SWEEP = 4,  /* one interpolation sweep, reconstruction  */
+  IPC_KERNEL_OUTLIERS = 5,        /* exact-value scatter                      */
+  IPC_KERNEL_ANCHOR = 6,          /* anchor store                             */
+  IPC_KERNEL_BUILD_RANK = 7,      /* tile-rank index of an imported field     */
+  IPC_KERNEL_KINDS = 8
+};
+/* ipc_profile_enable -- when on, every later launch is bracketed by CUDA
+ * events recorded on its stream. */
+int ipc_profile_enable(int on);
+/* ipc_profile_read -- waits for the recorded events and returns, for one
+ * kernel kind, the number of timed launches, their summed device time (ms)
+ * and their summed algorithmic bytes (compress sweep: input values of its
+ * targets + the compacted streams it produced; retrieve sweep: selected
+ * stream bytes + output values; range: input bytes). */
+int ipc_profile_read(int kind, uint64_t* launches, double* total_ms, double* alg_bytes);
+/* ipc_profile_reset -- clears the accumulated figures. */
+int ipc_profile_reset(void);
+/* ipc_launch_count -- number of kernels this library has launched. */
+uint64_t ipc_launch_count(void);
+
 /* ipc_last_error -- NUL-terminated description of the calling thread's last
  * failure (empty string if none). Owned by the library. */
 const char* ipc_last_error(void);

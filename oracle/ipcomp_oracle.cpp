@@ -188,6 +188,17 @@ uint64_t uncertainty(int d) {
   return (d % 2 == 1) ? (p - 1) / 3 : (p - 2) / 3;
 }
 
+/* Half bin width of the quantizer. Reading of Sec. 4.2.2: |y - yhat| <= eb
+ * must hold for the value reconstructed in the element type, whose two
+ * roundings (q*bin and pred + r) add up to about 3u(max|x| + eb); the bin is
+ * shrunk by 4u(max|x| + eb), but never below eb. */
+double half_bin(double eb, double xmaxabs, int dtype) {
+  const double u = dtype == 0 ? Prec<float>::unit() : Prec<double>::unit();
+  double eq = eb - 4.0 * u * (xmaxabs + eb);
+  if (!(eq >= 0.5 * eb)) eq = 0.5 * eb;
+  return eq;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Little-endian byte writer/reader for the container.                       */
 /* ------------------------------------------------------------------------ */
@@ -323,9 +334,12 @@ int compress_t(const T* x, ipco_field* f) {
   f->eb = eb;
   f->anchor = (double)x[0];
 
-  /* Quantizer constants (Sec. 4.2.2): bin width 2eb, |x - xhat| <= eb. */
-  const T inv2eb = (T)(1.0 / (2.0 * eb));
-  const T twoeb = (T)(2.0 * eb);
+  /* Quantizer constants (Sec. 4.2.2): the reconstructed value in T must be
+   * within eb of x, so the bin is 2 e_q with e_q = eb minus the rounding of
+   * pred + q*bin in T (see half_bin). */
+  const double eq = half_bin(eb, ma, sizeof(T) == 4 ? 0 : 1);
+  const T inv2eb = (T)(1.0 / (2.0 * eq));
+  const T twoeb = (T)(2.0 * eq);
   const T ebchk = (T)(eb * Prec<T>::shrink());
   const T R = (T)Prec<T>::radius();
   const bool cubic = f->interp == 1;
@@ -395,7 +409,7 @@ int compress_t(const T* x, ipco_field* f) {
 /* Build the word array of plane k of stage t (Sec. 4.3: the bits of the same
  * position across the integers form a plane). Word (r, j) bit i holds code
  * (r, 32j + i) of the row-major code order; a row's last word is zero-padded.*/
-void plane_words(const StageGeom& sg, const std::vector<int32_t>& q, int k,
+void plane_words(const StageGeom& sg, const std::vector<uint32_t>& E, int k,
                  std::vector<uint32_t>* out) {
   out->assign(sg.words, 0);
   const uint64_t m = (uint64_t)sg.m[2];
@@ -405,8 +419,7 @@ void plane_words(const StageGeom& sg, const std::vector<int32_t>& q, int k,
       for (uint64_t i = 0; i < 32; ++i) {
         uint64_t p = 32 * j + i;
         if (p >= m) break;
-        uint32_t e = xor_encode(negabinary(q[r * m + p]));
-        w |= ((e >> k) & 1u) << i;
+        w |= ((E[r * m + p] >> k) & 1u) << i;
       }
       (*out)[r * sg.wr + j] = w;
     }
@@ -427,15 +440,19 @@ void serialize(ipco_field* f) {
   w.u32(S); w.u32(0);
   /* Stream bytes are produced first so the size table can be written. */
   std::vector<std::vector<uint8_t>> streams(S * 32);
-  std::vector<uint32_t> words;
-  for (uint32_t t = 0; t < S; ++t)
+  std::vector<uint32_t> words, E;
+  for (uint32_t t = 0; t < S; ++t) {
+    /* the predictively coded negabinary form of every code of the stage */
+    E.resize(f->codes[t].size());
+    for (size_t c = 0; c < E.size(); ++c) E[c] = xor_encode(negabinary(f->codes[t][c]));
     for (int k = 31; k >= 0; --k) {
-      plane_words(g.stages[t], f->codes[t], k, &words);
+      plane_words(g.stages[t], E, k, &words);
       Writer sw;
       encode_stream(words, &sw);
       f->st[t].size[k] = sw.buf.size();
       streams[t * 32 + (31 - k)] = std::move(sw.buf);
     }
+  }
   for (uint32_t t = 0; t < S; ++t) {
     const StageGeom& sg = g.stages[t];
     w.u32((uint32_t)sg.level);
@@ -495,7 +512,8 @@ void option_tables(const ipco_field* f, double A, Options* o) {
   std::vector<double> P(std::max(S, K) + 1);
   P[0] = 1.0;
   for (size_t i = 1; i < P.size(); ++i) P[i] = P[i - 1] * p;
-  double twoeb_T = f->dtype == 0 ? (double)(float)(2.0 * f->eb) : 2.0 * f->eb;
+  const double eq = half_bin(f->eb, f->xmaxabs, f->dtype);
+  double twoeb_T = f->dtype == 0 ? (double)(float)(2.0 * eq) : 2.0 * eq;
   double bin = twoeb_T / f->eb;
   double u = f->dtype == 0 ? Prec<float>::unit() : Prec<double>::unit();
   double kappa = cubic ? 24.0 : 12.0;
@@ -647,7 +665,7 @@ int choose(const ipco_field* f, int kind, double value,
 template <class T>
 int reconstruct_t(const ipco_field* f, const std::vector<int>& bsel, T* out) {
   const Geometry& g = f->g;
-  const T twoeb = (T)(2.0 * f->eb);
+  const T twoeb = (T)(2.0 * half_bin(f->eb, f->xmaxabs, f->dtype));
   const bool cubic = f->interp == 1;
   const int64_t stride[3] = {g.N[1] * g.N[2], g.N[2], 1};
   out[0] = (T)f->anchor;

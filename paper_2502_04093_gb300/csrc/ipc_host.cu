@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +37,78 @@ int cuda_fail(cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                             \
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// Kernel profiler: CUDA events recorded on the launching stream around every
+// kernel launch (when enabled), accumulated per kernel kind together with the
+// algorithmic bytes of each launch. The launch counter always runs.
+// ---------------------------------------------------------------------------
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double bytes;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_pool;
+struct ProfAcc {
+  uint64_t launches;
+  double ms, bytes;
+} g_prof_acc[IPC_KERNEL_KINDS];
+std::atomic<unsigned long long> g_launches{0};
+
+cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+// Returns a handle for prof_end (or -1 when the profiler is off).
+long prof_begin(int kind, cudaStream_t st) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return -1;
+  ProfRec r{kind, prof_event(), prof_event(), 0.0};
+  if (!r.a || !r.b) return -1;
+  cudaEventRecord(r.a, st);
+  g_prof_pending.push_back(r);
+  return (long)g_prof_pending.size() - 1;
+}
+void prof_end(long h, cudaStream_t st, double bytes) {
+  if (h < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if ((size_t)h >= g_prof_pending.size()) return;
+  g_prof_pending[h].bytes = bytes;
+  cudaEventRecord(g_prof_pending[h].b, st);
+}
+void prof_set_bytes(long h, double bytes) {
+  if (h < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if ((size_t)h < g_prof_pending.size()) g_prof_pending[h].bytes = bytes;
+}
+void prof_drain() {  // caller holds g_prof_mu
+  for (ProfRec& r : g_prof_pending) {
+    float ms = 0;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ProfAcc& a = g_prof_acc[r.kind];
+      a.launches += 1;
+      a.ms += ms;
+      a.bytes += r.bytes;
+    }
+    cudaGetLastError();
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof_pending.clear();
+}
 
 const uint32_t kMagic = 0x31435049u;  // "IPC1"
 const uint32_t kVersion = 1u;
@@ -131,15 +204,16 @@ struct ipc_field {
   double eb_user, eb, xmin, xmax, xmaxabs, anchor;
   Geo g;
   std::vector<StageTab> st;
-  uint64_t mandatory;  // header + tables + outliers
-  uint64_t stream_bytes;
-  // device
-  uint32_t* d_blob;    // every stream, in container order (32-bit words)
-  uint32_t* d_rank;    // tile-rank index of every (stage, plane)
-  uint64_t* d_oidx;    // outliers: code indices, per stage contiguous
+  uint64_t mandatory;     // header + tables + outliers
+  uint64_t stream_bytes;  // packed streams of the container
+  // device: segmented plane streams, outliers
+  uint32_t* d_cap;
+  uint32_t* d_bm;
+  uint64_t cap_words, bm_words;
+  uint64_t* d_oidx;       // outliers: code indices, per stage contiguous
   double* d_oval;
-  std::vector<StageDescs> desc;       // per stage
-  std::vector<uint64_t> out_off;      // per stage offset into d_oidx/d_oval
+  std::vector<StageDescs> desc;   // per stage
+  std::vector<uint64_t> out_off;  // per stage offset into d_oidx/d_oval
 };
 
 struct ipc_view {
@@ -159,17 +233,11 @@ struct Workspace {
   std::mutex mu;
   void* xh = nullptr;
   uint64_t xh_bytes = 0;
-  uint32_t* cap = nullptr;
-  uint64_t cap_words = 0;
-  uint32_t* bitmap = nullptr;
-  uint64_t bitmap_words = 0;
-  uint32_t* tilecnt = nullptr;
-  uint64_t tilecnt_words = 0;
   unsigned long long* okey = nullptr;
   double* oval = nullptr;
   uint64_t ocap = 0;
   unsigned long long* small = nullptr;  // range acc[4] + outlier count
-  uint32_t* stat = nullptr;
+  uint32_t* stat = nullptr;             // 2 per stage
   uint64_t stat_words = 0;
   uint32_t* nnz = nullptr;              // 32 per stage
   uint64_t nnz_words = 0;
@@ -246,36 +314,88 @@ std::vector<uint8_t> header_bytes(const ipc_field* f) {
   return h;
 }
 
+void dfree(void* p) {
+  if (p) cudaFreeAsync(p, cudaStreamLegacy);
+}
+
 void free_field_device(ipc_field* f) {
-  if (f->d_blob) cudaFree(f->d_blob);
-  if (f->d_rank) cudaFree(f->d_rank);
-  if (f->d_oidx) cudaFree(f->d_oidx);
-  if (f->d_oval) cudaFree(f->d_oval);
-  f->d_blob = nullptr;
-  f->d_rank = nullptr;
+  dfree(f->d_cap);
+  dfree(f->d_bm);
+  dfree(f->d_oidx);
+  dfree(f->d_oval);
+  f->d_cap = nullptr;
+  f->d_bm = nullptr;
   f->d_oidx = nullptr;
   f->d_oval = nullptr;
 }
 
-// Lays out the streams (container order: stage-major, plane 31..0) and the
-// rank index from the per-plane nnz; allocates the device buffers.
-int layout_field(ipc_field* f) {
+int dalloc(void** p, uint64_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (cudaMallocAsync(p, std::max<uint64_t>(bytes, 16), st) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(IPC_ENOMEM, "device allocation failed");
+  }
+  return IPC_OK;
+}
+
+// Keeps freed pool memory for reuse instead of returning it to the driver
+// (process-local setting of the device's default pool).
+void keep_pool(int dev) {
+  static std::once_flag once[64];
+  if (dev < 0 || dev >= 64) return;
+  std::call_once(once[dev], [dev]() {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = ~uint64_t(0);
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
+}
+
+// Segmented layout of the device streams (independent of the data): per
+// stage, plane k at cap_base + k * ntiles * 256 and bm_base + k * ntiles * 8.
+int plan_field(ipc_field* f, cudaStream_t st) {
   const Geo& g = f->g;
-  uint64_t word = 0, rank = 0;
   f->desc.assign(g.stages.size(), StageDescs{});
+  uint64_t cw = 0, bw = 0;
+  for (size_t t = 0; t < g.stages.size(); ++t) {
+    const StageGeo& sg = g.stages[t];
+    for (int k = 0; k < 32; ++k) {
+      PlaneDesc& pd = f->desc[t].p[k];
+      pd.cap_off = cw + (uint64_t)k * sg.ntiles * kTileWords;
+      pd.bm_off = bw + (uint64_t)k * sg.ntiles * kTileBitmapWords;
+    }
+    cw += 32 * sg.ntiles * kTileWords;
+    bw += 32 * sg.ntiles * kTileBitmapWords;
+  }
+  f->cap_words = cw;
+  f->bm_words = bw;
+  int rc;
+  if ((rc = dalloc((void**)&f->d_cap, cw * 4, st)) || (rc = dalloc((void**)&f->d_bm, bw * 4, st))) {
+    free_field_device(f);
+    return rc;
+  }
+  return IPC_OK;
+}
+
+// Container layout from the per-plane nnz: stream sizes and modes, packed
+// offsets (stage-major, plane 31..0), mandatory bytes; uploads outliers.
+int finish_field(ipc_field* f, cudaStream_t st) {
+  const Geo& g = f->g;
+  uint64_t word = 0;
   for (size_t t = 0; t < g.stages.size(); ++t) {
     const StageGeo& sg = g.stages[t];
     for (int k = 31; k >= 0; --k) {
       StageTab& s = f->st[t];
       PlaneDesc& pd = f->desc[t].p[k];
-      pd.off = word;
       pd.nnz = (uint32_t)s.nnz[k];
       pd.mode = stream_mode(s.nnz[k], sg.words);
+      pd.pk_off = word;
       s.size[k] = stream_bytes(s.nnz[k], sg.words);
       word += s.size[k] / 4;
     }
-    for (int k = 0; k < 32; ++k) f->desc[t].p[k].rank_off = rank + (uint64_t)k * sg.ntiles;
-    rank += 32 * sg.ntiles;
   }
   f->stream_bytes = word * 4;
   uint64_t nout = 0;
@@ -286,31 +406,22 @@ int layout_field(ipc_field* f) {
   }
   f->out_off[g.stages.size()] = nout;
   f->mandatory = header_bytes(f).size();
-  if (cudaMalloc((void**)&f->d_blob, std::max<uint64_t>(word, 1) * 4) != cudaSuccess ||
-      cudaMalloc((void**)&f->d_rank, std::max<uint64_t>(rank, 1) * 4) != cudaSuccess ||
-      cudaMalloc((void**)&f->d_oidx, std::max<uint64_t>(nout, 1) * 8) != cudaSuccess ||
-      cudaMalloc((void**)&f->d_oval, std::max<uint64_t>(nout, 1) * 8) != cudaSuccess) {
-    cudaGetLastError();
-    free_field_device(f);
-    return fail(IPC_ENOMEM, "field allocation failed");
+  int rc;
+  if ((rc = dalloc((void**)&f->d_oidx, nout * 8, st)) || (rc = dalloc((void**)&f->d_oval, nout * 8, st)))
+    return rc;
+  if (nout) {
+    std::vector<uint64_t> idx;
+    std::vector<double> val;
+    idx.reserve(nout);
+    val.reserve(nout);
+    for (auto& s : f->st) {
+      idx.insert(idx.end(), s.out_idx.begin(), s.out_idx.end());
+      val.insert(val.end(), s.out_val.begin(), s.out_val.end());
+    }
+    CU(cudaMemcpyAsync(f->d_oidx, idx.data(), nout * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(f->d_oval, val.data(), nout * 8, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
   }
-  return IPC_OK;
-}
-
-int upload_outliers(ipc_field* f, cudaStream_t st) {
-  const uint64_t n = f->out_off.back();
-  if (n == 0) return IPC_OK;
-  std::vector<uint64_t> idx;
-  std::vector<double> val;
-  idx.reserve(n);
-  val.reserve(n);
-  for (auto& s : f->st) {
-    idx.insert(idx.end(), s.out_idx.begin(), s.out_idx.end());
-    val.insert(val.end(), s.out_val.begin(), s.out_val.end());
-  }
-  CU(cudaMemcpyAsync(f->d_oidx, idx.data(), n * 8, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(f->d_oval, val.data(), n * 8, cudaMemcpyHostToDevice, st));
-  CU(cudaStreamSynchronize(st));
   return IPC_OK;
 }
 
@@ -321,11 +432,25 @@ double okey_to_double(unsigned long long k) {
   return v;
 }
 
+// Quantizer half bin (Sec. 4.2.2): eb less 4u(max|x| + eb), the allowance
+// for the two roundings of pred + q*bin in the element type, at least eb/2.
+double half_bin(double eb, double xmaxabs, int dtype) {
+  const double u = dtype == 0 ? 1.0 / 16777216.0 : 1.0 / 9007199254740992.0;
+  double eq = eb - 4.0 * u * (xmaxabs + eb);
+  if (!(eq >= 0.5 * eb)) eq = 0.5 * eb;
+  return eq;
+}
+double bin_width(const ipc_field* f) {
+  const double eq = half_bin(f->eb, f->xmaxabs, f->dtype);
+  return f->dtype == 0 ? (double)(float)(2.0 * eq) : 2.0 * eq;
+}
+
 template <class T>
-void quant_args(double eb, void* out) {
+void quant_args(double eb, double xmaxabs, void* out) {
   QuantArgs<T> q;
-  q.inv2eb = (T)(1.0 / (2.0 * eb));
-  q.twoeb = (T)(2.0 * eb);
+  const double eq = half_bin(eb, xmaxabs, sizeof(T) == 4 ? 0 : 1);
+  q.inv2eb = (T)(1.0 / (2.0 * eq));
+  q.twoeb = (T)(2.0 * eq);
   const double shrink = sizeof(T) == 4 ? 1.0 - 1.0 / 1048576.0 : 1.0 - 1.0 / 1125899906842624.0;
   q.ebchk = (T)(eb * shrink);
   q.R = (T)(sizeof(T) == 4 ? 2097152.0 : 1073741824.0);
@@ -336,24 +461,14 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
   int dev = 0;
   CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(IPC_EINVAL, "device index out of range");
+  keep_pool(dev);
   Workspace& ws = g_ws[dev];
   std::lock_guard<std::mutex> lock(ws.mu);
   const Geo& g = f->g;
   const size_t esz = f->dtype == 0 ? 4 : 8;
   const size_t S = g.stages.size();
-
-  // scratch sizes
-  uint64_t capw = 0, bmw = 0, cntw = 0;
-  for (auto& sg : g.stages) {
-    capw += 32 * sg.ntiles * kTileWords;
-    bmw += 32 * sg.ntiles * kTileBitmapWords;
-    cntw += 32 * sg.ntiles;
-  }
   int rc;
   if ((rc = grow(&ws.xh, &ws.xh_bytes, g.n * esz, 1)) ||
-      (rc = grow(&ws.cap, &ws.cap_words, capw, 4)) ||
-      (rc = grow(&ws.bitmap, &ws.bitmap_words, bmw, 4)) ||
-      (rc = grow(&ws.tilecnt, &ws.tilecnt_words, cntw, 4)) ||
       (rc = grow(&ws.stat, &ws.stat_words, 2 * std::max<size_t>(S, 1), 4)) ||
       (rc = grow(&ws.nnz, &ws.nnz_words, 32 * std::max<size_t>(S, 1), 4)))
     return rc;
@@ -366,22 +481,22 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
     ws.ocap = 1 << 16;
   }
 
-  // a0: range over finite values
+  // a0: range over finite values, and the anchor
   unsigned long long init[5] = {~0ULL, 0ULL, 0ULL, 0ULL, 0ULL};
   CU(cudaMemcpyAsync(ws.small, init, sizeof(init), cudaMemcpyHostToDevice, st));
-  CU(launch_range(f->dtype, d_in, g.n, ws.small, st));
+  {
+    const long ph = prof_begin(IPC_KERNEL_RANGE, st);
+    CU(launch_range(f->dtype, d_in, g.n, ws.small, st));
+    prof_end(ph, st, (double)(g.n * esz));
+  }
   unsigned long long acc[5];
   CU(cudaMemcpyAsync(acc, ws.small, sizeof(acc), cudaMemcpyDeviceToHost, st));
   double x0 = 0;
-  if (f->dtype == 0) {
-    float v;
-    CU(cudaMemcpyAsync(&v, d_in, 4, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    x0 = v;
-  } else {
-    CU(cudaMemcpyAsync(&x0, d_in, 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-  }
+  float x0f = 0;
+  if (f->dtype == 0) CU(cudaMemcpyAsync(&x0f, d_in, 4, cudaMemcpyDeviceToHost, st));
+  else CU(cudaMemcpyAsync(&x0, d_in, 8, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (f->dtype == 0) x0 = x0f;
   const bool any = acc[3] > 0;
   f->xmin = any ? okey_to_double(acc[0]) : 0.0;
   f->xmax = any ? okey_to_double(acc[1]) : 0.0;
@@ -400,29 +515,34 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
   f->eb = eb;
   f->anchor = x0;
   alignas(16) unsigned char qbuf[64];
-  if (f->dtype == 0) quant_args<float>(eb, qbuf);
-  else quant_args<double>(eb, qbuf);
+  if (f->dtype == 0) quant_args<float>(eb, f->xmaxabs, qbuf);
+  else quant_args<double>(eb, f->xmaxabs, qbuf);
+  if ((rc = plan_field(f, st))) return rc;
 
+  std::vector<long> sweep_prof(S, -1);
+  unsigned long long nout = 0;
+  std::vector<uint32_t> stat(2 * std::max<size_t>(S, 1)), nnz(32 * std::max<size_t>(S, 1));
   for (int attempt = 0; attempt < 2; ++attempt) {
     CU(cudaMemsetAsync(ws.stat, 0, 2 * std::max<size_t>(S, 1) * 4, st));
+    CU(cudaMemsetAsync(ws.nnz, 0, 32 * std::max<size_t>(S, 1) * 4, st));
     CU(cudaMemsetAsync(ws.small + 4, 0, 8, st));
-    CompressScratch sc{ws.cap, ws.bitmap, ws.tilecnt, ws.okey, ws.oval, ws.small + 4, ws.ocap,
-                       ws.stat};
-    // the anchor is known exactly; xh[0] = x[0]
+    SweepOut so{f->d_cap, f->d_bm, ws.nnz, ws.okey, ws.oval, ws.small + 4, ws.ocap, ws.stat};
+    // the anchor is stored exactly: xh[0] = x[0]
     CU(cudaMemcpyAsync(ws.xh, d_in, esz, cudaMemcpyDeviceToDevice, st));
-    uint64_t capo = 0, bmo = 0, cnto = 0;
     for (size_t t = 0; t < S; ++t) {
       const StageGeo& sg = g.stages[t];
       StageArgs a = stage_args(g, sg, f->interp == IPC_CUBIC);
       const int write_xh = t + 1 < S;  // the last sweep's values are never read
-      CU(launch_compress_stage(f->dtype, a, d_in, ws.xh, write_xh, qbuf, (int)t, sc, capo, bmo,
-                               cnto, st));
-      capo += 32 * sg.ntiles * kTileWords;
-      bmo += 32 * sg.ntiles * kTileBitmapWords;
-      cnto += 32 * sg.ntiles;
+      const long ph = prof_begin(IPC_KERNEL_COMPRESS_SWEEP, st);
+      CU(launch_compress_stage(f->dtype, a, d_in, ws.xh, write_xh, qbuf, (int)t, so, f->desc[t], st));
+      prof_end(ph, st, (double)(sg.ncodes * esz));
+      sweep_prof[t] = ph;
     }
-    unsigned long long nout = 0;
     CU(cudaMemcpyAsync(&nout, ws.small + 4, 8, cudaMemcpyDeviceToHost, st));
+    if (S) {
+      CU(cudaMemcpyAsync(stat.data(), ws.stat, 8 * S, cudaMemcpyDeviceToHost, st));
+      CU(cudaMemcpyAsync(nnz.data(), ws.nnz, 128 * S, cudaMemcpyDeviceToHost, st));
+    }
     CU(cudaStreamSynchronize(st));
     if (nout <= ws.ocap) break;
     if (attempt == 1) return fail(IPC_ECUDA, "outlier count changed between passes");
@@ -433,89 +553,42 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
     ws.oval = nullptr;
     ws.ocap = 0;
     uint64_t oc = 0;
-    if ((rc = grow(&ws.okey, &oc, nout, 8)) || (rc = grow(&ws.oval, &oc, nout, 8)))
-      return rc;
+    if ((rc = grow(&ws.okey, &oc, nout, 8)) || (rc = grow(&ws.oval, &oc, nout, 8))) return rc;
     ws.ocap = nout;
   }
 
-  // statistics and outliers
   f->st.assign(S, StageTab{});
-  if (S) {
-    std::vector<uint32_t> stat(2 * S);
-    CU(cudaMemcpyAsync(stat.data(), ws.stat, 8 * S, cudaMemcpyDeviceToHost, st));
-    unsigned long long nout = 0;
-    CU(cudaMemcpyAsync(&nout, ws.small + 4, 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    for (size_t t = 0; t < S; ++t) {
-      uint32_t orv = stat[2 * t];
-      int h = -1;
-      while (orv) { ++h; orv >>= 1; }
-      f->st[t].H = h;
-      f->st[t].Q = stat[2 * t + 1];
-    }
-    if (nout) {
-      std::vector<unsigned long long> key(nout);
-      std::vector<double> val(nout);
-      CU(cudaMemcpyAsync(key.data(), ws.okey, nout * 8, cudaMemcpyDeviceToHost, st));
-      CU(cudaMemcpyAsync(val.data(), ws.oval, nout * 8, cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
-      std::vector<uint64_t> order(nout);
-      for (uint64_t i = 0; i < nout; ++i) order[i] = i;
-      std::sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return key[a] < key[b]; });
-      for (uint64_t i : order) {
-        const size_t t = (size_t)(key[i] >> 40);
-        f->st[t].out_idx.push_back(key[i] & ((1ULL << 40) - 1));
-        f->st[t].out_val.push_back(val[i]);
-      }
-    }
-  }
-
-  // per-plane nnz and tile ranks
-  uint64_t cnto = 0, rank_total = 0;
-  for (auto& sg : g.stages) rank_total += 32 * sg.ntiles;
-  uint32_t* d_rank = nullptr;
-  if (cudaMalloc((void**)&d_rank, std::max<uint64_t>(rank_total, 1) * 4) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(IPC_ENOMEM, "rank index allocation failed");
-  }
-  {
-    uint64_t ro = 0;
-    for (size_t t = 0; t < S; ++t) {
-      const StageGeo& sg = g.stages[t];
-      StageArgs a = stage_args(g, sg, 0);
-      cudaError_t e = launch_scan_stage(a, CompressScratch{nullptr, nullptr, ws.tilecnt}, cnto,
-                                        d_rank + ro, ws.nnz + 32 * t, st);
-      if (e != cudaSuccess) { cudaFree(d_rank); return cuda_fail(e, "scan"); }
-      cnto += 32 * sg.ntiles;
-      ro += 32 * sg.ntiles;
-    }
-    std::vector<uint32_t> nnz(32 * std::max<size_t>(S, 1));
-    cudaError_t e = cudaMemcpyAsync(nnz.data(), ws.nnz, 32 * S * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { cudaFree(d_rank); return cuda_fail(e, "nnz readback"); }
-    for (size_t t = 0; t < S; ++t)
-      for (int k = 0; k < 32; ++k) f->st[t].nnz[k] = nnz[32 * t + k];
-  }
-  rc = layout_field(f);
-  if (rc) { cudaFree(d_rank); return rc; }
-  cudaFree(f->d_rank);
-  f->d_rank = d_rank;
-
-  // pack the streams into the field blob
-  uint64_t capo = 0, bmo = 0;
-  cnto = 0;
   for (size_t t = 0; t < S; ++t) {
-    const StageGeo& sg = g.stages[t];
-    StageArgs a = stage_args(g, sg, 0);
-    CompressScratch sc{ws.cap, ws.bitmap, ws.tilecnt};
-    CU(launch_pack_stage(a, sc, capo, bmo, cnto, f->d_rank + f->desc[t].p[0].rank_off, f->desc[t],
-                         f->d_blob, st));
-    capo += 32 * sg.ntiles * kTileWords;
-    bmo += 32 * sg.ntiles * kTileBitmapWords;
-    cnto += 32 * sg.ntiles;
+    uint32_t orv = stat[2 * t];
+    int h = -1;
+    while (orv) { ++h; orv >>= 1; }
+    f->st[t].H = h;
+    f->st[t].Q = stat[2 * t + 1];
+    for (int k = 0; k < 32; ++k) f->st[t].nnz[k] = nnz[32 * t + k];
   }
-  CU(cudaStreamSynchronize(st));
-  return upload_outliers(f, st);
+  if (nout) {
+    std::vector<unsigned long long> key(nout);
+    std::vector<double> val(nout);
+    CU(cudaMemcpyAsync(key.data(), ws.okey, nout * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(val.data(), ws.oval, nout * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    std::vector<uint64_t> order(nout);
+    for (uint64_t i = 0; i < nout; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return key[a] < key[b]; });
+    for (uint64_t i : order) {
+      const size_t t = (size_t)(key[i] >> 40);
+      f->st[t].out_idx.push_back(key[i] & ((1ULL << 40) - 1));
+      f->st[t].out_val.push_back(val[i]);
+    }
+  }
+  if ((rc = finish_field(f, st))) return rc;
+  // the algorithmic output of each sweep: its compacted streams
+  for (size_t t = 0; t < S; ++t) {
+    double sb = 0;
+    for (int k = 0; k < 32; ++k) sb += (double)f->st[t].size[k];
+    prof_set_bytes(sweep_prof[t], (double)(g.stages[t].ncodes * esz) + sb);
+  }
+  return IPC_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -557,8 +630,7 @@ void build_tables(const ipc_field* f, double A, Tables* T) {
   std::vector<double> pw(std::max(S, K) + 1);
   pw[0] = 1.0;
   for (size_t i = 1; i < pw.size(); ++i) pw[i] = pw[i - 1] * p;
-  const double twoeb = f->dtype == 0 ? (double)(float)(2.0 * f->eb) : 2.0 * f->eb;
-  const double bin = twoeb / f->eb;
+  const double bin = bin_width(f) / f->eb;
   const double u = f->dtype == 0 ? 1.0 / 16777216.0 : 1.0 / 9007199254740992.0;
   const double kappa = cubic ? 24.0 : 12.0;
   T->K = K;
@@ -590,61 +662,137 @@ void build_tables(const ipc_field* f, double A, Tables* T) {
   }
 }
 
-// Pareto frontier DP, levels 1..K (finest first). Each label keeps its
-// parent so the prefix (b_1..b_j) can be rebuilt for lexicographic ties.
-struct Label {
+// Exact solver (meet in the middle). Every option of a level is a point
+// (cost, bytes); bytes fall strictly with b (each stream is >= 4 bytes), so an
+// option with a larger-b alternative of no greater cost can never be part of
+// an optimum and is dropped. The levels are split in two halves; each half's
+// Pareto frontier (cost ascending, bytes descending; equal points keep the
+// lexicographically larger part-vector) is built level by level, and the two
+// frontiers are joined with a binary search per entry of the first half.
+// Ties: eb mode -> fewer bytes, then smaller cost, then the lexicographically
+// larger (b_1, b_2, ...); bitrate mode -> smaller cost, then fewer bytes,
+// then the same lexicographic rule.
+struct Part {
   uint64_t c, y;
-  int parent;
-  int b;
+  uint8_t b[64];
 };
 
-void prefix_of(const std::vector<std::vector<Label>>& L, int level, int i, std::vector<int>* out) {
-  out->assign(level + 1, 0);
-  for (int j = level; j >= 0; --j) {
-    (*out)[j] = L[j][i].b;
-    i = L[j][i].parent;
+void half_frontier(const Tables& T, int l0, int l1, int kind, uint64_t limit,
+                   const std::vector<int>* upper, std::vector<Part>* out) {
+  const int n = l1 - l0;
+  std::vector<Part> F(1);
+  F[0].c = 0;
+  F[0].y = 0;
+  std::memset(F[0].b, 0, sizeof(F[0].b));
+  std::vector<Part> G;
+  for (int l = l0; l < l1; ++l) {
+    const int bmax = upper ? (*upper)[l] : 32;
+    int opt[33];
+    int nopt = 0;
+    uint64_t best = ~uint64_t(0);
+    for (int b = bmax; b >= 0; --b) {  // staircase: keep b only if strictly cheaper
+      const uint64_t c = T.cost[(size_t)l * 33 + b];
+      if (c < best) {
+        opt[nopt++] = b;
+        best = c;
+      }
+    }
+    G.clear();
+    G.reserve(F.size() * nopt);
+    for (const Part& e : F)
+      for (int i = 0; i < nopt; ++i) {
+        const int b = opt[i];
+        Part p = e;
+        p.c = sadd(e.c, T.cost[(size_t)l * 33 + b]);
+        p.y = e.y + T.bytes[(size_t)l * 33 + b];
+        if ((kind == 0 && p.c > limit) || (kind == 1 && p.y > limit)) continue;
+        p.b[l - l0] = (uint8_t)b;
+        G.push_back(p);
+      }
+    const int len = l - l0 + 1;
+    std::sort(G.begin(), G.end(), [len](const Part& x, const Part& z) {
+      if (x.c != z.c) return x.c < z.c;
+      if (x.y != z.y) return x.y < z.y;
+      return std::memcmp(x.b, z.b, len) > 0;
+    });
+    F.clear();
+    for (const Part& e : G)
+      if (F.empty() || e.y < F.back().y) F.push_back(e);
+    if (F.empty()) break;
   }
+  (void)n;
+  *out = std::move(F);
 }
 
 int solve(const Tables& T, int kind, uint64_t limit, const std::vector<int>* upper,
           std::vector<int>* best) {
   const int K = T.K;
-  if (K == 0) { best->clear(); return IPC_OK; }
-  std::vector<std::vector<Label>> L(K);
-  std::vector<int> pa, pb;
-  for (int l = 0; l < K; ++l) {
-    std::vector<Label> cand;
-    const int bmax = upper ? (*upper)[l] : 32;
-    const size_t nprev = l == 0 ? 1 : L[l - 1].size();
-    for (size_t i = 0; i < nprev; ++i) {
-      const uint64_t c0 = l == 0 ? 0 : L[l - 1][i].c, y0 = l == 0 ? 0 : L[l - 1][i].y;
-      for (int b = 0; b <= bmax; ++b) {
-        Label n{sadd(c0, T.cost[(size_t)l * 33 + b]), y0 + T.bytes[(size_t)l * 33 + b], (int)i, b};
-        if ((kind == 0 && n.c > limit) || (kind == 1 && n.y > limit)) continue;
-        cand.push_back(n);
-      }
-    }
-    if (cand.empty()) return kind == 0 ? IPC_EBOUND : IPC_EBUDGET;
-    L[l] = cand;  // temporarily, so prefixes can be rebuilt while sorting
-    std::vector<int> order(cand.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) {
-      const Label &x = cand[a], &z = cand[b];
-      if (x.c != z.c) return x.c < z.c;
-      if (x.y != z.y) return x.y < z.y;
-      prefix_of(L, l, a, &pa);
-      prefix_of(L, l, b, &pb);
-      return pa > pb;  // lexicographically larger (b_1, b_2, ...) first
-    });
-    std::vector<Label> keep;
-    for (int i : order) {
-      if (keep.empty() || cand[i].y < keep.back().y) keep.push_back(cand[i]);
-    }
-    L[l] = keep;
+  if (K == 0) {
+    best->clear();
+    return IPC_OK;
   }
-  // cost increases and bytes decrease along the frontier
-  const int pick = kind == 0 ? (int)L[K - 1].size() - 1 : 0;
-  prefix_of(L, K - 1, pick, best);
+  if (K > 64) return IPC_EINVAL;
+  const int h = K / 2;
+  std::vector<Part> A, B;
+  half_frontier(T, 0, h, kind, limit, upper, &A);
+  half_frontier(T, h, K, kind, limit, upper, &B);
+  if (A.empty() || B.empty()) return kind == 0 ? IPC_EBOUND : IPC_EBUDGET;
+  // B: cost ascending, bytes descending.
+  bool found = false;
+  uint64_t bc = 0, by = 0;
+  const Part *ba = nullptr, *bb = nullptr;
+  for (const Part& a : A) {
+    const Part* m = nullptr;
+    if (kind == 0) {
+      if (a.c > limit) continue;
+      const uint64_t lim = limit - a.c;  // largest cost <= lim has the fewest bytes
+      size_t lo = 0, hi = B.size();
+      while (lo < hi) {
+        const size_t mid = (lo + hi) / 2;
+        if (B[mid].c <= lim) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo == 0) continue;
+      m = &B[lo - 1];
+    } else {
+      if (a.y > limit) continue;
+      const uint64_t lim = limit - a.y;  // first entry with bytes <= lim: least cost
+      size_t lo = 0, hi = B.size();
+      while (lo < hi) {
+        const size_t mid = (lo + hi) / 2;
+        if (B[mid].y > lim) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo == B.size()) continue;
+      m = &B[lo];
+    }
+    const uint64_t c = sadd(a.c, m->c), y = a.y + m->y;
+    bool better;
+    if (!found) {
+      better = true;
+    } else if (kind == 0) {
+      better = y < by || (y == by && c < bc) ||
+               (y == by && c == bc &&
+                (std::memcmp(a.b, ba->b, h) > 0 ||
+                 (std::memcmp(a.b, ba->b, h) == 0 && std::memcmp(m->b, bb->b, K - h) > 0)));
+    } else {
+      better = c < bc || (c == bc && y < by) ||
+               (c == bc && y == by &&
+                (std::memcmp(a.b, ba->b, h) > 0 ||
+                 (std::memcmp(a.b, ba->b, h) == 0 && std::memcmp(m->b, bb->b, K - h) > 0)));
+    }
+    if (better) {
+      found = true;
+      bc = c;
+      by = y;
+      ba = &a;
+      bb = m;
+    }
+  }
+  if (!found) return kind == 0 ? IPC_EBOUND : IPC_EBUDGET;
+  best->assign(K, 0);
+  for (int l = 0; l < h; ++l) (*best)[l] = ba->b[l];
+  for (int l = h; l < K; ++l) (*best)[l] = bb->b[l - h];
   return IPC_OK;
 }
 
@@ -704,17 +852,29 @@ int select(const ipc_field* f, ipc_target tg, const std::vector<int>* upper, std
 // sweep (coarse to fine), each followed by its outlier scatter.
 int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream_t st) {
   const Geo& g = f->g;
-  CU(launch_set_anchor(f->dtype, d_out, f->anchor, st));
-  const double twoeb = f->dtype == 0 ? (double)(float)(2.0 * f->eb) : 2.0 * f->eb;
+  {
+    const long ph = prof_begin(IPC_KERNEL_ANCHOR, st);
+    CU(launch_set_anchor(f->dtype, d_out, f->anchor, st));
+    prof_end(ph, st, 8);
+  }
+  const double twoeb = bin_width(f);
+  const size_t esz = f->dtype == 0 ? 4 : 8;
   for (size_t t = 0; t < g.stages.size(); ++t) {
     const StageGeo& sg = g.stages[t];
     StageArgs a = stage_args(g, sg, f->interp == IPC_CUBIC);
-    CU(launch_retrieve_stage(f->dtype, a, d_out, twoeb, f->desc[t], b[sg.level - 1], f->d_blob,
-                             f->d_rank, st));
+    double sb = 0;
+    for (int k = b[sg.level - 1]; k < 32; ++k) sb += (double)f->st[t].size[k];
+    const long ph = prof_begin(IPC_KERNEL_RETRIEVE_SWEEP, st);
+    CU(launch_retrieve_stage(f->dtype, a, d_out, twoeb, f->desc[t], b[sg.level - 1], f->d_cap,
+                             f->d_bm, st));
+    prof_end(ph, st, (double)(sg.ncodes * esz) + sb);
     const uint64_t no = f->out_off[t + 1] - f->out_off[t];
-    if (no)
+    if (no) {
+      const long ph2 = prof_begin(IPC_KERNEL_OUTLIERS, st);
       CU(launch_outlier_scatter(f->dtype, a, d_out, f->d_oidx + f->out_off[t],
                                 f->d_oval + f->out_off[t], no, st));
+      prof_end(ph2, st, (double)(no * (16 + esz)));
+    }
   }
   return IPC_OK;
 }
@@ -874,9 +1034,39 @@ int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len) {
   DeviceGuard dg(f->device);
   std::vector<uint8_t> h = header_bytes(f);
   std::memcpy(host_buf, h.data(), h.size());
-  if (f->stream_bytes)
-    CU(cudaMemcpy((uint8_t*)host_buf + h.size(), f->d_blob, f->stream_bytes,
-                  cudaMemcpyDeviceToHost));
+  const Geo& g = f->g;
+  if (f->stream_bytes) {
+    cudaStream_t st = nullptr;
+    CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    uint32_t *blob = nullptr, *rank = nullptr;
+    unsigned int* bad = nullptr;
+    uint64_t rk = 0;
+    for (auto& sg : g.stages) rk = std::max<uint64_t>(rk, 32 * sg.ntiles);
+    int rc = IPC_OK;
+    if ((rc = dalloc((void**)&blob, f->stream_bytes, st)) ||
+        (rc = dalloc((void**)&rank, rk * 4, st)) || (rc = dalloc((void**)&bad, 4, st))) {
+      dfree(blob);
+      dfree(rank);
+      cudaStreamDestroy(st);
+      return rc;
+    }
+    cudaError_t e = cudaMemsetAsync(bad, 0, 4, st);
+    for (size_t t = 0; t < g.stages.size() && e == cudaSuccess; ++t) {
+      StageArgs a = stage_args(g, g.stages[t], 0);
+      e = launch_seg_rank(a, f->desc[t], 0, f->d_bm, rank, bad, st);
+      if (e == cudaSuccess) e = launch_pack(a, f->desc[t], f->d_cap, f->d_bm, rank, blob, st);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((uint8_t*)host_buf + h.size(), blob, f->stream_bytes,
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(blob, st);
+    cudaFreeAsync(rank, st);
+    cudaFreeAsync(bad, st);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess) return cuda_fail(e, "export");
+  }
   *len = total;
   return IPC_OK;
 }
@@ -916,11 +1106,12 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   if (!f) return fail(IPC_ENOMEM, "host allocation");
   f->tag = kFieldTag;
   cudaGetDevice(&f->device);
-  auto bad = [&](const char* why) {
+  keep_pool(f->device);
+  auto drop = [&](int code, const char* why) {
     free_field_device(f);
     f->tag = kDeadTag;
     delete f;
-    return fail(IPC_ECORRUPT, why);
+    return code == IPC_ECUDA ? code : fail(code, why);
   };
   f->dtype = (int)g32();
   f->interp = (int)g32();
@@ -940,10 +1131,10 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   g32();
   if (!ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 1 || f->bound < 0 ||
       f->bound > 1 || f->eb_mode < 0 || f->eb_mode > 1 || !(f->eb > 0) || !std::isfinite(f->eb))
-    return bad("bad header fields");
+    return drop(IPC_ECORRUPT, "bad header fields");
   if (ndim < 1 || ndim > 3 || !build_geo(ndim, dims, &f->g) || f->g.K != K ||
       f->g.stages.size() != S)
-    return bad("bad geometry");
+    return drop(IPC_ECORRUPT, "bad geometry");
   f->st.assign(S, StageTab{});
   std::vector<uint64_t> nout(S);
   for (uint32_t t = 0; t < S; ++t) {
@@ -955,79 +1146,110 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
     nout[t] = g64();
     if (!ok || (int)lv != sg.level || (int)dm != sg.dim3 - (3 - ndim) || nc != sg.ncodes ||
         f->st[t].H < -1 || f->st[t].H > 31 || nout[t] > nc)
-      return bad("bad stage table");
+      return drop(IPC_ECORRUPT, "bad stage table");
   }
   std::vector<uint64_t> size(32 * (size_t)S);
   for (uint32_t t = 0; t < S; ++t)
     for (int k = 31; k >= 0; --k) size[32 * t + k] = g64();
   for (uint32_t t = 0; t < S; ++t) {
-    if (!need(nout[t] * 16)) return bad("truncated outliers");
+    if (!need(nout[t] * 16)) return drop(IPC_ECORRUPT, "truncated outliers");
     for (uint64_t i = 0; i < nout[t]; ++i) {
       const uint64_t idx = g64();
       const double v = gd();
       if (idx >= f->g.stages[t].ncodes || (i && idx <= f->st[t].out_idx.back()))
-        return bad("bad outlier list");
+        return drop(IPC_ECORRUPT, "bad outlier list");
       f->st[t].out_idx.push_back(idx);
       f->st[t].out_val.push_back(v);
     }
   }
-  if (!ok) return bad("truncated tables");
+  if (!ok) return drop(IPC_ECORRUPT, "truncated tables");
   const uint64_t mand = pos;
-  // stream layout: read each nnz word and check the size follows from it
   uint64_t spos = pos;
   for (uint32_t t = 0; t < S; ++t) {
     const uint64_t W = f->g.stages[t].words;
     for (int k = 31; k >= 0; --k) {
-      if (spos + 4 > len) return bad("truncated streams");
-      uint32_t nnz = 0;
-      for (int i = 0; i < 4; ++i) nnz |= uint32_t(p[spos + i]) << (8 * i);
-      if (nnz > W || size[32 * t + k] != stream_bytes(nnz, W)) return bad("bad stream size");
-      f->st[t].nnz[k] = nnz;
+      if (spos + 4 > len) return drop(IPC_ECORRUPT, "truncated streams");
+      uint32_t nz = 0;
+      for (int i = 0; i < 4; ++i) nz |= uint32_t(p[spos + i]) << (8 * i);
+      if (nz > W || size[32 * t + k] != stream_bytes(nz, W)) return drop(IPC_ECORRUPT, "bad stream size");
+      f->st[t].nnz[k] = nz;
       spos += size[32 * t + k];
-      if (spos > len) return bad("truncated streams");
+      if (spos > len) return drop(IPC_ECORRUPT, "truncated streams");
     }
   }
-  if (spos != len) return bad("trailing bytes");
+  if (spos != len) return drop(IPC_ECORRUPT, "trailing bytes");
   DeviceGuard dg(f->device);
-  int rc = layout_field(f);
-  if (rc) {
-    f->tag = kDeadTag;
-    delete f;
-    return rc;
-  }
-  if (f->mandatory != mand) return bad("table size mismatch");
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned int* d_bad = nullptr;
+  int rc = plan_field(f, st);
+  if (rc) return drop(rc, "allocation");
+  rc = finish_field(f, st);
+  if (rc) return drop(rc, "allocation");
+  if (f->mandatory != mand) return drop(IPC_ECORRUPT, "table size mismatch");
+  // streams -> device, then unpack into the segmented layout
+  uint32_t *blob = nullptr, *rank = nullptr;
+  unsigned int* flags = nullptr;  // [0] bad, [1..] 32 counters per stage
+  uint64_t rk = 0;
+  for (auto& sg : f->g.stages) rk = std::max<uint64_t>(rk, 32 * sg.ntiles);
+  if ((rc = dalloc((void**)&blob, f->stream_bytes, st)) || (rc = dalloc((void**)&rank, rk * 4, st)) ||
+      (rc = dalloc((void**)&flags, (1 + 32 * (uint64_t)S) * 4, st))) {
+    dfree(blob);
+    dfree(rank);
+    return drop(rc, "allocation");
+  }
   cudaError_t e = cudaSuccess;
   if (f->stream_bytes)
-    e = cudaMemcpyAsync(f->d_blob, p + mand, f->stream_bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&d_bad, 4);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, 4, st);
+    e = cudaMemcpyAsync(blob, p + mand, f->stream_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, (1 + 32 * (uint64_t)S) * 4, st);
   for (uint32_t t = 0; t < S && e == cudaSuccess; ++t) {
     StageArgs a = stage_args(f->g, f->g.stages[t], 0);
-    e = launch_build_rank(a, f->desc[t], f->d_blob, f->d_rank, d_bad, st);
+    e = launch_seg_rank(a, f->desc[t], 1, blob, rank, flags, st);
+    if (e == cudaSuccess)
+      e = launch_unpack(a, f->desc[t], blob, rank, f->d_cap, f->d_bm, flags, flags + 1 + 32 * t, st);
   }
-  unsigned int hbad = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, d_bad, 4, cudaMemcpyDeviceToHost, st);
+  std::vector<unsigned int> hf(1 + 32 * (size_t)S);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hf.data(), flags, hf.size() * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (d_bad) cudaFree(d_bad);
+  cudaFreeAsync(blob, st);
+  cudaFreeAsync(rank, st);
+  cudaFreeAsync(flags, st);
   if (e != cudaSuccess) {
-    free_field_device(f);
-    f->tag = kDeadTag;
-    delete f;
-    return cuda_fail(e, "import");
+    cuda_fail(e, "import");
+    return drop(IPC_ECUDA, "");
   }
-  if (hbad) return bad("bitmap population differs from the stream's nnz");
-  rc = upload_outliers(f, st);
-  if (rc) {
-    free_field_device(f);
-    f->tag = kDeadTag;
-    delete f;
-    return rc;
-  }
+  if (hf[0]) return drop(IPC_ECORRUPT, "bitmap population differs from the stream's nnz");
+  for (uint32_t t = 0; t < S; ++t)
+    for (int k = 0; k < 32; ++k)
+      if (f->desc[t].p[k].mode == 2 && hf[1 + 32 * t + k] != f->desc[t].p[k].nnz)
+        return drop(IPC_ECORRUPT, "dense stream population differs from its nnz");
   *out = f;
   return IPC_OK;
 }
+
+int ipc_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return IPC_OK;
+}
+
+int ipc_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain();
+  for (auto& a : g_prof_acc) a = ProfAcc{0, 0.0, 0.0};
+  return IPC_OK;
+}
+
+int ipc_profile_read(int kind, uint64_t* launches, double* total_ms, double* alg_bytes) {
+  if (kind < 0 || kind >= IPC_KERNEL_KINDS) return fail(IPC_EINVAL, "kernel kind");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain();
+  if (launches) *launches = g_prof_acc[kind].launches;
+  if (total_ms) *total_ms = g_prof_acc[kind].ms;
+  if (alg_bytes) *alg_bytes = g_prof_acc[kind].bytes;
+  return IPC_OK;
+}
+
+uint64_t ipc_launch_count(void) { return g_launches.load(); }
 
 int ipc_field_info(const ipc_field* f, int* dtype, int* ndim, int64_t* dims, int* K, int* S,
                    double* eb, double* xmin, double* xmax) {

@@ -49,11 +49,16 @@ struct QuantArgs {
   T inv2eb, twoeb, ebchk, R;
 };
 
-// Scratch of one compression (library workspace).
-struct CompressScratch {
-  uint32_t* cap;        // per plane: ntiles*256 candidate words (compacted per tile)
-  uint32_t* bitmap;     // per plane: ntiles*8 words
-  uint32_t* tilecnt;    // per plane: ntiles counts
+// Outputs of the compression sweeps. The plane streams of a device-resident
+// field are kept "segmented": per (stage, plane) a capacity array of
+// ntiles * 256 words in which every 256-word segment stores its nonzero words
+// compacted at the segment's own start, plus the zero-word bitmap of the
+// whole plane (ntiles * 8 words). The packed container form is produced only
+// by export.
+struct SweepOut {
+  uint32_t* cap;        // field capacity arrays
+  uint32_t* bm;         // field bitmaps
+  uint32_t* nnz;        // 32 counters per stage (nonzero words per plane)
   unsigned long long* outl_key;  // (stage << 40) | code index
   double* outl_val;
   unsigned long long* outl_count;
@@ -61,12 +66,13 @@ struct CompressScratch {
   uint32_t* stat;       // per stage: [OR of negabinary codes, max |q|]
 };
 
-// Retrieval descriptor of one plane stream.
+// Per-plane descriptor of a device-resident stream.
 struct PlaneDesc {
-  uint64_t off;      // word offset of the stream's nnz word in the field blob
-  uint64_t rank_off; // offset of the stream's tile-rank index
+  uint64_t cap_off;  // word offset of the plane's capacity array (segmented)
+  uint64_t bm_off;   // word offset of the plane's bitmap
+  uint64_t pk_off;   // word offset of the stream (nnz word) in a packed blob
   uint32_t nnz;
-  uint32_t mode;     // 0 empty, 1 sparse (bitmap + payload), 2 dense
+  uint32_t mode;     // 0 empty, 1 sparse, 2 dense (packed container modes)
 };
 struct StageDescs {
   PlaneDesc p[32];
@@ -89,22 +95,28 @@ inline uint64_t stream_bytes(uint64_t nnz, uint64_t W) {
 cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long long* acc,
                          cudaStream_t st);
 cudaError_t launch_compress_stage(int dtype, const StageArgs& a, const void* x, void* xh,
-                                  int write_xh, const void* quant, int stage,
-                                  const CompressScratch& sc, uint64_t cap_off,
-                                  uint64_t bm_off, uint64_t cnt_off, cudaStream_t st);
-cudaError_t launch_scan_stage(const StageArgs& a, const CompressScratch& sc, uint64_t cnt_off,
-                              uint32_t* rank_out, uint32_t* nnz_out, cudaStream_t st);
-cudaError_t launch_pack_stage(const StageArgs& a, const CompressScratch& sc, uint64_t cap_off,
-                              uint64_t bm_off, uint64_t cnt_off, const uint32_t* rank,
-                              const StageDescs& d, uint32_t* blob, cudaStream_t st);
+                                  int write_xh, const void* quant, int stage, const SweepOut& o,
+                                  const StageDescs& d, cudaStream_t st);
 cudaError_t launch_retrieve_stage(int dtype, const StageArgs& a, void* out, double twoeb,
-                                  const StageDescs& d, int b, const uint32_t* blob,
-                                  const uint32_t* rank, cudaStream_t st);
+                                  const StageDescs& d, int b, const uint32_t* cap,
+                                  const uint32_t* bm, cudaStream_t st);
 cudaError_t launch_outlier_scatter(int dtype, const StageArgs& a, void* out,
                                    const uint64_t* idx, const double* val, uint64_t n,
                                    cudaStream_t st);
 cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st);
-cudaError_t launch_build_rank(const StageArgs& a, const StageDescs& d, const uint32_t* blob,
-                              uint32_t* rank, unsigned int* bad, cudaStream_t st);
+// Exclusive prefix, per plane, of the population of each 256-word segment of
+// a bitmap (bm = segmented bitmaps when packed == 0, the packed blob's sparse
+// bitmaps when packed != 0); flags bitmaps whose population differs from nnz.
+cudaError_t launch_seg_rank(const StageArgs& a, const StageDescs& d, int packed,
+                            const uint32_t* bm, uint32_t* rank, unsigned int* bad,
+                            cudaStream_t st);
+// Segmented -> packed container streams (export) and back (import).
+cudaError_t launch_pack(const StageArgs& a, const StageDescs& d, const uint32_t* cap,
+                        const uint32_t* bm, const uint32_t* rank, uint32_t* blob,
+                        cudaStream_t st);
+// chk: 32 counters per stage (nonzero words of dense streams); bad: flag.
+cudaError_t launch_unpack(const StageArgs& a, const StageDescs& d, const uint32_t* blob,
+                          const uint32_t* rank, uint32_t* cap, uint32_t* bm, unsigned int* bad,
+                          unsigned int* chk, cudaStream_t st);
 
 }  // namespace ipc

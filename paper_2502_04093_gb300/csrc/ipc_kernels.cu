@@ -155,24 +155,52 @@ __device__ __forceinline__ unsigned long long okey(double v) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
 }
 
+template <class T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
+template <> struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
+
+template <class T>
+struct RangeAcc {
+  T mn, mx, ma;
+  unsigned long long cnt;
+  __device__ __forceinline__ void add(T v) {
+    if (!isfinite(v)) return;
+    mn = cnt ? (v < mn ? v : mn) : v;
+    mx = cnt ? (v > mx ? v : mx) : v;
+    const T a = FP<T>::fabs_(v);
+    ma = cnt ? (a > ma ? a : ma) : a;
+    ++cnt;
+  }
+};
+
+// Min / max / max|x| in the element type (the values are exact, so no
+// wider arithmetic is needed), 16-byte vector loads, then one ordered-key
+// atomic per warp.
 template <class T>
 __global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, uint64_t n,
                                                unsigned long long* acc) {
-  double mn = 0, mx = 0, ma = 0;
-  unsigned long long cnt = 0;
+  typedef typename Vec16<T>::type V;
+  constexpr int VN = Vec16<T>::n;
+  RangeAcc<T> r{(T)0, (T)0, (T)0, 0ULL};
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = tid; i < n; i += nth) {
-    double v = (double)__ldg(x + i);
-    if (!isfinite(v)) continue;
-    if (cnt == 0) { mn = mx = v; }
-    mn = fmin(mn, v);
-    mx = fmax(mx, v);
-    ma = fmax(ma, fabs(v));
-    ++cnt;
+  // scalar head up to 16-byte alignment
+  const uint64_t mis = ((uintptr_t)x & 15) / sizeof(T);
+  const uint64_t head = mis ? ((uint64_t)VN - mis < n ? (uint64_t)VN - mis : n) : 0;
+  if (tid < head) r.add(__ldg(x + tid));
+  const uint64_t nv = (n - head) / VN;
+  const V* xv = reinterpret_cast<const V*>(x + head);
+  for (uint64_t i = tid; i < nv; i += nth) {
+    const V v = __ldg(xv + i);
+    const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int j = 0; j < VN; ++j) r.add(e[j]);
   }
-  unsigned long long kmn = cnt ? okey(mn) : ~0ULL, kmx = cnt ? okey(mx) : 0ULL;
-  unsigned long long kma = cnt ? (unsigned long long)__double_as_longlong(ma) : 0ULL;
+  for (uint64_t i = head + nv * VN + tid; i < n; i += nth) r.add(__ldg(x + i));
+  unsigned long long kmn = r.cnt ? okey((double)r.mn) : ~0ULL;
+  unsigned long long kmx = r.cnt ? okey((double)r.mx) : 0ULL;
+  unsigned long long kma = r.cnt ? (unsigned long long)__double_as_longlong((double)r.ma) : 0ULL;
+  unsigned long long cnt = r.cnt;
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     kmn = min(kmn, __shfl_xor_sync(~0u, kmn, o));
@@ -189,21 +217,20 @@ __global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, uint64_t
 }
 
 // ---------------------------------------------------------------------------
-// Compression of one sweep. CTA = 8 warps = one tile of 256 words.
+// Compression of one sweep. CTA = 8 warps = one 256-word segment.
 // Phase A (lane per code): warp wi walks its 32 words; lane L computes code
 //   32j + L of word (r, j): prediction from xhat, quantization, xhat write,
 //   negabinary + XOR -> E, stored to shared memory.
 // Phase B (thread per word): the 32 codes of one word are read back and the
-//   32x32 bit matrix transposed: a[k] = plane-k word.
-// Phase C: zero-word bitmap per plane (warp ballot), per-tile prefix of the
-//   nonzero counts, nonzero words written compacted into the tile's slot.
+//   32x32 bit matrix transposed: pw[k] = plane-k word.
+// Phase C: zero-word bitmap per plane (warp ballot), prefix of the warps'
+//   nonzero counts, nonzero words stored compacted at the segment's start of
+//   the plane's capacity array, per-plane nonzero counter.
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(256) k_compress(StageArgs a, const T* __restrict__ x,
                                                   T* xh, int write_xh, QuantArgs<T> qa,
-                                                  int stage, CompressScratch sc,
-                                                  uint64_t cap_off, uint64_t bm_off,
-                                                  uint64_t cnt_off) {
+                                                  int stage, SweepOut o, StageDescs ds) {
   __shared__ uint32_t Es[8][32][33];
   __shared__ uint32_t wcnt[32][8];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -247,11 +274,11 @@ __global__ void __launch_bounds__(256) k_compress(StageArgs a, const T* __restri
           }
         }
         if (outlier) {
-          unsigned long long slot = atomicAdd(sc.outl_count, 1ULL);
-          if (slot < sc.outl_cap) {
-            sc.outl_key[slot] = ((unsigned long long)stage << 40) |
-                                (unsigned long long)(cur.r * (uint64_t)a.m[2] + p);
-            sc.outl_val[slot] = (double)xv;
+          unsigned long long slot = atomicAdd(o.outl_count, 1ULL);
+          if (slot < o.outl_cap) {
+            o.outl_key[slot] = ((unsigned long long)stage << 40) |
+                               (unsigned long long)(cur.r * (uint64_t)a.m[2] + p);
+            o.outl_val[slot] = (double)xv;
           }
         }
         if (write_xh) xh[idx] = rec;
@@ -272,21 +299,19 @@ __global__ void __launch_bounds__(256) k_compress(StageArgs a, const T* __restri
   transpose32(pw);
 
   const uint32_t lt = lanemask_lt();
-  uint32_t* bitmap = sc.bitmap + bm_off;
-  const uint64_t nbm_pad = a.ntiles * kTileBitmapWords;
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
     const uint32_t mk = __ballot_sync(~0u, pw[k] != 0);
     if (lane == k) {
-      bitmap[(uint64_t)k * nbm_pad + tile * kTileBitmapWords + wi] = mk;
+      o.bm[ds.p[k].bm_off + tile * kTileBitmapWords + wi] = mk;
       wcnt[k][wi] = __popc(mk);
     }
   }
   orN = __reduce_or_sync(~0u, orN);
   qmax = __reduce_max_sync(~0u, qmax);
   if (lane == 0) {
-    if (orN) atomicOr(sc.stat + 2 * stage, orN);
-    if (qmax) atomicMax(sc.stat + 2 * stage + 1, qmax);
+    if (orN) atomicOr(o.stat + 2 * stage, orN);
+    if (qmax) atomicMax(o.stat + 2 * stage + 1, qmax);
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -298,21 +323,20 @@ __global__ void __launch_bounds__(256) k_compress(StageArgs a, const T* __restri
       wcnt[k][v] = run;
       run += c;
     }
-    sc.tilecnt[cnt_off + (uint64_t)k * a.ntiles + tile] = run;
+    if (run) atomicAdd(o.nnz + 32 * stage + k, run);
   }
   __syncthreads();
-  const uint64_t Wcap = a.ntiles * kTileWords;
-  uint32_t* cap = sc.cap + cap_off + tile * kTileWords;
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
     const uint32_t mk = __ballot_sync(~0u, pw[k] != 0);
-    if (pw[k]) cap[(uint64_t)k * Wcap + wcnt[k][wi] + __popc(mk & lt)] = pw[k];
+    if (pw[k])
+      o.cap[ds.p[k].cap_off + tile * kTileWords + wcnt[k][wi] + __popc(mk & lt)] = pw[k];
   }
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim = 1024).
 __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* total,
-                                                 uint32_t* sh /* 32 */) {
+                                                 uint32_t* sh /* 33 */) {
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   uint32_t inc = v;
 #pragma unroll
@@ -339,112 +363,170 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* total,
   return sh[wi] + inc - v;
 }
 
-// Per plane (blockIdx.x = k): tile ranks = exclusive prefix of tile counts;
-// nnz of the stream = total.
-__global__ void __launch_bounds__(1024) k_scan(uint64_t ntiles, const uint32_t* __restrict__ cnt,
-                                               uint32_t* __restrict__ rank,
-                                               uint32_t* __restrict__ nnz) {
+// Per plane (blockIdx.x = k) of a sparse stream: exclusive prefix of the
+// population of every 256-word segment. `packed` selects the bitmap source.
+__global__ void __launch_bounds__(1024) k_seg_rank(StageArgs a, StageDescs ds, int packed,
+                                                   const uint32_t* __restrict__ bm,
+                                                   uint32_t* __restrict__ rank,
+                                                   unsigned int* bad) {
   __shared__ uint32_t sh[33];
   const int k = blockIdx.x;
+  const PlaneDesc pd = ds.p[k];
+  if (pd.mode != 1) return;
+  const uint64_t nbm = (a.W + 31) / 32;
+  const uint32_t* src = packed ? bm + pd.pk_off + 1 : bm + pd.bm_off;
   uint32_t run = 0;
-  for (uint64_t base = 0; base < ntiles; base += 1024) {
+  for (uint64_t base = 0; base < a.ntiles; base += 1024) {
     const uint64_t t = base + threadIdx.x;
-    const uint32_t v = t < ntiles ? cnt[(uint64_t)k * ntiles + t] : 0;
+    uint32_t v = 0;
+    if (t < a.ntiles) {
+#pragma unroll
+      for (int j = 0; j < kTileBitmapWords; ++j) {
+        const uint64_t bw = t * kTileBitmapWords + j;
+        if (bw < nbm) v += __popc(src[bw]);
+      }
+    }
     uint32_t tot;
     const uint32_t ex = block_exscan(v, &tot, sh);
-    if (t < ntiles) rank[(uint64_t)k * ntiles + t] = run + ex;
+    if (t < a.ntiles) rank[(uint64_t)k * a.ntiles + t] = run + ex;
     run += tot;
   }
-  if (threadIdx.x == 0) nnz[k] = run;
+  if (threadIdx.x == 0) {
+    const uint32_t tail = (uint32_t)(a.W & 31);
+    const bool extra = tail && (src[nbm - 1] >> tail) != 0;
+    if (run != pd.nnz || extra) atomicOr(bad, 1u);
+  }
 }
 
-// Pack one stage's streams into the field blob. grid = (ntiles, 32).
-__global__ void __launch_bounds__(256) k_pack(StageArgs a, CompressScratch sc, uint64_t cap_off,
-                                              uint64_t bm_off, uint64_t cnt_off,
-                                              const uint32_t* __restrict__ rank, StageDescs ds,
+// Segmented -> packed stream of one (segment, plane) (export). grid = (ntiles, 32).
+__global__ void __launch_bounds__(256) k_pack(StageArgs a, StageDescs ds,
+                                              const uint32_t* __restrict__ cap,
+                                              const uint32_t* __restrict__ bm,
+                                              const uint32_t* __restrict__ rank,
                                               uint32_t* __restrict__ blob) {
-  __shared__ uint32_t bm[8];
-  __shared__ uint32_t pre[8];
+  __shared__ uint32_t sbm[8];
+  __shared__ uint32_t pre[9];
   const int k = blockIdx.y;
   const uint64_t tile = blockIdx.x;
   const PlaneDesc pd = ds.p[k];
-  if (tile == 0 && threadIdx.x == 0) blob[pd.off] = pd.nnz;
+  if (tile == 0 && threadIdx.x == 0) blob[pd.pk_off] = pd.nnz;
   if (pd.mode == 0) return;
   const uint64_t W = a.W, nbm = (W + 31) / 32;
-  const uint64_t nbm_pad = a.ntiles * kTileBitmapWords;
-  const uint32_t* bmp = sc.bitmap + bm_off + (uint64_t)k * nbm_pad + tile * kTileBitmapWords;
-  const uint32_t* cap = sc.cap + cap_off + (uint64_t)k * a.ntiles * kTileWords + tile * kTileWords;
-  const uint32_t cnt = sc.tilecnt[cnt_off + (uint64_t)k * a.ntiles + tile];
+  if (threadIdx.x < 8) sbm[threadIdx.x] = bm[pd.bm_off + tile * kTileBitmapWords + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int v = 0; v < 8; ++v) { pre[v] = run; run += __popc(sbm[v]); }
+    pre[8] = run;
+  }
+  __syncthreads();
+  const uint32_t* seg = cap + pd.cap_off + tile * kTileWords;
   if (pd.mode == 1) {
     if (threadIdx.x < 8) {
       const uint64_t bw = tile * kTileBitmapWords + threadIdx.x;
-      if (bw < nbm) blob[pd.off + 1 + bw] = bmp[threadIdx.x];
+      if (bw < nbm) blob[pd.pk_off + 1 + bw] = sbm[threadIdx.x];
     }
     const uint32_t r0 = rank[(uint64_t)k * a.ntiles + tile];
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
-      blob[pd.off + 1 + nbm + r0 + i] = cap[i];
+    for (uint32_t i = threadIdx.x; i < pre[8]; i += blockDim.x)
+      blob[pd.pk_off + 1 + nbm + r0 + i] = seg[i];
     return;
   }
-  // dense: expand the tile's words from bitmap + compacted payload
-  if (threadIdx.x < 8) {
-    bm[threadIdx.x] = bmp[threadIdx.x];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const uint64_t w = tile * kTileWords + threadIdx.x;
+  if (w < W) {
+    const uint32_t m = sbm[wi];
+    blob[pd.pk_off + 1 + w] = ((m >> lane) & 1u) ? seg[pre[wi] + __popc(m & lanemask_lt())] : 0u;
+  }
+}
+
+// Packed stream -> segmented (import). grid = (ntiles, 32). Flags payload
+// words that are zero; counts the nonzero words of dense streams in chk.
+__global__ void __launch_bounds__(256) k_unpack(StageArgs a, StageDescs ds,
+                                                const uint32_t* __restrict__ blob,
+                                                const uint32_t* __restrict__ rank,
+                                                uint32_t* __restrict__ cap,
+                                                uint32_t* __restrict__ bm, unsigned int* bad,
+                                                unsigned int* chk) {
+  __shared__ uint32_t sbm[8];
+  __shared__ uint32_t pre[9];
+  const int k = blockIdx.y;
+  const uint64_t tile = blockIdx.x;
+  const PlaneDesc pd = ds.p[k];
+  const uint64_t W = a.W, nbm = (W + 31) / 32;
+  uint32_t* seg = cap + pd.cap_off + tile * kTileWords;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  if (pd.mode == 0) {
+    if (threadIdx.x < 8) bm[pd.bm_off + tile * kTileBitmapWords + threadIdx.x] = 0u;
+    return;
+  }
+  if (pd.mode == 1) {
+    if (threadIdx.x < 8) {
+      const uint64_t bw = tile * kTileBitmapWords + threadIdx.x;
+      const uint32_t v = bw < nbm ? blob[pd.pk_off + 1 + bw] : 0u;
+      sbm[threadIdx.x] = v;
+      bm[pd.bm_off + bw] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int v = 0; v < 8; ++v) run += __popc(sbm[v]);
+      pre[8] = run;
+    }
+    __syncthreads();
+    const uint32_t r0 = rank[(uint64_t)k * a.ntiles + tile];
+    for (uint32_t i = threadIdx.x; i < pre[8]; i += blockDim.x) {
+      const uint64_t src = 1 + nbm + (uint64_t)r0 + i;
+      const uint32_t v = src < 1 + nbm + pd.nnz ? blob[pd.pk_off + src] : 0u;
+      if (v == 0) atomicOr(bad, 1u);
+      seg[i] = v;
+    }
+    return;
+  }
+  const uint64_t w = tile * kTileWords + threadIdx.x;
+  const uint32_t v = w < W ? blob[pd.pk_off + 1 + w] : 0u;
+  const uint32_t m = __ballot_sync(~0u, v != 0);
+  if (lane == 0) {
+    sbm[wi] = m;
+    bm[pd.bm_off + tile * kTileBitmapWords + wi] = m;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
-    for (int v = 0; v < 8; ++v) { pre[v] = run; run += __popc(bm[v]); }
+    for (int q = 0; q < 8; ++q) { pre[q] = run; run += __popc(sbm[q]); }
+    if (run) atomicAdd(chk + k, run);
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const uint64_t w = tile * kTileWords + threadIdx.x;
-  if (w < W) {
-    const uint32_t m = bm[wi];
-    uint32_t v = 0;
-    if ((m >> lane) & 1u) v = cap[pre[wi] + __popc(m & lanemask_lt())];
-    blob[pd.off + 1 + w] = v;
-  }
+  if (v) seg[pre[wi] + __popc(m & lanemask_lt())] = v;
 }
 
 // ---------------------------------------------------------------------------
-// Reconstruction of one sweep (Algorithm 1). CTA = one tile of 256 words.
-// Thread per word: fetch the word of every selected plane (dense: direct;
-// sparse: bitmap bit + rank into the payload), transpose back to per-code
-// E, undo the XOR, drop the unloaded digits, keep N in shared memory.
+// Reconstruction of one sweep (Algorithm 1). CTA = one 256-word segment.
+// Thread per word: fetch the word of every selected plane (bitmap bit + rank
+// inside the segment), transpose back to per-code E, undo the XOR, drop the
+// unloaded digits, keep N in shared memory.
 // Lane per code: q' = negabinary^-1(N), xhat' = P xhat' + q' 2eb.
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(256) k_retrieve(StageArgs a, T* out, T twoeb, StageDescs ds,
-                                                  int b, const uint32_t* __restrict__ blob,
-                                                  const uint32_t* __restrict__ rank) {
+                                                  int b, const uint32_t* __restrict__ cap,
+                                                  const uint32_t* __restrict__ bm) {
   __shared__ uint32_t Ns[8][32][33];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const uint64_t tile = blockIdx.x;
-  const uint64_t W = a.W, nbm = (W + 31) / 32;
+  const uint64_t W = a.W;
   const uint64_t wbase = tile * kTileWords + (uint64_t)wi * 32;
-  const uint64_t w = wbase + lane;
   const uint32_t lt = lanemask_lt();
   uint32_t pw[32];
 #pragma unroll
   for (int k = 31; k >= 0; --k) {
     pw[k] = 0;
-    if (k >= b) {
-      const PlaneDesc pd = ds.p[k];
-      if (pd.mode == 2) {
-        if (w < W) pw[k] = __ldg(blob + pd.off + 1 + w);
-      } else if (pd.mode == 1) {
-        const uint64_t bw = tile * kTileBitmapWords + wi;
-        const uint32_t m = bw < nbm ? __ldg(blob + pd.off + 1 + bw) : 0u;
-        uint32_t before = 0;
-        if (lane < wi) {
-          const uint64_t bv = tile * kTileBitmapWords + lane;
-          if (bv < nbm) before = __popc(__ldg(blob + pd.off + 1 + bv));
-        }
-        before = __reduce_add_sync(~0u, before);
-        if ((m >> lane) & 1u) {
-          const uint32_t r = __ldg(rank + pd.rank_off + tile) + before + __popc(m & lt);
-          pw[k] = __ldg(blob + pd.off + 1 + nbm + r);
-        }
-      }
+    if (k >= b && ds.p[k].nnz) {
+      const uint32_t* bmp = bm + ds.p[k].bm_off + tile * kTileBitmapWords;
+      const uint32_t m = __ldg(bmp + wi);
+      uint32_t before = lane < wi ? __popc(__ldg(bmp + lane)) : 0u;
+      before = __reduce_add_sync(~0u, before);
+      if ((m >> lane) & 1u)
+        pw[k] = __ldg(cap + ds.p[k].cap_off + tile * kTileWords + before + __popc(m & lt));
     }
   }
   transpose32(pw);
@@ -492,40 +574,6 @@ __global__ void k_outliers(StageArgs a, T* out, const uint64_t* __restrict__ idx
 template <class T>
 __global__ void k_anchor(T* out, double v) { out[0] = (T)v; }
 
-// Tile ranks of the sparse streams of an imported stage (blockIdx.x = k);
-// flags a stream whose bitmap population differs from its nnz word.
-__global__ void __launch_bounds__(1024) k_build_rank(StageArgs a, StageDescs ds,
-                                                     const uint32_t* __restrict__ blob,
-                                                     uint32_t* __restrict__ rank,
-                                                     unsigned int* bad) {
-  __shared__ uint32_t sh[33];
-  const int k = blockIdx.x;
-  const PlaneDesc pd = ds.p[k];
-  if (pd.mode != 1) return;
-  const uint64_t nbm = (a.W + 31) / 32;
-  uint32_t run = 0;
-  for (uint64_t base = 0; base < a.ntiles; base += 1024) {
-    const uint64_t t = base + threadIdx.x;
-    uint32_t v = 0;
-    if (t < a.ntiles) {
-      for (int j = 0; j < kTileBitmapWords; ++j) {
-        const uint64_t bw = t * kTileBitmapWords + j;
-        if (bw < nbm) v += __popc(blob[pd.off + 1 + bw]);
-      }
-    }
-    uint32_t tot;
-    const uint32_t ex = block_exscan(v, &tot, sh);
-    if (t < a.ntiles) rank[pd.rank_off + t] = run + ex;
-    run += tot;
-  }
-  if (threadIdx.x == 0) {
-    // bits beyond W in the last bitmap word must be clear
-    const uint32_t tail = (uint32_t)(a.W & 31);
-    bool extra = tail && (blob[pd.off + 1 + nbm - 1] >> tail) != 0;
-    if (run != pd.nnz || extra) atomicOr(bad, 1u);
-  }
-}
-
 unsigned grid_for(uint64_t n, unsigned block, unsigned cap) {
   uint64_t g = (n + block - 1) / block;
   if (g > cap) g = cap;
@@ -539,50 +587,33 @@ unsigned grid_for(uint64_t n, unsigned block, unsigned cap) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long long* acc,
                          cudaStream_t st) {
-  const unsigned grid = grid_for(n, 256, 152 * 16);
+  const unsigned grid = grid_for(n / 4 + 1, 256, 152 * 8);
   if (dtype == 0) k_range<float><<<grid, 256, 0, st>>>((const float*)x, n, acc);
   else k_range<double><<<grid, 256, 0, st>>>((const double*)x, n, acc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_compress_stage(int dtype, const StageArgs& a, const void* x, void* xh,
-                                  int write_xh, const void* quant, int stage,
-                                  const CompressScratch& sc, uint64_t cap_off,
-                                  uint64_t bm_off, uint64_t cnt_off, cudaStream_t st) {
+                                  int write_xh, const void* quant, int stage, const SweepOut& o,
+                                  const StageDescs& d, cudaStream_t st) {
   const unsigned grid = (unsigned)a.ntiles;
   if (dtype == 0)
     k_compress<float><<<grid, 256, 0, st>>>(a, (const float*)x, (float*)xh, write_xh,
-                                            *(const QuantArgs<float>*)quant, stage, sc,
-                                            cap_off, bm_off, cnt_off);
+                                            *(const QuantArgs<float>*)quant, stage, o, d);
   else
     k_compress<double><<<grid, 256, 0, st>>>(a, (const double*)x, (double*)xh, write_xh,
-                                             *(const QuantArgs<double>*)quant, stage, sc,
-                                             cap_off, bm_off, cnt_off);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_scan_stage(const StageArgs& a, const CompressScratch& sc, uint64_t cnt_off,
-                              uint32_t* rank_out, uint32_t* nnz_out, cudaStream_t st) {
-  k_scan<<<32, 1024, 0, st>>>(a.ntiles, sc.tilecnt + cnt_off, rank_out, nnz_out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pack_stage(const StageArgs& a, const CompressScratch& sc, uint64_t cap_off,
-                              uint64_t bm_off, uint64_t cnt_off, const uint32_t* rank,
-                              const StageDescs& d, uint32_t* blob, cudaStream_t st) {
-  dim3 grid((unsigned)a.ntiles, 32);
-  k_pack<<<grid, 256, 0, st>>>(a, sc, cap_off, bm_off, cnt_off, rank, d, blob);
+                                             *(const QuantArgs<double>*)quant, stage, o, d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_retrieve_stage(int dtype, const StageArgs& a, void* out, double twoeb,
-                                  const StageDescs& d, int b, const uint32_t* blob,
-                                  const uint32_t* rank, cudaStream_t st) {
+                                  const StageDescs& d, int b, const uint32_t* cap,
+                                  const uint32_t* bm, cudaStream_t st) {
   const unsigned grid = (unsigned)a.ntiles;
   if (dtype == 0)
-    k_retrieve<float><<<grid, 256, 0, st>>>(a, (float*)out, (float)twoeb, d, b, blob, rank);
+    k_retrieve<float><<<grid, 256, 0, st>>>(a, (float*)out, (float)twoeb, d, b, cap, bm);
   else
-    k_retrieve<double><<<grid, 256, 0, st>>>(a, (double*)out, twoeb, d, b, blob, rank);
+    k_retrieve<double><<<grid, 256, 0, st>>>(a, (double*)out, twoeb, d, b, cap, bm);
   return cudaGetLastError();
 }
 
@@ -602,9 +633,24 @@ cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_rank(const StageArgs& a, const StageDescs& d, const uint32_t* blob,
-                              uint32_t* rank, unsigned int* bad, cudaStream_t st) {
-  k_build_rank<<<32, 1024, 0, st>>>(a, d, blob, rank, bad);
+cudaError_t launch_seg_rank(const StageArgs& a, const StageDescs& d, int packed,
+                            const uint32_t* bm, uint32_t* rank, unsigned int* bad,
+                            cudaStream_t st) {
+  k_seg_rank<<<32, 1024, 0, st>>>(a, d, packed, bm, rank, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const StageArgs& a, const StageDescs& d, const uint32_t* cap,
+                        const uint32_t* bm, const uint32_t* rank, uint32_t* blob,
+                        cudaStream_t st) {
+  k_pack<<<dim3((unsigned)a.ntiles, 32), 256, 0, st>>>(a, d, cap, bm, rank, blob);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const StageArgs& a, const StageDescs& d, const uint32_t* blob,
+                          const uint32_t* rank, uint32_t* cap, uint32_t* bm, unsigned int* bad,
+                          unsigned int* chk, cudaStream_t st) {
+  k_unpack<<<dim3((unsigned)a.ntiles, 32), 256, 0, st>>>(a, d, blob, rank, cap, bm, bad, chk);
   return cudaGetLastError();
 }
 

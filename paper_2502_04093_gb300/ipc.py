@@ -69,6 +69,9 @@ def lib() -> C.CDLL:
                                  C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.ipc_last_error.restype = C.c_char_p
+    L.ipc_profile_enable.argtypes = [C.c_int]
+    L.ipc_profile_read.argtypes = [C.c_int, u64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.ipc_launch_count.restype = C.c_uint64
     _lib = L
     return L
 
@@ -175,6 +178,32 @@ def ipc_field_info(field) -> dict:
                                 C.byref(eb), C.byref(mn), C.byref(mx)), "ipc_field_info")
     return dict(dtype=dt.value, ndim=nd.value, dims=tuple(dims)[:nd.value], K=K.value,
                 S=S.value, eb=eb.value, xmin=mn.value, xmax=mx.value)
+
+
+IPC_KERNEL_NAMES = ["range", "compress_sweep", "scan", "pack", "retrieve_sweep", "outliers",
+                    "anchor", "build_rank"]
+
+
+def ipc_profile_enable(on: bool) -> None:
+    _check(lib().ipc_profile_enable(1 if on else 0), "ipc_profile_enable")
+
+
+def ipc_profile_reset() -> None:
+    _check(lib().ipc_profile_reset(), "ipc_profile_reset")
+
+
+def ipc_profile_read(kind: int):
+    """(launches, total device ms, algorithmic bytes) of one kernel kind."""
+    n = C.c_uint64()
+    ms = C.c_double()
+    by = C.c_double()
+    _check(lib().ipc_profile_read(int(kind), C.byref(n), C.byref(ms), C.byref(by)),
+           "ipc_profile_read")
+    return n.value, ms.value, by.value
+
+
+def ipc_launch_count() -> int:
+    return int(lib().ipc_launch_count())
 
 
 def ipc_last_error() -> str:

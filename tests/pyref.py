@@ -10,7 +10,8 @@ byte-for-byte on grids of a few hundred points.
   the largest dimension e with v2(i_e) = l - 1 (Sec. 4.1, Fig. 3).
 * prediction along that dimension with stride s = 2^(l-1): Eq. 2 (cubic) when
   i-3s and i+3s are inside, Eq. 1 when i+s is inside, else copy of i-s.
-* quantization with bin 2eb, outliers stored exactly (Sec. 4.2.2).
+* quantization with bin 2(eb - 4u(max|x| + eb)), outliers stored exactly
+  (Sec. 4.2.2).
 * negabinary + 2-prefix XOR (Sec. 4.4), 32 planes per stage (Sec. 4.3).
 """
 from __future__ import annotations
@@ -136,6 +137,14 @@ def _unlin(p, N):
     return (p // (N[1] * N[2]), (p // N[2]) % N[1], p % N[2])
 
 
+def half_bin(eb, xmaxabs, is32):
+    """Quantizer half bin: eb less 4u(max|x| + eb), at least eb/2, so that
+    the value rebuilt in the element type stays within eb."""
+    u = 2.0 ** -24 if is32 else 2.0 ** -53
+    eq = eb - 4.0 * u * (xmaxabs + eb)
+    return eq if eq >= 0.5 * eb else 0.5 * eb
+
+
 def compress(x: np.ndarray, eb_user: float, eb_mode=0, cubic=True, bound=0):
     """Returns (container bytes, per-stage codes)."""
     T = _T(x.dtype)
@@ -149,8 +158,9 @@ def compress(x: np.ndarray, eb_user: float, eb_mode=0, cubic=True, bound=0):
     if eb_mode == 1:
         r = xmax - xmin
         eb = eb_user * r if r > 0 else eb_user
-    inv2eb = T.t(1.0 / (2.0 * eb))
-    twoeb = T.t(2.0 * eb)
+    eq = half_bin(eb, xmaxabs, T.is32)
+    inv2eb = T.t(1.0 / (2.0 * eq))
+    twoeb = T.t(2.0 * eq)
     ebchk = T.t(eb * ((1 - 2.0 ** -20) if T.is32 else (1 - 2.0 ** -50)))
     R = T.t(2.0 ** 21 if T.is32 else 2.0 ** 30)
     xh = list(flat)  # targets are overwritten in stage order
@@ -244,14 +254,15 @@ def _stream(words):
     return out
 
 
-def reconstruct(x_shape, dtype, codes, outliers, anchor, eb, b_per_level, cubic=True):
+def reconstruct(x_shape, dtype, codes, outliers, anchor, eb, b_per_level, cubic=True,
+                xmaxabs=0.0):
     """Algorithm 1 from per-stage codes: drop b_l low planes at level l."""
     T = _T(dtype)
     N = padded(x_shape)
     n = N[0] * N[1] * N[2]
     out = [T.t(0)] * n
     out[0] = T.t(anchor)
-    twoeb = T.t(2.0 * eb)
+    twoeb = T.t(2.0 * half_bin(eb, xmaxabs, T.is32))
     st, K = stages(x_shape)
     with np.errstate(all="ignore"):
         for si, (l, d, pts) in enumerate(st):

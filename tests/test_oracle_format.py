@@ -53,7 +53,7 @@ def test_reconstruction_equals_restatement(oracle, shape, dtype, kind, eb, cubic
     for b in [[0] * K, [32] * K] + [list(rng.integers(0, 33, size=K)) for _ in range(6)]:
         mine = f.reconstruct(b)
         ref = pyref.reconstruct(shape, dtype, codes, outl, float(x.reshape(-1)[0]),
-                                info["eb"], b, bool(cubic))
+                                info["eb"], b, bool(cubic), info["xmaxabs"])
         assert np.array_equal(mine, ref, equal_nan=True), b
 
 

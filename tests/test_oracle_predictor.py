@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import pyref
+from helpers import exact_eb
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 
@@ -77,7 +78,7 @@ def _positions_1d(N, l, ncodes):
 def test_cubic_exact_on_cubic_polynomials(oracle, N):
     i = np.arange(N, dtype=np.float64)
     x = (i ** 3 - 7 * i ** 2 + 3 * i - 11).astype(np.float32)
-    f = oracle.compress(x, 0.25, oracle.ABS, oracle.CUBIC)
+    f = oracle.compress(x, exact_eb(x), oracle.ABS, oracle.CUBIC)
     checked = 0
     for t in range(f.info()["S"]):
         st = f.stage(t)
@@ -95,7 +96,7 @@ def test_cubic_exact_on_cubic_polynomials(oracle, N):
 def test_linear_exact_on_linear_functions(oracle, N):
     i = np.arange(N, dtype=np.float64)
     x = (3 * i - 5).astype(np.float32)
-    f = oracle.compress(x, 0.25, oracle.ABS, oracle.LINEAR)
+    f = oracle.compress(x, exact_eb(x), oracle.ABS, oracle.LINEAR)
     for t in range(f.info()["S"]):
         st = f.stage(t)
         q = f.codes(t)
@@ -112,7 +113,7 @@ def test_separable_cubic_3d(oracle):
     g = np.indices(N).astype(np.float64)
     p = lambda v: v ** 3 - 4 * v ** 2 + v
     x = (p(g[0]) + p(g[1]) + p(g[2])).astype(np.float32)
-    f = oracle.compress(x, 0.25, oracle.ABS, oracle.CUBIC)
+    f = oracle.compress(x, exact_eb(x), oracle.ABS, oracle.CUBIC)
     st_list, _ = pyref.stages(N)
     zeros = 0
     for t, (l, d, pts) in enumerate(st_list):

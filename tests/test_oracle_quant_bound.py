@@ -6,27 +6,30 @@ import math
 import numpy as np
 import pytest
 
+from helpers import eb_for_bin
 from paper_2502_04093_gb300 import synth
 
 
 def test_bin_width_two_eb(oracle):
-    # 1-D N = 2: x[1] is predicted by copying the anchor, so q = (x1-x0)/2eb.
-    eb = 2.0 ** -8
-    for k in range(-60, 61):
-        x = np.array([0.75, 0.75 + k * 2 * eb], dtype=np.float32)
-        f = oracle.compress(x, eb)
-        assert f.codes(0)[0] == k
-    # residuals round to the nearest bin; an exact half-bin residual would
-    # leave an error of exactly eb, which the (shrunk) check stores exactly
+    # 1-D N = 2: x[1] is predicted by copying the anchor, so q = (x1-x0)/bin,
+    # the bin being 2eb less the element-type rounding allowance (here chosen
+    # to be exactly 2^-7).
+    for dt in (np.float32, np.float64):
+        for k in range(-60, 61):
+            x = np.array([0.75, 0.75 + k * 2.0 ** -7], dtype=dt)
+            eb = eb_for_bin(float(np.abs(x).max()), dt == np.float32, 2.0 ** -8)
+            f = oracle.compress(x, eb)
+            assert f.codes(0)[0] == k
+            assert f.stage(0)["noutliers"] == 0
+    # residuals round to the nearest bin, exact half bins to the even one
     for k in range(-9, 10):
-        for frac, want in ((0.49, k), (0.51, k + 1)):
-            x = np.array([0.0, (k + frac) * 2 * eb], dtype=np.float64)
-            assert oracle.compress(x, eb).codes(0)[0] == want
-        x = np.array([0.0, (k + 0.5) * 2 * eb], dtype=np.float64)
-        f = oracle.compress(x, eb)
-        assert f.codes(0)[0] == 0 and f.stage(0)["noutliers"] == 1
-        y, _ = f.retrieve(oracle.EB, eb)
-        assert y[1] == x[1]
+        for frac in (0.49, 0.5, 0.51):
+            x = np.array([0.0, (k + frac) * 2.0 ** -7], dtype=np.float64)
+            eb = eb_for_bin(float(np.abs(x).max()), False, 2.0 ** -8)
+            f = oracle.compress(x, eb)
+            assert f.codes(0)[0] == int(np.rint(k + frac))
+            y, _ = f.retrieve(oracle.EB, eb)
+            assert abs(y[1] - x[1]) <= eb
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
