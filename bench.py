@@ -187,7 +187,7 @@ def run_ours(args, rank, world, local_rank):
     launches = ipc.ipc_launch_count() - launches0
     elapsed_ms = e_start.elapsed_time(e_end)
     ipc.ipc_profile_enable(False)
-    prof = {ipc.IPC_KERNEL_NAMES[k]: ipc.ipc_profile_read(k) for k in range(8)}
+    prof = {ipc.IPC_KERNEL_NAMES[k]: ipc.ipc_profile_read(k) for k in range(len(ipc.IPC_KERNEL_NAMES))}
     csize = ipc.ipc_compressed_size(fields[-1][0])
     ipc.ipc_free(fields[-1][0])
 

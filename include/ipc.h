@@ -137,24 +137,22 @@ int ipc_field_info(const ipc_field* f, int* dtype, int* ndim, int64_t* dims,
 /* ---- kernel profiler (not part of the method; measurement support) ------ */
 /* Kinds of kernels the library launches. */
 enum {
-  IPC_KERNEL_RANGE = 0,           /* min / max / max|x| reduction            */
-  IPC_KERNEL_COMPRESS_SWEEP = 1,  /* one interpolation sweep, compression     */
-  IPC_KERNEL_SCAN = 2,            /* per-plane prefix of tile counts          */
-  IPC_KERNEL_PACK = 3,            /* stream packing                           */
-  IPC_KERNEL_RETRIEVE_SWEEP = 4,  /* one interpolation sweep, reconstruction  */
-  IPC_KERNEL_OUTLIERS = 5,        /* exact-value scatter                      */
-  IPC_KERNEL_ANCHOR = 6,          /* anchor store                             */
-  IPC_KERNEL_BUILD_RANK = 7,      /* tile-rank index of an imported field     */
-  IPC_KERNEL_KINDS = 8
+  IPC_KERNEL_RANGE = 0,           /* min / max / max|x| reduction               */
+  IPC_KERNEL_COMPRESS_LEVEL = 1,  /* all sweeps of one level, compression       */
+  IPC_KERNEL_RETRIEVE_LEVEL = 2,  /* all sweeps of one level, reconstruction    */
+  IPC_KERNEL_ANCHOR = 3,          /* anchor store                               */
+  IPC_KERNEL_PACK = 4,            /* device streams -> container (export)       */
+  IPC_KERNEL_UNPACK = 5,          /* container -> device streams (import)       */
+  IPC_KERNEL_KINDS = 6
 };
 /* ipc_profile_enable -- when on, every later launch is bracketed by CUDA
  * events recorded on its stream. */
 int ipc_profile_enable(int on);
 /* ipc_profile_read -- waits for the recorded events and returns, for one
  * kernel kind, the number of timed launches, their summed device time (ms)
- * and their summed algorithmic bytes (compress sweep: input values of its
- * targets + the compacted streams it produced; retrieve sweep: selected
- * stream bytes + output values; range: input bytes). */
+ * and their summed algorithmic bytes (compress level: input values of its
+ * targets + the compacted streams it produced; retrieve level: selected
+ * stream bytes + its output values; range: input bytes). */
 int ipc_profile_read(int kind, uint64_t* launches, double* total_ms, double* alg_bytes);
 /* ipc_profile_reset -- clears the accumulated figures. */
 int ipc_profile_reset(void);

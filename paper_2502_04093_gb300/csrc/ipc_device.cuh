@@ -1,0 +1,97 @@
+// Device helpers shared by the sm_103a kernels of libipcomp.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ipc_internal.h"
+
+namespace ipc {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// Element-type arithmetic (round-to-nearest, no contraction).
+// ---------------------------------------------------------------------------
+template <class T> struct FP;
+template <> struct FP<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fabs_(float a) { return fabsf(a); }
+  // Round-to-nearest-even of |t| <= 2^21 by adding 1.5*2^23: the sum lies in
+  // [2^23, 2^24) where the spacing is 1, so the addition itself rounds. The
+  // integer is the distance of the bit patterns; the sign of a zero result
+  // follows t (as nearbyint does).
+  static __device__ __forceinline__ float rint_(float t, int32_t* qi) {
+    const float magic = 12582912.0f;
+    float y = __fadd_rn(t, magic);
+    *qi = __float_as_int(y) - 0x4B400000;
+    return copysignf(__fsub_rn(y, magic), t);
+  }
+  static __device__ __forceinline__ float from_code(int64_t q) {
+    return __int2float_rn((int)q);
+  }
+};
+template <> struct FP<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fabs_(double a) { return fabs(a); }
+  static __device__ __forceinline__ double rint_(double t, int32_t* qi) {
+    const double magic = 6755399441055744.0;  // 1.5 * 2^52
+    double y = __dadd_rn(t, magic);
+    *qi = (int32_t)(__double_as_longlong(y) - 0x4338000000000000LL);
+    return copysign(__dsub_rn(y, magic), t);
+  }
+  static __device__ __forceinline__ double from_code(int64_t q) { return __ll2double_rn(q); }
+};
+
+__device__ __forceinline__ uint32_t negabinary(int32_t q) {
+  return ((uint32_t)q + 0xAAAAAAAAu) ^ 0xAAAAAAAAu;
+}
+__device__ __forceinline__ int64_t negabinary_inv(uint32_t n) {
+  return (int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu;
+}
+// 2-prefix predictive XOR (Sec. 4.4.1): e = n ^ n>>1 ^ n>>2.
+__device__ __forceinline__ uint32_t xor_encode(uint32_t n) { return n ^ (n >> 1) ^ (n >> 2); }
+// Inverse: n = e * (1 + x + x^2)^-1 over GF(2) with x the right shift.
+// (1 + x + x^2)^-1 = (1 + x) / (1 + x^3): a prefix XOR at stride 3 (four
+// doubling steps reach shifts >= 32) followed by one XOR with the shift by 1.
+__device__ __forceinline__ uint32_t xor_decode(uint32_t e) {
+  uint32_t g = e;
+  g ^= g >> 3;
+  g ^= g >> 6;
+  g ^= g >> 12;
+  g ^= g >> 24;
+  return g ^ (g >> 1);
+}
+
+// In-register transpose of a 32x32 bit matrix (row i = a[i], column k = bit
+// k): afterwards bit i of a[k] is the former bit k of a[i]. Five rounds of
+// block swaps (16, 8, 4, 2, 1).
+template <int J, uint32_t M>
+__device__ __forceinline__ void tround(uint32_t (&a)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    if ((i & J) == 0) {
+      uint32_t t = ((a[i] >> J) ^ a[i + J]) & M;
+      a[i + J] ^= t;
+      a[i] ^= t << J;
+    }
+  }
+}
+__device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+  tround<16, 0x0000FFFFu>(a);
+  tround<8, 0x00FF00FFu>(a);
+  tround<4, 0x0F0F0F0Fu>(a);
+  tround<2, 0x33333333u>(a);
+  tround<1, 0x55555555u>(a);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace dev
+}  // namespace ipc

@@ -123,13 +123,13 @@ const uint64_t kSaturate = 1ull << 62;
 // of s, coordinates before d multiples of s, after d multiples of 2s.
 // ---------------------------------------------------------------------------
 namespace ipc {
-bool build_geo(int ndim, const int64_t* dims, Geo* g) {
+bool build_geo(int ndim, const int64_t* dims, int dtype, Geo* g) {
   if (ndim < 1 || ndim > 3 || !dims) return false;
   g->ndim = ndim;
   g->N[0] = g->N[1] = g->N[2] = 1;
   uint64_t n = 1;
   for (int e = 0; e < ndim; ++e) {
-    if (dims[e] < 1 || dims[e] > (int64_t(1) << 40)) return false;
+    if (dims[e] < 1 || dims[e] > (int64_t(1) << 31) - 1) return false;
     g->N[3 - ndim + e] = dims[e];
     n *= (uint64_t)dims[e];
     if (n > (uint64_t(1) << 42)) return false;
@@ -140,6 +140,8 @@ bool build_geo(int ndim, const int64_t* dims, Geo* g) {
   while ((int64_t(1) << K) < mx) ++K;
   g->K = K;
   g->stages.clear();
+  for (int d = 0; d < 3; ++d) g->level_stage[d].assign(K, -1);
+  const uint32_t BR = (uint32_t)level_rows(dtype), CWD = (uint32_t)(kLevelCols / 64);
   for (int l = K; l >= 1; --l) {
     const int64_t s = int64_t(1) << (l - 1);
     for (int d = 0; d < 3; ++d) {
@@ -158,30 +160,31 @@ bool build_geo(int ndim, const int64_t* dims, Geo* g) {
       sg.ncodes = sg.rows * (uint64_t)sg.m[2];
       sg.wr = ((uint64_t)sg.m[2] + 31) / 32;
       sg.words = sg.rows * sg.wr;
-      sg.ntiles = (sg.words + kTileWords - 1) / kTileWords;
+      // segments = the words of one level-kernel CTA (see ipc_level.cu)
+      sg.RB = d == 2 ? BR : BR / 2;
+      sg.CW = (uint32_t)std::min<uint64_t>(CWD, sg.wr);
+      sg.nrb = ((uint64_t)sg.m[1] + sg.RB - 1) / sg.RB;
+      sg.nct = (sg.wr + sg.CW - 1) / sg.CW;
+      sg.nseg = (uint64_t)sg.m[0] * sg.nrb * sg.nct;
+      sg.bw = ((uint64_t)sg.RB * sg.CW + 31) / 32;
+      g->level_stage[d][l - 1] = (int)g->stages.size();
       g->stages.push_back(sg);
     }
   }
   return true;
 }
 
-StageArgs stage_args(const Geo& g, const StageGeo& sg, int cubic) {
+StageArgs stage_args(const StageGeo& sg) {
   StageArgs a{};
-  for (int e = 0; e < 3; ++e) {
-    a.N[e] = g.N[e];
-    a.start[e] = sg.start[e];
-    a.step[e] = sg.step[e];
-    a.m[e] = sg.m[e];
-  }
-  a.stride[2] = 1;
-  a.stride[1] = g.N[2];
-  a.stride[0] = g.N[1] * g.N[2];
-  a.s = int64_t(1) << (sg.level - 1);
   a.W = sg.words;
   a.wr = sg.wr;
-  a.ntiles = sg.ntiles;
-  a.d = sg.dim3;
-  a.cubic = cubic;
+  a.m1 = (uint64_t)sg.m[1];
+  a.RB = sg.RB;
+  a.CW = sg.CW;
+  a.nrb = sg.nrb;
+  a.nct = sg.nct;
+  a.bw = sg.bw;
+  a.nbm = (sg.words + 31) / 32;
   return a;
 }
 }  // namespace ipc
@@ -355,20 +358,21 @@ void keep_pool(int dev) {
 }
 
 // Segmented layout of the device streams (independent of the data): per
-// stage, plane k at cap_base + k * ntiles * 256 and bm_base + k * ntiles * 8.
+// stage and plane, nseg segments of RB*CW capacity words and bw bitmap words.
 int plan_field(ipc_field* f, cudaStream_t st) {
   const Geo& g = f->g;
   f->desc.assign(g.stages.size(), StageDescs{});
   uint64_t cw = 0, bw = 0;
   for (size_t t = 0; t < g.stages.size(); ++t) {
     const StageGeo& sg = g.stages[t];
+    const uint64_t pc = sg.nseg * (uint64_t)sg.RB * sg.CW, pb = sg.nseg * sg.bw;
     for (int k = 0; k < 32; ++k) {
       PlaneDesc& pd = f->desc[t].p[k];
-      pd.cap_off = cw + (uint64_t)k * sg.ntiles * kTileWords;
-      pd.bm_off = bw + (uint64_t)k * sg.ntiles * kTileBitmapWords;
+      pd.cap_off = cw + (uint64_t)k * pc;
+      pd.bm_off = bw + (uint64_t)k * pb;
     }
-    cw += 32 * sg.ntiles * kTileWords;
-    bw += 32 * sg.ntiles * kTileBitmapWords;
+    cw += 32 * pc;
+    bw += 32 * pb;
   }
   f->cap_words = cw;
   f->bm_words = bw;
@@ -378,6 +382,55 @@ int plan_field(ipc_field* f, cudaStream_t st) {
     return rc;
   }
   return IPC_OK;
+}
+
+// Kernel arguments of level l (1..K).
+LevelArgs level_args(const ipc_field* f, int l) {
+  const Geo& g = f->g;
+  LevelArgs L{};
+  const int64_t s = int64_t(1) << (l - 1);
+  for (int e = 0; e < 3; ++e) {
+    L.N[e] = g.N[e];
+    L.M[e] = (g.N[e] - 1) / s + 1;
+  }
+  L.stride[2] = 1;
+  L.stride[1] = g.N[2];
+  L.stride[0] = g.N[1] * g.N[2];
+  L.s = s;
+  L.cubic = f->interp == IPC_CUBIC;
+  const int BR = level_rows(f->dtype);
+  L.nrb = ((uint64_t)L.M[1] + BR - 1) / BR;
+  L.nct = ((uint64_t)L.M[2] + kLevelCols - 1) / kLevelCols;
+  for (int d = 0; d < 3; ++d) {
+    LevelStage& S = L.st[d];
+    const int t = g.level_stage[d][l - 1];
+    S.present = t >= 0;
+    S.t = t;
+    if (t < 0) continue;
+    const StageGeo& sg = g.stages[t];
+    S.RB = sg.RB;
+    S.CW = sg.CW;
+    S.nrb = sg.nrb;
+    S.nct = sg.nct;
+    S.bw = sg.bw;
+    S.m1 = (uint64_t)sg.m[1];
+    S.m2 = (uint64_t)sg.m[2];
+    S.wr = sg.wr;
+    if (!f->out_off.empty()) {
+      S.out_begin = f->out_off[t];
+      S.out_end = f->out_off[t + 1];
+    }
+  }
+  return L;
+}
+
+LevelDescs level_descs(const ipc_field* f, int l) {
+  LevelDescs D{};
+  for (int d = 0; d < 3; ++d) {
+    const int t = f->g.level_stage[d][l - 1];
+    if (t >= 0) D.s[d] = f->desc[t];
+  }
+  return D;
 }
 
 // Container layout from the per-plane nnz: stream sizes and modes, packed
@@ -519,7 +572,7 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
   else quant_args<double>(eb, f->xmaxabs, qbuf);
   if ((rc = plan_field(f, st))) return rc;
 
-  std::vector<long> sweep_prof(S, -1);
+  std::vector<long> level_prof(g.K, -1);
   unsigned long long nout = 0;
   std::vector<uint32_t> stat(2 * std::max<size_t>(S, 1)), nnz(32 * std::max<size_t>(S, 1));
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -529,14 +582,18 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
     SweepOut so{f->d_cap, f->d_bm, ws.nnz, ws.okey, ws.oval, ws.small + 4, ws.ocap, ws.stat};
     // the anchor is stored exactly: xh[0] = x[0]
     CU(cudaMemcpyAsync(ws.xh, d_in, esz, cudaMemcpyDeviceToDevice, st));
-    for (size_t t = 0; t < S; ++t) {
-      const StageGeo& sg = g.stages[t];
-      StageArgs a = stage_args(g, sg, f->interp == IPC_CUBIC);
-      const int write_xh = t + 1 < S;  // the last sweep's values are never read
-      const long ph = prof_begin(IPC_KERNEL_COMPRESS_SWEEP, st);
-      CU(launch_compress_stage(f->dtype, a, d_in, ws.xh, write_xh, qbuf, (int)t, so, f->desc[t], st));
-      prof_end(ph, st, (double)(sg.ncodes * esz));
-      sweep_prof[t] = ph;
+    for (int l = g.K; l >= 1; --l) {
+      LevelArgs L = level_args(f, l);
+      L.vec = 1;  // the workspace is allocated aligned
+      const LevelDescs D = level_descs(f, l);
+      const long ph = prof_begin(IPC_KERNEL_COMPRESS_LEVEL, st);
+      // the finest level's values are never read again
+      CU(launch_level_compress(f->dtype, L, d_in, ws.xh, l > 1, qbuf, so, D, st));
+      uint64_t nc = 0;
+      for (int d = 0; d < 3; ++d)
+        if (g.level_stage[d][l - 1] >= 0) nc += g.stages[g.level_stage[d][l - 1]].ncodes;
+      prof_end(ph, st, (double)(nc * esz));
+      level_prof[l - 1] = ph;
     }
     CU(cudaMemcpyAsync(&nout, ws.small + 4, 8, cudaMemcpyDeviceToHost, st));
     if (S) {
@@ -582,11 +639,16 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
     }
   }
   if ((rc = finish_field(f, st))) return rc;
-  // the algorithmic output of each sweep: its compacted streams
-  for (size_t t = 0; t < S; ++t) {
-    double sb = 0;
-    for (int k = 0; k < 32; ++k) sb += (double)f->st[t].size[k];
-    prof_set_bytes(sweep_prof[t], (double)(g.stages[t].ncodes * esz) + sb);
+  // algorithmic bytes of each level launch: its input values + its streams
+  for (int l = 1; l <= g.K; ++l) {
+    double by = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int t = g.level_stage[d][l - 1];
+      if (t < 0) continue;
+      by += (double)(g.stages[t].ncodes * esz);
+      for (int k = 0; k < 32; ++k) by += (double)f->st[t].size[k];
+    }
+    prof_set_bytes(level_prof[l - 1], by);
   }
   return IPC_OK;
 }
@@ -848,8 +910,8 @@ int select(const ipc_field* f, ipc_target tg, const std::vector<int>* upper, std
   return fail(IPC_EINVAL, "unknown target kind");
 }
 
-// Algorithm 1 on the device: anchor, then one reconstruction launch per
-// sweep (coarse to fine), each followed by its outlier scatter.
+// Algorithm 1 on the device: the anchor, then one fused launch per level
+// (coarse to fine); outliers are applied inside the level kernels.
 int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream_t st) {
   const Geo& g = f->g;
   {
@@ -859,22 +921,22 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
   }
   const double twoeb = bin_width(f);
   const size_t esz = f->dtype == 0 ? 4 : 8;
-  for (size_t t = 0; t < g.stages.size(); ++t) {
-    const StageGeo& sg = g.stages[t];
-    StageArgs a = stage_args(g, sg, f->interp == IPC_CUBIC);
-    double sb = 0;
-    for (int k = b[sg.level - 1]; k < 32; ++k) sb += (double)f->st[t].size[k];
-    const long ph = prof_begin(IPC_KERNEL_RETRIEVE_SWEEP, st);
-    CU(launch_retrieve_stage(f->dtype, a, d_out, twoeb, f->desc[t], b[sg.level - 1], f->d_cap,
-                             f->d_bm, st));
-    prof_end(ph, st, (double)(sg.ncodes * esz) + sb);
-    const uint64_t no = f->out_off[t + 1] - f->out_off[t];
-    if (no) {
-      const long ph2 = prof_begin(IPC_KERNEL_OUTLIERS, st);
-      CU(launch_outlier_scatter(f->dtype, a, d_out, f->d_oidx + f->out_off[t],
-                                f->d_oval + f->out_off[t], no, st));
-      prof_end(ph2, st, (double)(no * (16 + esz)));
+  for (int l = g.K; l >= 1; --l) {
+    LevelArgs L = level_args(f, l);
+    L.vec = ((uintptr_t)d_out % (2 * esz)) == 0;
+    const LevelDescs D = level_descs(f, l);
+    double by = 0;
+    uint64_t nc = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int t = g.level_stage[d][l - 1];
+      if (t < 0) continue;
+      nc += g.stages[t].ncodes;
+      for (int k = b[l - 1]; k < 32; ++k) by += (double)f->st[t].size[k];
     }
+    const long ph = prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st);
+    CU(launch_level_retrieve(f->dtype, L, d_out, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
+                             f->d_oval, D, st));
+    prof_end(ph, st, by + (double)(nc * esz));
   }
   return IPC_OK;
 }
@@ -911,7 +973,7 @@ int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims, int
   ipc_field* f = new (std::nothrow) ipc_field();
   if (!f) return fail(IPC_ENOMEM, "host allocation");
   f->tag = kFieldTag;
-  if (!build_geo(ndim, dims, &f->g)) {
+  if (!build_geo(ndim, dims, dtype, &f->g)) {
     delete f;
     return fail(IPC_EINVAL, "shape");
   }
@@ -1038,31 +1100,27 @@ int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len) {
   if (f->stream_bytes) {
     cudaStream_t st = nullptr;
     CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    uint32_t *blob = nullptr, *rank = nullptr;
-    unsigned int* bad = nullptr;
-    uint64_t rk = 0;
-    for (auto& sg : g.stages) rk = std::max<uint64_t>(rk, 32 * sg.ntiles);
+    uint32_t *blob = nullptr, *tmp = nullptr;
+    uint64_t tw = 0;
+    for (auto& sg : g.stages) tw = std::max<uint64_t>(tw, 2 * 32 * ((sg.words + 31) / 32));
     int rc = IPC_OK;
-    if ((rc = dalloc((void**)&blob, f->stream_bytes, st)) ||
-        (rc = dalloc((void**)&rank, rk * 4, st)) || (rc = dalloc((void**)&bad, 4, st))) {
+    if ((rc = dalloc((void**)&blob, f->stream_bytes, st)) || (rc = dalloc((void**)&tmp, tw * 4, st))) {
       dfree(blob);
-      dfree(rank);
       cudaStreamDestroy(st);
       return rc;
     }
-    cudaError_t e = cudaMemsetAsync(bad, 0, 4, st);
+    cudaError_t e = cudaSuccess;
     for (size_t t = 0; t < g.stages.size() && e == cudaSuccess; ++t) {
-      StageArgs a = stage_args(g, g.stages[t], 0);
-      e = launch_seg_rank(a, f->desc[t], 0, f->d_bm, rank, bad, st);
-      if (e == cudaSuccess) e = launch_pack(a, f->desc[t], f->d_cap, f->d_bm, rank, blob, st);
+      const long ph = prof_begin(IPC_KERNEL_PACK, st);
+      e = launch_pack(stage_args(g.stages[t]), f->desc[t], f->d_cap, f->d_bm, tmp, blob, st);
+      prof_end(ph, st, 0);
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync((uint8_t*)host_buf + h.size(), blob, f->stream_bytes,
                           cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(blob, st);
-    cudaFreeAsync(rank, st);
-    cudaFreeAsync(bad, st);
+    cudaFreeAsync(tmp, st);
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (e != cudaSuccess) return cuda_fail(e, "export");
@@ -1132,7 +1190,7 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   if (!ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 1 || f->bound < 0 ||
       f->bound > 1 || f->eb_mode < 0 || f->eb_mode > 1 || !(f->eb > 0) || !std::isfinite(f->eb))
     return drop(IPC_ECORRUPT, "bad header fields");
-  if (ndim < 1 || ndim > 3 || !build_geo(ndim, dims, &f->g) || f->g.K != K ||
+  if (ndim < 1 || ndim > 3 || !build_geo(ndim, dims, f->dtype, &f->g) || f->g.K != K ||
       f->g.stages.size() != S)
     return drop(IPC_ECORRUPT, "bad geometry");
   f->st.assign(S, StageTab{});
@@ -1186,42 +1244,37 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   if (rc) return drop(rc, "allocation");
   if (f->mandatory != mand) return drop(IPC_ECORRUPT, "table size mismatch");
   // streams -> device, then unpack into the segmented layout
-  uint32_t *blob = nullptr, *rank = nullptr;
-  unsigned int* flags = nullptr;  // [0] bad, [1..] 32 counters per stage
-  uint64_t rk = 0;
-  for (auto& sg : f->g.stages) rk = std::max<uint64_t>(rk, 32 * sg.ntiles);
-  if ((rc = dalloc((void**)&blob, f->stream_bytes, st)) || (rc = dalloc((void**)&rank, rk * 4, st)) ||
-      (rc = dalloc((void**)&flags, (1 + 32 * (uint64_t)S) * 4, st))) {
+  uint32_t *blob = nullptr, *tmp = nullptr;
+  unsigned int* flags = nullptr;  // [0] corruption flag
+  uint64_t tw = 0;
+  for (auto& sg : f->g.stages) tw = std::max<uint64_t>(tw, 2 * 32 * ((sg.words + 31) / 32));
+  if ((rc = dalloc((void**)&blob, f->stream_bytes, st)) || (rc = dalloc((void**)&tmp, tw * 4, st)) ||
+      (rc = dalloc((void**)&flags, 4, st))) {
     dfree(blob);
-    dfree(rank);
+    dfree(tmp);
     return drop(rc, "allocation");
   }
   cudaError_t e = cudaSuccess;
   if (f->stream_bytes)
     e = cudaMemcpyAsync(blob, p + mand, f->stream_bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, (1 + 32 * (uint64_t)S) * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 4, st);
   for (uint32_t t = 0; t < S && e == cudaSuccess; ++t) {
-    StageArgs a = stage_args(f->g, f->g.stages[t], 0);
-    e = launch_seg_rank(a, f->desc[t], 1, blob, rank, flags, st);
-    if (e == cudaSuccess)
-      e = launch_unpack(a, f->desc[t], blob, rank, f->d_cap, f->d_bm, flags, flags + 1 + 32 * t, st);
+    const long ph = prof_begin(IPC_KERNEL_UNPACK, st);
+    e = launch_unpack(stage_args(f->g.stages[t]), f->desc[t], f->g.stages[t].nseg, blob, tmp,
+                      f->d_cap, f->d_bm, flags, st);
+    prof_end(ph, st, 0);
   }
-  std::vector<unsigned int> hf(1 + 32 * (size_t)S);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hf.data(), flags, hf.size() * 4, cudaMemcpyDeviceToHost, st);
+  unsigned int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, flags, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFreeAsync(blob, st);
-  cudaFreeAsync(rank, st);
+  cudaFreeAsync(tmp, st);
   cudaFreeAsync(flags, st);
   if (e != cudaSuccess) {
     cuda_fail(e, "import");
     return drop(IPC_ECUDA, "");
   }
-  if (hf[0]) return drop(IPC_ECORRUPT, "bitmap population differs from the stream's nnz");
-  for (uint32_t t = 0; t < S; ++t)
-    for (int k = 0; k < 32; ++k)
-      if (f->desc[t].p[k].mode == 2 && hf[1 + 32 * t + k] != f->desc[t].p[k].nnz)
-        return drop(IPC_ECORRUPT, "dense stream population differs from its nnz");
+  if (hbad) return drop(IPC_ECORRUPT, "stream contents disagree with their nnz / bitmap");
   *out = f;
   return IPC_OK;
 }

@@ -8,19 +8,27 @@
 
 namespace ipc {
 
-// Words of a compaction tile: one CTA of the sweep kernels owns 256
-// consecutive plane words (8 warps x 32 words, 8192 codes) of a stage.
-constexpr int kTileWords = 256;
-constexpr int kTileBitmapWords = kTileWords / 32;
+// Work unit of the fused level kernels: one plane of the level lattice,
+// kLevelRows rows and kLevelCols lattice columns (a multiple of 64, so a
+// tile's codes of one column parity fill whole 32-code words).
+constexpr int kLevelRowsF32 = 16;
+constexpr int kLevelRowsF64 = 8;
+constexpr int kLevelCols = 512;
 
 // One non-empty (level, dimension) sweep over the padded 3-D index space.
 // Targets are the lattice start[e] + c_e * step[e], c_e < m[e]; codes are in
 // row-major lattice order, a row being a line along the last dimension.
+// Device storage is split into segments: the words one level-kernel CTA
+// owns, RB rows x CW words of the stage's word grid (rows x wr), numbered
+// (plane, row block, column tile).
 struct StageGeo {
   int level;          // 1..K
   int dim3;           // sweep dimension (padded index 0..2)
   int64_t start[3], step[3], m[3];
-  uint64_t ncodes, rows, wr, words, ntiles;
+  uint64_t ncodes, rows, wr, words;
+  uint32_t RB, CW;    // segment: rows x words
+  uint64_t nrb, nct;  // row blocks per stage plane, column tiles per row
+  uint64_t nseg, bw;  // segments; bitmap words per segment
 };
 
 struct Geo {
@@ -29,20 +37,35 @@ struct Geo {
   int K;
   uint64_t n;
   std::vector<StageGeo> stages;
+  std::vector<int> level_stage[3];  // per level (index l-1) the stage of sweep d, or -1
 };
-bool build_geo(int ndim, const int64_t* dims, Geo* g);
+bool build_geo(int ndim, const int64_t* dims, int dtype, Geo* g);
 
-// Kernel-side view of a stage (passed by value).
-struct StageArgs {
-  int64_t N[3];
-  int64_t stride[3];
-  int64_t start[3], step[3], m[3];
-  int64_t s;       // level stride 2^(l-1)
-  uint64_t W, wr, ntiles;
-  int d;           // sweep dimension
-  int cubic;
+// Kernel-side view of one sweep of a level (passed by value).
+struct LevelStage {
+  int present;
+  int t;              // stage index
+  uint32_t RB, CW;
+  uint64_t nrb, nct, bw;
+  uint64_t m1, m2, wr;  // stage lattice: rows per plane, codes per row, words per row
+  uint64_t out_begin, out_end;  // outlier range of the stage (reconstruction)
 };
-StageArgs stage_args(const Geo& g, const StageGeo& sg, int cubic);
+struct LevelArgs {
+  int64_t N[3], stride[3], M[3];  // extents, element strides, lattice extents
+  int64_t s;
+  int cubic;
+  int vec;            // output base aligned to two elements (paired stores allowed)
+  uint64_t nrb, nct;  // CTA row blocks per plane, column tiles
+  LevelStage st[3];
+};
+
+// Kernel-side view of a stage's word grid and segments (pack / unpack).
+struct StageArgs {
+  uint64_t W, wr, m1;   // words, words per row, rows per stage plane
+  uint32_t RB, CW;
+  uint64_t nrb, nct, bw, nbm;  // nbm = packed bitmap words = ceil(W / 32)
+};
+StageArgs stage_args(const StageGeo& sg);
 
 template <class T>
 struct QuantArgs {
@@ -77,6 +100,9 @@ struct PlaneDesc {
 struct StageDescs {
   PlaneDesc p[32];
 };
+struct LevelDescs {
+  StageDescs s[3];  // by sweep dimension
+};
 
 // Stream mode and byte size from (nnz, W) (format definition).
 inline uint32_t stream_mode(uint64_t nnz, uint64_t W) {
@@ -91,32 +117,25 @@ inline uint64_t stream_bytes(uint64_t nnz, uint64_t W) {
   return 4 + 4 * W;
 }
 
-// ---- kernel launchers (ipc_kernels.cu) ------------------------------------
+// ---- kernel launchers -------------------------------------------------------
 cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long long* acc,
                          cudaStream_t st);
-cudaError_t launch_compress_stage(int dtype, const StageArgs& a, const void* x, void* xh,
-                                  int write_xh, const void* quant, int stage, const SweepOut& o,
-                                  const StageDescs& d, cudaStream_t st);
-cudaError_t launch_retrieve_stage(int dtype, const StageArgs& a, void* out, double twoeb,
-                                  const StageDescs& d, int b, const uint32_t* cap,
-                                  const uint32_t* bm, cudaStream_t st);
-cudaError_t launch_outlier_scatter(int dtype, const StageArgs& a, void* out,
-                                   const uint64_t* idx, const double* val, uint64_t n,
-                                   cudaStream_t st);
 cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st);
-// Exclusive prefix, per plane, of the population of each 256-word segment of
-// a bitmap (bm = segmented bitmaps when packed == 0, the packed blob's sparse
-// bitmaps when packed != 0); flags bitmaps whose population differs from nnz.
-cudaError_t launch_seg_rank(const StageArgs& a, const StageDescs& d, int packed,
-                            const uint32_t* bm, uint32_t* rank, unsigned int* bad,
-                            cudaStream_t st);
-// Segmented -> packed container streams (export) and back (import).
+// Fused level kernels (ipc_level.cu).
+cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, void* xh,
+                                  int write_xh, const void* quant, const SweepOut& o,
+                                  const LevelDescs& d, cudaStream_t st);
+cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
+                                  const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
+                                  const double* oval, const LevelDescs& d, cudaStream_t st);
+int level_rows(int dtype);
+// Segmented <-> packed container streams of one stage (export / import).
+// tmp: 2 * 32 * nbm words of scratch; flags[0] = corruption flag,
+// flags[1 + k] = nonzero words found in plane k (import).
 cudaError_t launch_pack(const StageArgs& a, const StageDescs& d, const uint32_t* cap,
-                        const uint32_t* bm, const uint32_t* rank, uint32_t* blob,
-                        cudaStream_t st);
-// chk: 32 counters per stage (nonzero words of dense streams); bad: flag.
-cudaError_t launch_unpack(const StageArgs& a, const StageDescs& d, const uint32_t* blob,
-                          const uint32_t* rank, uint32_t* cap, uint32_t* bm, unsigned int* bad,
-                          unsigned int* chk, cudaStream_t st);
+                        const uint32_t* bm, uint32_t* tmp, uint32_t* blob, cudaStream_t st);
+cudaError_t launch_unpack(const StageArgs& a, const StageDescs& d, uint64_t nseg,
+                          const uint32_t* blob, uint32_t* tmp, uint32_t* cap, uint32_t* bm,
+                          unsigned int* flags, cudaStream_t st);
 
 }  // namespace ipc

@@ -180,8 +180,7 @@ def ipc_field_info(field) -> dict:
                 S=S.value, eb=eb.value, xmin=mn.value, xmax=mx.value)
 
 
-IPC_KERNEL_NAMES = ["range", "compress_sweep", "scan", "pack", "retrieve_sweep", "outliers",
-                    "anchor", "build_rank"]
+IPC_KERNEL_NAMES = ["range", "compress_level", "retrieve_level", "anchor", "pack", "unpack"]
 
 
 def ipc_profile_enable(on: bool) -> None:
