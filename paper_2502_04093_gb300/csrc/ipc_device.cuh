@@ -27,8 +27,14 @@ template <> struct FP<float> {
     *qi = __float_as_int(y) - 0x4B400000;
     return copysignf(__fsub_rn(y, magic), t);
   }
+  // Exact int -> float for |q| < 2^22 by the same magic-number trick (two
+  // integer/float ops); larger codes (possible only after truncation) take
+  // the conversion instruction. Both give the exact value (|q| < 2^24).
   static __device__ __forceinline__ float from_code(int64_t q) {
-    return __int2float_rn((int)q);
+    const int qi = (int)q;
+    if (qi >= -(1 << 22) && qi < (1 << 22))
+      return __fsub_rn(__int_as_float(0x4B400000 + qi), 12582912.0f);
+    return __int2float_rn(qi);
   }
 };
 template <> struct FP<double> {
@@ -85,6 +91,26 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
   tround<4, 0x0F0F0F0Fu>(a);
   tround<2, 0x33333333u>(a);
   tround<1, 0x55555555u>(a);
+}
+
+// Predictive XOR on plane words (bit-sliced over 32 codes): e_k = n_k ^
+// n_{k+1} ^ n_{k+2}, missing prefix planes 0. Ascending k reads only planes
+// not yet rewritten.
+__device__ __forceinline__ void xor_encode_planes(uint32_t (&p)[32]) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t p1 = k + 1 < 32 ? p[k + 1] : 0u, p2 = k + 2 < 32 ? p[k + 2] : 0u;
+    p[k] ^= p1 ^ p2;
+  }
+}
+// Inverse, top-down: n_k = e_k ^ n_{k+1} ^ n_{k+2}; the planes below b were
+// not loaded and are set to zero.
+__device__ __forceinline__ void xor_decode_planes(uint32_t (&p)[32], int b) {
+#pragma unroll
+  for (int k = 31; k >= 0; --k) {
+    const uint32_t p1 = k + 1 < 32 ? p[k + 1] : 0u, p2 = k + 2 < 32 ? p[k + 2] : 0u;
+    p[k] = k >= b ? (p[k] ^ p1 ^ p2) : 0u;
+  }
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

@@ -137,11 +137,10 @@ __device__ __forceinline__ Loc locate(const StageArgs& a, uint64_t w) {
   l.li = (uint32_t)((rr % a.RB) * a.CW + j % a.CW);
   return l;
 }
-// Rank of a set bit among the segment's bits before it.
+// Slot of a nonzero word in its segment: the words of every 32-word group
+// are compacted at the group's own 32-word slot.
 __device__ __forceinline__ uint32_t seg_rank(const uint32_t* segbm, uint32_t li) {
-  uint32_t r = __popc(segbm[li >> 5] & ((1u << (li & 31)) - 1u));
-  for (uint32_t v = 0; v < (li >> 5); ++v) r += __popc(segbm[v]);
-  return r;
+  return (li & ~31u) + __popc(segbm[li >> 5] & ((1u << (li & 31)) - 1u));
 }
 
 // Export step 1: packed bitmap word q of every plane (gathered from the

@@ -20,10 +20,11 @@
 // operations), so no CTA waits for another.
 //
 // Stream storage: per stage, the CTA's own codes form one "segment"
-// (RB rows x CW words of the stage's word grid); every plane of a segment
-// keeps its zero-word bitmap and its nonzero words compacted at the
-// segment's slot. Retrieval decodes words of its own segments plus the
-// neighbouring segments' words that its halo targets need.
+// (RB rows x CW words of the stage's word grid). Within a segment, every
+// group of 32 words (one warp in phase 4) keeps, per plane, its zero-word
+// bitmap word and its nonzero words compacted at the group's 32-word slot.
+// Retrieval decodes words of its own segments plus the neighbouring
+// segments' words that its halo targets need.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -209,7 +210,6 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
   uint32_t* E2 = reinterpret_cast<uint32_t*>(VO + BR * G::HC);  // [BR][PITCH]
   uint32_t* E1 = E2 + BR * G::PITCH;                      // [BR/2][PITCH]
   uint32_t* E0 = E1 + (BR / 2) * G::PITCH;                // [BR/2][PITCH]
-  __shared__ uint32_t wcnt[32][8];
 
   const CtaPos c = cta_pos(L, BR, BC);
   const bool podd = (c.P & 1) != 0;
@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
   const int M0 = (int)L.M[0], M1 = (int)L.M[1], M2 = (int)L.M[2];
   uint32_t orN[3] = {0, 0, 0}, qmx[3] = {0, 0, 0};
 
-  for (int i = tid; i < 2 * BR * G::PITCH; i += 256) E2[i] = 0;  // E2, E1, E0
+  // codes outside the grid (edge tiles) must read as zero in phase 4
+  if (c.R1 - c.R0 < BR || c.C1 - c.C0 < BC)
+    for (int i = tid; i < 2 * BR * G::PITCH; i += 256) E2[i] = 0;  // E2, E1, E0
   __syncthreads();
 
   // Phase 1: even rows of VE.
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
         const uint32_t N = negabinary(q);
         orN[0] |= N;
         qmx[0] = max(qmx[0], (uint32_t)(q < 0 ? -q : q));
-        E0[((c1 - c.R0) >> 1) * G::PITCH + sw((c2 - c.C0) >> 1)] = xor_encode(N);
+        E0[((c1 - c.R0) >> 1) * G::PITCH + sw((c2 - c.C0) >> 1)] = N;
         if (outl)
           record_outlier(o, S0.t,
                          ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
       const uint32_t N = negabinary(q);
       orN[1] |= N;
       qmx[1] = max(qmx[1], (uint32_t)(q < 0 ? -q : q));
-      E1[jr * G::PITCH + sw((c2 - c.C0) >> 1)] = xor_encode(N);
+      E1[jr * G::PITCH + sw((c2 - c.C0) >> 1)] = N;
       if (outl)
         record_outlier(o, S1.t,
                        ((uint64_t)c.P * S1.m1 + (uint64_t)((c1 - 1) >> 1)) * S1.m2 +
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
     const uint32_t N = negabinary(q);
     orN[2] |= N;
     qmx[2] = max(qmx[2], (uint32_t)(q < 0 ? -q : q));
-    E2[lr * G::PITCH + sw(jo)] = xor_encode(N);
+    E2[lr * G::PITCH + sw(jo)] = N;
     if (outl)
       record_outlier(o, S2.t,
                      ((uint64_t)c.P * S2.m1 + (uint64_t)c1) * S2.m2 + (uint64_t)((c2 - 1) >> 1),
@@ -346,19 +348,15 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
     for (int i = 0; i < 32; ++i) pw[i] = mine ? Eb[lr * G::PITCH + lj * 33 + i] : 0u;
   }
   transpose32(pw);
+  xor_encode_planes(pw);
   const uint64_t pi = sidx == 0 ? (uint64_t)((c.P - 1) >> 1) : (uint64_t)c.P;
   const uint64_t g = active ? seg_id(S, pi, c.rb, c.ct) : 0;
   const uint32_t bwords = (uint32_t)((nwords + 31) / 32);
   const PlaneDesc* pds = D.s[sidx].p;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    const uint32_t mk = __ballot_sync(~0u, pw[k] != 0);
-    if (lane == k) {
-      const int wl = li >> 5;  // bitmap word of the segment
-      if (active && wl < (int)bwords) o.bm[pds[k].bm_off + g * S.bw + wl] = mk;
-      wcnt[k][wi] = __popc(mk);
-    }
-  }
+  const int wl = li >> 5;  // 32-word group of the segment (one warp)
+  const bool wact = active && wl < (int)bwords;
+  __shared__ uint32_t scnt[3][32];
+  if (tid < 96) scnt[tid >> 5][tid & 31] = 0;
 #pragma unroll
   for (int st = 0; st < 3; ++st) {
     const uint32_t a = __reduce_or_sync(~0u, orN[st]);
@@ -369,37 +367,34 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
     }
   }
   __syncthreads();
-  if (tid < 96) {  // prefix of the warps' counts per (stage, plane)
-    const int st = tid / 32, k = tid & 31;
-    const int w0 = st == 0 ? 0 : (st == 1 ? 4 : 6), nw = st == 0 ? 4 : 2;
-    const int sx = st == 0 ? 2 : (st == 1 ? 1 : 0);
-    uint32_t run = 0;
-    for (int v = w0; v < w0 + nw; ++v) {
-      const uint32_t cnt = wcnt[k][v];
-      wcnt[k][v] = run;
-      run += cnt;
+  const uint32_t lt = lanemask_lt();
+  const uint64_t capg = g * (uint64_t)nwords + (uint64_t)wl * 32;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t mk = __ballot_sync(~0u, pw[k] != 0);
+    if (wact) {
+      if (lane == k) {
+        o.bm[pds[k].bm_off + g * S.bw + wl] = mk;
+        if (mk) atomicAdd(&scnt[sidx][k], (uint32_t)__popc(mk));
+      }
+      if (pw[k]) o.cap[pds[k].cap_off + capg + __popc(mk & lt)] = pw[k];
     }
-    if (run) atomicAdd(o.nnz + 32 * L.st[sx].t + k, run);
   }
   __syncthreads();
-  if (active) {
-    const uint32_t lt = lanemask_lt();
-    const uint64_t capseg = g * (uint64_t)nwords;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const uint32_t mk = __ballot_sync(~0u, pw[k] != 0);
-      if (pw[k]) o.cap[pds[k].cap_off + capseg + wcnt[k][wi] + __popc(mk & lt)] = pw[k];
-    }
+  if (tid < 96) {
+    const uint32_t n = scnt[tid >> 5][tid & 31];
+    if (n) atomicAdd(o.nnz + 32 * L.st[tid >> 5].t + (tid & 31), n);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Reconstruction of one level (Algorithm 1).
-// The CTA touches at most 13 segments: stage 2 its own; stage 1 its own and
-// the left/right neighbours (halo columns); stage 0 the 3x3 neighbourhood
-// (halo rows and columns). Their bitmaps of every selected plane and the
-// prefix population of each bitmap word are staged in shared memory, so a
-// word's fetch issues its (up to 32) payload loads independently.
+// Words come from the CTA's own segments and, for halo targets, from the
+// neighbouring segments (stage 1: left/right; stage 0: the 3x3 block) --
+// at most 13 segments. Their group bitmap words of every selected plane are
+// staged in shared memory first; a word's plane value is then found from
+// its group's bitmap word alone (rank = population below its bit), so its
+// 32 plane loads are independent of each other.
 // ---------------------------------------------------------------------------
 constexpr int kSlots = 13;
 constexpr int kMaxBw = 4;  // bitmap words per segment (RB * CW <= 128)
@@ -418,8 +413,7 @@ __global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, 
   uint32_t* Q2 = reinterpret_cast<uint32_t*>(VO + BR * G::HC);  // [BR][PITCH]
   uint32_t* Q1 = Q2 + BR * G::PITCH;                            // [BR/2][QEP]
   uint32_t* Q0 = Q1 + (BR / 2) * G::QEP;                        // [BR/2+3][QEP]
-  __shared__ uint32_t SB[kSlots][32][kMaxBw];  // segment bitmaps
-  __shared__ uint32_t SP[kSlots][32][kMaxBw];  // exclusive prefix population
+  __shared__ uint32_t SB[kSlots][32][kMaxBw];  // group bitmaps of the segments
   __shared__ unsigned long long SG[kSlots];    // segment id (or ~0 if absent)
 
   const CtaPos c = cta_pos(L, BR, BC);
@@ -455,16 +449,6 @@ __global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, 
     SB[slot][k][v] = w;
   }
   __syncthreads();
-  for (int u = tid; u < kSlots * 32; u += 256) {
-    const int slot = u / 32, k = u & 31;
-    uint32_t run = 0;
-#pragma unroll
-    for (int v = 0; v < kMaxBw; ++v) {
-      SP[slot][k][v] = run;
-      run += __popc(SB[slot][k][v]);
-    }
-  }
-  __syncthreads();
 
   // Phase 0: decode the words the CTA needs.
   //  stage 2: own rows x own words
@@ -476,16 +460,14 @@ __global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, 
   const int hw = G::CWD + 2;
   const int nw1 = S1.present ? n1r * hw : 0;
   const int nw0 = (S0.present && podd) ? (BR / 2 + 3) * hw : 0;
-  const uint32_t keep = b >= 32 ? 0u : (0xFFFFFFFFu << b);
   for (int it = tid; it < nw2 + nw1 + nw0; it += 256) {
-    int sx, lr, slot;
+    int sx, lr;
     int64_t rr, j;
     if (it < nw2) {
       sx = 2;
       lr = it / (int)S2.CW;
       j = (int64_t)c.ct * S2.CW + (it - lr * (int)S2.CW);
       rr = c.R0 + lr;
-      slot = 0;
     } else if (it < nw2 + nw1) {
       const int u = it - nw2;
       sx = 1;
@@ -502,26 +484,27 @@ __global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, 
     const LevelStage& S = L.st[sx];
     if (rr < 0 || (uint64_t)rr >= S.m1 || j < 0 || (uint64_t)j >= S.wr) continue;
     const uint64_t rbw = (uint64_t)rr / S.RB, ctw = (uint64_t)j / S.CW;
+    int slot = 0;
     if (sx == 1) slot = 2 + (int)((int64_t)ctw - (int64_t)c.ct);
     else if (sx == 0)
       slot = 4 + ((int)((int64_t)rbw - (int64_t)c.rb) + 1) * 3 + (int)((int64_t)ctw - (int64_t)c.ct) + 1;
     const uint64_t g = SG[slot];
     const uint32_t li = (uint32_t)(((uint64_t)rr % S.RB) * S.CW + ((uint64_t)j % S.CW));
     const uint32_t wl = li >> 5, bmask = (1u << (li & 31)) - 1u, bit = 1u << (li & 31);
-    const uint64_t segw = g * (uint64_t)S.RB * S.CW;
+    const uint64_t capg = g * (uint64_t)S.RB * S.CW + (uint64_t)wl * 32;
     const PlaneDesc* pds = D.s[sx].p;
     uint32_t nv[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
       const uint32_t m = SB[slot][k][wl];  // zero for unselected / empty planes
-      nv[k] = (m & bit) ? __ldg(cap + pds[k].cap_off + segw + SP[slot][k][wl] + __popc(m & bmask))
-                        : 0u;
+      nv[k] = (m & bit) ? __ldg(cap + pds[k].cap_off + capg + __popc(m & bmask)) : 0u;
     }
+    xor_decode_planes(nv, b);
     transpose32(nv);
     if (sx == 2) {
+      const int lj = (int)(j - (int64_t)c.ct * S2.CW);
 #pragma unroll
-      for (int i = 0; i < 32; ++i)
-        Q2[lr * G::PITCH + (int)(j - (int64_t)c.ct * S2.CW) * 33 + i] = xor_decode(nv[i] & keep) & keep;
+      for (int i = 0; i < 32; ++i) Q2[lr * G::PITCH + lj * 33 + i] = nv[i];
     } else {
       // keep the codes of the halo window: code column C0/2 - 1 + e, e < VEC
       uint32_t* Qr = (sx == 1 ? Q1 : Q0) + lr * G::QEP;
@@ -529,7 +512,7 @@ __global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, 
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const int e = base + i;
-        if (e >= 0 && e < G::VEC) Qr[sw(e)] = xor_decode(nv[i] & keep) & keep;
+        if (e >= 0 && e < G::VEC) Qr[sw(e)] = nv[i];
       }
     }
   }
