@@ -103,7 +103,8 @@ int ipc_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream,
  * loaded) leaves the view and d_out unchanged and returns IPC_OK. */
 int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream);
 
-/* ipc_free -- frees a field or a view (NULL is accepted). */
+/* ipc_free -- frees a field, a view or a plan (NULL is accepted). No work
+ * that uses the handle may still be pending on any stream. */
 int ipc_free(void* handle);
 
 /* ipc_selection -- the view's per-level selection b_per_level[l-1] = planes
@@ -126,6 +127,49 @@ int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len);
  * IPC_ENOMEM, IPC_ECUDA. Synchronises `stream`. */
 int ipc_import(const void* host_buf, uint64_t len, void* stream,
                ipc_field** out);
+
+/* ---- batches (uneven fields in one launch per level) --------------------- */
+/* One field of a batched compression; the fields are the same as ipc_compress
+ * arguments. dims[] holds ndim extents. */
+typedef struct {
+  const void* d_in;
+  int dtype;
+  int ndim;
+  int64_t dims[3];
+  int eb_mode;
+  double eb;
+  int interp;
+  int bound;
+} ipc_batch_item;
+
+/* ipc_compress_batch -- compresses nfields fields of any shapes (Sec. 4.1-4.4
+ * applied to each). Per element type: one range launch per field and one
+ * host sync, then ONE kernel launch per interpolation level covering that
+ * level's work of every field, and one sync for the statistics. The output
+ * of field i is byte-identical to ipc_compress of that field alone.
+ * outs: host array of nfields handles. On error nothing is returned.
+ * Synchronises `stream`. */
+int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream,
+                       ipc_field** outs);
+
+/* ipc_retrieve_batch -- Sec. 5.2/5.3 selection per field, then Algorithm 1
+ * for all of them with one anchor launch and ONE launch per level over every
+ * field of an element type. d_outs[i] receives field i's reconstruction,
+ * bitwise equal to ipc_retrieve of that field alone. outs (may be NULL)
+ * receives one view per field. Asynchronous on `stream`. */
+int ipc_retrieve_batch(int n, ipc_field* const* fields, const ipc_target* targets,
+                       void* const* d_outs, void* stream, ipc_view** outs);
+
+/* A captured batched retrieval (CUDA graph) that can be replayed. */
+typedef struct ipc_plan ipc_plan;
+/* ipc_plan_retrieve_batch -- selects as ipc_retrieve_batch does (one element
+ * type per plan), uploads the launch tables and captures the launches into a
+ * CUDA graph. The fields and outputs must outlive the plan. Synchronises
+ * `stream` once (table upload). Free with ipc_free. */
+int ipc_plan_retrieve_batch(int n, ipc_field* const* fields, const ipc_target* targets,
+                            void* const* d_outs, void* stream, ipc_plan** out);
+/* ipc_plan_launch -- replays the plan's launches on `stream`. */
+int ipc_plan_launch(ipc_plan* p, void* stream);
 
 /* ---- introspection ------------------------------------------------------- */
 /* ipc_field_info -- dtype, ndim, dims (host array of 3), K (levels), S

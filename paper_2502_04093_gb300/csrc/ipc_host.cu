@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -112,7 +113,8 @@ void prof_drain() {  // caller holds g_prof_mu
 
 const uint32_t kMagic = 0x31435049u;  // "IPC1"
 const uint32_t kVersion = 1u;
-const uint32_t kFieldTag = 0x46435049u, kViewTag = 0x56435049u, kDeadTag = 0xDEADDEADu;
+const uint32_t kFieldTag = 0x46435049u, kViewTag = 0x56435049u, kPlanTag = 0x50435049u;
+const uint32_t kDeadTag = 0xDEADDEADu;
 const uint64_t kSaturate = 1ull << 62;
 
 }  // namespace
@@ -227,6 +229,15 @@ struct ipc_view {
   double bound;
 };
 
+struct ipc_plan {
+  uint32_t tag;
+  int device;
+  void* d_tab;              // entries + anchors (device)
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  uint64_t launches;        // kernels per replay
+};
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -239,7 +250,8 @@ struct Workspace {
   unsigned long long* okey = nullptr;
   double* oval = nullptr;
   uint64_t ocap = 0;
-  unsigned long long* small = nullptr;  // range acc[4] + outlier count
+  unsigned long long* small = nullptr;  // range acc[4] per field + outlier count
+  uint64_t small_words = 0;
   uint32_t* stat = nullptr;             // 2 per stage
   uint64_t stat_words = 0;
   uint32_t* nnz = nullptr;              // 32 per stage
@@ -510,100 +522,178 @@ void quant_args(double eb, double xmaxabs, void* out) {
   std::memcpy(out, &q, sizeof(q));
 }
 
-int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
+// Compression of a batch of fields of one element type (a single field is
+// a batch of one): one range launch per field and one host sync; then, for
+// every level from the coarsest, ONE launch covering that level's CTAs of
+// every field (entry table in device memory); one sync to read the
+// per-stage statistics, plane populations and outliers back.
+int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>& ins,
+                    cudaStream_t st) {
   int dev = 0;
   CU(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(IPC_EINVAL, "device index out of range");
   keep_pool(dev);
   Workspace& ws = g_ws[dev];
   std::lock_guard<std::mutex> lock(ws.mu);
-  const Geo& g = f->g;
-  const size_t esz = f->dtype == 0 ? 4 : 8;
-  const size_t S = g.stages.size();
+  const size_t nf = fs.size();
+  if (nf == 0) return IPC_OK;
+  if (nf > 65535) return fail(IPC_EINVAL, "too many fields in one batch");
+  const int dtype = fs[0]->dtype;
+  const size_t esz = dtype == 0 ? 4 : 8;
+  // per-field offsets into the shared scratch
+  std::vector<uint64_t> xo(nf + 1, 0), so(nf + 1, 0);
+  int Kmax = 0;
+  for (size_t i = 0; i < nf; ++i) {
+    xo[i + 1] = xo[i] + ((fs[i]->g.n * esz + 255) / 256) * 256;
+    so[i + 1] = so[i] + std::max<size_t>(fs[i]->g.stages.size(), 1);
+    Kmax = std::max(Kmax, fs[i]->g.K);
+  }
   int rc;
-  if ((rc = grow(&ws.xh, &ws.xh_bytes, g.n * esz, 1)) ||
-      (rc = grow(&ws.stat, &ws.stat_words, 2 * std::max<size_t>(S, 1), 4)) ||
-      (rc = grow(&ws.nnz, &ws.nnz_words, 32 * std::max<size_t>(S, 1), 4)))
-    return rc;
   uint64_t dummy = 0;
-  if (!ws.small && (rc = grow(&ws.small, &dummy, 8, 8))) return rc;
+  if ((rc = grow(&ws.xh, &ws.xh_bytes, xo[nf], 1)) ||
+      (rc = grow(&ws.stat, &ws.stat_words, 2 * so[nf], 4)) ||
+      (rc = grow(&ws.nnz, &ws.nnz_words, 32 * so[nf], 4)))
+    return rc;
+  if (ws.small_words < 5 * nf + 1) {
+    if (ws.small) cudaFree(ws.small);
+    ws.small = nullptr;
+    ws.small_words = 0;
+    if ((rc = grow(&ws.small, &dummy, 5 * nf + 1, 8))) return rc;
+    ws.small_words = 5 * nf + 1;
+  }
   if (ws.ocap == 0) {
     uint64_t oc = 0;
     if ((rc = grow(&ws.okey, &oc, 1 << 16, 8)) || (rc = grow(&ws.oval, &oc, 1 << 16, 8)))
       return rc;
     ws.ocap = 1 << 16;
   }
+  unsigned long long* acc = ws.small;         // 4 per field
+  unsigned long long* ocount = ws.small + 4 * nf;
 
   // a0: range over finite values, and the anchor
-  unsigned long long init[5] = {~0ULL, 0ULL, 0ULL, 0ULL, 0ULL};
-  CU(cudaMemcpyAsync(ws.small, init, sizeof(init), cudaMemcpyHostToDevice, st));
   {
+    std::vector<unsigned long long> init(4 * nf);
+    for (size_t i = 0; i < nf; ++i) {
+      init[4 * i] = ~0ULL;
+      init[4 * i + 1] = init[4 * i + 2] = init[4 * i + 3] = 0ULL;
+    }
+    CU(cudaMemcpyAsync(acc, init.data(), 32 * nf, cudaMemcpyHostToDevice, st));
+  }
+  for (size_t i = 0; i < nf; ++i) {
     const long ph = prof_begin(IPC_KERNEL_RANGE, st);
-    CU(launch_range(f->dtype, d_in, g.n, ws.small, st));
-    prof_end(ph, st, (double)(g.n * esz));
+    CU(launch_range(dtype, ins[i], fs[i]->g.n, acc + 4 * i, st));
+    prof_end(ph, st, (double)(fs[i]->g.n * esz));
   }
-  unsigned long long acc[5];
-  CU(cudaMemcpyAsync(acc, ws.small, sizeof(acc), cudaMemcpyDeviceToHost, st));
-  double x0 = 0;
-  float x0f = 0;
-  if (f->dtype == 0) CU(cudaMemcpyAsync(&x0f, d_in, 4, cudaMemcpyDeviceToHost, st));
-  else CU(cudaMemcpyAsync(&x0, d_in, 8, cudaMemcpyDeviceToHost, st));
+  std::vector<unsigned long long> hacc(4 * nf);
+  std::vector<double> x0(nf, 0.0);
+  std::vector<float> x0f(nf, 0.0f);
+  CU(cudaMemcpyAsync(hacc.data(), acc, 32 * nf, cudaMemcpyDeviceToHost, st));
+  for (size_t i = 0; i < nf; ++i) {
+    if (dtype == 0) CU(cudaMemcpyAsync(&x0f[i], ins[i], 4, cudaMemcpyDeviceToHost, st));
+    else CU(cudaMemcpyAsync(&x0[i], ins[i], 8, cudaMemcpyDeviceToHost, st));
+  }
   CU(cudaStreamSynchronize(st));
-  if (f->dtype == 0) x0 = x0f;
-  const bool any = acc[3] > 0;
-  f->xmin = any ? okey_to_double(acc[0]) : 0.0;
-  f->xmax = any ? okey_to_double(acc[1]) : 0.0;
-  {
+  std::vector<std::array<unsigned char, 32>> quant(nf);
+  for (size_t i = 0; i < nf; ++i) {
+    ipc_field* f = fs[i];
+    const unsigned long long* a4 = &hacc[4 * i];
+    const bool any = a4[3] > 0;
+    f->xmin = any ? okey_to_double(a4[0]) : 0.0;
+    f->xmax = any ? okey_to_double(a4[1]) : 0.0;
     double ma = 0;
-    std::memcpy(&ma, &acc[2], 8);
+    std::memcpy(&ma, &a4[2], 8);
     f->xmaxabs = any ? ma : 0.0;
-  }
-  double eb = f->eb_user;
-  if (f->eb_mode == IPC_EB_REL) {
-    if (!any) return fail(IPC_EINVAL, "relative error bound on a field without finite values");
-    const double r = f->xmax - f->xmin;
-    eb = r > 0 ? f->eb_user * r : f->eb_user;
-  }
-  if (!(eb > 0) || !std::isfinite(eb)) return fail(IPC_EINVAL, "error bound must be > 0 and finite");
-  f->eb = eb;
-  f->anchor = x0;
-  alignas(16) unsigned char qbuf[64];
-  if (f->dtype == 0) quant_args<float>(eb, f->xmaxabs, qbuf);
-  else quant_args<double>(eb, f->xmaxabs, qbuf);
-  if ((rc = plan_field(f, st))) return rc;
-
-  std::vector<long> level_prof(g.K, -1);
-  unsigned long long nout = 0;
-  std::vector<uint32_t> stat(2 * std::max<size_t>(S, 1)), nnz(32 * std::max<size_t>(S, 1));
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    CU(cudaMemsetAsync(ws.stat, 0, 2 * std::max<size_t>(S, 1) * 4, st));
-    CU(cudaMemsetAsync(ws.nnz, 0, 32 * std::max<size_t>(S, 1) * 4, st));
-    CU(cudaMemsetAsync(ws.small + 4, 0, 8, st));
-    SweepOut so{f->d_cap, f->d_bm, ws.nnz, ws.okey, ws.oval, ws.small + 4, ws.ocap, ws.stat};
+    double eb = f->eb_user;
+    if (f->eb_mode == IPC_EB_REL) {
+      if (!any) return fail(IPC_EINVAL, "relative error bound on a field without finite values");
+      const double r = f->xmax - f->xmin;
+      eb = r > 0 ? f->eb_user * r : f->eb_user;
+    }
+    if (!(eb > 0) || !std::isfinite(eb)) return fail(IPC_EINVAL, "error bound must be > 0 and finite");
+    f->eb = eb;
+    f->anchor = dtype == 0 ? (double)x0f[i] : x0[i];
+    quant[i].fill(0);
+    if (dtype == 0) quant_args<float>(eb, f->xmaxabs, quant[i].data());
+    else quant_args<double>(eb, f->xmaxabs, quant[i].data());
+    if ((rc = plan_field(f, st))) return rc;
     // the anchor is stored exactly: xh[0] = x[0]
-    CU(cudaMemcpyAsync(ws.xh, d_in, esz, cudaMemcpyDeviceToDevice, st));
-    for (int l = g.K; l >= 1; --l) {
-      LevelArgs L = level_args(f, l);
-      L.vec = 1;  // the workspace is allocated aligned
-      const LevelDescs D = level_descs(f, l);
+    CU(cudaMemcpyAsync((uint8_t*)ws.xh + xo[i], ins[i], esz, cudaMemcpyDeviceToDevice, st));
+  }
+
+  // entry table of every level (coarsest first)
+  std::vector<uint64_t> lev_off(Kmax + 1, 0), lev_ctas(Kmax + 1, 0);
+  std::vector<CompressEntry> ents;
+  std::vector<std::pair<size_t, int>> who;  // (field, level) of each entry
+  auto build_entries = [&]() {
+    ents.clear();
+    who.clear();
+    for (int l = Kmax; l >= 1; --l) {
+      lev_off[l] = ents.size();
+      uint64_t cta = 0;
+      for (size_t i = 0; i < nf; ++i) {
+        ipc_field* f = fs[i];
+        if (l > f->g.K) continue;
+        CompressEntry e{};
+        e.L = level_args(f, l);
+        e.L.vec = 1;  // the scratch is allocated aligned
+        e.D = level_descs(f, l);
+        e.o = SweepOut{f->d_cap, f->d_bm, ws.nnz + 32 * so[i], ws.okey, ws.oval, ocount,
+                       ws.ocap, ws.stat + 2 * so[i], (uint32_t)i};
+        e.x = ins[i];
+        e.xh = (uint8_t*)ws.xh + xo[i];
+        std::memcpy(e.quant, quant[i].data(), 32);
+        e.write_xh = l > 1;  // the finest level's values are never read again
+        e.cta_begin = cta;
+        cta += (uint64_t)e.L.M[0] * e.L.nrb * e.L.nct;
+        ents.push_back(e);
+        who.push_back({i, l});
+      }
+      lev_ctas[l] = cta;
+    }
+  };
+  build_entries();
+  CompressEntry* d_ents = nullptr;
+  if ((rc = dalloc((void**)&d_ents, ents.size() * sizeof(CompressEntry), st))) return rc;
+  struct EntGuard {
+    CompressEntry*& p;
+    cudaStream_t s;
+    ~EntGuard() { if (p) cudaFreeAsync(p, s); }
+  } eguard{d_ents, st};
+
+  std::vector<long> level_prof(Kmax + 1, -1);
+  unsigned long long nout = 0;
+  std::vector<uint32_t> stat(2 * so[nf]), nnz(32 * so[nf]);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    CU(cudaMemcpyAsync(d_ents, ents.data(), ents.size() * sizeof(CompressEntry),
+                       cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(ws.stat, 0, 2 * so[nf] * 4, st));
+    CU(cudaMemsetAsync(ws.nnz, 0, 32 * so[nf] * 4, st));
+    CU(cudaMemsetAsync(ocount, 0, 8, st));
+    for (int l = Kmax; l >= 1; --l) {
+      const int n_l = (int)((l > 1 ? lev_off[l - 1] : ents.size()) - lev_off[l]);
       const long ph = prof_begin(IPC_KERNEL_COMPRESS_LEVEL, st);
-      // the finest level's values are never read again
-      CU(launch_level_compress(f->dtype, L, d_in, ws.xh, l > 1, qbuf, so, D, st));
+      if (n_l == 1) {  // one field: arguments in the parameter space
+        const CompressEntry& e = ents[lev_off[l]];
+        CU(launch_level_compress(dtype, e.L, e.x, e.xh, e.write_xh, e.quant, e.o, e.D, st));
+      } else {
+        CU(launch_level_compress_batch(dtype, d_ents + lev_off[l], n_l, lev_ctas[l], st));
+      }
       uint64_t nc = 0;
-      for (int d = 0; d < 3; ++d)
-        if (g.level_stage[d][l - 1] >= 0) nc += g.stages[g.level_stage[d][l - 1]].ncodes;
+      for (int q = 0; q < n_l; ++q) {
+        const ipc_field* f = fs[who[lev_off[l] + q].first];
+        for (int d = 0; d < 3; ++d)
+          if (f->g.level_stage[d][l - 1] >= 0) nc += f->g.stages[f->g.level_stage[d][l - 1]].ncodes;
+      }
       prof_end(ph, st, (double)(nc * esz));
-      level_prof[l - 1] = ph;
+      level_prof[l] = ph;
     }
-    CU(cudaMemcpyAsync(&nout, ws.small + 4, 8, cudaMemcpyDeviceToHost, st));
-    if (S) {
-      CU(cudaMemcpyAsync(stat.data(), ws.stat, 8 * S, cudaMemcpyDeviceToHost, st));
-      CU(cudaMemcpyAsync(nnz.data(), ws.nnz, 128 * S, cudaMemcpyDeviceToHost, st));
-    }
+    CU(cudaMemcpyAsync(&nout, ocount, 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(stat.data(), ws.stat, 8 * so[nf], cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(nnz.data(), ws.nnz, 128 * so[nf], cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (nout <= ws.ocap) break;
     if (attempt == 1) return fail(IPC_ECUDA, "outlier count changed between passes");
-    // grow the outlier buffers to the exact count and run the sweeps again
+    // grow the outlier buffers to the exact count and run the levels again
     cudaFree(ws.okey);
     cudaFree(ws.oval);
     ws.okey = nullptr;
@@ -612,16 +702,21 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
     uint64_t oc = 0;
     if ((rc = grow(&ws.okey, &oc, nout, 8)) || (rc = grow(&ws.oval, &oc, nout, 8))) return rc;
     ws.ocap = nout;
+    build_entries();
   }
 
-  f->st.assign(S, StageTab{});
-  for (size_t t = 0; t < S; ++t) {
-    uint32_t orv = stat[2 * t];
-    int h = -1;
-    while (orv) { ++h; orv >>= 1; }
-    f->st[t].H = h;
-    f->st[t].Q = stat[2 * t + 1];
-    for (int k = 0; k < 32; ++k) f->st[t].nnz[k] = nnz[32 * t + k];
+  for (size_t i = 0; i < nf; ++i) {
+    ipc_field* f = fs[i];
+    const size_t S = f->g.stages.size();
+    f->st.assign(S, StageTab{});
+    for (size_t t = 0; t < S; ++t) {
+      uint32_t orv = stat[2 * (so[i] + t)];
+      int h = -1;
+      while (orv) { ++h; orv >>= 1; }
+      f->st[t].H = h;
+      f->st[t].Q = stat[2 * (so[i] + t) + 1];
+      for (int k = 0; k < 32; ++k) f->st[t].nnz[k] = nnz[32 * (so[i] + t) + k];
+    }
   }
   if (nout) {
     std::vector<unsigned long long> key(nout);
@@ -633,22 +728,27 @@ int compress_impl(const void* d_in, ipc_field* f, cudaStream_t st) {
     for (uint64_t i = 0; i < nout; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return key[a] < key[b]; });
     for (uint64_t i : order) {
-      const size_t t = (size_t)(key[i] >> 40);
-      f->st[t].out_idx.push_back(key[i] & ((1ULL << 40) - 1));
-      f->st[t].out_val.push_back(val[i]);
+      const size_t fi = (size_t)(key[i] >> 48), t = (size_t)((key[i] >> 40) & 0xFF);
+      fs[fi]->st[t].out_idx.push_back(key[i] & ((1ULL << 40) - 1));
+      fs[fi]->st[t].out_val.push_back(val[i]);
     }
   }
-  if ((rc = finish_field(f, st))) return rc;
-  // algorithmic bytes of each level launch: its input values + its streams
-  for (int l = 1; l <= g.K; ++l) {
+  for (size_t i = 0; i < nf; ++i)
+    if ((rc = finish_field(fs[i], st))) return rc;
+  // algorithmic bytes of each level launch: input values + produced streams
+  for (int l = 1; l <= Kmax; ++l) {
     double by = 0;
-    for (int d = 0; d < 3; ++d) {
-      const int t = g.level_stage[d][l - 1];
-      if (t < 0) continue;
-      by += (double)(g.stages[t].ncodes * esz);
-      for (int k = 0; k < 32; ++k) by += (double)f->st[t].size[k];
+    for (size_t i = 0; i < nf; ++i) {
+      const ipc_field* f = fs[i];
+      if (l > f->g.K) continue;
+      for (int d = 0; d < 3; ++d) {
+        const int t = f->g.level_stage[d][l - 1];
+        if (t < 0) continue;
+        by += (double)(f->g.stages[t].ncodes * esz);
+        for (int k = 0; k < 32; ++k) by += (double)f->st[t].size[k];
+      }
     }
-    prof_set_bytes(level_prof[l - 1], by);
+    prof_set_bytes(level_prof[l], by);
   }
   return IPC_OK;
 }
@@ -941,6 +1041,106 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
   return IPC_OK;
 }
 
+// Batched reconstruction of fields of one element type: the anchors in one
+// launch, then ONE launch per level over that level's CTAs of every field.
+// The entry table is copied to `tab` (device) first. When `plan` is set the
+// launches go to a capturing stream and no profiler events are recorded.
+struct BatchTable {
+  std::vector<RetrieveEntry> ents;
+  std::vector<AnchorEntry> anchors;
+  std::vector<uint64_t> lev_off, lev_ctas;
+  int Kmax = 0;
+  double alg_bytes = 0;
+};
+
+void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<std::vector<int>>& bs,
+                          const std::vector<void*>& outs, BatchTable* T) {
+  const size_t nf = fs.size();
+  T->Kmax = 0;
+  for (auto* f : fs) T->Kmax = std::max(T->Kmax, f->g.K);
+  T->lev_off.assign(T->Kmax + 2, 0);
+  T->lev_ctas.assign(T->Kmax + 2, 0);
+  T->ents.clear();
+  T->anchors.clear();
+  T->alg_bytes = 0;
+  for (size_t i = 0; i < nf; ++i) T->anchors.push_back(AnchorEntry{outs[i], fs[i]->anchor});
+  for (int l = T->Kmax; l >= 1; --l) {
+    T->lev_off[l] = T->ents.size();
+    uint64_t cta = 0;
+    for (size_t i = 0; i < nf; ++i) {
+      ipc_field* f = fs[i];
+      if (l > f->g.K) continue;
+      const size_t esz = f->dtype == 0 ? 4 : 8;
+      RetrieveEntry e{};
+      e.L = level_args(f, l);
+      e.L.vec = ((uintptr_t)outs[i] % (2 * esz)) == 0;
+      e.D = level_descs(f, l);
+      e.out = outs[i];
+      e.cap = f->d_cap;
+      e.bm = f->d_bm;
+      e.oidx = f->d_oidx;
+      e.oval = f->d_oval;
+      e.twoeb = bin_width(f);
+      e.b = bs[i][l - 1];
+      e.cta_begin = cta;
+      cta += (uint64_t)e.L.M[0] * e.L.nrb * e.L.nct;
+      T->ents.push_back(e);
+      for (int d = 0; d < 3; ++d) {
+        const int t = f->g.level_stage[d][l - 1];
+        if (t < 0) continue;
+        T->alg_bytes += (double)(f->g.stages[t].ncodes * esz);
+        for (int k = e.b; k < 32; ++k) T->alg_bytes += (double)f->st[t].size[k];
+      }
+    }
+    T->lev_ctas[l] = cta;
+  }
+  T->lev_off[0] = T->ents.size();
+}
+
+int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_t st,
+                          bool profile, uint64_t* launches) {
+  RetrieveEntry* d_ents = (RetrieveEntry*)tab;
+  AnchorEntry* d_anch = (AnchorEntry*)((uint8_t*)tab + T.ents.size() * sizeof(RetrieveEntry));
+  uint64_t nl = 0;
+  {
+    const long ph = profile ? prof_begin(IPC_KERNEL_ANCHOR, st) : -1;
+    CU(launch_set_anchors(dtype, d_anch, (int)T.anchors.size(), st));
+    if (profile) prof_end(ph, st, 16.0 * T.anchors.size());
+    ++nl;
+  }
+  // the per-level share of the algorithmic bytes is reported for the batch
+  for (int l = T.Kmax; l >= 1; --l) {
+    // level l's entries: [lev_off[l], lev_off[l-1]) with lev_off[0] = size
+    const int nn = (int)(T.lev_off[l - 1] - T.lev_off[l]);
+    const long ph = profile ? prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st) : -1;
+    CU(launch_level_retrieve_batch(dtype, d_ents + T.lev_off[l], nn, T.lev_ctas[l], st));
+    if (profile) prof_end(ph, st, l == 1 ? T.alg_bytes : 0.0);
+    ++nl;
+  }
+  if (!profile) g_launches.fetch_add(nl, std::memory_order_relaxed);
+  if (launches) *launches = nl;
+  return IPC_OK;
+}
+
+int upload_table(const BatchTable& T, void** tab, cudaStream_t st, bool pooled) {
+  const size_t bytes = T.ents.size() * sizeof(RetrieveEntry) + T.anchors.size() * sizeof(AnchorEntry);
+  int rc;
+  if (pooled) {
+    if ((rc = dalloc(tab, bytes, st))) return rc;
+  } else if (cudaMalloc(tab, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IPC_ENOMEM, "device allocation failed");
+  }
+  std::vector<uint8_t> h(bytes);
+  std::memcpy(h.data(), T.ents.data(), T.ents.size() * sizeof(RetrieveEntry));
+  std::memcpy(h.data() + T.ents.size() * sizeof(RetrieveEntry), T.anchors.data(),
+              T.anchors.size() * sizeof(AnchorEntry));
+  // pageable source: the copy is staged before the call returns
+  CU(cudaMemcpyAsync(*tab, h.data(), bytes, cudaMemcpyHostToDevice, st));
+  if (!pooled) CU(cudaStreamSynchronize(st));
+  return IPC_OK;
+}
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -983,7 +1183,9 @@ int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims, int
   f->bound = bound;
   f->eb_mode = eb_mode;
   f->eb_user = eb;
-  int rc = compress_impl(d_in, f, (cudaStream_t)stream);
+  std::vector<ipc_field*> fs{f};
+  std::vector<const void*> ins{d_in};
+  int rc = compress_fields(fs, ins, (cudaStream_t)stream);
   if (rc) {
     free_field_device(f);
     f->tag = kDeadTag;
@@ -1063,6 +1265,16 @@ int ipc_free(void* handle) {
     ipc_view* v = (ipc_view*)handle;
     v->tag = kDeadTag;
     delete v;
+    return IPC_OK;
+  }
+  if (tag == kPlanTag) {
+    ipc_plan* p = (ipc_plan*)handle;
+    DeviceGuard dg(p->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->d_tab) cudaFree(p->d_tab);
+    p->tag = kDeadTag;
+    delete p;
     return IPC_OK;
   }
   return fail(IPC_EINVAL, "not a live ipc handle");
@@ -1276,6 +1488,181 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   }
   if (hbad) return drop(IPC_ECORRUPT, "stream contents disagree with their nnz / bitmap");
   *out = f;
+  return IPC_OK;
+}
+
+int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, ipc_field** outs) {
+  g_err.clear();
+  if (nfields < 0 || (nfields > 0 && (!items || !outs))) return fail(IPC_EINVAL, "null argument");
+  std::vector<ipc_field*> all(nfields, nullptr);
+  auto cleanup = [&](int rc) {
+    for (auto* f : all)
+      if (f) {
+        free_field_device(f);
+        f->tag = kDeadTag;
+        delete f;
+      }
+    return rc;
+  };
+  for (int i = 0; i < nfields; ++i) {
+    const ipc_batch_item& it = items[i];
+    if (!it.d_in || (it.dtype != IPC_F32 && it.dtype != IPC_F64) ||
+        (it.interp != IPC_LINEAR && it.interp != IPC_CUBIC) ||
+        (it.bound != IPC_BOUND_STRICT && it.bound != IPC_BOUND_PAPER) ||
+        (it.eb_mode != IPC_EB_ABS && it.eb_mode != IPC_EB_REL) || !std::isfinite(it.eb) ||
+        !(it.eb > 0))
+      return cleanup(fail(IPC_EINVAL, "invalid batch item"));
+    ipc_field* f = new (std::nothrow) ipc_field();
+    if (!f) return cleanup(fail(IPC_ENOMEM, "host allocation"));
+    all[i] = f;
+    f->tag = kFieldTag;
+    if (!build_geo(it.ndim, it.dims, it.dtype, &f->g)) return cleanup(fail(IPC_EINVAL, "shape"));
+    cudaGetDevice(&f->device);
+    f->dtype = it.dtype;
+    f->interp = it.interp;
+    f->bound = it.bound;
+    f->eb_mode = it.eb_mode;
+    f->eb_user = it.eb;
+  }
+  for (int dt = 0; dt < 2; ++dt) {
+    std::vector<ipc_field*> fs;
+    std::vector<const void*> ins;
+    for (int i = 0; i < nfields; ++i)
+      if (items[i].dtype == dt) {
+        fs.push_back(all[i]);
+        ins.push_back(items[i].d_in);
+      }
+    if (fs.empty()) continue;
+    const int rc = compress_fields(fs, ins, (cudaStream_t)stream);
+    if (rc) return cleanup(rc);
+  }
+  for (int i = 0; i < nfields; ++i) outs[i] = all[i];
+  return IPC_OK;
+}
+
+namespace {
+// Shared front end of the batched retrieval and its plan: validation and
+// selection of every field, grouped by element type.
+int batch_select(int n, ipc_field* const* fields, const ipc_target* targets, void* const* d_outs,
+                 std::vector<std::vector<int>>* bs, std::vector<uint64_t>* bytes,
+                 std::vector<double>* bounds) {
+  if (n < 0 || (n > 0 && (!fields || !targets || !d_outs))) return fail(IPC_EINVAL, "null argument");
+  bs->assign(n, {});
+  bytes->assign(n, 0);
+  bounds->assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    if (!fields[i] || fields[i]->tag != kFieldTag || !d_outs[i])
+      return fail(IPC_EINVAL, "invalid field or output");
+    const int rc = select(fields[i], targets[i], nullptr, &(*bs)[i], &(*bytes)[i], &(*bounds)[i]);
+    if (rc) return rc;
+  }
+  return IPC_OK;
+}
+}  // namespace
+
+int ipc_retrieve_batch(int n, ipc_field* const* fields, const ipc_target* targets,
+                       void* const* d_outs, void* stream, ipc_view** outs) {
+  g_err.clear();
+  std::vector<std::vector<int>> bs;
+  std::vector<uint64_t> bytes;
+  std::vector<double> bounds;
+  int rc = batch_select(n, fields, targets, d_outs, &bs, &bytes, &bounds);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<ipc_view*> views;
+  if (outs) {
+    for (int i = 0; i < n; ++i) {
+      ipc_view* v = new (std::nothrow) ipc_view();
+      if (!v) {
+        for (auto* w : views) delete w;
+        return fail(IPC_ENOMEM, "host allocation");
+      }
+      v->tag = kViewTag;
+      v->f = fields[i];
+      v->b = bs[i];
+      v->bytes = bytes[i];
+      v->bound = bounds[i];
+      views.push_back(v);
+    }
+  }
+  for (int dt = 0; dt < 2; ++dt) {
+    std::vector<ipc_field*> fs;
+    std::vector<std::vector<int>> b2;
+    std::vector<void*> o2;
+    for (int i = 0; i < n; ++i)
+      if (fields[i]->dtype == dt) {
+        fs.push_back(fields[i]);
+        b2.push_back(bs[i]);
+        o2.push_back(d_outs[i]);
+      }
+    if (fs.empty()) continue;
+    BatchTable T;
+    build_retrieve_table(fs, b2, o2, &T);
+    void* tab = nullptr;
+    rc = upload_table(T, &tab, st, true);
+    if (!rc) rc = launch_retrieve_table(dt, T, tab, st, true, nullptr);
+    if (tab) cudaFreeAsync(tab, st);
+    if (rc) {
+      for (auto* w : views) delete w;
+      return rc;
+    }
+  }
+  if (outs)
+    for (int i = 0; i < n; ++i) outs[i] = views[i];
+  return IPC_OK;
+}
+
+int ipc_plan_retrieve_batch(int n, ipc_field* const* fields, const ipc_target* targets,
+                            void* const* d_outs, void* stream, ipc_plan** out) {
+  g_err.clear();
+  if (!out) return fail(IPC_EINVAL, "null argument");
+  std::vector<std::vector<int>> bs;
+  std::vector<uint64_t> bytes;
+  std::vector<double> bounds;
+  int rc = batch_select(n, fields, targets, d_outs, &bs, &bytes, &bounds);
+  if (rc) return rc;
+  for (int i = 1; i < n; ++i)
+    if (fields[i]->dtype != fields[0]->dtype) return fail(IPC_EINVAL, "a plan takes one element type");
+  ipc_plan* p = new (std::nothrow) ipc_plan();
+  if (!p) return fail(IPC_ENOMEM, "host allocation");
+  p->tag = kPlanTag;
+  cudaGetDevice(&p->device);
+  std::vector<ipc_field*> fs(fields, fields + n);
+  std::vector<void*> o2(d_outs, d_outs + n);
+  BatchTable T;
+  build_retrieve_table(fs, bs, o2, &T);
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = upload_table(T, &p->d_tab, st, false);
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!rc) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (!rc && e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (!rc && e == cudaSuccess) {
+    rc = launch_retrieve_table(n ? fields[0]->dtype : 0, T, p->d_tab, cs, false, &p->launches);
+    g_launches.fetch_sub(p->launches, std::memory_order_relaxed);  // counted at replay
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    p->graph = g;
+    if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, g, 0);
+  }
+  if (cs) cudaStreamDestroy(cs);
+  if (rc || e != cudaSuccess) {
+    if (e != cudaSuccess) cuda_fail(e, "graph capture");
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->d_tab) cudaFree(p->d_tab);
+    delete p;
+    return rc ? rc : IPC_ECUDA;
+  }
+  *out = p;
+  return IPC_OK;
+}
+
+int ipc_plan_launch(ipc_plan* p, void* stream) {
+  if (!p || p->tag != kPlanTag) return fail(IPC_EINVAL, "invalid plan");
+  CU(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+  g_launches.fetch_add(p->launches, std::memory_order_relaxed);
   return IPC_OK;
 }
 

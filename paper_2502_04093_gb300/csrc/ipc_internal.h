@@ -87,6 +87,7 @@ struct SweepOut {
   unsigned long long* outl_count;
   uint64_t outl_cap;
   uint32_t* stat;       // per stage: [OR of negabinary codes, max |q|]
+  uint32_t field;       // batch index (tags outlier keys)
 };
 
 // Per-plane descriptor of a device-resident stream.
@@ -117,10 +118,40 @@ inline uint64_t stream_bytes(uint64_t nnz, uint64_t W) {
   return 4 + 4 * W;
 }
 
+// One field's share of a batched level launch (device memory).
+struct CompressEntry {
+  LevelArgs L;
+  LevelDescs D;
+  SweepOut o;
+  const void* x;
+  void* xh;
+  alignas(16) unsigned char quant[32];  // QuantArgs<T>
+  int write_xh;
+  uint64_t cta_begin;
+};
+struct RetrieveEntry {
+  LevelArgs L;
+  LevelDescs D;
+  void* out;
+  const uint32_t* cap;
+  const uint32_t* bm;
+  const uint64_t* oidx;
+  const double* oval;
+  double twoeb;
+  int b;
+  uint64_t cta_begin;
+};
+
+struct AnchorEntry {
+  void* out;
+  double v;
+};
+
 // ---- kernel launchers -------------------------------------------------------
 cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long long* acc,
                          cudaStream_t st);
 cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st);
+cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStream_t st);
 // Fused level kernels (ipc_level.cu).
 cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, void* xh,
                                   int write_xh, const void* quant, const SweepOut& o,
@@ -129,6 +160,11 @@ cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, doub
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
                                   const double* oval, const LevelDescs& d, cudaStream_t st);
 int level_rows(int dtype);
+// Batched level launches: `ents` (device memory) sorted by cta_begin.
+cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,
+                                        uint64_t ctas, cudaStream_t st);
+cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
+                                        uint64_t ctas, cudaStream_t st);
 // Segmented <-> packed container streams of one stage (export / import).
 // tmp: 2 * 32 * nbm words of scratch; flags[0] = corruption flag,
 // flags[1 + k] = nonzero words found in plane k (import).

@@ -90,6 +90,12 @@ __global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, uint64_t
 template <class T>
 __global__ void k_anchor(T* out, double v) { out[0] = (T)v; }
 
+template <class T>
+__global__ void k_anchors(const AnchorEntry* __restrict__ a, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ((T*)a[i].out)[0] = (T)a[i].v;
+}
+
 // Block-wide exclusive scan of one value per thread (blockDim = 1024).
 __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* total,
                                                  uint32_t* sh /* 33 */) {
@@ -313,6 +319,14 @@ cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long lon
 cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st) {
   if (dtype == 0) k_anchor<float><<<1, 1, 0, st>>>((float*)out, v);
   else k_anchor<double><<<1, 1, 0, st>>>((double*)out, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 127) / 128);
+  if (dtype == 0) k_anchors<float><<<grid, 128, 0, st>>>(a, n);
+  else k_anchors<double><<<grid, 128, 0, st>>>(a, n);
   return cudaGetLastError();
 }
 

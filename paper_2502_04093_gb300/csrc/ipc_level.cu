@@ -59,9 +59,9 @@ struct CtaPos {
   int64_t rs;     // element offset of one lattice row (c1 -> c1 + 1)
 };
 
-__device__ __forceinline__ CtaPos cta_pos(const LevelArgs& L, int BR, int BC) {
+__device__ __forceinline__ CtaPos cta_pos(const LevelArgs& L, uint64_t cta, int BR, int BC) {
   CtaPos c;
-  uint64_t b = blockIdx.x;
+  uint64_t b = cta;
   c.ct = b % L.nct;
   b /= L.nct;
   c.rb = b % L.nrb;
@@ -118,7 +118,8 @@ __device__ __forceinline__ void record_outlier(const SweepOut& o, int stage, uin
                                                double v) {
   const unsigned long long slot = atomicAdd(o.outl_count, 1ULL);
   if (slot < o.outl_cap) {
-    o.outl_key[slot] = ((unsigned long long)stage << 40) | (unsigned long long)ci;
+    o.outl_key[slot] = ((unsigned long long)o.field << 48) | ((unsigned long long)stage << 40) |
+                       (unsigned long long)ci;
     o.outl_val[slot] = v;
   }
 }
@@ -200,18 +201,18 @@ __device__ __forceinline__ void store_tile(const LevelArgs& L, const CtaPos& c, 
 // Compression of one level.
 // ---------------------------------------------------------------------------
 template <class T, int BR, int BC>
-__global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T* __restrict__ x,
-                                                           T* xh, int write_xh, QuantArgs<T> qa,
-                                                           SweepOut o, LevelDescs D) {
+__device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T* __restrict__ x,
+                                                    T* xh, int write_xh, const QuantArgs<T>& qa,
+                                                    const SweepOut& o, const LevelDescs& D,
+                                                    uint64_t cta, unsigned char* smem) {
   typedef Tile<BR, BC> G;
-  extern __shared__ __align__(16) unsigned char smem[];
   T* VE = reinterpret_cast<T*>(smem);                     // [VR][VEC]
   T* VO = VE + G::VR * G::VEC;                            // [BR][HC]
   uint32_t* E2 = reinterpret_cast<uint32_t*>(VO + BR * G::HC);  // [BR][PITCH]
   uint32_t* E1 = E2 + BR * G::PITCH;                      // [BR/2][PITCH]
   uint32_t* E0 = E1 + (BR / 2) * G::PITCH;                // [BR/2][PITCH]
 
-  const CtaPos c = cta_pos(L, BR, BC);
+  const CtaPos c = cta_pos(L, cta, BR, BC);
   const bool podd = (c.P & 1) != 0;
   const int tid = threadIdx.x;
   const int cubic = L.cubic;
@@ -400,14 +401,14 @@ constexpr int kSlots = 13;
 constexpr int kMaxBw = 4;  // bitmap words per segment (RB * CW <= 128)
 
 template <class T, int BR, int BC>
-__global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, T twoeb, int b,
-                                                           const uint32_t* __restrict__ cap,
-                                                           const uint32_t* __restrict__ bm,
-                                                           const uint64_t* __restrict__ oidx,
-                                                           const double* __restrict__ oval,
-                                                           LevelDescs D) {
+__device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, T twoeb, int b,
+                                                    const uint32_t* __restrict__ cap,
+                                                    const uint32_t* __restrict__ bm,
+                                                    const uint64_t* __restrict__ oidx,
+                                                    const double* __restrict__ oval,
+                                                    const LevelDescs& D, uint64_t cta,
+                                                    unsigned char* smem) {
   typedef Tile<BR, BC> G;
-  extern __shared__ __align__(16) unsigned char smem[];
   T* VE = reinterpret_cast<T*>(smem);                           // [VR][VEC]
   T* VO = VE + G::VR * G::VEC;                                  // [BR][HC]
   uint32_t* Q2 = reinterpret_cast<uint32_t*>(VO + BR * G::HC);  // [BR][PITCH]
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, 
   __shared__ uint32_t SB[kSlots][32][kMaxBw];  // group bitmaps of the segments
   __shared__ unsigned long long SG[kSlots];    // segment id (or ~0 if absent)
 
-  const CtaPos c = cta_pos(L, BR, BC);
+  const CtaPos c = cta_pos(L, cta, BR, BC);
   const bool podd = (c.P & 1) != 0;
   const int tid = threadIdx.x;
   const int cubic = L.cubic;
@@ -593,6 +594,63 @@ __global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, 
   store_tile<T, BR, G::HC, G::VEC>(L, c, VE, VO, out);
 }
 
+// Single-field kernels: arguments in the parameter space.
+template <class T, int BR, int BC>
+__global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T* __restrict__ x,
+                                                           T* xh, int write_xh, QuantArgs<T> qa,
+                                                           SweepOut o, LevelDescs D) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  level_compress_body<T, BR, BC>(L, x, xh, write_xh, qa, o, D, blockIdx.x, smem);
+}
+
+template <class T, int BR, int BC>
+__global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, T twoeb, int b,
+                                                           const uint32_t* __restrict__ cap,
+                                                           const uint32_t* __restrict__ bm,
+                                                           const uint64_t* __restrict__ oidx,
+                                                           const double* __restrict__ oval,
+                                                           LevelDescs D) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  level_retrieve_body<T, BR, BC>(L, out, twoeb, b, cap, bm, oidx, oval, D, blockIdx.x, smem);
+}
+
+// Batched kernels: one grid covers the level's CTAs of every field of a
+// batch; entry i owns CTAs [cta_begin_i, cta_begin_{i+1}).
+template <class E>
+__device__ __forceinline__ const E& find_entry(const E* __restrict__ ents, int n) {
+  __shared__ int sel;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (ents[mid].cta_begin <= blockIdx.x) lo = mid;
+      else hi = mid;
+    }
+    sel = lo;
+  }
+  __syncthreads();
+  return ents[sel];
+}
+
+template <class T, int BR, int BC>
+__global__ void __launch_bounds__(256, 3) k_level_compress_batch(
+    const CompressEntry* __restrict__ ents, int n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const CompressEntry& e = find_entry(ents, n);
+  level_compress_body<T, BR, BC>(e.L, (const T*)e.x, (T*)e.xh, e.write_xh,
+                                 *reinterpret_cast<const QuantArgs<T>*>(e.quant), e.o, e.D,
+                                 blockIdx.x - e.cta_begin, smem);
+}
+
+template <class T, int BR, int BC>
+__global__ void __launch_bounds__(256, 2) k_level_retrieve_batch(
+    const RetrieveEntry* __restrict__ ents, int n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const RetrieveEntry& e = find_entry(ents, n);
+  level_retrieve_body<T, BR, BC>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx, e.oval,
+                                 e.D, blockIdx.x - e.cta_begin, smem);
+}
+
 template <class T, int BR, int BC>
 size_t smem_compress() {
   typedef Tile<BR, BC> G;
@@ -613,6 +671,14 @@ cudaError_t setup_once() {
                                          (int)smem_compress<T, BR, BC>());
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(k_level_retrieve<T, BR, BC>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_retrieve<T, BR, BC>());
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_level_compress_batch<T, BR, BC>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_compress<T, BR, BC>());
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_level_retrieve_batch<T, BR, BC>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_retrieve<T, BR, BC>());
     return r;
@@ -660,6 +726,38 @@ cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, doub
     k_level_retrieve<double, kLevelRowsF64, kLevelCols>
         <<<(unsigned)grid, 256, smem_retrieve<double, kLevelRowsF64, kLevelCols>(), st>>>(
             L, (double*)out, twoeb, b, cap, bm, oidx, oval, d);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,
+                                        uint64_t ctas, cudaStream_t st) {
+  if (ctas == 0 || n == 0) return cudaSuccess;
+  cudaError_t e;
+  if (dtype == 0) {
+    if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
+    k_level_compress_batch<float, kLevelRowsF32, kLevelCols>
+        <<<(unsigned)ctas, 256, smem_compress<float, kLevelRowsF32, kLevelCols>(), st>>>(ents, n);
+  } else {
+    if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
+    k_level_compress_batch<double, kLevelRowsF64, kLevelCols>
+        <<<(unsigned)ctas, 256, smem_compress<double, kLevelRowsF64, kLevelCols>(), st>>>(ents, n);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
+                                        uint64_t ctas, cudaStream_t st) {
+  if (ctas == 0 || n == 0) return cudaSuccess;
+  cudaError_t e;
+  if (dtype == 0) {
+    if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
+    k_level_retrieve_batch<float, kLevelRowsF32, kLevelCols>
+        <<<(unsigned)ctas, 256, smem_retrieve<float, kLevelRowsF32, kLevelCols>(), st>>>(ents, n);
+  } else {
+    if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
+    k_level_retrieve_batch<double, kLevelRowsF64, kLevelCols>
+        <<<(unsigned)ctas, 256, smem_retrieve<double, kLevelRowsF64, kLevelCols>(), st>>>(ents, n);
   }
   return cudaGetLastError();
 }

@@ -32,6 +32,12 @@ class ipc_target(C.Structure):
     _fields_ = [("kind", C.c_int), ("value", C.c_double)]
 
 
+class ipc_batch_item(C.Structure):
+    _fields_ = [("d_in", C.c_void_p), ("dtype", C.c_int), ("ndim", C.c_int),
+                ("dims", C.c_int64 * 3), ("eb_mode", C.c_int), ("eb", C.c_double),
+                ("interp", C.c_int), ("bound", C.c_int)]
+
+
 class IpcError(RuntimeError):
     def __init__(self, rc: int, what: str, detail: str):
         super().__init__("%s failed with status %d: %s" % (what, rc, detail))
@@ -69,6 +75,12 @@ def lib() -> C.CDLL:
                                  C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.ipc_last_error.restype = C.c_char_p
+    L.ipc_compress_batch.argtypes = [C.c_int, C.POINTER(ipc_batch_item), vp, C.POINTER(vp)]
+    L.ipc_retrieve_batch.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(ipc_target),
+                                     C.POINTER(vp), vp, C.POINTER(vp)]
+    L.ipc_plan_retrieve_batch.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(ipc_target),
+                                          C.POINTER(vp), vp, C.POINTER(vp)]
+    L.ipc_plan_launch.argtypes = [vp, vp]
     L.ipc_profile_enable.argtypes = [C.c_int]
     L.ipc_profile_read.argtypes = [C.c_int, u64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.ipc_launch_count.restype = C.c_uint64
@@ -178,6 +190,64 @@ def ipc_field_info(field) -> dict:
                                 C.byref(eb), C.byref(mn), C.byref(mx)), "ipc_field_info")
     return dict(dtype=dt.value, ndim=nd.value, dims=tuple(dims)[:nd.value], K=K.value,
                 S=S.value, eb=eb.value, xmin=mn.value, xmax=mx.value)
+
+
+def ipc_compress_batch(xs, ebs, eb_mode=IPC_EB_ABS, interp=IPC_CUBIC, bound=IPC_BOUND_STRICT,
+                       stream=None):
+    """Compress a list of CUDA tensors (any shapes) in one batch; returns the
+    list of ipc_field handles."""
+    n = len(xs)
+    items = (ipc_batch_item * max(n, 1))()
+    for i, x in enumerate(xs):
+        _require_cuda(x, "x")
+        it = items[i]
+        it.d_in = x.data_ptr()
+        it.dtype = _dtype_code(x)
+        it.ndim = x.dim()
+        for e, d in enumerate(x.shape):
+            it.dims[e] = int(d)
+        it.eb_mode = int(eb_mode[i] if isinstance(eb_mode, (list, tuple)) else eb_mode)
+        it.eb = float(ebs[i] if isinstance(ebs, (list, tuple)) else ebs)
+        it.interp = int(interp)
+        it.bound = int(bound)
+    outs = (C.c_void_p * max(n, 1))()
+    _check(lib().ipc_compress_batch(n, items, _stream(stream), outs), "ipc_compress_batch")
+    return [C.c_void_p(outs[i]) for i in range(n)]
+
+
+def _batch_args(fields, targets, outs):
+    n = len(fields)
+    fa = (C.c_void_p * max(n, 1))(*[f.value if isinstance(f, C.c_void_p) else f for f in fields])
+    ta = (ipc_target * max(n, 1))()
+    for i, (k, v) in enumerate(targets):
+        ta[i].kind = int(k)
+        ta[i].value = float(v)
+    for o in outs:
+        _require_cuda(o, "out")
+    oa = (C.c_void_p * max(n, 1))(*[o.data_ptr() for o in outs])
+    return n, fa, ta, oa
+
+
+def ipc_retrieve_batch(fields, targets, outs, stream=None, want_views=False):
+    """targets: list of (kind, value); outs: CUDA tensors. Returns the views
+    (or None)."""
+    n, fa, ta, oa = _batch_args(fields, targets, outs)
+    va = (C.c_void_p * max(n, 1))()
+    _check(lib().ipc_retrieve_batch(n, fa, ta, oa, _stream(stream), va if want_views else None),
+           "ipc_retrieve_batch")
+    return [C.c_void_p(va[i]) for i in range(n)] if want_views else None
+
+
+def ipc_plan_retrieve_batch(fields, targets, outs, stream=None):
+    n, fa, ta, oa = _batch_args(fields, targets, outs)
+    h = C.c_void_p()
+    _check(lib().ipc_plan_retrieve_batch(n, fa, ta, oa, _stream(stream), C.byref(h)),
+           "ipc_plan_retrieve_batch")
+    return h
+
+
+def ipc_plan_launch(plan, stream=None):
+    _check(lib().ipc_plan_launch(plan, _stream(stream)), "ipc_plan_launch")
 
 
 IPC_KERNEL_NAMES = ["range", "compress_level", "retrieve_level", "anchor", "pack", "unpack"]
