@@ -171,6 +171,59 @@ int ipc_plan_retrieve_batch(int n, ipc_field* const* fields, const ipc_target* t
 /* ipc_plan_launch -- replays the plan's launches on `stream`. */
 int ipc_plan_launch(ipc_plan* p, void* stream);
 
+/* ---- serving: continuous batching of retrievals ---------------------------- */
+typedef struct ipc_server ipc_server;
+typedef struct {
+  uint64_t mem_budget;   /* bytes of output buffers the server may hold         */
+  uint64_t hbm_reserve;  /* free device memory a new output must leave untouched */
+  int max_batch;         /* requests per launched batch (<= 0: unlimited)       */
+  int max_inflight;      /* batches on the device at once (>= 1)                */
+  int nstreams;          /* streams the batches rotate over (1..16)             */
+  int plain;             /* 1: single-field launches per request (a baseline)   */
+} ipc_server_cfg;
+enum { IPC_REQ_RETRIEVE = 0, IPC_REQ_REFINE = 1, IPC_REQ_RELEASE = 2 };
+/* RETRIEVE(field, target): a new view with a server-owned output buffer.
+ * REFINE(view_id, target): Algorithm 2 on that view (planes only added).
+ * RELEASE(view_id): frees the view and its buffer. */
+typedef struct {
+  int kind;
+  ipc_field* field;
+  uint64_t view_id;
+  ipc_target target;
+  uint64_t user_tag;
+} ipc_request;
+typedef struct {
+  uint64_t ticket, user_tag;
+  int status;            /* IPC_OK or the request's error                       */
+  uint64_t view_id;      /* view created / refined / released                   */
+  void* d_out;           /* the view's reconstruction (valid until released)    */
+  uint64_t bytes;        /* loaded bytes of the view's selection                */
+  double bound;          /* guaranteed L-inf bound of the selection             */
+  double latency_us;     /* submit -> completion seen by the server             */
+  double queue_us;       /* submit -> launch                                    */
+} ipc_completion;
+
+/* ipc_server_create -- starts a server on the current device: a worker
+ * thread admits submitted requests in arrival order while output memory
+ * (mem_budget, and free HBM above hbm_reserve) allows, groups everything it
+ * admitted into one batched reconstruction (ipc_retrieve_batch's launches)
+ * and rotates batches over `nstreams` streams, so requests that arrive
+ * while others run are launched and overlap on the device. A request's
+ * reconstruction is bitwise equal to the same request served alone. A
+ * retrieve larger than mem_budget completes with IPC_ENOMEM. */
+int ipc_server_create(const ipc_server_cfg* cfg, ipc_server** out);
+/* ipc_server_submit -- queues a request; returns its ticket. Fields must
+ * outlive the server. IPC_EBUSY after destroy began. */
+int ipc_server_submit(ipc_server* s, const ipc_request* r, uint64_t* ticket);
+/* ipc_server_poll -- up to `max` completions; waits up to timeout_us for
+ * the first one (0: no wait). IPC_ETIMEOUT when the wait ran out. */
+int ipc_server_poll(ipc_server* s, ipc_completion* out, int max, int* n, int timeout_us);
+/* ipc_server_stats -- batches launched, requests launched, output bytes held. */
+int ipc_server_stats(ipc_server* s, uint64_t* batches, uint64_t* requests, uint64_t* mem_used);
+/* ipc_server_destroy -- finishes in-flight work, completes requests that
+ * can no longer be admitted with IPC_EBUSY, frees every view. */
+int ipc_server_destroy(ipc_server* s);
+
 /* ---- introspection ------------------------------------------------------- */
 /* ipc_field_info -- dtype, ndim, dims (host array of 3), K (levels), S
  * (non-empty sweeps), absolute eb, and the value range over finite inputs.

@@ -18,6 +18,7 @@
 
 #include "ipc.h"
 #include "ipc_internal.h"
+#include "ipc_serve_internal.h"
 
 using namespace ipc;
 
@@ -1490,6 +1491,57 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   *out = f;
   return IPC_OK;
 }
+
+}  // extern "C"
+
+// ---- hooks of the serving loop (ipc_serve.cu) ---------------------------------
+int ipc_internal_select(ipc_field* f, ipc_target tg, const std::vector<int>* upper,
+                        std::vector<int>* b, uint64_t* bytes, double* bound) {
+  return select(f, tg, upper, b, bytes, bound);
+}
+
+void ipc_internal_field_shape(const ipc_field* f, uint64_t* n, int* dtype) {
+  *n = f->g.n;
+  *dtype = f->dtype;
+}
+
+int ipc_internal_reconstruct_each(const std::vector<ipc_field*>& fs,
+                                  const std::vector<std::vector<int>>& bs,
+                                  const std::vector<void*>& outs, cudaStream_t st) {
+  for (size_t i = 0; i < fs.size(); ++i) {
+    const int rc = reconstruct(fs[i], bs[i], outs[i], st);
+    if (rc) return rc;
+  }
+  return IPC_OK;
+}
+
+int ipc_internal_reconstruct_batch(const std::vector<ipc_field*>& fs,
+                                   const std::vector<std::vector<int>>& bs,
+                                   const std::vector<void*>& outs, cudaStream_t st,
+                                   std::vector<void*>* tabs) {
+  for (int dt = 0; dt < 2; ++dt) {
+    std::vector<ipc_field*> f2;
+    std::vector<std::vector<int>> b2;
+    std::vector<void*> o2;
+    for (size_t i = 0; i < fs.size(); ++i)
+      if (fs[i]->dtype == dt) {
+        f2.push_back(fs[i]);
+        b2.push_back(bs[i]);
+        o2.push_back(outs[i]);
+      }
+    if (f2.empty()) continue;
+    BatchTable T;
+    build_retrieve_table(f2, b2, o2, &T);
+    void* tab = nullptr;
+    int rc = upload_table(T, &tab, st, true);
+    if (tab) tabs->push_back(tab);
+    if (!rc) rc = launch_retrieve_table(dt, T, tab, st, true, nullptr);
+    if (rc) return rc;
+  }
+  return IPC_OK;
+}
+
+extern "C" {
 
 int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, ipc_field** outs) {
   g_err.clear();

@@ -1,0 +1,24 @@
+// Library-internal hooks the serving loop uses (defined in ipc_host.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ipc.h"
+
+// Selection for a target (constrained to b <= *upper when upper != null).
+int ipc_internal_select(ipc_field* f, ipc_target tg, const std::vector<int>* upper,
+                        std::vector<int>* b, uint64_t* bytes, double* bound);
+// Element count and dtype of a field.
+void ipc_internal_field_shape(const ipc_field* f, uint64_t* n, int* dtype);
+// One reconstruction per field with the single-field kernels.
+int ipc_internal_reconstruct_each(const std::vector<ipc_field*>& fs,
+                                  const std::vector<std::vector<int>>& bs,
+                                  const std::vector<void*>& outs, cudaStream_t st);
+// Batched reconstruction (one launch per level per element type); the
+// device tables to free once the stream has passed are appended to `tabs`.
+int ipc_internal_reconstruct_batch(const std::vector<ipc_field*>& fs,
+                                   const std::vector<std::vector<int>>& bs,
+                                   const std::vector<void*>& outs, cudaStream_t st,
+                                   std::vector<void*>* tabs);

@@ -38,6 +38,25 @@ class ipc_batch_item(C.Structure):
                 ("interp", C.c_int), ("bound", C.c_int)]
 
 
+class ipc_server_cfg(C.Structure):
+    _fields_ = [("mem_budget", C.c_uint64), ("hbm_reserve", C.c_uint64), ("max_batch", C.c_int),
+                ("max_inflight", C.c_int), ("nstreams", C.c_int), ("plain", C.c_int)]
+
+
+class ipc_request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("field", C.c_void_p), ("view_id", C.c_uint64),
+                ("target", ipc_target), ("user_tag", C.c_uint64)]
+
+
+class ipc_completion(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("user_tag", C.c_uint64), ("status", C.c_int),
+                ("view_id", C.c_uint64), ("d_out", C.c_void_p), ("bytes", C.c_uint64),
+                ("bound", C.c_double), ("latency_us", C.c_double), ("queue_us", C.c_double)]
+
+
+IPC_REQ_RETRIEVE, IPC_REQ_REFINE, IPC_REQ_RELEASE = 0, 1, 2
+
+
 class IpcError(RuntimeError):
     def __init__(self, rc: int, what: str, detail: str):
         super().__init__("%s failed with status %d: %s" % (what, rc, detail))
@@ -81,6 +100,12 @@ def lib() -> C.CDLL:
     L.ipc_plan_retrieve_batch.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(ipc_target),
                                           C.POINTER(vp), vp, C.POINTER(vp)]
     L.ipc_plan_launch.argtypes = [vp, vp]
+    L.ipc_server_create.argtypes = [C.POINTER(ipc_server_cfg), C.POINTER(vp)]
+    L.ipc_server_submit.argtypes = [vp, C.POINTER(ipc_request), C.POINTER(C.c_uint64)]
+    L.ipc_server_poll.argtypes = [vp, C.POINTER(ipc_completion), C.c_int, C.POINTER(C.c_int),
+                                  C.c_int]
+    L.ipc_server_stats.argtypes = [vp, u64p, u64p, u64p]
+    L.ipc_server_destroy.argtypes = [vp]
     L.ipc_profile_enable.argtypes = [C.c_int]
     L.ipc_profile_read.argtypes = [C.c_int, u64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.ipc_launch_count.restype = C.c_uint64
@@ -248,6 +273,59 @@ def ipc_plan_retrieve_batch(fields, targets, outs, stream=None):
 
 def ipc_plan_launch(plan, stream=None):
     _check(lib().ipc_plan_launch(plan, _stream(stream)), "ipc_plan_launch")
+
+
+def ipc_server_create(mem_budget, max_batch=0, max_inflight=2, nstreams=2, plain=False,
+                      hbm_reserve=1 << 30):
+    cfg = ipc_server_cfg(int(mem_budget), int(hbm_reserve), int(max_batch), int(max_inflight),
+                         int(nstreams), 1 if plain else 0)
+    h = C.c_void_p()
+    _check(lib().ipc_server_create(C.byref(cfg), C.byref(h)), "ipc_server_create")
+    return h
+
+
+def ipc_server_submit(server, kind, field=None, view_id=0, target=(0, 0.0), user_tag=0):
+    r = ipc_request(int(kind), field.value if isinstance(field, C.c_void_p) else field,
+                    int(view_id), ipc_target(int(target[0]), float(target[1])), int(user_tag))
+    t = C.c_uint64()
+    _check(lib().ipc_server_submit(server, C.byref(r), C.byref(t)), "ipc_server_submit")
+    return t.value
+
+
+def ipc_server_poll(server, max_n=256, timeout_us=0):
+    """List of completions (dicts); empty when none arrived in time."""
+    buf = (ipc_completion * max_n)()
+    n = C.c_int()
+    rc = lib().ipc_server_poll(server, buf, max_n, C.byref(n), int(timeout_us))
+    if rc not in (IPC_OK, IPC_ETIMEOUT):
+        _check(rc, "ipc_server_poll")
+    return [dict(ticket=c.ticket, user_tag=c.user_tag, status=c.status, view_id=c.view_id,
+                 d_out=c.d_out, bytes=c.bytes, bound=c.bound, latency_us=c.latency_us,
+                 queue_us=c.queue_us) for c in buf[:n.value]]
+
+
+def ipc_server_stats(server):
+    b, r, m = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _check(lib().ipc_server_stats(server, C.byref(b), C.byref(r), C.byref(m)), "ipc_server_stats")
+    return dict(batches=b.value, requests=r.value, mem_used=m.value)
+
+
+def ipc_server_destroy(server):
+    _check(lib().ipc_server_destroy(server), "ipc_server_destroy")
+
+
+def device_view(ptr, shape, dtype):
+    """A torch tensor aliasing device memory the library owns (no copy)."""
+    import torch
+
+    class _Arr:
+        pass
+
+    a = _Arr()
+    a.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape),
+                                  "typestr": "<f4" if dtype in (torch.float32, "f4") else "<f8",
+                                  "data": (int(ptr), False), "version": 2}
+    return torch.as_tensor(a, device="cuda")
 
 
 IPC_KERNEL_NAMES = ["range", "compress_level", "retrieve_level", "anchor", "pack", "unpack"]

@@ -14,6 +14,7 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "timeout(seconds): per-test limit (pytest-timeout)")
 
 
 @pytest.fixture(scope="session")

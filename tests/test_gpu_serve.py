@@ -1,0 +1,137 @@
+"""Serving loop: continuous batching must not change any result. Every
+served reconstruction equals the same request served alone (bitwise);
+admission respects the memory budget; failures come back as statuses."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(240)]
+
+from paper_2502_04093_gb300 import ipc, synth  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_04093_gb300 import build
+    build.build()
+
+
+def drain(server, want, timeout_s=60.0):
+    got = {}
+    t0 = time.time()
+    while len(got) < want and time.time() - t0 < timeout_s:
+        for c in ipc.ipc_server_poll(server, 64, 20000):
+            got[c["ticket"]] = c
+    assert len(got) == want, "server did not complete every request"
+    return got
+
+
+@pytest.fixture(scope="module")
+def fields():
+    shapes = [(40, 48, 36), (64, 64, 64), (33, 70, 21), (96, 80), (128, 129)]
+    xs = [torch.from_numpy(synth.random_field(s, seed=i)).cuda() for i, s in enumerate(shapes)]
+    fs = [ipc.Field.compress(x, 1e-5, ipc.IPC_EB_REL) for x in xs]
+    return xs, fs
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_results_same_alone_and_in_the_mix(fields, plain):
+    xs, fs = fields
+    srv = ipc.ipc_server_create(8 << 30, max_inflight=3, nstreams=3, plain=plain,
+                                max_batch=1 if plain else 0)
+    try:
+        rng = np.random.default_rng(3)
+        reqs = []
+        for i in range(40):
+            f = int(rng.integers(len(fs)))
+            if i % 4 == 3:
+                tgt = (ipc.IPC_TARGET_BITRATE, float(rng.uniform(1, 12)))
+            else:
+                tgt = (ipc.IPC_TARGET_EB, float(10 ** rng.uniform(-5, -1)))
+            t = ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, fs[f].h, target=tgt, user_tag=i)
+            reqs.append((t, f, tgt))
+        got = drain(srv, len(reqs))
+        views = {}
+        nok = 0
+        for t, f, tgt in reqs:
+            c = got[t]
+            try:
+                alone, v = fs[f].retrieve(*tgt)
+            except ipc.IpcError as e:  # e.g. a bitrate below the mandatory bytes
+                assert c["status"] == e.rc
+                continue
+            assert c["status"] == 0
+            served = ipc.device_view(c["d_out"], xs[f].shape, xs[f].dtype).clone()
+            torch.cuda.synchronize()
+            assert torch.equal(served, alone)
+            assert (c["bytes"], c["bound"]) == v.selection()[1:]
+            views[c["view_id"]] = (f, tgt)
+            nok += 1
+        assert nok >= 30
+        # refine chains on live views, submitted all at once (each view's
+        # refines must run in order), then compared with fresh retrieval
+        vids = list(views)[:8]
+        reqs2 = []
+        for vid in vids:
+            f, tgt = views[vid]
+            for E in (1e-3, 1e-4, 1e-5):
+                t = ipc.ipc_server_submit(srv, ipc.IPC_REQ_REFINE, view_id=vid,
+                                          target=(ipc.IPC_TARGET_EB, E))
+                reqs2.append((t, vid, f, E))
+        got2 = drain(srv, len(reqs2))
+        for vid in vids:
+            f, _ = views[vid]
+            last = [r for r in reqs2 if r[1] == vid][-1]
+            c = got2[last[0]]
+            assert c["status"] == 0
+            served = ipc.device_view(c["d_out"], xs[f].shape, xs[f].dtype).clone()
+            full, _ = fs[f].retrieve(ipc.IPC_TARGET_EB, 1e-5)
+            torch.cuda.synchronize()
+            assert torch.equal(served, full)
+        rel = [ipc.ipc_server_submit(srv, ipc.IPC_REQ_RELEASE, view_id=v) for v in views]
+        got3 = drain(srv, len(rel))
+        assert all(c["status"] == 0 for c in got3.values())
+        assert ipc.ipc_server_stats(srv)["mem_used"] == 0
+    finally:
+        ipc.ipc_server_destroy(srv)
+
+
+def test_memory_admission_and_failures(fields):
+    xs, fs = fields
+    big = fs[1]  # 64^3 f32 = 1 MiB output
+    srv = ipc.ipc_server_create(int(1.5 * (1 << 20)), max_inflight=2, nstreams=2)
+    try:
+        # a request that can never fit the budget fails with ENOMEM
+        tiny = ipc.ipc_server_create(1024, max_inflight=1, nstreams=1)
+        try:
+            t = ipc.ipc_server_submit(tiny, ipc.IPC_REQ_RETRIEVE, big.h, target=(0, 1e-2))
+            c = drain(tiny, 1)[t]
+            assert c["status"] == ipc.IPC_ENOMEM
+        finally:
+            ipc.ipc_server_destroy(tiny)
+        # two 1 MiB views do not fit a 1.5 MiB budget: the second waits for
+        # the first one's release
+        t1 = ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, big.h, target=(0, 1e-2))
+        t2 = ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, big.h, target=(0, 1e-3))
+        c1 = drain(srv, 1)[t1]
+        assert c1["status"] == 0
+        assert ipc.ipc_server_poll(srv, 8, 50000) == []  # t2 is held back
+        ipc.ipc_server_submit(srv, ipc.IPC_REQ_RELEASE, view_id=c1["view_id"])
+        got = drain(srv, 2)
+        c2 = got[t2]
+        assert c2["status"] == 0
+        alone, _ = big.retrieve(0, 1e-3)
+        torch.cuda.synchronize()
+        assert torch.equal(ipc.device_view(c2["d_out"], xs[1].shape, xs[1].dtype), alone)
+        # unknown view / bad target statuses
+        t = ipc.ipc_server_submit(srv, ipc.IPC_REQ_REFINE, view_id=12345, target=(0, 1e-3))
+        assert drain(srv, 1)[t]["status"] == ipc.IPC_EINVAL
+        t = ipc.ipc_server_submit(srv, ipc.IPC_REQ_REFINE, view_id=c2["view_id"],
+                                  target=(0, 1e-9))
+        assert drain(srv, 1)[t]["status"] == ipc.IPC_EBOUND
+    finally:
+        ipc.ipc_server_destroy(srv)
