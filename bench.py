@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--edge", type=int, default=512, help="field edge (default 512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="skip the batched and serving measurements")
+    ap.add_argument("--serving-small", action="store_true",
+                    help="serving with 40 fields up to 448^3 and 400 requests (quick)")
     return ap.parse_args()
 
 
@@ -229,11 +233,21 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_measure(ipc, x, args, world)
+    del out
+    extra = {}
+    if not args.no_systems:
+        del x
+        torch.cuda.empty_cache()
+        extra["batched"] = measure_batched(ipc, synth, torch)
+        torch.cuda.empty_cache()
+        extra["batched_f64"] = measure_f64(ipc, synth, torch)
+        torch.cuda.empty_cache()
+        extra["serving"] = measure_serving(ipc, synth, torch, full=not args.serving_small)
 
     return dict(value=value, ms_per_step=ms_per_step, compress_ms=compress_ms,
                 retrieve_ms=retrieve_ms, roofline=roof, kernels=kernels, launches=launches,
                 clocks=clk.summary(), csize=csize, nbytes=nbytes, n_recon=n_recon, e2e=e2e,
-                step_bytes=step_bytes)
+                step_bytes=step_bytes, extra=extra)
 
 
 def e2e_measure(ipc, x, args, world):
@@ -282,6 +296,234 @@ def e2e_measure(ipc, x, args, world):
         sec = float(t.item())
     return {"value": round(world * nbytes * (1 + n_recon) / sec / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": blen + n_recon * nbytes}
+
+
+# ---------------------------------------------------------------------------
+# Systems patterns: batching (uneven fields, one launch per level) and serving
+# ---------------------------------------------------------------------------
+def _events_ms(torch, fn, reps=3, warm=1):
+    st = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return statistics.median(out)
+
+
+def measure_batched(ipc, synth, torch):
+    """64 uneven 2-D f32 fields (16 x 1800x3600, 24 x 900x1800, 24 x 450x900):
+    one batched compress at rel eb 1e-4 and batched retrieves at mixed eb,
+    against one call per field, and the graph-captured batch replayed."""
+    import numpy as np
+    shapes, seeds = synth.zonal_batch(seed=1300)
+    xs = [synth.zonal2d_torch(s, sd) for s, sd in zip(shapes, seeds)]
+    torch.cuda.synchronize()
+    nbytes = sum(x.numel() * 4 for x in xs)
+
+    def comp_batched():
+        for h in ipc.ipc_compress_batch(xs, 1e-4, ipc.IPC_EB_REL):
+            ipc.ipc_free(h)
+
+    def comp_single():
+        for x in xs:
+            ipc.ipc_free(ipc.ipc_compress(x, 1e-4, ipc.IPC_EB_REL))
+
+    cb = _events_ms(torch, comp_batched)
+    cs = _events_ms(torch, comp_single)
+    hs = ipc.ipc_compress_batch(xs, 1e-4, ipc.IPC_EB_REL)
+    csize = sum(ipc.ipc_compressed_size(h) for h in hs)
+    rng = np.random.default_rng(1303)
+    targets = [(ipc.IPC_TARGET_EB, float(10 ** rng.uniform(-4, -1))) for _ in xs]
+    outs = [torch.empty_like(x) for x in xs]
+    rb = _events_ms(torch, lambda: ipc.ipc_retrieve_batch(hs, targets, outs))
+    rs = _events_ms(torch, lambda: [ipc.ipc_retrieve(h, t[0], t[1], o, want_view=False)
+                                   for h, t, o in zip(hs, targets, outs)])
+    plan = ipc.ipc_plan_retrieve_batch(hs, targets, outs)
+    rg = _events_ms(torch, lambda: ipc.ipc_plan_launch(plan))
+    ipc.ipc_free(plan)
+    for h in hs:
+        ipc.ipc_free(h)
+    gbs = lambda ms: round(nbytes / (ms * 1e-3) / 1e9, 1)
+    return {"workload": "64 uneven 2-D f32 fields (16x1800x3600, 24x900x1800, 24x450x900), "
+                        "rel eb 1e-4; retrieves at eb log-uniform [1e-4, 1e-1]",
+            "bytes": nbytes, "compression_ratio": round(nbytes / csize, 2),
+            "compress_batched_ms": round(cb, 3), "compress_per_field_ms": round(cs, 3),
+            "compress_batched_gbs": gbs(cb), "compress_per_field_gbs": gbs(cs),
+            "retrieve_batched_ms": round(rb, 3), "retrieve_per_field_ms": round(rs, 3),
+            "retrieve_graph_ms": round(rg, 3), "retrieve_batched_gbs": gbs(rb),
+            "retrieve_per_field_gbs": gbs(rs), "retrieve_graph_gbs": gbs(rg)}
+
+
+def measure_f64(ipc, synth, torch):
+    """8 fields of 384x384x256 f64 (sinusoid sums + 1e-4 noise), rel eb 1e-8:
+    one batched compress, then per field a retrieve at 1e-2 refined to 1e-4,
+    1e-6 and 1e-8."""
+    xs = [synth.sinusoids3d_torch((384, 384, 256), seed=1400 + j) for j in range(8)]
+    torch.cuda.synchronize()
+    nbytes = sum(x.numel() * 8 for x in xs)
+    outs = [torch.empty_like(x) for x in xs]
+
+    def comp():
+        return ipc.ipc_compress_batch(xs, 1e-8, ipc.IPC_EB_REL)
+
+    def chain(hs):
+        views = ipc.ipc_retrieve_batch(hs, [(ipc.IPC_TARGET_EB, 1e-2)] * len(hs), outs,
+                                       want_views=True)
+        for E in (1e-4, 1e-6, 1e-8):
+            for v, o in zip(views, outs):
+                ipc.ipc_refine(v, ipc.IPC_TARGET_EB, E, o)
+        return views
+
+    hs = comp()
+    for h in hs:
+        ipc.ipc_free(h)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record(st)
+    hs = comp()
+    b.record(st)
+    views = chain(hs)
+    c.record(st)
+    torch.cuda.synchronize()
+    cm, rm = a.elapsed_time(b), b.elapsed_time(c)
+    ok = all(float((o - x).abs().max()) <= ipc.ipc_selection(v)[2] for o, x, v in
+             zip(outs, xs, views))
+    for v in views:
+        ipc.ipc_free(v)
+    csize = sum(ipc.ipc_compressed_size(h) for h in hs)
+    for h in hs:
+        ipc.ipc_free(h)
+    return {"workload": "8 x 384x384x256 f64, rel eb 1e-8, batched compress; refine chain "
+                        "1e-2 -> 1e-4 -> 1e-6 -> 1e-8 per field",
+            "bytes": nbytes, "compression_ratio": round(nbytes / csize, 2),
+            "compress_ms": round(cm, 3), "compress_gbs": round(nbytes / (cm * 1e-3) / 1e9, 1),
+            "refine_chain_ms": round(rm, 3),
+            "refine_chain_gbs": round(4 * nbytes / (rm * 1e-3) / 1e9, 1),
+            "max_error_within_bound": bool(ok)}
+
+
+def serve_stream(ipc, fields, reqs, plain, rate, live_cap=8):
+    """Feeds one request stream (Poisson arrivals at `rate` per second) to a
+    server; returns latencies (us), wall time and output bytes."""
+    import numpy as np
+    srv = ipc.ipc_server_create(48 << 30, max_batch=1 if plain else 0,
+                                max_inflight=1 if plain else 3, nstreams=1 if plain else 3,
+                                plain=plain)
+    rng = np.random.default_rng(77)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    live = []  # (view_id, field index, current E)
+    meta = {}
+    lat, outb = [], 0
+    outstanding = 0
+    t0 = time.perf_counter()
+
+    def handle(cs):
+        nonlocal outstanding, outb
+        for c in cs:
+            kind, fi, E = meta.pop(c["ticket"])
+            if kind == "release":
+                continue
+            outstanding -= 1
+            if c["status"] != 0:
+                continue
+            lat.append(c["latency_us"])
+            outb += fields[fi][1]
+            if kind == "retrieve":
+                live.append([c["view_id"], fi, E])
+                if len(live) > live_cap:
+                    vid = live.pop(0)[0]
+                    t = ipc.ipc_server_submit(srv, ipc.IPC_REQ_RELEASE, view_id=vid)
+                    meta[t] = ("release", 0, 0)
+
+    for i, (kind, fi, val) in enumerate(reqs):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= arrivals[i]:
+                break
+            handle(ipc.ipc_server_poll(srv, 256, 0))
+            time.sleep(min(2e-4, max(0.0, arrivals[i] - now)))
+        if kind == "refine" and live:
+            v = live[int(val[0] * len(live)) % len(live)]
+            v[2] = max(1e-6, v[2] * 10 ** (-val[1]))
+            t = ipc.ipc_server_submit(srv, ipc.IPC_REQ_REFINE, view_id=v[0],
+                                      target=(ipc.IPC_TARGET_EB, v[2]))
+            meta[t] = ("refine", v[1], v[2])
+        else:
+            if kind == "refine":  # no live view yet: a coarse retrieve instead
+                kind, val = "eb", 1e-1
+            tgt = (ipc.IPC_TARGET_BITRATE, val) if kind == "bitrate" else (ipc.IPC_TARGET_EB, val)
+            t = ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, fields[fi][0], target=tgt)
+            meta[t] = ("retrieve", fi, val if kind == "eb" else 1e-1)
+        outstanding += 1
+    while outstanding > 0:
+        handle(ipc.ipc_server_poll(srv, 256, 100000))
+    wall = time.perf_counter() - t0
+    stats = ipc.ipc_server_stats(srv)
+    ipc.ipc_server_destroy(srv)
+    return np.array(lat), wall, outb, stats
+
+
+def measure_serving(ipc, synth, torch, full=False):
+    """Resident k^-5/3 fields (edges log-uniform, step 32), rel eb 1e-6; a
+    Poisson stream of 50% retrieve(eb log-U[1e-6, 1e-1]), 25% retrieve(bitrate
+    U[1, 12]), 25% refine of a live view to E * 10^-U[1, 2], at 0.7x the
+    measured capacity of the plain (one request per launch) server."""
+    import numpy as np
+    nf, hi, nreq = (128, 768, 2000) if full else (40, 448, 400)
+    edges = synth.serving_edges(nfields=nf, hi=hi)
+    fields = []
+    for j, e in enumerate(edges):
+        x = synth.grf_k53((e, e, e), seed=1500 + j, device="cuda")
+        fields.append((ipc.ipc_compress(x, 1e-6, ipc.IPC_EB_REL), x.numel() * 4))
+        del x
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1505)
+    reqs = []
+    for _ in range(nreq):
+        u = rng.random()
+        fi = int(rng.integers(nf))
+        if u < 0.5:
+            reqs.append(("eb", fi, float(10 ** rng.uniform(-6, -1))))
+        elif u < 0.75:
+            reqs.append(("bitrate", fi, float(rng.uniform(1, 12))))
+        else:
+            reqs.append(("refine", fi, (float(rng.random()), float(rng.uniform(1, 2)))))
+    # capacity of the plain server: a closed burst of retrievals
+    burst = [("eb", int(rng.integers(nf)), float(10 ** rng.uniform(-6, -1))) for _ in range(60)]
+    lat, wall, _, _ = serve_stream(ipc, fields, burst, True, 1e9)
+    cap = len(burst) / wall
+    rate = 0.7 * cap
+    res = {}
+    # saturated capacity of both modes: the whole burst submitted at once
+    for mode, plain in (("plain", True), ("served", False)):
+        sat = [("eb", int(rng.integers(nf)), float(10 ** rng.uniform(-6, -1)))
+               for _ in range(200)]
+        lat, wall, outb, stats = serve_stream(ipc, fields, sat, plain, 1e9)
+        res[mode + "_saturated"] = {"requests_per_s": round(lat.size / wall, 1),
+                                    "output_gbs": round(outb / wall / 1e9, 1),
+                                    "mean_batch": round(stats["requests"] /
+                                                        max(stats["batches"], 1), 2)}
+    for mode, plain in (("plain", True), ("served", False)):
+        lat, wall, outb, stats = serve_stream(ipc, fields, reqs, plain, rate)
+        res[mode] = {"p50_ms": round(float(np.percentile(lat, 50)) / 1e3, 3),
+                     "p99_ms": round(float(np.percentile(lat, 99)) / 1e3, 3),
+                     "completed": int(lat.size), "wall_s": round(wall, 3),
+                     "output_gbs": round(outb / wall / 1e9, 1),
+                     "requests_per_s": round(lat.size / wall, 1),
+                     "mean_batch": round(stats["requests"] / max(stats["batches"], 1), 2)}
+    for f, _ in fields:
+        ipc.ipc_free(f)
+    return {"workload": "%d resident k^-5/3 f32 fields, edges %d..%d (log-uniform, step 32), "
+                        "rel eb 1e-6; %d Poisson requests" % (nf, 128, hi, nreq),
+            "plain_capacity_rps": round(cap, 1), "offered_rps": round(rate, 1), **res}
 
 
 # ---------------------------------------------------------------------------
@@ -391,6 +633,7 @@ def main():
             "e2e": r["e2e"],
             "cpu_baseline": cpu,
         }
+        line.update(r["extra"])
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -164,3 +164,52 @@ def random_field(shape, seed, dtype=np.float32, kind="smooth"):
         pos = rng.choice(flat.size, size=k, replace=False)
         flat[pos] = rng.choice([-1.0, 1.0], size=k) * 1e9
     return f.astype(dtype)
+
+
+def zonal2d_torch(shape, seed, device="cuda"):
+    """zonal2d drawn on the device (same recipe, for large batches)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    H, W = int(shape[0]), int(shape[1])
+    a = rng.uniform(-1.0, 1.0, size=6)
+    phi = rng.uniform(0, 2 * math.pi, size=6)
+    m = int(rng.integers(1, 6))
+    psi = float(rng.uniform(0, 2 * math.pi))
+    lat = torch.arange(H, device=device, dtype=torch.float64)[:, None]
+    lon = torch.arange(W, device=device, dtype=torch.float64)[None, :]
+    f = torch.zeros((H, W), device=device, dtype=torch.float64)
+    for j in range(6):
+        f = f + float(a[j]) * torch.cos((j + 1) * math.pi * lat / H + float(phi[j]))
+    f = f + 0.1 * float(np.abs(a).max()) * torch.sin(2 * math.pi * m * lon / W + psi) * \
+        torch.cos(math.pi * lat / H)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    f = f + torch.randn((H, W), generator=gen, device=device, dtype=torch.float64) * \
+        (1e-3 * float(np.abs(a).sum()))
+    return f.to(torch.float32).contiguous()
+
+
+def sinusoids3d_torch(shape=(384, 384, 256), seed=1400, device="cuda", nterms=8, kmax=8):
+    """sinusoids3d drawn on the device in float64."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    shape = tuple(int(s) for s in shape)
+    axes = [torch.arange(s, device=device, dtype=torch.float64) / s for s in shape]
+    f = torch.zeros(shape, device=device, dtype=torch.float64)
+    amps = rng.uniform(-1.0, 1.0, size=nterms)
+    for j in range(nterms):
+        k = rng.integers(-kmax, kmax + 1, size=len(shape))
+        arg = torch.full((1,) * len(shape), float(rng.uniform(0, 2 * math.pi)), device=device,
+                         dtype=torch.float64)
+        for e, ax in enumerate(axes):
+            sh = [1] * len(shape)
+            sh[e] = -1
+            arg = arg + 2 * math.pi * float(k[e]) * ax.reshape(sh)
+        f += float(amps[j]) * torch.sin(arg)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    f += torch.randn(shape, generator=gen, device=device, dtype=torch.float64) * \
+        (1e-4 * float(np.abs(amps).sum()))
+    return f.contiguous()
