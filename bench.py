@@ -122,6 +122,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# Multi-rank timing: every rank runs its own field (weak scaling); the job
+# time is the slowest rank's, the job throughput counts every rank's bytes.
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, device, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world: int, bytes_per_rank_step: float, steps: int, seconds: float) -> float:
+    return world * bytes_per_rank_step * steps / seconds / 1e9
+
+
+# ---------------------------------------------------------------------------
 # The GPU step (through the C ABI)
 # ---------------------------------------------------------------------------
 def gpu_step(ipc, x, out, ev=None):
@@ -195,14 +213,9 @@ def run_ours(args, rank, world, local_rank):
     csize = ipc.ipc_compressed_size(fields[-1][0])
     ipc.ipc_free(fields[-1][0])
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-
+    elapsed_ms = max_over_ranks(elapsed_ms, dev, world)
     ms_per_step = elapsed_ms / args.steps
-    value = world * step_bytes * args.steps / (elapsed_ms * 1e-3) / 1e9
+    value = job_gbs(world, step_bytes, args.steps, elapsed_ms * 1e-3)
 
     # phase split measured separately (same step, events between phases)
     cm, rm = [], []
@@ -288,13 +301,8 @@ def e2e_measure(ipc, x, args, world):
     for _ in range(steps):
         blen = step()
     t1 = time.perf_counter()
-    sec = (t1 - t0) / steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([sec], device=x.device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-    return {"value": round(world * nbytes * (1 + n_recon) / sec / 1e9, 2), "unit": "GB/s",
+    sec = max_over_ranks((t1 - t0) / steps, x.device, world)
+    return {"value": round(job_gbs(world, nbytes * (1 + n_recon), 1, sec), 2), "unit": "GB/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": blen + n_recon * nbytes}
 
 

@@ -51,6 +51,20 @@ template <> struct FP<double> {
   static __device__ __forceinline__ double from_code(int64_t q) { return __ll2double_rn(q); }
 };
 
+// Value of a (possibly truncated) negabinary code in the element type,
+// exactly: codes below 2^31 convert in 32-bit integer arithmetic (their
+// value lies in (-2^31, 2^31)), small ones by the magic-number trick.
+__device__ __forceinline__ float code_value(uint32_t n, float) {
+  if (n >> 31) return __ll2float_rn((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
+  const int q = (int)((n ^ 0xAAAAAAAAu) - 0xAAAAAAAAu);
+  if ((unsigned)(q + (1 << 22)) < (1u << 23))
+    return __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f);
+  return __int2float_rn(q);
+}
+__device__ __forceinline__ double code_value(uint32_t n, double) {
+  return __ll2double_rn((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
+}
+
 __device__ __forceinline__ uint32_t negabinary(int32_t q) {
   return ((uint32_t)q + 0xAAAAAAAAu) ^ 0xAAAAAAAAu;
 }
@@ -74,10 +88,10 @@ __device__ __forceinline__ uint32_t xor_decode(uint32_t e) {
 // In-register transpose of a 32x32 bit matrix (row i = a[i], column k = bit
 // k): afterwards bit i of a[k] is the former bit k of a[i]. Five rounds of
 // block swaps (16, 8, 4, 2, 1).
-template <int J, uint32_t M>
-__device__ __forceinline__ void tround(uint32_t (&a)[32]) {
+template <int J, uint32_t M, int NW>
+__device__ __forceinline__ void tround(uint32_t (&a)[NW]) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
+  for (int i = 0; i < NW; ++i) {
     if ((i & J) == 0) {
       uint32_t t = ((a[i] >> J) ^ a[i + J]) & M;
       a[i + J] ^= t;
@@ -87,6 +101,18 @@ __device__ __forceinline__ void tround(uint32_t (&a)[32]) {
 }
 __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
   tround<16, 0x0000FFFFu>(a);
+  tround<8, 0x00FF00FFu>(a);
+  tround<4, 0x0F0F0F0Fu>(a);
+  tround<2, 0x33333333u>(a);
+  tround<1, 0x55555555u>(a);
+}
+// Two 16x16 transposes side by side: a[k] holds row k of the left matrix in
+// its low half and row k of the right matrix in its high half. The masks of
+// the four rounds never move a bit across the halves, so afterwards the low
+// half of a[i] is column i of the left matrix and the high half column i of
+// the right one. With a[k] = plane k of 32 codes (planes >= 16 all zero),
+// code i is the low half of a[i] and code 16 + i the high half.
+__device__ __forceinline__ void transpose16x2(uint32_t (&a)[16]) {
   tround<8, 0x00FF00FFu>(a);
   tround<4, 0x0F0F0F0Fu>(a);
   tround<2, 0x33333333u>(a);

@@ -46,7 +46,6 @@ struct Tile {
   static constexpr int PITCH = HC + CWD;  // code-row pitch (33 words per 32 codes)
   static constexpr int VR = BR + 5;       // VE rows: c1 in [R0-2, R0+BR+2]
   static constexpr int VEC = HC + 3;      // VE columns: even c2 in [C0-2, C0+BC+2]
-  static constexpr int QEP = HC + 3 + (HC + 3) / 32 + 1;  // pitch of halo code rows
 };
 
 // Swizzled index of code column lc in a code row (one pad word per 32).
@@ -326,7 +325,7 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
 
   // Phase 4: bitplane transpose and compaction of the three segments.
   // Threads [0,128) words of stage 2, [128,192) stage 1, [192,256) stage 0.
-  const int lane = tid & 31, wi = tid >> 5;
+  const int lane = tid & 31;
   int sidx, li;
   if (tid < 128) { sidx = 2; li = tid; }
   else if (tid < 192) { sidx = 1; li = tid - 128; }
@@ -390,15 +389,127 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
 
 // ---------------------------------------------------------------------------
 // Reconstruction of one level (Algorithm 1).
-// Words come from the CTA's own segments and, for halo targets, from the
-// neighbouring segments (stage 1: left/right; stage 0: the 3x3 block) --
-// at most 13 segments. Their group bitmap words of every selected plane are
-// staged in shared memory first; a word's plane value is then found from
-// its group's bitmap word alone (rank = population below its bit), so its
-// 32 plane loads are independent of each other.
+//
+// Setup: warp 0 finds the planes to load (plane k >= b with nonzero words in
+// the stage) and the top loaded plane; the CTA stages, for the loaded planes
+// of at most 13 segments (its own, and for halo targets the neighbouring
+// segments: stage 1 left/right, stage 0 the 3x3 block), the group bitmap
+// words and the payload base. A word's plane value is then found from its
+// group's bitmap word alone (rank = population below its bit).
+// Phase 0: one thread per word of the tile's own code columns: load the
+//   selected planes, undo the predictive XOR top-down, transpose (a 16-plane
+//   window when the loaded planes span at most 16, else all 32) and store the
+//   32 codes. The three halo code columns (one left, two right) are extracted
+//   bit by bit from their words without a transpose.
+// Phase 1: even value rows (sweep 0 of an odd plane from the known planes
+//   P +- 1, P +- 3, or the known points of an even plane), one column per
+//   thread.
+// Phase 2: odd value rows (sweep 1), one column per thread, the four row
+//   neighbours kept in registers.
+// Phase 3: sweep 2 fused with the output: each thread computes four odd
+//   columns of a row and stores them with the five even columns around them
+//   as one run of eight elements.
 // ---------------------------------------------------------------------------
 constexpr int kSlots = 13;
 constexpr int kMaxBw = 4;  // bitmap words per segment (RB * CW <= 128)
+
+template <int BR, int BC>
+struct RTile {
+  static constexpr int HC = BC / 2;      // codes of one stage per tile row
+  static constexpr int CWD = BC / 64;    // words per tile row
+  static constexpr int QP = CWD * 36;    // code-row pitch: 36 words per 32 codes
+  static constexpr int VR = BR + 5;      // value rows: c1 in [R0-2, R0+BR+2]
+  static constexpr int VP = HC + 4;      // value-row pitch (a 16-byte multiple)
+  static constexpr int H1 = BR / 2;      // stage-1 code rows (own odd c1)
+  static constexpr int H0 = BR / 2 + 3;  // stage-0 code rows (even c1, with halo)
+};
+
+// Position of tile code column e in a code row: 32 codes + 4 pad words per
+// block, so that one thread's 32 codes are eight conflict-free 16-byte
+// stores and four consecutive codes one 16-byte load.
+__device__ __forceinline__ int qoff(int e) { return (e >> 5) * 36 + (e & 31); }
+
+template <class T>
+__device__ __forceinline__ void lds8(const T* p, T (&w)[8]);
+template <>
+__device__ __forceinline__ void lds8<float>(const float* p, float (&w)[8]) {
+  const float4 u = reinterpret_cast<const float4*>(p)[0], v = reinterpret_cast<const float4*>(p)[1];
+  w[0] = u.x; w[1] = u.y; w[2] = u.z; w[3] = u.w;
+  w[4] = v.x; w[5] = v.y; w[6] = v.z; w[7] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds8<double>(const double* p, double (&w)[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 u = reinterpret_cast<const double2*>(p)[i];
+    w[2 * i] = u.x;
+    w[2 * i + 1] = u.y;
+  }
+}
+
+// Stores the values v[0..7] of lattice columns c2e .. c2e+7 of one row
+// (element offset of lattice point (P, c1, 0) is `row`). At stride 1 they
+// are consecutive elements; at stride 2 each value is written twice so that
+// whole sectors are written (the element in between is a target of the next
+// level and is never read as a known value); larger strides store singly.
+template <class T>
+__device__ __forceinline__ void store_run(T* row, const LevelArgs& L, int c2e, int C1,
+                                          const T (&v)[8]) {
+  typedef typename Vec2<T>::type V2;
+  if (L.s == 1) {
+    T* p = row + c2e;
+    if (c2e + 8 <= C1 && ((uintptr_t)p & 15) == 0) {
+      if (sizeof(T) == 4) {
+        float4* q = reinterpret_cast<float4*>(p);
+        q[0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+        q[1] = make_float4((float)v[4], (float)v[5], (float)v[6], (float)v[7]);
+      } else {
+        V2* q = reinterpret_cast<V2*>(p);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          V2 t;
+          t.x = v[2 * i];
+          t.y = v[2 * i + 1];
+          q[i] = t;
+        }
+      }
+      return;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (c2e + i < C1) p[i] = v[i];
+    return;
+  }
+  if (L.s == 2) {
+    T* p = row + 2 * (int64_t)c2e;
+    if (c2e + 8 <= C1 && 2 * (int64_t)(c2e + 7) + 1 < L.N[2] && ((uintptr_t)p & 15) == 0) {
+      if (sizeof(T) == 4) {
+        float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          q[i] = make_float4((float)v[2 * i], (float)v[2 * i], (float)v[2 * i + 1],
+                             (float)v[2 * i + 1]);
+      } else {
+        V2* q = reinterpret_cast<V2*>(p);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          V2 t;
+          t.x = v[i];
+          t.y = v[i];
+          q[i] = t;
+        }
+      }
+      return;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (c2e + i < C1) p[2 * i] = v[i];
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (c2e + i < C1) row[(int64_t)(c2e + i) * L.s] = v[i];
+}
 
 template <class T, int BR, int BC>
 __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, T twoeb, int b,
@@ -408,14 +519,18 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
                                                     const double* __restrict__ oval,
                                                     const LevelDescs& D, uint64_t cta,
                                                     unsigned char* smem) {
-  typedef Tile<BR, BC> G;
-  T* VE = reinterpret_cast<T*>(smem);                           // [VR][VEC]
-  T* VO = VE + G::VR * G::VEC;                                  // [BR][HC]
-  uint32_t* Q2 = reinterpret_cast<uint32_t*>(VO + BR * G::HC);  // [BR][PITCH]
-  uint32_t* Q1 = Q2 + BR * G::PITCH;                            // [BR/2][QEP]
-  uint32_t* Q0 = Q1 + (BR / 2) * G::QEP;                        // [BR/2+3][QEP]
-  __shared__ uint32_t SB[kSlots][32][kMaxBw];  // group bitmaps of the segments
+  typedef RTile<BR, BC> G;
+  static_assert(G::HC == 256, "one thread per code column of a tile row");
+  T* VE = reinterpret_cast<T*>(smem);                            // [VR][VP]
+  uint32_t* Q2 = reinterpret_cast<uint32_t*>(VE + G::VR * G::VP);  // [BR][QP]
+  uint32_t* Q1 = Q2 + BR * G::QP;                                // [H1][QP]
+  uint32_t* Q0 = Q1 + G::H1 * G::QP;                             // [H0][QP]
+  uint32_t* QH = Q0 + G::H0 * G::QP;                             // [H1 + H0][4]
+  __shared__ uint32_t SB[kSlots][32][kMaxBw];  // group bitmaps of the loaded planes
+  __shared__ const uint32_t* SP[kSlots][32];   // payload base of (segment, plane)
   __shared__ unsigned long long SG[kSlots];    // segment id (or ~0 if absent)
+  __shared__ uint32_t s_km[3];                 // planes to load, per stage
+  __shared__ int s_ktop;
 
   const CtaPos c = cta_pos(L, cta, BR, BC);
   const bool podd = (c.P & 1) != 0;
@@ -424,174 +539,304 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   const int M0 = (int)L.M[0], M1 = (int)L.M[1], M2 = (int)L.M[2];
   const LevelStage &S0 = L.st[0], &S1 = L.st[1], &S2 = L.st[2];
 
+  if (tid < 32) {
+    uint32_t any = 0;
+#pragma unroll
+    for (int sx = 0; sx < 3; ++sx) {
+      const bool ld = L.st[sx].present && (sx != 0 || podd) && tid >= b && D.s[sx].p[tid].nnz > 0;
+      const uint32_t m = __ballot_sync(~0u, ld);
+      if (tid == 0) s_km[sx] = m;
+      any |= m;
+    }
+    if (tid == 0) s_ktop = any ? 31 - __clz((int)any) : -1;
+  }
   // slots: 0 = stage 2 own; 1..3 = stage 1 (ct-1, ct, ct+1);
   //        4..12 = stage 0 (rb-1..rb+1) x (ct-1..ct+1)
-  if (tid < kSlots) {
+  if (tid >= 32 && tid < 32 + kSlots) {
+    const int sl = tid - 32;
     int sx, drb, dct;
-    if (tid == 0) { sx = 2; drb = 0; dct = 0; }
-    else if (tid < 4) { sx = 1; drb = 0; dct = tid - 2; }
-    else { sx = 0; drb = (tid - 4) / 3 - 1; dct = (tid - 4) % 3 - 1; }
+    if (sl == 0) { sx = 2; drb = 0; dct = 0; }
+    else if (sl < 4) { sx = 1; drb = 0; dct = sl - 2; }
+    else { sx = 0; drb = (sl - 4) / 3 - 1; dct = (sl - 4) % 3 - 1; }
     const LevelStage& S = L.st[sx];
     const int64_t rbs = (int64_t)c.rb + drb, cts = (int64_t)c.ct + dct;
     const bool ok = S.present && (sx != 0 || podd) && rbs >= 0 && (uint64_t)rbs < S.nrb &&
                     cts >= 0 && (uint64_t)cts < S.nct;
     const uint64_t pi = sx == 0 ? (uint64_t)((c.P - 1) >> 1) : (uint64_t)c.P;
-    SG[tid] = ok ? seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts) : ~0ULL;
+    SG[sl] = ok ? seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts) : ~0ULL;
   }
   __syncthreads();
-  for (int u = tid; u < kSlots * 32 * kMaxBw; u += 256) {
-    const int slot = u / (32 * kMaxBw), k = (u / kMaxBw) & 31, v = u % kMaxBw;
-    const int sx = slot == 0 ? 2 : (slot < 4 ? 1 : 0);
+  for (int u = tid; u < kSlots * 32; u += 256) {
+    const int sl = u >> 5, k = u & 31;
+    const int sx = sl == 0 ? 2 : (sl < 4 ? 1 : 0);
+    const unsigned long long g = SG[sl];
+    if (g == ~0ULL || !((s_km[sx] >> k) & 1u)) continue;
     const LevelStage& S = L.st[sx];
     const PlaneDesc& pd = D.s[sx].p[k];
-    uint32_t w = 0;
-    if (SG[slot] != ~0ULL && k >= b && pd.nnz && (uint64_t)v < S.bw)
-      w = __ldg(bm + pd.bm_off + SG[slot] * S.bw + v);
-    SB[slot][k][v] = w;
+    SP[sl][k] = cap + pd.cap_off + g * (uint64_t)S.RB * S.CW;
+    const uint32_t* bp = bm + pd.bm_off + g * S.bw;
+    for (int v = 0; v < (int)S.bw; ++v) SB[sl][k][v] = __ldg(bp + v);
   }
   __syncthreads();
 
-  // Phase 0: decode the words the CTA needs.
-  //  stage 2: own rows x own words
-  //  stage 1: own odd rows x words [C0/64 - 1, C0/64 + CWD] (halo columns)
-  //  stage 0: even rows [R0-2, R1+2] x the same word range (odd planes)
-  const int cw0 = c.C0 >> 6;  // first own word of a code row
+  // Phase 0: decode the words of the tile's code columns.
+  const int ktop = s_ktop;
+  const bool w16 = ktop - b <= 15;              // the loaded planes fit in 16
+  const int wb = w16 ? max(0, ktop - 15) : 0;  // plane of window slot 0
+  const int cw0 = (int)c.ct * G::CWD;          // first own word of a row
   const int n2r = c.R1 - c.R0, n1r = (c.R1 - c.R0) >> 1;
-  const int nw2 = (S2.present && c.ct < S2.nct && c.rb < S2.nrb) ? n2r * (int)S2.CW : 0;
-  const int hw = G::CWD + 2;
-  const int nw1 = S1.present ? n1r * hw : 0;
-  const int nw0 = (S0.present && podd) ? (BR / 2 + 3) * hw : 0;
-  for (int it = tid; it < nw2 + nw1 + nw0; it += 256) {
-    int sx, lr;
-    int64_t rr, j;
-    if (it < nw2) {
-      sx = 2;
-      lr = it / (int)S2.CW;
-      j = (int64_t)c.ct * S2.CW + (it - lr * (int)S2.CW);
-      rr = c.R0 + lr;
-    } else if (it < nw2 + nw1) {
-      const int u = it - nw2;
-      sx = 1;
-      lr = u / hw;
-      j = cw0 - 1 + (u - lr * hw);
-      rr = (c.R0 >> 1) + lr;
+  const bool st0 = S0.present && podd;
+  const int nA = (S2.present && c.ct < S2.nct) ? n2r * G::CWD : 0;
+  const int nB = S1.present ? n1r * G::CWD : 0;
+  const int nC = st0 ? G::H0 * G::CWD : 0;
+  const int nD1 = S1.present ? 2 * n1r : 0;
+  const int nD0 = st0 ? 2 * G::H0 : 0;
+  const int nit = nA + nB + nC + nD1 + nD0;
+  for (int it = tid; it < nit; it += 256) {
+    int sx, qrow, side, rr, j;  // side: -1 own word, 0 left / 1 right halo word
+    if (it < nA) {
+      sx = 2; qrow = it / G::CWD; j = cw0 + it % G::CWD; rr = c.R0 + qrow; side = -1;
+    } else if (it < nA + nB) {
+      const int u = it - nA;
+      sx = 1; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (c.R0 >> 1) + qrow; side = -1;
+    } else if (it < nA + nB + nC) {
+      const int u = it - nA - nB;
+      sx = 0; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (c.R0 >> 1) - 1 + qrow; side = -1;
+    } else if (it < nA + nB + nC + nD1) {
+      const int u = it - nA - nB - nC;
+      sx = 1; qrow = u >> 1; side = u & 1; rr = (c.R0 >> 1) + qrow;
+      j = side ? cw0 + G::CWD : cw0 - 1;
     } else {
-      const int u = it - nw2 - nw1;
-      sx = 0;
-      lr = u / hw;
-      j = cw0 - 1 + (u - lr * hw);
-      rr = (c.R0 >> 1) - 1 + lr;  // stage-0 row = c1 / 2 for c1 = R0 - 2 + 2 lr
+      const int u = it - nA - nB - nC - nD1;
+      sx = 0; qrow = u >> 1; side = u & 1; rr = (c.R0 >> 1) - 1 + qrow;
+      j = side ? cw0 + G::CWD : cw0 - 1;
     }
     const LevelStage& S = L.st[sx];
     if (rr < 0 || (uint64_t)rr >= S.m1 || j < 0 || (uint64_t)j >= S.wr) continue;
-    const uint64_t rbw = (uint64_t)rr / S.RB, ctw = (uint64_t)j / S.CW;
-    int slot = 0;
-    if (sx == 1) slot = 2 + (int)((int64_t)ctw - (int64_t)c.ct);
-    else if (sx == 0)
-      slot = 4 + ((int)((int64_t)rbw - (int64_t)c.rb) + 1) * 3 + (int)((int64_t)ctw - (int64_t)c.ct) + 1;
-    const uint64_t g = SG[slot];
-    const uint32_t li = (uint32_t)(((uint64_t)rr % S.RB) * S.CW + ((uint64_t)j % S.CW));
-    const uint32_t wl = li >> 5, bmask = (1u << (li & 31)) - 1u, bit = 1u << (li & 31);
-    const uint64_t capg = g * (uint64_t)S.RB * S.CW + (uint64_t)wl * 32;
-    const PlaneDesc* pds = D.s[sx].p;
-    uint32_t nv[32];
+    const int RB = sx == 2 ? BR : BR / 2;
+    const int CW = (int)S.CW;  // G::CWD, or the whole (short) row when nct == 1
+    const int ctw = CW == G::CWD ? (int)((unsigned)j / G::CWD) : 0;
+    const int rbw = sx == 2 ? (int)((unsigned)rr / BR) : (int)((unsigned)rr / (BR / 2));
+    int sl = 0;
+    if (sx == 1) sl = 2 + (ctw - (int)c.ct);
+    else if (sx == 0) sl = 4 + (rbw - (int)c.rb + 1) * 3 + (ctw - (int)c.ct) + 1;
+    const int li = (rr - rbw * RB) * CW + (j - ctw * CW);
+    const int wl = li >> 5;
+    const uint32_t bit = 1u << (li & 31), below = bit - 1u;
+    const uint32_t km = s_km[sx];
+    const uint32_t* sb = &SB[sl][0][wl];
+    const uint32_t* const* sp = SP[sl];
+    const uint32_t off = (uint32_t)wl * 32;
+    uint32_t* QHr = QH + (sx == 1 ? qrow : G::H1 + qrow) * 4;
+    uint32_t* Qr = (sx == 2 ? Q2 : (sx == 1 ? Q1 : Q0)) + qrow * G::QP + (j - cw0) * 36;
+    if (w16) {
+      uint32_t a[16];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      const uint32_t m = SB[slot][k][wl];  // zero for unselected / empty planes
-      nv[k] = (m & bit) ? __ldg(cap + pds[k].cap_off + capg + __popc(m & bmask)) : 0u;
-    }
-    xor_decode_planes(nv, b);
-    transpose32(nv);
-    if (sx == 2) {
-      const int lj = (int)(j - (int64_t)c.ct * S2.CW);
+      for (int i = 0; i < 16; ++i) {
+        const int k = wb + i;
+        uint32_t w = 0u;
+        if ((km >> k) & 1u) {
+          const uint32_t m = sb[k * kMaxBw];
+          if (m & bit) w = __ldg(sp[k] + off + __popc(m & below));
+        }
+        a[i] = w;
+      }
 #pragma unroll
-      for (int i = 0; i < 32; ++i) Q2[lr * G::PITCH + lj * 33 + i] = nv[i];
+      for (int i = 15; i >= 0; --i) {
+        const uint32_t p1 = i + 1 < 16 ? a[i + 1] : 0u, p2 = i + 2 < 16 ? a[i + 2] : 0u;
+        a[i] = wb + i >= b ? (a[i] ^ p1 ^ p2) : 0u;
+      }
+      if (side < 0) {
+        transpose16x2(a);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          reinterpret_cast<uint4*>(Qr)[m] =
+              make_uint4((a[4 * m] & 0xFFFFu) << wb, (a[4 * m + 1] & 0xFFFFu) << wb,
+                         (a[4 * m + 2] & 0xFFFFu) << wb, (a[4 * m + 3] & 0xFFFFu) << wb);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          reinterpret_cast<uint4*>(Qr)[4 + m] =
+              make_uint4((a[4 * m] >> 16) << wb, (a[4 * m + 1] >> 16) << wb,
+                         (a[4 * m + 2] >> 16) << wb, (a[4 * m + 3] >> 16) << wb);
+      } else {
+        uint32_t v0 = 0u, v1 = 0u;
+        const int i0 = side ? 0 : 31;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          v0 |= ((a[i] >> i0) & 1u) << i;
+          v1 |= ((a[i] >> 1) & 1u) << i;
+        }
+        if (side) {
+          QHr[1] = v0 << wb;
+          QHr[2] = v1 << wb;
+        } else {
+          QHr[0] = v0 << wb;
+        }
+      }
     } else {
-      // keep the codes of the halo window: code column C0/2 - 1 + e, e < VEC
-      uint32_t* Qr = (sx == 1 ? Q1 : Q0) + lr * G::QEP;
-      const int base = (int)(j * 32 - ((c.C0 >> 1) - 1));
+      uint32_t a[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int e = base + i;
-        if (e >= 0 && e < G::VEC) Qr[sw(e)] = nv[i];
+      for (int k = 0; k < 32; ++k) {
+        uint32_t w = 0u;
+        if ((km >> k) & 1u) {
+          const uint32_t m = sb[k * kMaxBw];
+          if (m & bit) w = __ldg(sp[k] + off + __popc(m & below));
+        }
+        a[k] = w;
+      }
+      xor_decode_planes(a, b);
+      if (side < 0) {
+        transpose32(a);
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          reinterpret_cast<uint4*>(Qr)[m] = make_uint4(a[4 * m], a[4 * m + 1], a[4 * m + 2], a[4 * m + 3]);
+      } else {
+        uint32_t v0 = 0u, v1 = 0u;
+        const int i0 = side ? 0 : 31;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          v0 |= ((a[k] >> i0) & 1u) << k;
+          v1 |= ((a[k] >> 1) & 1u) << k;
+        }
+        if (side) {
+          QHr[1] = v0;
+          QHr[2] = v1;
+        } else {
+          QHr[0] = v0;
+        }
       }
     }
   }
   __syncthreads();
 
-  // Phase 1: even rows of VE (sweep 0 of an odd plane, else known points).
-  const int64_t so = L.s * L.stride[0];
-  const bool r1 = c.P + 1 <= M0 - 1;
-  const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
+  // Phase 1: even value rows (sweep 0 of an odd plane, else known points).
+  // Column slot js < HC is own code column js (value column js + 1); the
+  // three halo columns (value columns 0, HC+1, HC+2) are spread over threads.
+  {
+    const int64_t so = L.s * L.stride[0];
+    const bool r1 = c.P + 1 <= M0 - 1;
+    const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
+    const bool has0 = S0.out_end > S0.out_begin;
+    auto item = [&](int je, int jr, uint32_t n) {
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
+      const T* p = out + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s;
+      T v;
+      if (!podd) {
+        v = __ldg(p);
+      } else {
+        const T bb = __ldg(p - so);
+        const T cc = r1 ? __ldg(p + so) : bb;
+        const T a = r3 ? __ldg(p - 3 * so) : bb;
+        const T d = r3 ? __ldg(p + 3 * so) : bb;
+        const T pred = pred4<T>(a, bb, cc, d, c.P, M0, cubic);
+        v = FP<T>::add(pred, FP<T>::mul(code_value(n, T()), twoeb));
+        if (has0) {
+          const uint64_t ci = ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
+                              (uint64_t)(c2 >> 1);
+          find_outlier<T>(S0, oidx, oval, ci, &v);
+        }
+      }
+      VE[(2 * jr) * G::VP + je] = v;
+    };
+    {
+      const int js = tid, je = js + 1, c2 = c.C0 + 2 * js;
+      if (c2 < M2) {
 #pragma unroll 2
-  for (int it = tid; it < (BR / 2 + 3) * G::VEC; it += 256) {
-    const int jr = it / G::VEC, je = it - jr * G::VEC;
-    const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-    if (c1 < 0 || c1 >= M1 || c2 < 0 || c2 >= M2 || c2 > c.C1 + 2) continue;
-    const int64_t e = eidx(L, c, c1, c2);
-    T v;
-    if (!podd) {
-      v = __ldg(out + e);
-    } else {
-      const T bb = __ldg(out + e - so);
-      const T cc = r1 ? __ldg(out + e + so) : bb;
-      const T a = r3 ? __ldg(out + e - 3 * so) : bb;
-      const T d = r3 ? __ldg(out + e + 3 * so) : bb;
-      const T pred = pred4<T>(a, bb, cc, d, c.P, M0, cubic);
-      const int64_t q = negabinary_inv(Q0[jr * G::QEP + sw(je)]);
-      v = FP<T>::add(pred, FP<T>::mul(FP<T>::from_code(q), twoeb));
-      if (S0.out_end > S0.out_begin) {
-        const uint64_t ci = ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
+        for (int jr = 0; jr < G::H0; ++jr) {
+          const int c1 = c.R0 - 2 + 2 * jr;
+          if (c1 < 0 || c1 >= M1) continue;
+          item(je, jr, podd ? Q0[jr * G::QP + qoff(js)] : 0u);
+        }
+      }
+    }
+    if (tid < 3 * G::H0) {
+      const int h = tid / G::H0, jr = tid - h * G::H0;
+      const int je = h == 0 ? 0 : G::HC + h;
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
+      if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2)
+        item(je, jr, podd ? QH[(G::H1 + jr) * 4 + h] : 0u);
+    }
+  }
+  __syncthreads();
+
+  // Phase 2: sweep 1 on the odd rows, columns [C0-2, C1+2].
+  {
+    const bool has1 = S1.out_end > S1.out_begin;
+    auto value = [&](T a, T bb, T cc, T d, int c1, int c2, uint32_t n) {
+      const T pred = pred4<T>(a, bb, cc, d, c1, M1, cubic);
+      T v = FP<T>::add(pred, FP<T>::mul(code_value(n, T()), twoeb));
+      if (has1) {
+        const uint64_t ci = ((uint64_t)c.P * S1.m1 + (uint64_t)((c1 - 1) >> 1)) * S1.m2 +
                             (uint64_t)(c2 >> 1);
-        find_outlier<T>(S0, oidx, oval, ci, &v);
+        find_outlier<T>(S1, oidx, oval, ci, &v);
+      }
+      return v;
+    };
+    if (S1.present) {
+      const int js = tid, c2 = c.C0 + 2 * js;
+      if (c2 < M2) {
+        T* col = VE + js + 1;
+        T a = col[0], bb = col[2 * G::VP], cc = col[4 * G::VP];
+        for (int jr = 0; jr < G::H1; ++jr) {
+          const int c1 = c.R0 + 1 + 2 * jr;
+          if (c1 >= c.R1) break;
+          const T d = col[(2 * jr + 6) * G::VP];
+          col[(2 * jr + 3) * G::VP] = value(a, bb, cc, d, c1, c2, Q1[jr * G::QP + qoff(js)]);
+          a = bb;
+          bb = cc;
+          cc = d;
+        }
+      }
+      if (tid < 3 * G::H1) {
+        const int h = tid / G::H1, jr = tid - h * G::H1;
+        const int je = h == 0 ? 0 : G::HC + h;
+        const int c1 = c.R0 + 1 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
+        if (c1 < c.R1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) {
+          const T* col = VE + je;
+          VE[(2 * jr + 3) * G::VP + je] =
+              value(col[(2 * jr) * G::VP], col[(2 * jr + 2) * G::VP], col[(2 * jr + 4) * G::VP],
+                    col[(2 * jr + 6) * G::VP], c1, c2, QH[jr * 4 + h]);
+        }
       }
     }
-    VE[(2 * jr) * G::VEC + je] = v;
   }
   __syncthreads();
 
-  // Phase 2: sweep 1.
-#pragma unroll 2
-  for (int it = tid; it < (BR / 2) * G::VEC; it += 256) {
-    const int jr = it / G::VEC, je = it - jr * G::VEC;
-    const int c1 = c.R0 + 1 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-    if (c1 >= c.R1 || c2 < 0 || c2 >= M2 || c2 > c.C1 + 2) continue;
-    const T bb = VE[(2 * jr + 2) * G::VEC + je];
-    const T cc = VE[(2 * jr + 4) * G::VEC + je];
-    const T a = VE[(2 * jr) * G::VEC + je];
-    const T d = VE[(2 * jr + 6) * G::VEC + je];
-    const T pred = pred4<T>(a, bb, cc, d, c1, M1, cubic);
-    const int64_t q = negabinary_inv(Q1[jr * G::QEP + sw(je)]);
-    T v = FP<T>::add(pred, FP<T>::mul(FP<T>::from_code(q), twoeb));
-    if (S1.out_end > S1.out_begin) {
-      const uint64_t ci = ((uint64_t)c.P * S1.m1 + (uint64_t)((c1 - 1) >> 1)) * S1.m2 +
-                          (uint64_t)(c2 >> 1);
-      find_outlier<T>(S1, oidx, oval, ci, &v);
+  // Phase 3: sweep 2 and the output. Thread: four odd columns (code columns
+  // 4g .. 4g+3) of the rows rq, rq+4, ...
+  {
+    const bool has2 = S2.out_end > S2.out_begin;
+    const int g = tid & 63, rq = tid >> 6;
+    const int c2e = c.C0 + 8 * g;  // first (even) lattice column of the run
+    if (c2e < c.C1) {
+      for (int lr = rq; lr < BR; lr += 4) {
+        const int c1 = c.R0 + lr;
+        if (c1 >= c.R1) break;
+        T w[8];
+        lds8<T>(VE + (lr + 2) * G::VP + 4 * g, w);
+        const uint4 qn = *reinterpret_cast<const uint4*>(Q2 + lr * G::QP + qoff(4 * g));
+        const uint32_t qa[4] = {qn.x, qn.y, qn.z, qn.w};
+        T v[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c2o = c2e + 2 * k + 1;
+          v[2 * k] = w[k + 1];
+          T vo = w[k + 1];
+          if (c2o < c.C1) {
+            const T pred = pred4<T>(w[k], w[k + 1], w[k + 2], w[k + 3], c2o, M2, cubic);
+            vo = FP<T>::add(pred, FP<T>::mul(code_value(qa[k], T()), twoeb));
+            if (has2) {
+              const uint64_t ci =
+                  ((uint64_t)c.P * S2.m1 + (uint64_t)c1) * S2.m2 + (uint64_t)((c2o - 1) >> 1);
+              find_outlier<T>(S2, oidx, oval, ci, &vo);
+            }
+          }
+          v[2 * k + 1] = vo;
+        }
+        store_run<T>(out + c.pbase + (int64_t)c1 * c.rs, L, c2e, c.C1, v);
+      }
     }
-    VE[(2 * jr + 3) * G::VEC + je] = v;
   }
-  __syncthreads();
-
-  // Phase 3: sweep 2.
-#pragma unroll 4
-  for (int it = tid; it < BR * G::HC; it += 256) {
-    const int lr = it / G::HC, jo = it - lr * G::HC;
-    const int c1 = c.R0 + lr, c2 = c.C0 + 1 + 2 * jo;
-    if (c1 >= c.R1 || c2 >= c.C1) continue;
-    const T* row = VE + (lr + 2) * G::VEC;
-    const T pred = pred4<T>(row[jo], row[jo + 1], row[jo + 2], row[jo + 3], c2, M2, cubic);
-    const int64_t q = negabinary_inv(Q2[lr * G::PITCH + sw(jo)]);
-    T v = FP<T>::add(pred, FP<T>::mul(FP<T>::from_code(q), twoeb));
-    if (S2.out_end > S2.out_begin) {
-      const uint64_t ci = ((uint64_t)c.P * S2.m1 + (uint64_t)c1) * S2.m2 + (uint64_t)((c2 - 1) >> 1);
-      find_outlier<T>(S2, oidx, oval, ci, &v);
-    }
-    VO[lr * G::HC + jo] = v;
-  }
-  __syncthreads();
-
-  // Phase 3b: write the plane tile (every lattice point of the CTA).
-  store_tile<T, BR, G::HC, G::VEC>(L, c, VE, VO, out);
 }
 
 // Single-field kernels: arguments in the parameter space.
@@ -604,7 +849,7 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
 }
 
 template <class T, int BR, int BC>
-__global__ void __launch_bounds__(256, 2) k_level_retrieve(LevelArgs L, T* out, T twoeb, int b,
+__global__ void __launch_bounds__(256, 3) k_level_retrieve(LevelArgs L, T* out, T twoeb, int b,
                                                            const uint32_t* __restrict__ cap,
                                                            const uint32_t* __restrict__ bm,
                                                            const uint64_t* __restrict__ oidx,
@@ -643,7 +888,7 @@ __global__ void __launch_bounds__(256, 3) k_level_compress_batch(
 }
 
 template <class T, int BR, int BC>
-__global__ void __launch_bounds__(256, 2) k_level_retrieve_batch(
+__global__ void __launch_bounds__(256, 3) k_level_retrieve_batch(
     const RetrieveEntry* __restrict__ ents, int n) {
   extern __shared__ __align__(16) unsigned char smem[];
   const RetrieveEntry& e = find_entry(ents, n);
@@ -658,9 +903,8 @@ size_t smem_compress() {
 }
 template <class T, int BR, int BC>
 size_t smem_retrieve() {
-  typedef Tile<BR, BC> G;
-  return sizeof(T) * (G::VR * G::VEC + BR * G::HC) +
-         4 * (BR * G::PITCH + (BR / 2) * G::QEP + (BR / 2 + 3) * G::QEP);
+  typedef RTile<BR, BC> G;
+  return sizeof(T) * G::VR * G::VP + 4 * ((BR + G::H1 + G::H0) * G::QP + (G::H1 + G::H0) * 4);
 }
 
 template <class T, int BR, int BC>
