@@ -54,12 +54,21 @@ template <> struct FP<double> {
 // Value of a (possibly truncated) negabinary code in the element type,
 // exactly: codes below 2^31 convert in 32-bit integer arithmetic (their
 // value lies in (-2^31, 2^31)), small ones by the magic-number trick.
+static __device__ __noinline__ float code_value_wide(uint32_t n) {
+  return __ll2float_rn((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
+}
+// 1 if the code's value needs the wide conversion (|q| >= 2^22 or n >= 2^31).
+__device__ __forceinline__ unsigned code_wide(uint32_t n, int* q) {
+  *q = (int)((n ^ 0xAAAAAAAAu) - 0xAAAAAAAAu);
+  return (n >> 31) | ((unsigned)(*q + (1 << 22)) >> 23);
+}
+__device__ __forceinline__ float code_small(int q) {
+  return __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f);
+}
 __device__ __forceinline__ float code_value(uint32_t n, float) {
-  if (n >> 31) return __ll2float_rn((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
-  const int q = (int)((n ^ 0xAAAAAAAAu) - 0xAAAAAAAAu);
-  if ((unsigned)(q + (1 << 22)) < (1u << 23))
-    return __fsub_rn(__int_as_float(0x4B400000 + q), 12582912.0f);
-  return __int2float_rn(q);
+  int q;
+  if (code_wide(n, &q) == 0u) return code_small(q);
+  return code_value_wide(n);
 }
 __device__ __forceinline__ double code_value(uint32_t n, double) {
   return __ll2double_rn((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
@@ -137,6 +146,15 @@ __device__ __forceinline__ void xor_decode_planes(uint32_t (&p)[32], int b) {
     const uint32_t p1 = k + 1 < 32 ? p[k + 1] : 0u, p2 = k + 2 < 32 ? p[k + 2] : 0u;
     p[k] = k >= b ? (p[k] ^ p1 ^ p2) : 0u;
   }
+}
+
+// Asynchronous 4-byte global -> shared copy (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {

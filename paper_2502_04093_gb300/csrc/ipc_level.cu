@@ -391,19 +391,22 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
 // Reconstruction of one level (Algorithm 1).
 //
 // Setup: warp 0 finds the planes to load (plane k >= b with nonzero words in
-// the stage) and the top loaded plane; the CTA stages, for the loaded planes
-// of at most 13 segments (its own, and for halo targets the neighbouring
-// segments: stage 1 left/right, stage 0 the 3x3 block), the group bitmap
-// words and the payload base. A word's plane value is then found from its
-// group's bitmap word alone (rank = population below its bit).
+// the stage) and the top loaded plane; the CTA starts asynchronous copies,
+// for the loaded planes of at most 13 segments (its own, and for halo
+// targets the neighbouring segments: stage 1 left/right, stage 0 the 3x3
+// block), of the group bitmap words, and notes the payload bases. A word's
+// plane value is then found from its group's bitmap word alone (rank =
+// population below its bit).
+// Phase 1a (while the copies land): even value rows -- the sweep-0
+//   predictions of an odd plane from the known planes P +- 1, P +- 3, or the
+//   known points of an even plane; one column per thread.
 // Phase 0: one thread per word of the tile's own code columns: load the
 //   selected planes, undo the predictive XOR top-down, transpose (a 16-plane
 //   window when the loaded planes span at most 16, else all 32) and store the
 //   32 codes. The three halo code columns (one left, two right) are extracted
 //   bit by bit from their words without a transpose.
-// Phase 1: even value rows (sweep 0 of an odd plane from the known planes
-//   P +- 1, P +- 3, or the known points of an even plane), one column per
-//   thread.
+// Phase 1b (odd planes): add the sweep-0 codes to the predictions -- the same
+//   two operations, in the same order, as when they follow at once.
 // Phase 2: odd value rows (sweep 1), one column per thread, the four row
 //   neighbours kept in registers.
 // Phase 3: sweep 2 fused with the output: each thread computes four odd
@@ -428,6 +431,25 @@ struct RTile {
 // block, so that one thread's 32 codes are eight conflict-free 16-byte
 // stores and four consecutive codes one 16-byte load.
 __device__ __forceinline__ int qoff(int e) { return (e >> 5) * 36 + (e & 31); }
+
+// Values of four codes: the small-code conversion when all four allow it.
+__device__ __forceinline__ void code_values4(const uint32_t (&n)[4], float (&v)[4]) {
+  int q[4];
+  unsigned wide = 0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) wide |= code_wide(n[k], &q[k]);
+  if (wide == 0u) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = code_small(q[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = code_value(n[k], 0.0f);
+  }
+}
+__device__ __forceinline__ void code_values4(const uint32_t (&n)[4], double (&v)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = code_value(n[k], 0.0);
+}
 
 template <class T>
 __device__ __forceinline__ void lds8(const T* p, T (&w)[8]);
@@ -575,8 +597,51 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const PlaneDesc& pd = D.s[sx].p[k];
     SP[sl][k] = cap + pd.cap_off + g * (uint64_t)S.RB * S.CW;
     const uint32_t* bp = bm + pd.bm_off + g * S.bw;
-    for (int v = 0; v < (int)S.bw; ++v) SB[sl][k][v] = __ldg(bp + v);
+    for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[sl][k][v], bp + v);
   }
+
+  // Phase 1a: even value rows -- the sweep-0 predictions of an odd plane
+  // (its codes are added in phase 1b), or the known points of an even plane.
+  // Column slot js < HC is own code column js (value column js + 1); the
+  // three halo columns (value columns 0, HC+1, HC+2) are spread over threads.
+  const bool has0 = S0.out_end > S0.out_begin;
+  {
+    const int64_t so = L.s * L.stride[0];
+    const bool r1 = c.P + 1 <= M0 - 1;
+    const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
+    auto item = [&](int je, int jr) {
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
+      const T* p = out + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s;
+      T v;
+      if (!podd) {
+        v = __ldg(p);
+      } else {
+        const T bb = __ldg(p - so);
+        const T cc = r1 ? __ldg(p + so) : bb;
+        const T a = r3 ? __ldg(p - 3 * so) : bb;
+        const T d = r3 ? __ldg(p + 3 * so) : bb;
+        v = pred4<T>(a, bb, cc, d, c.P, M0, cubic);
+      }
+      VE[(2 * jr) * G::VP + je] = v;
+    };
+    {
+      const int js = tid, c2 = c.C0 + 2 * js;
+      if (c2 < M2) {
+#pragma unroll 4
+        for (int jr = 0; jr < G::H0; ++jr) {
+          const int c1 = c.R0 - 2 + 2 * jr;
+          if (c1 >= 0 && c1 < M1) item(js + 1, jr);
+        }
+      }
+    }
+    if (tid < 3 * G::H0) {
+      const int h = tid / G::H0, jr = tid - h * G::H0;
+      const int je = h == 0 ? 0 : G::HC + h;
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
+      if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) item(je, jr);
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
 
   // Phase 0: decode the words of the tile's code columns.
@@ -709,43 +774,26 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   }
   __syncthreads();
 
-  // Phase 1: even value rows (sweep 0 of an odd plane, else known points).
-  // Column slot js < HC is own code column js (value column js + 1); the
-  // three halo columns (value columns 0, HC+1, HC+2) are spread over threads.
-  {
-    const int64_t so = L.s * L.stride[0];
-    const bool r1 = c.P + 1 <= M0 - 1;
-    const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
-    const bool has0 = S0.out_end > S0.out_begin;
+  // Phase 1b: the codes of sweep 0 (odd planes), over the items of phase 1a.
+  if (podd) {
     auto item = [&](int je, int jr, uint32_t n) {
-      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-      const T* p = out + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s;
-      T v;
-      if (!podd) {
-        v = __ldg(p);
-      } else {
-        const T bb = __ldg(p - so);
-        const T cc = r1 ? __ldg(p + so) : bb;
-        const T a = r3 ? __ldg(p - 3 * so) : bb;
-        const T d = r3 ? __ldg(p + 3 * so) : bb;
-        const T pred = pred4<T>(a, bb, cc, d, c.P, M0, cubic);
-        v = FP<T>::add(pred, FP<T>::mul(code_value(n, T()), twoeb));
-        if (has0) {
-          const uint64_t ci = ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
-                              (uint64_t)(c2 >> 1);
-          find_outlier<T>(S0, oidx, oval, ci, &v);
-        }
+      T* p = VE + (2 * jr) * G::VP + je;
+      T v = FP<T>::add(*p, FP<T>::mul(code_value(n, T()), twoeb));
+      if (has0) {
+        const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
+        const uint64_t ci = ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
+                            (uint64_t)(c2 >> 1);
+        find_outlier<T>(S0, oidx, oval, ci, &v);
       }
-      VE[(2 * jr) * G::VP + je] = v;
+      *p = v;
     };
     {
-      const int js = tid, je = js + 1, c2 = c.C0 + 2 * js;
+      const int js = tid, c2 = c.C0 + 2 * js;
       if (c2 < M2) {
-#pragma unroll 2
+#pragma unroll 4
         for (int jr = 0; jr < G::H0; ++jr) {
           const int c1 = c.R0 - 2 + 2 * jr;
-          if (c1 < 0 || c1 >= M1) continue;
-          item(je, jr, podd ? Q0[jr * G::QP + qoff(js)] : 0u);
+          if (c1 >= 0 && c1 < M1) item(js + 1, jr, Q0[jr * G::QP + qoff(js)]);
         }
       }
     }
@@ -754,10 +802,10 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       const int je = h == 0 ? 0 : G::HC + h;
       const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
       if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2)
-        item(je, jr, podd ? QH[(G::H1 + jr) * 4 + h] : 0u);
+        item(je, jr, QH[(G::H1 + jr) * 4 + h]);
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   // Phase 2: sweep 1 on the odd rows, columns [C0-2, C1+2].
   {
@@ -808,6 +856,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const bool has2 = S2.out_end > S2.out_begin;
     const int g = tid & 63, rq = tid >> 6;
     const int c2e = c.C0 + 8 * g;  // first (even) lattice column of the run
+    const bool interior = c2e + 8 <= c.C1 && (cubic ? (c2e >= 2 && c2e + 10 <= M2 - 1)
+                                                     : c2e + 8 <= M2 - 1);
     if (c2e < c.C1) {
       for (int lr = rq; lr < BR; lr += 4) {
         const int c1 = c.R0 + lr;
@@ -817,21 +867,46 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         const uint4 qn = *reinterpret_cast<const uint4*>(Q2 + lr * G::QP + qoff(4 * g));
         const uint32_t qa[4] = {qn.x, qn.y, qn.z, qn.w};
         T v[8];
+        if (interior) {
+          // all four targets have every stencil neighbour inside the row
+          T val[4];
+          code_values4(qa, val);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int c2o = c2e + 2 * k + 1;
-          v[2 * k] = w[k + 1];
-          T vo = w[k + 1];
-          if (c2o < c.C1) {
-            const T pred = pred4<T>(w[k], w[k + 1], w[k + 2], w[k + 3], c2o, M2, cubic);
-            vo = FP<T>::add(pred, FP<T>::mul(code_value(qa[k], T()), twoeb));
-            if (has2) {
+          for (int k = 0; k < 4; ++k) {
+            T pred;
+            if (cubic) {
+              const T u = FP<T>::add(w[k + 1], w[k + 2]);
+              const T z = FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3]));
+              pred = FP<T>::mul(z, (T)0.0625);
+            } else {
+              pred = FP<T>::mul(FP<T>::add(w[k + 1], w[k + 2]), (T)0.5);
+            }
+            v[2 * k] = w[k + 1];
+            v[2 * k + 1] = FP<T>::add(pred, FP<T>::mul(val[k], twoeb));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int c2o = c2e + 2 * k + 1;
+            v[2 * k] = w[k + 1];
+            T vo = w[k + 1];
+            if (c2o < c.C1) {
+              const T pred = pred4<T>(w[k], w[k + 1], w[k + 2], w[k + 3], c2o, M2, cubic);
+              vo = FP<T>::add(pred, FP<T>::mul(code_value(qa[k], T()), twoeb));
+            }
+            v[2 * k + 1] = vo;
+          }
+        }
+        if (has2) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int c2o = c2e + 2 * k + 1;
+            if (c2o < c.C1) {
               const uint64_t ci =
                   ((uint64_t)c.P * S2.m1 + (uint64_t)c1) * S2.m2 + (uint64_t)((c2o - 1) >> 1);
-              find_outlier<T>(S2, oidx, oval, ci, &vo);
+              find_outlier<T>(S2, oidx, oval, ci, &v[2 * k + 1]);
             }
           }
-          v[2 * k + 1] = vo;
         }
         store_run<T>(out + c.pbase + (int64_t)c1 * c.rs, L, c2e, c.C1, v);
       }
