@@ -114,6 +114,17 @@ int ipc_free(void* handle);
 int ipc_selection(const ipc_view* v, int* b_per_level, int* nlevels,
                   uint64_t* bytes, double* guaranteed_bound);
 
+/* ipc_select_container -- the selection of ipc_retrieve (Sec. 5.2 eb mode,
+ * Sec. 5.3 bitrate mode) computed on the host from a container's leading
+ * bytes alone: the header, the stage table and the plane-size table (the
+ * outlier lists need not be present). No device work and no device needed;
+ * it tells which plane streams of a stored container a retrieval reads.
+ * Outputs as for ipc_selection (b_per_level: at least 64 ints, may be NULL).
+ * Errors: IPC_EINVAL (null buffer, bad target), IPC_ECORRUPT (the leading
+ * bytes are not a valid header or are too short), IPC_EBOUND, IPC_EBUDGET. */
+int ipc_select_container(const void* buf, uint64_t len, ipc_target target, int* b_per_level,
+                         int* nlevels, uint64_t* bytes, double* guaranteed_bound);
+
 /* ipc_compressed_size -- bytes of the exported container. */
 int ipc_compressed_size(const ipc_field* f, uint64_t* bytes);
 

@@ -18,6 +18,7 @@
 
 #include "ipc.h"
 #include "ipc_internal.h"
+#include "ipc_select.h"
 #include "ipc_serve_internal.h"
 
 using namespace ipc;
@@ -116,7 +117,6 @@ const uint32_t kMagic = 0x31435049u;  // "IPC1"
 const uint32_t kVersion = 1u;
 const uint32_t kFieldTag = 0x46435049u, kViewTag = 0x56435049u, kPlanTag = 0x50435049u;
 const uint32_t kDeadTag = 0xDEADDEADu;
-const uint64_t kSaturate = 1ull << 62;
 
 }  // namespace
 
@@ -755,260 +755,39 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
 }
 
 // ---------------------------------------------------------------------------
-// Optimized loader (Sec. 5.2 / 5.3): exact knapsack over the levels on the
-// Pareto frontier of (error cost, loaded bytes).
-// Cost of dropping b planes at level l, in units of eb * 2^-16:
-//   M(t, b) = 0 (b = 0) | U(b) (b <= H_t) | Q_t (b > H_t), U the negabinary
-//   uncertainty of b digits (Sec. 4.4.2).
-//   strict: sum_{t in l} ceil(p^(S-1-t) * M * bin * 2^16) + [b > 0] rho_l,
-//           rho_l = ceil(kappa * u * (A / eb) * 2^16 * sum_{t: level <= l} p^(S-1-t))
-//   paper : ceil(p^(l-1) * max_{t in l} M * bin * 2^16)   (Theorem 1)
-// with bin = fl(2eb) / eb, kappa = 24 (cubic) / 12 (linear), u the unit
-// roundoff of the element type, A a bound on the magnitudes involved.
+// Optimized loader (Sec. 5.2 / 5.3): the field's stage statistics and plane
+// sizes go to the host selector (ipc_select.cu).
 // ---------------------------------------------------------------------------
-uint64_t sadd(uint64_t a, uint64_t b) {
-  const uint64_t c = a + b;
-  return (c < a || c > kSaturate) ? kSaturate : c;
-}
-uint64_t units(double v) {
-  if (!(v < (double)kSaturate)) return kSaturate;
-  return v <= 0 ? 0 : (uint64_t)std::ceil(v);
-}
-uint64_t uncert(int b) {
-  if (b <= 0) return 0;
-  const uint64_t p = uint64_t(1) << (b + 1);
-  return (b & 1) ? (p - 1) / 3 : (p - 2) / 3;
-}
-
-struct Tables {
-  int K;
-  std::vector<uint64_t> cost, bytes;  // [l-1][b]
-};
-
-void build_tables(const ipc_field* f, double A, Tables* T) {
-  const Geo& g = f->g;
-  const int K = g.K, S = (int)g.stages.size();
-  const bool cubic = f->interp == IPC_CUBIC, strict = f->bound == IPC_BOUND_STRICT;
-  const double p = cubic ? 1.25 : 1.0;
-  std::vector<double> pw(std::max(S, K) + 1);
-  pw[0] = 1.0;
-  for (size_t i = 1; i < pw.size(); ++i) pw[i] = pw[i - 1] * p;
-  const double bin = bin_width(f) / f->eb;
-  const double u = f->dtype == 0 ? 1.0 / 16777216.0 : 1.0 / 9007199254740992.0;
-  const double kappa = cubic ? 24.0 : 12.0;
-  T->K = K;
-  T->cost.assign((size_t)K * 33, 0);
-  T->bytes.assign((size_t)K * 33, 0);
-  for (int l = 1; l <= K; ++l) {
-    double asum = 0;
-    for (int t = 0; t < S; ++t)
-      if (g.stages[t].level <= l) asum += (strict && cubic) ? pw[S - 1 - t] : 1.0;
-    const uint64_t rho = units(kappa * u * (A / f->eb) * 65536.0 * asum);
-    for (int b = 0; b <= 32; ++b) {
-      uint64_t c = 0, y = 0, mmax = 0;
-      for (int t = 0; t < S; ++t) {
-        if (g.stages[t].level != l) continue;
-        const StageTab& s = f->st[t];
-        const uint64_t M = b <= 0 ? 0 : (b <= s.H ? uncert(b) : (uint64_t)s.Q);
-        if (strict) c = sadd(c, units((cubic ? pw[S - 1 - t] : 1.0) * (double)M * bin * 65536.0));
-        else mmax = std::max(mmax, M);
-        for (int k = b; k < 32; ++k) y += s.size[k];
-      }
-      if (strict) {
-        if (b > 0) c = sadd(c, rho);
-      } else {
-        c = units(pw[l - 1] * (double)mmax * bin * 65536.0);
-      }
-      T->cost[(size_t)(l - 1) * 33 + b] = c;
-      T->bytes[(size_t)(l - 1) * 33 + b] = y;
-    }
+SelInput sel_input(const ipc_field* f) {
+  SelInput in;
+  in.K = f->g.K;
+  in.dtype = f->dtype;
+  in.interp = f->interp;
+  in.bound = f->bound;
+  in.eb_mode = f->eb_mode;
+  in.eb = f->eb;
+  in.bin = bin_width(f) / f->eb;
+  in.xmin = f->xmin;
+  in.xmax = f->xmax;
+  in.xmaxabs = f->xmaxabs;
+  in.n = f->g.n;
+  in.mandatory = f->mandatory;
+  in.st.resize(f->g.stages.size());
+  for (size_t t = 0; t < in.st.size(); ++t) {
+    SelStage& s = in.st[t];
+    s.level = f->g.stages[t].level;
+    s.H = f->st[t].H;
+    s.Q = f->st[t].Q;
+    std::memcpy(s.size, f->st[t].size, sizeof(s.size));
   }
-}
-
-// Exact solver (meet in the middle). Every option of a level is a point
-// (cost, bytes); bytes fall strictly with b (each stream is >= 4 bytes), so an
-// option with a larger-b alternative of no greater cost can never be part of
-// an optimum and is dropped. The levels are split in two halves; each half's
-// Pareto frontier (cost ascending, bytes descending; equal points keep the
-// lexicographically larger part-vector) is built level by level, and the two
-// frontiers are joined with a binary search per entry of the first half.
-// Ties: eb mode -> fewer bytes, then smaller cost, then the lexicographically
-// larger (b_1, b_2, ...); bitrate mode -> smaller cost, then fewer bytes,
-// then the same lexicographic rule.
-struct Part {
-  uint64_t c, y;
-  uint8_t b[64];
-};
-
-void half_frontier(const Tables& T, int l0, int l1, int kind, uint64_t limit,
-                   const std::vector<int>* upper, std::vector<Part>* out) {
-  const int n = l1 - l0;
-  std::vector<Part> F(1);
-  F[0].c = 0;
-  F[0].y = 0;
-  std::memset(F[0].b, 0, sizeof(F[0].b));
-  std::vector<Part> G;
-  for (int l = l0; l < l1; ++l) {
-    const int bmax = upper ? (*upper)[l] : 32;
-    int opt[33];
-    int nopt = 0;
-    uint64_t best = ~uint64_t(0);
-    for (int b = bmax; b >= 0; --b) {  // staircase: keep b only if strictly cheaper
-      const uint64_t c = T.cost[(size_t)l * 33 + b];
-      if (c < best) {
-        opt[nopt++] = b;
-        best = c;
-      }
-    }
-    G.clear();
-    G.reserve(F.size() * nopt);
-    for (const Part& e : F)
-      for (int i = 0; i < nopt; ++i) {
-        const int b = opt[i];
-        Part p = e;
-        p.c = sadd(e.c, T.cost[(size_t)l * 33 + b]);
-        p.y = e.y + T.bytes[(size_t)l * 33 + b];
-        if ((kind == 0 && p.c > limit) || (kind == 1 && p.y > limit)) continue;
-        p.b[l - l0] = (uint8_t)b;
-        G.push_back(p);
-      }
-    const int len = l - l0 + 1;
-    std::sort(G.begin(), G.end(), [len](const Part& x, const Part& z) {
-      if (x.c != z.c) return x.c < z.c;
-      if (x.y != z.y) return x.y < z.y;
-      return std::memcmp(x.b, z.b, len) > 0;
-    });
-    F.clear();
-    for (const Part& e : G)
-      if (F.empty() || e.y < F.back().y) F.push_back(e);
-    if (F.empty()) break;
-  }
-  (void)n;
-  *out = std::move(F);
-}
-
-int solve(const Tables& T, int kind, uint64_t limit, const std::vector<int>* upper,
-          std::vector<int>* best) {
-  const int K = T.K;
-  if (K == 0) {
-    best->clear();
-    return IPC_OK;
-  }
-  if (K > 64) return IPC_EINVAL;
-  const int h = K / 2;
-  std::vector<Part> A, B;
-  half_frontier(T, 0, h, kind, limit, upper, &A);
-  half_frontier(T, h, K, kind, limit, upper, &B);
-  if (A.empty() || B.empty()) return kind == 0 ? IPC_EBOUND : IPC_EBUDGET;
-  // B: cost ascending, bytes descending.
-  bool found = false;
-  uint64_t bc = 0, by = 0;
-  const Part *ba = nullptr, *bb = nullptr;
-  for (const Part& a : A) {
-    const Part* m = nullptr;
-    if (kind == 0) {
-      if (a.c > limit) continue;
-      const uint64_t lim = limit - a.c;  // largest cost <= lim has the fewest bytes
-      size_t lo = 0, hi = B.size();
-      while (lo < hi) {
-        const size_t mid = (lo + hi) / 2;
-        if (B[mid].c <= lim) lo = mid + 1;
-        else hi = mid;
-      }
-      if (lo == 0) continue;
-      m = &B[lo - 1];
-    } else {
-      if (a.y > limit) continue;
-      const uint64_t lim = limit - a.y;  // first entry with bytes <= lim: least cost
-      size_t lo = 0, hi = B.size();
-      while (lo < hi) {
-        const size_t mid = (lo + hi) / 2;
-        if (B[mid].y > lim) lo = mid + 1;
-        else hi = mid;
-      }
-      if (lo == B.size()) continue;
-      m = &B[lo];
-    }
-    const uint64_t c = sadd(a.c, m->c), y = a.y + m->y;
-    bool better;
-    if (!found) {
-      better = true;
-    } else if (kind == 0) {
-      better = y < by || (y == by && c < bc) ||
-               (y == by && c == bc &&
-                (std::memcmp(a.b, ba->b, h) > 0 ||
-                 (std::memcmp(a.b, ba->b, h) == 0 && std::memcmp(m->b, bb->b, K - h) > 0)));
-    } else {
-      better = c < bc || (c == bc && y < by) ||
-               (c == bc && y == by &&
-                (std::memcmp(a.b, ba->b, h) > 0 ||
-                 (std::memcmp(a.b, ba->b, h) == 0 && std::memcmp(m->b, bb->b, K - h) > 0)));
-    }
-    if (better) {
-      found = true;
-      bc = c;
-      by = y;
-      ba = &a;
-      bb = m;
-    }
-  }
-  if (!found) return kind == 0 ? IPC_EBOUND : IPC_EBUDGET;
-  best->assign(K, 0);
-  for (int l = 0; l < h; ++l) (*best)[l] = ba->b[l];
-  for (int l = h; l < K; ++l) (*best)[l] = bb->b[l - h];
-  return IPC_OK;
-}
-
-uint64_t loaded(const ipc_field* f, const std::vector<int>& b) {
-  uint64_t y = f->mandatory;
-  for (size_t t = 0; t < f->g.stages.size(); ++t)
-    for (int k = b[f->g.stages[t].level - 1]; k < 32; ++k) y += f->st[t].size[k];
-  return y;
-}
-uint64_t cost_of(const Tables& T, const std::vector<int>& b) {
-  uint64_t c = 0;
-  for (size_t l = 0; l < b.size(); ++l) c = sadd(c, T.cost[l * 33 + b[l]]);
-  return c;
+  return in;
 }
 
 int select(const ipc_field* f, ipc_target tg, const std::vector<int>* upper, std::vector<int>* b,
            uint64_t* bytes, double* bound) {
-  if (!std::isfinite(tg.value)) return fail(IPC_EINVAL, "target must be finite");
-  const double range = f->xmax - f->xmin;
-  Tables T;
-  if (tg.kind == IPC_TARGET_EB) {
-    double E = tg.value;
-    if (f->eb_mode == IPC_EB_REL) E = range > 0 ? tg.value * range : tg.value;
-    if (!(E >= f->eb)) return fail(IPC_EBOUND, "target error bound is below the compression bound");
-    build_tables(f, f->xmaxabs + E, &T);
-    const double Bd = std::floor(((E - f->eb) / f->eb) * 65536.0);
-    const uint64_t B = Bd >= (double)kSaturate ? kSaturate : (uint64_t)Bd;
-    int rc = solve(T, 0, B, upper, b);
-    if (rc) return fail(rc, "no selection meets the error bound");
-    *bytes = loaded(f, *b);
-    *bound = f->eb + (double)cost_of(T, *b) * f->eb / 65536.0;
-    return IPC_OK;
-  }
-  if (tg.kind == IPC_TARGET_BITRATE) {
-    if (!(tg.value >= 0)) return fail(IPC_EINVAL, "bitrate must be >= 0");
-    const double Sd = std::floor(tg.value * (double)f->g.n / 8.0);
-    const uint64_t Sb = Sd >= 1.8e19 ? ~uint64_t(0) : (uint64_t)Sd;
-    if (f->mandatory > Sb) return fail(IPC_EBUDGET, "bitrate below the mandatory bytes");
-    double A = f->xmaxabs + std::max(range, f->eb);
-    build_tables(f, A, &T);
-    int rc = solve(T, 1, Sb - f->mandatory, upper, b);
-    if (rc) return fail(rc, "no selection fits the bitrate");
-    *bytes = loaded(f, *b);
-    double G = f->eb + (double)cost_of(T, *b) * f->eb / 65536.0;
-    for (int it = 0; it < 16 && G > A - f->xmaxabs; ++it) {
-      A = f->xmaxabs + G;
-      build_tables(f, A, &T);
-      G = f->eb + (double)cost_of(T, *b) * f->eb / 65536.0;
-    }
-    *bound = G;
-    return IPC_OK;
-  }
-  return fail(IPC_EINVAL, "unknown target kind");
+  const char* why = "";
+  const int rc = select_planes(sel_input(f), tg.kind, tg.value, upper, b, bytes, bound, &why);
+  return rc ? fail(rc, why) : IPC_OK;
 }
 
 // Algorithm 1 on the device: the anchor, then one fused launch per level
@@ -1157,6 +936,104 @@ struct DeviceGuard {
 
 // ===========================================================================
 // C ABI
+// Little-endian reads of the container.
+uint32_t get32(const uint8_t* p) {
+  uint32_t v = 0;
+  for (int i = 0; i < 4; ++i) v |= uint32_t(p[i]) << (8 * i);
+  return v;
+}
+uint64_t get64(const uint8_t* p) {
+  uint64_t v = 0;
+  for (int i = 0; i < 8; ++i) v |= uint64_t(p[i]) << (8 * i);
+  return v;
+}
+
+// Reads the container header, the stage table and the plane-size table into
+// the host fields of f (geometry, statistics). On success *pos is the offset
+// of the outlier lists, nout[t] the outliers of stage t and size[32 t + k]
+// the stream bytes of plane k of stage t.
+int parse_head(const uint8_t* p, uint64_t len, ipc_field* f, uint64_t* pos_out,
+               std::vector<uint64_t>* nout, std::vector<uint64_t>* size, const char** why) {
+  uint64_t pos = 0;
+  bool ok = true;
+  auto need = [&](uint64_t k) {
+    if (pos + k > len || pos + k < pos) ok = false;
+    return ok;
+  };
+  auto g32 = [&]() -> uint32_t {
+    if (!need(4)) return 0;
+    const uint32_t v = get32(p + pos);
+    pos += 4;
+    return v;
+  };
+  auto g64 = [&]() -> uint64_t {
+    if (!need(8)) return 0;
+    const uint64_t v = get64(p + pos);
+    pos += 8;
+    return v;
+  };
+  auto gd = [&]() {
+    const uint64_t u = g64();
+    double d;
+    std::memcpy(&d, &u, 8);
+    return d;
+  };
+  if (!p || g32() != kMagic || g32() != kVersion || !ok) {
+    *why = "bad magic/version";
+    return IPC_ECORRUPT;
+  }
+  f->dtype = (int)g32();
+  f->interp = (int)g32();
+  f->bound = (int)g32();
+  const int ndim = (int)g32();
+  int64_t dims[3];
+  for (int e = 0; e < 3; ++e) dims[e] = (int64_t)g64();
+  f->eb_mode = (int)g32();
+  const int K = (int)g32();
+  f->eb_user = gd();
+  f->eb = gd();
+  f->xmin = gd();
+  f->xmax = gd();
+  f->xmaxabs = gd();
+  f->anchor = gd();
+  const uint32_t S = g32();
+  g32();
+  if (!ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 1 || f->bound < 0 ||
+      f->bound > 1 || f->eb_mode < 0 || f->eb_mode > 1 || !(f->eb > 0) || !std::isfinite(f->eb)) {
+    *why = "bad header fields";
+    return IPC_ECORRUPT;
+  }
+  if (ndim < 1 || ndim > 3 || !build_geo(ndim, dims, f->dtype, &f->g) || f->g.K != K ||
+      f->g.stages.size() != S) {
+    *why = "bad geometry";
+    return IPC_ECORRUPT;
+  }
+  f->st.assign(S, StageTab{});
+  nout->assign(S, 0);
+  for (uint32_t t = 0; t < S; ++t) {
+    const StageGeo& sg = f->g.stages[t];
+    const uint32_t lv = g32(), dm = g32();
+    const uint64_t nc = g64();
+    f->st[t].H = (int32_t)g32();
+    f->st[t].Q = g32();
+    (*nout)[t] = g64();
+    if (!ok || (int)lv != sg.level || (int)dm != sg.dim3 - (3 - ndim) || nc != sg.ncodes ||
+        f->st[t].H < -1 || f->st[t].H > 31 || (*nout)[t] > nc) {
+      *why = "bad stage table";
+      return IPC_ECORRUPT;
+    }
+  }
+  size->assign(32 * (size_t)S, 0);
+  for (uint32_t t = 0; t < S; ++t)
+    for (int k = 31; k >= 0; --k) (*size)[32 * t + k] = g64();
+  if (!ok) {
+    *why = "truncated tables";
+    return IPC_ECORRUPT;
+  }
+  *pos_out = pos;
+  return IPC_OK;
+}
+
 // ===========================================================================
 extern "C" {
 
@@ -1281,6 +1158,47 @@ int ipc_free(void* handle) {
   return fail(IPC_EINVAL, "not a live ipc handle");
 }
 
+int ipc_select_container(const void* buf, uint64_t len, ipc_target target, int* b_per_level,
+                         int* nlevels, uint64_t* bytes, double* guaranteed_bound) {
+  g_err.clear();
+  if (!buf) return fail(IPC_EINVAL, "null argument");
+  ipc_field f{};
+  uint64_t pos = 0;
+  std::vector<uint64_t> nout, size;
+  const char* why = "";
+  if (parse_head((const uint8_t*)buf, len, &f, &pos, &nout, &size, &why))
+    return fail(IPC_ECORRUPT, why);
+  uint64_t mand = pos;  // the outlier lists count, whether present or not
+  for (size_t t = 0; t < f.st.size(); ++t) {
+    mand += 16 * nout[t];
+    const uint64_t W = f.g.stages[t].words, nbm = (W + 31) / 32;
+    for (int k = 0; k < 32; ++k) {
+      const uint64_t z = size[32 * t + k];
+      // a stream size is 4 (empty), 4 + 4 W (dense) or 4 + 4 (nbm + nnz)
+      // with nnz >= 1 and nbm + nnz < W (sparse)
+      bool valid = z == 4 || z == 4 + 4 * W;
+      if (!valid && z > 4 && z % 4 == 0 && (z - 4) / 4 > nbm) {
+        const uint64_t nnz = (z - 4) / 4 - nbm;
+        valid = stream_bytes(nnz, W) == z;
+      }
+      if (!valid) return fail(IPC_ECORRUPT, "bad plane size");
+      f.st[t].size[k] = z;
+    }
+  }
+  f.mandatory = mand;
+  std::vector<int> b;
+  uint64_t y = 0;
+  double bound = 0;
+  const int rc = select_planes(sel_input(&f), target.kind, target.value, nullptr, &b, &y, &bound, &why);
+  if (rc) return fail(rc, why);
+  if (nlevels) *nlevels = (int)b.size();
+  if (b_per_level)
+    for (size_t i = 0; i < b.size(); ++i) b_per_level[i] = b[i];
+  if (bytes) *bytes = y;
+  if (guaranteed_bound) *guaranteed_bound = bound;
+  return IPC_OK;
+}
+
 int ipc_selection(const ipc_view* v, int* b_per_level, int* nlevels, uint64_t* bytes,
                   double* guaranteed_bound) {
   if (!v || v->tag != kViewTag) return fail(IPC_EINVAL, "invalid view");
@@ -1346,33 +1264,6 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   g_err.clear();
   if (!out || (!host_buf && len)) return fail(IPC_EINVAL, "null argument");
   const uint8_t* p = (const uint8_t*)host_buf;
-  uint64_t pos = 0;
-  bool ok = true;
-  auto need = [&](uint64_t k) {
-    if (pos + k > len || pos + k < pos) ok = false;
-    return ok;
-  };
-  auto g32 = [&]() -> uint32_t {
-    if (!need(4)) return 0;
-    uint32_t v = 0;
-    for (int i = 0; i < 4; ++i) v |= uint32_t(p[pos + i]) << (8 * i);
-    pos += 4;
-    return v;
-  };
-  auto g64 = [&]() -> uint64_t {
-    if (!need(8)) return 0;
-    uint64_t v = 0;
-    for (int i = 0; i < 8; ++i) v |= uint64_t(p[pos + i]) << (8 * i);
-    pos += 8;
-    return v;
-  };
-  auto gd = [&]() {
-    uint64_t u = g64();
-    double d;
-    std::memcpy(&d, &u, 8);
-    return d;
-  };
-  if (g32() != kMagic || g32() != kVersion || !ok) return fail(IPC_ECORRUPT, "bad magic/version");
   ipc_field* f = new (std::nothrow) ipc_field();
   if (!f) return fail(IPC_ENOMEM, "host allocation");
   f->tag = kFieldTag;
@@ -1384,56 +1275,25 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
     delete f;
     return code == IPC_ECUDA ? code : fail(code, why);
   };
-  f->dtype = (int)g32();
-  f->interp = (int)g32();
-  f->bound = (int)g32();
-  const int ndim = (int)g32();
-  int64_t dims[3];
-  for (int e = 0; e < 3; ++e) dims[e] = (int64_t)g64();
-  f->eb_mode = (int)g32();
-  const int K = (int)g32();
-  f->eb_user = gd();
-  f->eb = gd();
-  f->xmin = gd();
-  f->xmax = gd();
-  f->xmaxabs = gd();
-  f->anchor = gd();
-  const uint32_t S = g32();
-  g32();
-  if (!ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 1 || f->bound < 0 ||
-      f->bound > 1 || f->eb_mode < 0 || f->eb_mode > 1 || !(f->eb > 0) || !std::isfinite(f->eb))
-    return drop(IPC_ECORRUPT, "bad header fields");
-  if (ndim < 1 || ndim > 3 || !build_geo(ndim, dims, f->dtype, &f->g) || f->g.K != K ||
-      f->g.stages.size() != S)
-    return drop(IPC_ECORRUPT, "bad geometry");
-  f->st.assign(S, StageTab{});
-  std::vector<uint64_t> nout(S);
+  uint64_t pos = 0;
+  std::vector<uint64_t> nout, size;
+  const char* why = "";
+  if (parse_head(p, len, f, &pos, &nout, &size, &why)) return drop(IPC_ECORRUPT, why);
+  const uint32_t S = (uint32_t)f->g.stages.size();
   for (uint32_t t = 0; t < S; ++t) {
-    const StageGeo& sg = f->g.stages[t];
-    const uint32_t lv = g32(), dm = g32();
-    const uint64_t nc = g64();
-    f->st[t].H = (int32_t)g32();
-    f->st[t].Q = g32();
-    nout[t] = g64();
-    if (!ok || (int)lv != sg.level || (int)dm != sg.dim3 - (3 - ndim) || nc != sg.ncodes ||
-        f->st[t].H < -1 || f->st[t].H > 31 || nout[t] > nc)
-      return drop(IPC_ECORRUPT, "bad stage table");
-  }
-  std::vector<uint64_t> size(32 * (size_t)S);
-  for (uint32_t t = 0; t < S; ++t)
-    for (int k = 31; k >= 0; --k) size[32 * t + k] = g64();
-  for (uint32_t t = 0; t < S; ++t) {
-    if (!need(nout[t] * 16)) return drop(IPC_ECORRUPT, "truncated outliers");
+    if (pos + nout[t] * 16 > len) return drop(IPC_ECORRUPT, "truncated outliers");
     for (uint64_t i = 0; i < nout[t]; ++i) {
-      const uint64_t idx = g64();
-      const double v = gd();
+      const uint64_t idx = get64(p + pos);
+      double v;
+      const uint64_t vb = get64(p + pos + 8);
+      std::memcpy(&v, &vb, 8);
+      pos += 16;
       if (idx >= f->g.stages[t].ncodes || (i && idx <= f->st[t].out_idx.back()))
         return drop(IPC_ECORRUPT, "bad outlier list");
       f->st[t].out_idx.push_back(idx);
       f->st[t].out_val.push_back(v);
     }
   }
-  if (!ok) return drop(IPC_ECORRUPT, "truncated tables");
   const uint64_t mand = pos;
   uint64_t spos = pos;
   for (uint32_t t = 0; t < S; ++t) {

@@ -627,7 +627,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     {
       const int js = tid, c2 = c.C0 + 2 * js;
       if (c2 < M2) {
-#pragma unroll 4
+#pragma unroll
         for (int jr = 0; jr < G::H0; ++jr) {
           const int c1 = c.R0 - 2 + 2 * jr;
           if (c1 >= 0 && c1 < M1) item(js + 1, jr);
@@ -856,8 +856,15 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const bool has2 = S2.out_end > S2.out_begin;
     const int g = tid & 63, rq = tid >> 6;
     const int c2e = c.C0 + 8 * g;  // first (even) lattice column of the run
-    const bool interior = c2e + 8 <= c.C1 && (cubic ? (c2e >= 2 && c2e + 10 <= M2 - 1)
-                                                     : c2e + 8 <= M2 - 1);
+    // per odd column k of the run: 2 = cubic, 1 = linear, 0 = copy (the
+    // boundary rule of pred4), two bits each
+    uint32_t rule = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = c2e + 2 * k + 1;
+      const uint32_t r = i + 1 > M2 - 1 ? 0u : ((cubic && i - 3 >= 0 && i + 3 <= M2 - 1) ? 2u : 1u);
+      rule |= r << (2 * k);
+    }
     if (c2e < c.C1) {
       for (int lr = rq; lr < BR; lr += 4) {
         const int c1 = c.R0 + lr;
@@ -866,36 +873,20 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         lds8<T>(VE + (lr + 2) * G::VP + 4 * g, w);
         const uint4 qn = *reinterpret_cast<const uint4*>(Q2 + lr * G::QP + qoff(4 * g));
         const uint32_t qa[4] = {qn.x, qn.y, qn.z, qn.w};
+        T val[4];
+        code_values4(qa, val);
         T v[8];
-        if (interior) {
-          // all four targets have every stencil neighbour inside the row
-          T val[4];
-          code_values4(qa, val);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            T pred;
-            if (cubic) {
-              const T u = FP<T>::add(w[k + 1], w[k + 2]);
-              const T z = FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3]));
-              pred = FP<T>::mul(z, (T)0.0625);
-            } else {
-              pred = FP<T>::mul(FP<T>::add(w[k + 1], w[k + 2]), (T)0.5);
-            }
-            v[2 * k] = w[k + 1];
-            v[2 * k + 1] = FP<T>::add(pred, FP<T>::mul(val[k], twoeb));
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int c2o = c2e + 2 * k + 1;
-            v[2 * k] = w[k + 1];
-            T vo = w[k + 1];
-            if (c2o < c.C1) {
-              const T pred = pred4<T>(w[k], w[k + 1], w[k + 2], w[k + 3], c2o, M2, cubic);
-              vo = FP<T>::add(pred, FP<T>::mul(code_value(qa[k], T()), twoeb));
-            }
-            v[2 * k + 1] = vo;
-          }
+        for (int k = 0; k < 4; ++k) {
+          // Eq. 2 and Eq. 1 side by side (same operations as pred4), then
+          // the rule for this column; no lane takes a separate path.
+          const T u = FP<T>::add(w[k + 1], w[k + 2]);
+          const T cub = FP<T>::mul(FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])),
+                                   (T)0.0625);
+          const T lin = FP<T>::mul(u, (T)0.5);
+          const T pred = (rule >> (2 * k) & 3u) == 2u ? cub : ((rule >> (2 * k) & 3u) == 1u ? lin : w[k + 1]);
+          v[2 * k] = w[k + 1];
+          v[2 * k + 1] = FP<T>::add(pred, FP<T>::mul(val[k], twoeb));
         }
         if (has2) {
 #pragma unroll

@@ -1,0 +1,36 @@
+// Host-side plane selection of libipcomp (Sec. 5.1-5.3): the per-level
+// option tables (error cost, loaded bytes) and the exact knapsack over the
+// levels. Host code only: it needs nothing but the stage statistics and the
+// plane sizes of a field, so it also runs on a container header alone.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+namespace ipc {
+
+struct SelStage {
+  int level;          // 1..K
+  int32_t H;          // highest nonzero negabinary digit of the stage (-1: none)
+  uint32_t Q;         // max |q| over the stage's non-outlier codes
+  uint64_t size[32];  // packed stream bytes of plane k
+};
+
+struct SelInput {
+  int K;
+  int dtype, interp, bound, eb_mode;
+  double eb;       // absolute compression bound
+  double bin;      // quantization bin width in the element type, divided by eb
+  double xmin, xmax, xmaxabs;
+  uint64_t n;          // values
+  uint64_t mandatory;  // container bytes always loaded (header, tables, outliers)
+  std::vector<SelStage> st;
+};
+
+// Selection for a target (kind 0: error bound in the field's eb mode, kind 1:
+// bitrate in bits/value). upper (optional) bounds b_l from above (refine).
+// Returns 0 or a negative IPC_* status; `why` names the failure.
+int select_planes(const SelInput& in, int kind, double value, const std::vector<int>* upper,
+                  std::vector<int>* b, uint64_t* bytes, double* bound, const char** why);
+
+}  // namespace ipc

@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
     L.ipc_free.argtypes = [vp]
     L.ipc_selection.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
                                 C.POINTER(C.c_double)]
+    L.ipc_select_container.argtypes = [C.c_char_p, C.c_uint64, ipc_target, C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), u64p, C.POINTER(C.c_double)]
     L.ipc_compressed_size.argtypes = [vp, u64p]
     L.ipc_export.argtypes = [vp, vp, u64p]
     L.ipc_import.argtypes = [vp, C.c_uint64, vp, C.POINTER(vp)]
@@ -183,6 +185,20 @@ def ipc_selection(view):
     by = C.c_uint64()
     bd = C.c_double()
     _check(lib().ipc_selection(view, b, C.byref(nl), C.byref(by), C.byref(bd)), "ipc_selection")
+    return list(b)[:nl.value], by.value, bd.value
+
+
+def ipc_select_container(buf: bytes, kind: int, value: float):
+    """Selection of a retrieval computed on the host from a container's
+    leading bytes (header, stage and plane-size tables): (b_per_level list,
+    loaded bytes, guaranteed bound). Needs no GPU."""
+    b = (C.c_int * 64)()
+    nl = C.c_int()
+    by = C.c_uint64()
+    bd = C.c_double()
+    _check(lib().ipc_select_container(bytes(buf), len(buf), ipc_target(int(kind), float(value)), b,
+                                      C.byref(nl), C.byref(by), C.byref(bd)),
+           "ipc_select_container")
     return list(b)[:nl.value], by.value, bd.value
 
 
