@@ -790,6 +790,22 @@ int select(const ipc_field* f, ipc_target tg, const std::vector<int>* upper, std
   return rc ? fail(rc, why) : IPC_OK;
 }
 
+// Whether the planes loaded at level l (k >= b with nonzero words in one of
+// the level's stages) span at most 16: the kernel then keeps 16-bit codes.
+bool level_w16(const ipc_field* f, int l, int b) {
+  int ktop = -1;
+  for (int d = 0; d < 3; ++d) {
+    const int t = f->g.level_stage[d][l - 1];
+    if (t < 0) continue;
+    for (int k = 31; k > ktop && k >= b; --k)
+      if (f->st[t].nnz[k]) {
+        ktop = k;
+        break;
+      }
+  }
+  return ktop - b <= 15;
+}
+
 // Algorithm 1 on the device: the anchor, then one fused launch per level
 // (coarse to fine); outliers are applied inside the level kernels.
 int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream_t st) {
@@ -815,7 +831,7 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
     }
     const long ph = prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st);
     CU(launch_level_retrieve(f->dtype, L, d_out, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
-                             f->d_oval, D, st));
+                             f->d_oval, D, level_w16(f, l, b[l - 1]) ? 1 : 0, st));
     prof_end(ph, st, by + (double)(nc * esz));
   }
   return IPC_OK;
@@ -829,6 +845,7 @@ struct BatchTable {
   std::vector<RetrieveEntry> ents;
   std::vector<AnchorEntry> anchors;
   std::vector<uint64_t> lev_off, lev_ctas;
+  std::vector<int> lev_w16;  // every entry of the level keeps 16-bit codes
   int Kmax = 0;
   double alg_bytes = 0;
 };
@@ -840,6 +857,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   for (auto* f : fs) T->Kmax = std::max(T->Kmax, f->g.K);
   T->lev_off.assign(T->Kmax + 2, 0);
   T->lev_ctas.assign(T->Kmax + 2, 0);
+  T->lev_w16.assign(T->Kmax + 2, 1);
   T->ents.clear();
   T->anchors.clear();
   T->alg_bytes = 0;
@@ -862,6 +880,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       e.oval = f->d_oval;
       e.twoeb = bin_width(f);
       e.b = bs[i][l - 1];
+      if (!level_w16(f, l, e.b)) T->lev_w16[l] = 0;
       e.cta_begin = cta;
       cta += (uint64_t)e.L.M[0] * e.L.nrb * e.L.nct;
       T->ents.push_back(e);
@@ -893,7 +912,8 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
     // level l's entries: [lev_off[l], lev_off[l-1]) with lev_off[0] = size
     const int nn = (int)(T.lev_off[l - 1] - T.lev_off[l]);
     const long ph = profile ? prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st) : -1;
-    CU(launch_level_retrieve_batch(dtype, d_ents + T.lev_off[l], nn, T.lev_ctas[l], st));
+    CU(launch_level_retrieve_batch(dtype, d_ents + T.lev_off[l], nn, T.lev_ctas[l], T.lev_w16[l],
+                                   st));
     if (profile) prof_end(ph, st, l == 1 ? T.alg_bytes : 0.0);
     ++nl;
   }

@@ -156,15 +156,17 @@ cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStrea
 cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, void* xh,
                                   int write_xh, const void* quant, const SweepOut& o,
                                   const LevelDescs& d, cudaStream_t st);
+// w16: the planes loaded at the level span at most 16 (16-bit code rows).
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
-                                  const double* oval, const LevelDescs& d, cudaStream_t st);
+                                  const double* oval, const LevelDescs& d, int w16,
+                                  cudaStream_t st);
 int level_rows(int dtype);
 // Batched level launches: `ents` (device memory) sorted by cta_begin.
 cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,
                                         uint64_t ctas, cudaStream_t st);
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
-                                        uint64_t ctas, cudaStream_t st);
+                                        uint64_t ctas, int w16, cudaStream_t st);
 // Segmented <-> packed container streams of one stage (export / import).
 // tmp: 2 * 32 * nbm words of scratch; flags[0] = corruption flag,
 // flags[1 + k] = nonzero words found in plane k (import).

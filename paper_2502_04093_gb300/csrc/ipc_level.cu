@@ -416,21 +416,56 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
 constexpr int kSlots = 13;
 constexpr int kMaxBw = 4;  // bitmap words per segment (RB * CW <= 128)
 
-template <int BR, int BC>
+// Code rows hold the tile's codes of one stage row. When the loaded planes
+// of a level span at most 16 (the usual case; decided on the host per
+// launch) a code is its 16-plane window value, stored in 16 bits (the
+// window base is a shift applied on reading); otherwise the full 32 bits.
+// Layout: blocks of 32 codes plus pad, so that one thread's 32 codes are
+// conflict-free 16-byte stores and four consecutive codes one load.
+template <bool W16> struct QCfg;
+template <> struct QCfg<true> {
+  typedef uint16_t QT;
+  static constexpr int BLK = 40;  // codes + pad per block (80 bytes)
+  static constexpr int NPL = 16;  // planes staged per segment
+};
+template <> struct QCfg<false> {
+  typedef uint32_t QT;
+  static constexpr int BLK = 36;  // 144 bytes
+  static constexpr int NPL = 32;
+};
+
+template <int BR, int BC, bool W16>
 struct RTile {
   static constexpr int HC = BC / 2;      // codes of one stage per tile row
   static constexpr int CWD = BC / 64;    // words per tile row
-  static constexpr int QP = CWD * 36;    // code-row pitch: 36 words per 32 codes
+  static constexpr int QP = CWD * QCfg<W16>::BLK;  // code-row pitch
   static constexpr int VR = BR + 5;      // value rows: c1 in [R0-2, R0+BR+2]
   static constexpr int VP = HC + 4;      // value-row pitch (a 16-byte multiple)
   static constexpr int H1 = BR / 2;      // stage-1 code rows (own odd c1)
   static constexpr int H0 = BR / 2 + 3;  // stage-0 code rows (even c1, with halo)
 };
 
-// Position of tile code column e in a code row: 32 codes + 4 pad words per
-// block, so that one thread's 32 codes are eight conflict-free 16-byte
-// stores and four consecutive codes one 16-byte load.
-__device__ __forceinline__ int qoff(int e) { return (e >> 5) * 36 + (e & 31); }
+// Position of tile code column e in a code row.
+template <bool W16>
+__device__ __forceinline__ int qoff(int e) { return (e >> 5) * QCfg<W16>::BLK + (e & 31); }
+
+// Four consecutive codes (negabinary, window shift applied).
+__device__ __forceinline__ void load4(const uint16_t* p, int wb, uint32_t (&n)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  n[0] = (v.x & 0xFFFFu) << wb;
+  n[1] = (v.x >> 16) << wb;
+  n[2] = (v.y & 0xFFFFu) << wb;
+  n[3] = (v.y >> 16) << wb;
+}
+__device__ __forceinline__ void load4(const uint32_t* p, int, uint32_t (&n)[4]) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  n[0] = v.x;
+  n[1] = v.y;
+  n[2] = v.z;
+  n[3] = v.w;
+}
+__device__ __forceinline__ uint32_t code_at(const uint16_t* p, int wb) { return (uint32_t)*p << wb; }
+__device__ __forceinline__ uint32_t code_at(const uint32_t* p, int) { return *p; }
 
 // Values of four codes: the small-code conversion when all four allow it.
 __device__ __forceinline__ void code_values4(const uint32_t (&n)[4], float (&v)[4]) {
@@ -533,7 +568,7 @@ __device__ __forceinline__ void store_run(T* row, const LevelArgs& L, int c2e, i
     if (c2e + i < C1) row[(int64_t)(c2e + i) * L.s] = v[i];
 }
 
-template <class T, int BR, int BC>
+template <class T, int BR, int BC, bool W16>
 __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, T twoeb, int b,
                                                     const uint32_t* __restrict__ cap,
                                                     const uint32_t* __restrict__ bm,
@@ -541,17 +576,19 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
                                                     const double* __restrict__ oval,
                                                     const LevelDescs& D, uint64_t cta,
                                                     unsigned char* smem) {
-  typedef RTile<BR, BC> G;
+  typedef RTile<BR, BC, W16> G;
+  typedef typename QCfg<W16>::QT QT;
+  constexpr int NPL = QCfg<W16>::NPL;
   static_assert(G::HC == 256, "one thread per code column of a tile row");
-  T* VE = reinterpret_cast<T*>(smem);                            // [VR][VP]
-  uint32_t* Q2 = reinterpret_cast<uint32_t*>(VE + G::VR * G::VP);  // [BR][QP]
-  uint32_t* Q1 = Q2 + BR * G::QP;                                // [H1][QP]
-  uint32_t* Q0 = Q1 + G::H1 * G::QP;                             // [H0][QP]
-  uint32_t* QH = Q0 + G::H0 * G::QP;                             // [H1 + H0][4]
-  __shared__ uint32_t SB[kSlots][32][kMaxBw];  // group bitmaps of the loaded planes
-  __shared__ const uint32_t* SP[kSlots][32];   // payload base of (segment, plane)
-  __shared__ unsigned long long SG[kSlots];    // segment id (or ~0 if absent)
-  __shared__ uint32_t s_km[3];                 // planes to load, per stage
+  T* VE = reinterpret_cast<T*>(smem);                        // [VR][VP]
+  QT* Q2 = reinterpret_cast<QT*>(VE + G::VR * G::VP);        // [BR][QP]
+  QT* Q1 = Q2 + BR * G::QP;                                  // [H1][QP]
+  QT* Q0 = Q1 + G::H1 * G::QP;                               // [H0][QP]
+  uint32_t* QH = reinterpret_cast<uint32_t*>(Q0 + G::H0 * G::QP);  // [H1 + H0][4]
+  __shared__ uint32_t SB[kSlots][NPL][kMaxBw];  // group bitmaps of the window's planes
+  __shared__ const uint32_t* SP[kSlots][NPL];   // payload base of (segment, plane)
+  __shared__ unsigned long long SG[kSlots];     // segment id (or ~0 if absent)
+  __shared__ uint32_t s_km[3];                  // planes to load, per stage
   __shared__ int s_ktop;
 
   const CtaPos c = cta_pos(L, cta, BR, BC);
@@ -588,16 +625,21 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     SG[sl] = ok ? seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts) : ~0ULL;
   }
   __syncthreads();
-  for (int u = tid; u < kSlots * 32; u += 256) {
-    const int sl = u >> 5, k = u & 31;
+  // Plane window: slot i of the staged tables is plane wb + i. With 16-bit
+  // codes the loaded planes [b, ktop] lie in [wb, wb + 15] (checked on the
+  // host for the level; a CTA's ktop is at most the level's).
+  const int ktop = s_ktop;
+  const int wb = W16 ? max(0, ktop - 15) : 0;
+  for (int u = tid; u < kSlots * NPL; u += 256) {
+    const int sl = u / NPL, i = u % NPL, k = wb + i;
     const int sx = sl == 0 ? 2 : (sl < 4 ? 1 : 0);
     const unsigned long long g = SG[sl];
-    if (g == ~0ULL || !((s_km[sx] >> k) & 1u)) continue;
+    if (g == ~0ULL || k > 31 || !((s_km[sx] >> k) & 1u)) continue;
     const LevelStage& S = L.st[sx];
     const PlaneDesc& pd = D.s[sx].p[k];
-    SP[sl][k] = cap + pd.cap_off + g * (uint64_t)S.RB * S.CW;
+    SP[sl][i] = cap + pd.cap_off + g * (uint64_t)S.RB * S.CW;
     const uint32_t* bp = bm + pd.bm_off + g * S.bw;
-    for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[sl][k][v], bp + v);
+    for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[sl][i][v], bp + v);
   }
 
   // Phase 1a: even value rows -- the sweep-0 predictions of an odd plane
@@ -645,9 +687,6 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   __syncthreads();
 
   // Phase 0: decode the words of the tile's code columns.
-  const int ktop = s_ktop;
-  const bool w16 = ktop - b <= 15;              // the loaded planes fit in 16
-  const int wb = w16 ? max(0, ktop - 15) : 0;  // plane of window slot 0
   const int cw0 = (int)c.ct * G::CWD;          // first own word of a row
   const int n2r = c.R1 - c.R0, n1r = (c.R1 - c.R0) >> 1;
   const bool st0 = S0.present && podd;
@@ -693,82 +732,61 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const uint32_t* const* sp = SP[sl];
     const uint32_t off = (uint32_t)wl * 32;
     uint32_t* QHr = QH + (sx == 1 ? qrow : G::H1 + qrow) * 4;
-    uint32_t* Qr = (sx == 2 ? Q2 : (sx == 1 ? Q1 : Q0)) + qrow * G::QP + (j - cw0) * 36;
-    if (w16) {
-      uint32_t a[16];
+    QT* Qr = (sx == 2 ? Q2 : (sx == 1 ? Q1 : Q0)) + qrow * G::QP + (j - cw0) * QCfg<W16>::BLK;
+    uint32_t a[NPL];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int k = wb + i;
-        uint32_t w = 0u;
-        if ((km >> k) & 1u) {
-          const uint32_t m = sb[k * kMaxBw];
-          if (m & bit) w = __ldg(sp[k] + off + __popc(m & below));
-        }
-        a[i] = w;
+    for (int i = 0; i < NPL; ++i) {
+      const int k = wb + i;
+      uint32_t w = 0u;
+      if (k <= 31 && ((km >> k) & 1u)) {
+        const uint32_t m = sb[i * kMaxBw];
+        if (m & bit) w = __ldg(sp[i] + off + __popc(m & below));
       }
+      a[i] = w;
+    }
+    // inverse predictive XOR, top-down; planes below b are zero, planes
+    // above the window are zero
 #pragma unroll
-      for (int i = 15; i >= 0; --i) {
-        const uint32_t p1 = i + 1 < 16 ? a[i + 1] : 0u, p2 = i + 2 < 16 ? a[i + 2] : 0u;
-        a[i] = wb + i >= b ? (a[i] ^ p1 ^ p2) : 0u;
-      }
-      if (side < 0) {
+    for (int i = NPL - 1; i >= 0; --i) {
+      const uint32_t p1 = i + 1 < NPL ? a[i + 1] : 0u, p2 = i + 2 < NPL ? a[i + 2] : 0u;
+      a[i] = wb + i >= b ? (a[i] ^ p1 ^ p2) : 0u;
+    }
+    if (side < 0) {
+      if constexpr (W16) {
         transpose16x2(a);
+        // code i (i < 16) is the low half of a[i], code 16 + i the high half
+        uint4* q = reinterpret_cast<uint4*>(Qr);
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-          reinterpret_cast<uint4*>(Qr)[m] =
-              make_uint4((a[4 * m] & 0xFFFFu) << wb, (a[4 * m + 1] & 0xFFFFu) << wb,
-                         (a[4 * m + 2] & 0xFFFFu) << wb, (a[4 * m + 3] & 0xFFFFu) << wb);
+        for (int m = 0; m < 2; ++m)
+          q[m] = make_uint4(__byte_perm(a[8 * m], a[8 * m + 1], 0x5410),
+                            __byte_perm(a[8 * m + 2], a[8 * m + 3], 0x5410),
+                            __byte_perm(a[8 * m + 4], a[8 * m + 5], 0x5410),
+                            __byte_perm(a[8 * m + 6], a[8 * m + 7], 0x5410));
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-          reinterpret_cast<uint4*>(Qr)[4 + m] =
-              make_uint4((a[4 * m] >> 16) << wb, (a[4 * m + 1] >> 16) << wb,
-                         (a[4 * m + 2] >> 16) << wb, (a[4 * m + 3] >> 16) << wb);
+        for (int m = 0; m < 2; ++m)
+          q[2 + m] = make_uint4(__byte_perm(a[8 * m], a[8 * m + 1], 0x7632),
+                                __byte_perm(a[8 * m + 2], a[8 * m + 3], 0x7632),
+                                __byte_perm(a[8 * m + 4], a[8 * m + 5], 0x7632),
+                                __byte_perm(a[8 * m + 6], a[8 * m + 7], 0x7632));
       } else {
-        uint32_t v0 = 0u, v1 = 0u;
-        const int i0 = side ? 0 : 31;
+        transpose32(a);
+        uint4* q = reinterpret_cast<uint4*>(Qr);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          v0 |= ((a[i] >> i0) & 1u) << i;
-          v1 |= ((a[i] >> 1) & 1u) << i;
-        }
-        if (side) {
-          QHr[1] = v0 << wb;
-          QHr[2] = v1 << wb;
-        } else {
-          QHr[0] = v0 << wb;
-        }
+        for (int m = 0; m < 8; ++m) q[m] = make_uint4(a[4 * m], a[4 * m + 1], a[4 * m + 2], a[4 * m + 3]);
       }
     } else {
-      uint32_t a[32];
+      uint32_t v0 = 0u, v1 = 0u;
+      const int i0 = side ? 0 : 31;
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        uint32_t w = 0u;
-        if ((km >> k) & 1u) {
-          const uint32_t m = sb[k * kMaxBw];
-          if (m & bit) w = __ldg(sp[k] + off + __popc(m & below));
-        }
-        a[k] = w;
+      for (int i = 0; i < NPL; ++i) {
+        v0 |= ((a[i] >> i0) & 1u) << i;
+        v1 |= ((a[i] >> 1) & 1u) << i;
       }
-      xor_decode_planes(a, b);
-      if (side < 0) {
-        transpose32(a);
-#pragma unroll
-        for (int m = 0; m < 8; ++m)
-          reinterpret_cast<uint4*>(Qr)[m] = make_uint4(a[4 * m], a[4 * m + 1], a[4 * m + 2], a[4 * m + 3]);
+      if (side) {
+        QHr[1] = v0 << wb;
+        QHr[2] = v1 << wb;
       } else {
-        uint32_t v0 = 0u, v1 = 0u;
-        const int i0 = side ? 0 : 31;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          v0 |= ((a[k] >> i0) & 1u) << k;
-          v1 |= ((a[k] >> 1) & 1u) << k;
-        }
-        if (side) {
-          QHr[1] = v0;
-          QHr[2] = v1;
-        } else {
-          QHr[0] = v0;
-        }
+        QHr[0] = v0 << wb;
       }
     }
   }
@@ -793,7 +811,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
 #pragma unroll 4
         for (int jr = 0; jr < G::H0; ++jr) {
           const int c1 = c.R0 - 2 + 2 * jr;
-          if (c1 >= 0 && c1 < M1) item(js + 1, jr, Q0[jr * G::QP + qoff(js)]);
+          if (c1 >= 0 && c1 < M1) item(js + 1, jr, code_at(Q0 + jr * G::QP + qoff<W16>(js), wb));
         }
       }
     }
@@ -829,7 +847,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
           const int c1 = c.R0 + 1 + 2 * jr;
           if (c1 >= c.R1) break;
           const T d = col[(2 * jr + 6) * G::VP];
-          col[(2 * jr + 3) * G::VP] = value(a, bb, cc, d, c1, c2, Q1[jr * G::QP + qoff(js)]);
+          col[(2 * jr + 3) * G::VP] = value(a, bb, cc, d, c1, c2, code_at(Q1 + jr * G::QP + qoff<W16>(js), wb));
           a = bb;
           bb = cc;
           cc = d;
@@ -871,8 +889,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         if (c1 >= c.R1) break;
         T w[8];
         lds8<T>(VE + (lr + 2) * G::VP + 4 * g, w);
-        const uint4 qn = *reinterpret_cast<const uint4*>(Q2 + lr * G::QP + qoff(4 * g));
-        const uint32_t qa[4] = {qn.x, qn.y, qn.z, qn.w};
+        uint32_t qa[4];
+        load4(Q2 + lr * G::QP + qoff<W16>(4 * g), wb, qa);
         T val[4];
         code_values4(qa, val);
         T v[8];
@@ -914,15 +932,14 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
   level_compress_body<T, BR, BC>(L, x, xh, write_xh, qa, o, D, blockIdx.x, smem);
 }
 
-template <class T, int BR, int BC>
-__global__ void __launch_bounds__(256, 3) k_level_retrieve(LevelArgs L, T* out, T twoeb, int b,
-                                                           const uint32_t* __restrict__ cap,
-                                                           const uint32_t* __restrict__ bm,
-                                                           const uint64_t* __restrict__ oidx,
-                                                           const double* __restrict__ oval,
-                                                           LevelDescs D) {
+// 16-bit code rows leave room for four CTAs per SM, 32-bit ones for three.
+template <class T, int BR, int BC, bool W16>
+__global__ void __launch_bounds__(256, W16 ? 4 : 3) k_level_retrieve(
+    LevelArgs L, T* out, T twoeb, int b, const uint32_t* __restrict__ cap,
+    const uint32_t* __restrict__ bm, const uint64_t* __restrict__ oidx,
+    const double* __restrict__ oval, LevelDescs D) {
   extern __shared__ __align__(16) unsigned char smem[];
-  level_retrieve_body<T, BR, BC>(L, out, twoeb, b, cap, bm, oidx, oval, D, blockIdx.x, smem);
+  level_retrieve_body<T, BR, BC, W16>(L, out, twoeb, b, cap, bm, oidx, oval, D, blockIdx.x, smem);
 }
 
 // Batched kernels: one grid covers the level's CTAs of every field of a
@@ -953,13 +970,13 @@ __global__ void __launch_bounds__(256, 3) k_level_compress_batch(
                                  blockIdx.x - e.cta_begin, smem);
 }
 
-template <class T, int BR, int BC>
-__global__ void __launch_bounds__(256, 3) k_level_retrieve_batch(
+template <class T, int BR, int BC, bool W16>
+__global__ void __launch_bounds__(256, W16 ? 4 : 3) k_level_retrieve_batch(
     const RetrieveEntry* __restrict__ ents, int n) {
   extern __shared__ __align__(16) unsigned char smem[];
   const RetrieveEntry& e = find_entry(ents, n);
-  level_retrieve_body<T, BR, BC>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx, e.oval,
-                                 e.D, blockIdx.x - e.cta_begin, smem);
+  level_retrieve_body<T, BR, BC, W16>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx,
+                                      e.oval, e.D, blockIdx.x - e.cta_begin, smem);
 }
 
 template <class T, int BR, int BC>
@@ -967,10 +984,23 @@ size_t smem_compress() {
   typedef Tile<BR, BC> G;
   return sizeof(T) * (G::VR * G::VEC + BR * G::HC) + 4 * (2 * BR * G::PITCH);
 }
-template <class T, int BR, int BC>
+template <class T, int BR, int BC, bool W16>
 size_t smem_retrieve() {
-  typedef RTile<BR, BC> G;
-  return sizeof(T) * G::VR * G::VP + 4 * ((BR + G::H1 + G::H0) * G::QP + (G::H1 + G::H0) * 4);
+  typedef RTile<BR, BC, W16> G;
+  return sizeof(T) * G::VR * G::VP +
+         sizeof(typename QCfg<W16>::QT) * (BR + G::H1 + G::H0) * G::QP + 4 * (G::H1 + G::H0) * 4;
+}
+
+template <class T, int BR, int BC, bool W16>
+cudaError_t setup_retrieve() {
+  cudaError_t r = cudaFuncSetAttribute(k_level_retrieve<T, BR, BC, W16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_retrieve<T, BR, BC, W16>());
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(k_level_retrieve_batch<T, BR, BC, W16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_retrieve<T, BR, BC, W16>());
+  return r;
 }
 
 template <class T, int BR, int BC>
@@ -980,20 +1010,27 @@ cudaError_t setup_once() {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_compress<T, BR, BC>());
     if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_level_retrieve<T, BR, BC>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_retrieve<T, BR, BC>());
-    if (r == cudaSuccess)
       r = cudaFuncSetAttribute(k_level_compress_batch<T, BR, BC>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_compress<T, BR, BC>());
-    if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_level_retrieve_batch<T, BR, BC>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_retrieve<T, BR, BC>());
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false>();
     return r;
   }();
   return e;
+}
+
+template <class T, int BR, int BC, bool W16>
+void retrieve_kernel(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
+                     const uint32_t* bm, const uint64_t* oidx, const double* oval,
+                     const LevelDescs& d, uint64_t grid, cudaStream_t st) {
+  k_level_retrieve<T, BR, BC, W16><<<(unsigned)grid, 256, smem_retrieve<T, BR, BC, W16>(), st>>>(
+      L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval, d);
+}
+template <class T, int BR, int BC, bool W16>
+void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t ctas, cudaStream_t st) {
+  k_level_retrieve_batch<T, BR, BC, W16>
+      <<<(unsigned)ctas, 256, smem_retrieve<T, BR, BC, W16>(), st>>>(ents, n);
 }
 
 }  // namespace
@@ -1022,20 +1059,23 @@ cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, 
 
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
-                                  const double* oval, const LevelDescs& d, cudaStream_t st) {
+                                  const double* oval, const LevelDescs& d, int w16,
+                                  cudaStream_t st) {
   const uint64_t grid = (uint64_t)L.M[0] * L.nrb * L.nct;
   if (grid == 0) return cudaSuccess;
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    k_level_retrieve<float, kLevelRowsF32, kLevelCols>
-        <<<(unsigned)grid, 256, smem_retrieve<float, kLevelRowsF32, kLevelCols>(), st>>>(
-            L, (float*)out, (float)twoeb, b, cap, bm, oidx, oval, d);
+    if (w16)
+      retrieve_kernel<float, kLevelRowsF32, kLevelCols, true>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
+    else
+      retrieve_kernel<float, kLevelRowsF32, kLevelCols, false>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    k_level_retrieve<double, kLevelRowsF64, kLevelCols>
-        <<<(unsigned)grid, 256, smem_retrieve<double, kLevelRowsF64, kLevelCols>(), st>>>(
-            L, (double*)out, twoeb, b, cap, bm, oidx, oval, d);
+    if (w16)
+      retrieve_kernel<double, kLevelRowsF64, kLevelCols, true>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
+    else
+      retrieve_kernel<double, kLevelRowsF64, kLevelCols, false>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
   }
   return cudaGetLastError();
 }
@@ -1057,17 +1097,17 @@ cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, in
 }
 
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
-                                        uint64_t ctas, cudaStream_t st) {
+                                        uint64_t ctas, int w16, cudaStream_t st) {
   if (ctas == 0 || n == 0) return cudaSuccess;
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    k_level_retrieve_batch<float, kLevelRowsF32, kLevelCols>
-        <<<(unsigned)ctas, 256, smem_retrieve<float, kLevelRowsF32, kLevelCols>(), st>>>(ents, n);
+    if (w16) retrieve_batch_kernel<float, kLevelRowsF32, kLevelCols, true>(ents, n, ctas, st);
+    else retrieve_batch_kernel<float, kLevelRowsF32, kLevelCols, false>(ents, n, ctas, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    k_level_retrieve_batch<double, kLevelRowsF64, kLevelCols>
-        <<<(unsigned)ctas, 256, smem_retrieve<double, kLevelRowsF64, kLevelCols>(), st>>>(ents, n);
+    if (w16) retrieve_batch_kernel<double, kLevelRowsF64, kLevelCols, true>(ents, n, ctas, st);
+    else retrieve_batch_kernel<double, kLevelRowsF64, kLevelCols, false>(ents, n, ctas, st);
   }
   return cudaGetLastError();
 }
