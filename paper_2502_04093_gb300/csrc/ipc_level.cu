@@ -440,7 +440,8 @@ struct RTile {
   static constexpr int CWD = BC / 64;    // words per tile row
   static constexpr int QP = CWD * QCfg<W16>::BLK;  // code-row pitch
   static constexpr int VR = BR + 5;      // value rows: c1 in [R0-2, R0+BR+2]
-  static constexpr int VP = HC + 4;      // value-row pitch (a 16-byte multiple)
+  static constexpr int V0 = 4;           // value column of code column 0 (16-byte aligned)
+  static constexpr int VP = HC + 8;      // value-row pitch: code columns -1 .. HC+1 (+ pad)
   static constexpr int H1 = BR / 2;      // stage-1 code rows (own odd c1)
   static constexpr int H0 = BR / 2 + 3;  // stage-0 code rows (even c1, with halo)
 };
@@ -464,8 +465,6 @@ __device__ __forceinline__ void load4(const uint32_t* p, int, uint32_t (&n)[4]) 
   n[2] = v.z;
   n[3] = v.w;
 }
-__device__ __forceinline__ uint32_t code_at(const uint16_t* p, int wb) { return (uint32_t)*p << wb; }
-__device__ __forceinline__ uint32_t code_at(const uint32_t* p, int) { return *p; }
 
 // Values of four codes: the small-code conversion when all four allow it.
 __device__ __forceinline__ void code_values4(const uint32_t (&n)[4], float (&v)[4]) {
@@ -486,22 +485,38 @@ __device__ __forceinline__ void code_values4(const uint32_t (&n)[4], double (&v)
   for (int k = 0; k < 4; ++k) v[k] = code_value(n[k], 0.0);
 }
 
+// w[0] = p[-1] and w[1..8] = p[0..7], p 16-byte aligned (the value columns
+// of code columns 4g-1 .. 4g+7 of one row).
 template <class T>
-__device__ __forceinline__ void lds8(const T* p, T (&w)[8]);
+__device__ __forceinline__ void lds9(const T* p, T (&w)[9]);
 template <>
-__device__ __forceinline__ void lds8<float>(const float* p, float (&w)[8]) {
+__device__ __forceinline__ void lds9<float>(const float* p, float (&w)[9]) {
+  w[0] = p[-1];
   const float4 u = reinterpret_cast<const float4*>(p)[0], v = reinterpret_cast<const float4*>(p)[1];
-  w[0] = u.x; w[1] = u.y; w[2] = u.z; w[3] = u.w;
-  w[4] = v.x; w[5] = v.y; w[6] = v.z; w[7] = v.w;
+  w[1] = u.x; w[2] = u.y; w[3] = u.z; w[4] = u.w;
+  w[5] = v.x; w[6] = v.y; w[7] = v.z; w[8] = v.w;
 }
 template <>
-__device__ __forceinline__ void lds8<double>(const double* p, double (&w)[8]) {
+__device__ __forceinline__ void lds9<double>(const double* p, double (&w)[9]) {
+  w[0] = p[-1];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const double2 u = reinterpret_cast<const double2*>(p)[i];
-    w[2 * i] = u.x;
-    w[2 * i + 1] = u.y;
+    w[1 + 2 * i] = u.x;
+    w[2 + 2 * i] = u.y;
   }
+}
+
+// Two consecutive codes (negabinary, window shift applied).
+__device__ __forceinline__ void code_pair(const uint16_t* p, int wb, uint32_t (&n)[2]) {
+  const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
+  n[0] = (v & 0xFFFFu) << wb;
+  n[1] = (v >> 16) << wb;
+}
+__device__ __forceinline__ void code_pair(const uint32_t* p, int, uint32_t (&n)[2]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  n[0] = v.x;
+  n[1] = v.y;
 }
 
 // Stores the values v[0..7] of lattice columns c2e .. c2e+7 of one row
@@ -644,43 +659,73 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
 
   // Phase 1a: even value rows -- the sweep-0 predictions of an odd plane
   // (its codes are added in phase 1b), or the known points of an even plane.
-  // Column slot js < HC is own code column js (value column js + 1); the
-  // three halo columns (value columns 0, HC+1, HC+2) are spread over threads.
+  // Own code columns go in pairs (2p, 2p+1) to the threads p = tid % 128;
+  // the first 128 threads take the upper rows, the others the lower rows. At
+  // stride 1 the two values of a pair and the element between them (and the
+  // one after) are one 16-byte load per plane. The three halo columns are
+  // spread over threads.
   const bool has0 = S0.out_end > S0.out_begin;
+  const int pp = tid & 127, jsp = 2 * pp;            // the pair's first code column
+  const int c2p = c.C0 + 2 * jsp;                    // its lattice column
+  const bool pa = c2p < M2, pb = c2p + 2 < M2;        // columns present
+  constexpr int H0A = (G::H0 + 1) / 2, H1A = G::H1 / 2;
   {
     const int64_t so = L.s * L.stride[0];
     const bool r1 = c.P + 1 <= M0 - 1;
     const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
-    auto item = [&](int je, int jr) {
-      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-      const T* p = out + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s;
-      T v;
-      if (!podd) {
-        v = __ldg(p);
-      } else {
-        const T bb = __ldg(p - so);
-        const T cc = r1 ? __ldg(p + so) : bb;
-        const T a = r3 ? __ldg(p - 3 * so) : bb;
-        const T d = r3 ? __ldg(p + 3 * so) : bb;
-        v = pred4<T>(a, bb, cc, d, c.P, M0, cubic);
-      }
-      VE[(2 * jr) * G::VP + je] = v;
+    auto one = [&](const T* p) -> T {
+      if (!podd) return __ldg(p);
+      const T bb = __ldg(p - so);
+      const T cc = r1 ? __ldg(p + so) : bb;
+      const T a = r3 ? __ldg(p - 3 * so) : bb;
+      const T d = r3 ? __ldg(p + 3 * so) : bb;
+      return pred4<T>(a, bb, cc, d, c.P, M0, cubic);
     };
-    {
-      const int js = tid, c2 = c.C0 + 2 * js;
-      if (c2 < M2) {
+    if (pa) {
+      const int jr0 = tid < 128 ? 0 : H0A, jr1 = tid < 128 ? H0A : G::H0;
+      const T* colp = out + c.pbase + (int64_t)c2p * L.s;
+      // 16-byte loads: float, stride 1, all four elements inside the row,
+      // every plane and row offset a multiple of four elements
+      const bool vec = sizeof(T) == 4 && L.s == 1 && c2p + 3 < M2 && (so & 3) == 0 &&
+                       (c.rs & 3) == 0 && ((uintptr_t)colp & 15) == 0;
 #pragma unroll
-        for (int jr = 0; jr < G::H0; ++jr) {
-          const int c1 = c.R0 - 2 + 2 * jr;
-          if (c1 >= 0 && c1 < M1) item(js + 1, jr);
+      for (int q = 0; q < H0A; ++q) {
+        const int jr = jr0 + q;
+        if (jr >= jr1) break;
+        const int c1 = c.R0 - 2 + 2 * jr;
+        if (c1 < 0 || c1 >= M1) continue;
+        const T* p = colp + (int64_t)c1 * c.rs;
+        T va, vb;
+        if (vec) {
+          const float* pf = reinterpret_cast<const float*>(p);
+          if (!podd) {
+            const float4 k = __ldg(reinterpret_cast<const float4*>(pf));
+            va = (T)k.x;
+            vb = (T)k.z;
+          } else {
+            const float4 bb = __ldg(reinterpret_cast<const float4*>(pf - so));
+            const float4 cc = r1 ? __ldg(reinterpret_cast<const float4*>(pf + so)) : bb;
+            const float4 a = r3 ? __ldg(reinterpret_cast<const float4*>(pf - 3 * so)) : bb;
+            const float4 d = r3 ? __ldg(reinterpret_cast<const float4*>(pf + 3 * so)) : bb;
+            va = (T)pred4<float>(a.x, bb.x, cc.x, d.x, c.P, M0, cubic);
+            vb = (T)pred4<float>(a.z, bb.z, cc.z, d.z, c.P, M0, cubic);
+          }
+        } else {
+          va = one(p);
+          vb = pb ? one(p + 2 * L.s) : va;
         }
+        typename Vec2<T>::type v2;
+        v2.x = va;
+        v2.y = vb;
+        *reinterpret_cast<typename Vec2<T>::type*>(VE + (2 * jr) * G::VP + G::V0 + jsp) = v2;
       }
     }
     if (tid < 3 * G::H0) {
       const int h = tid / G::H0, jr = tid - h * G::H0;
-      const int je = h == 0 ? 0 : G::HC + h;
-      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-      if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) item(je, jr);
+      const int js = h == 0 ? -1 : G::HC + h - 1;
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 + 2 * js;
+      if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2)
+        VE[(2 * jr) * G::VP + G::V0 + js] = one(out + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s);
     }
   }
   cp_async_wait_all();
@@ -794,38 +839,50 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
 
   // Phase 1b: the codes of sweep 0 (odd planes), over the items of phase 1a.
   if (podd) {
-    auto item = [&](int je, int jr, uint32_t n) {
-      T* p = VE + (2 * jr) * G::VP + je;
-      T v = FP<T>::add(*p, FP<T>::mul(code_value(n, T()), twoeb));
-      if (has0) {
-        const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-        const uint64_t ci = ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
-                            (uint64_t)(c2 >> 1);
-        find_outlier<T>(S0, oidx, oval, ci, &v);
-      }
-      *p = v;
+    auto fix = [&](int jr, int js, T* v) {
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 + 2 * js;
+      const uint64_t ci = ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
+                          (uint64_t)(c2 >> 1);
+      find_outlier<T>(S0, oidx, oval, ci, v);
     };
-    {
-      const int js = tid, c2 = c.C0 + 2 * js;
-      if (c2 < M2) {
-#pragma unroll 4
-        for (int jr = 0; jr < G::H0; ++jr) {
-          const int c1 = c.R0 - 2 + 2 * jr;
-          if (c1 >= 0 && c1 < M1) item(js + 1, jr, code_at(Q0 + jr * G::QP + qoff<W16>(js), wb));
+    if (pa) {
+      const int jr0 = tid < 128 ? 0 : H0A, jr1 = tid < 128 ? H0A : G::H0;
+#pragma unroll
+      for (int q = 0; q < H0A; ++q) {
+        const int jr = jr0 + q;
+        if (jr >= jr1) break;
+        const int c1 = c.R0 - 2 + 2 * jr;
+        if (c1 < 0 || c1 >= M1) continue;
+        typedef typename Vec2<T>::type V2;
+        V2* pv = reinterpret_cast<V2*>(VE + (2 * jr) * G::VP + G::V0 + jsp);
+        V2 v = *pv;
+        uint32_t n[2];
+        code_pair(Q0 + jr * G::QP + qoff<W16>(jsp), wb, n);
+        v.x = FP<T>::add(v.x, FP<T>::mul(code_value(n[0], T()), twoeb));
+        v.y = FP<T>::add(v.y, FP<T>::mul(code_value(n[1], T()), twoeb));
+        if (has0) {
+          fix(jr, jsp, &v.x);
+          if (pb) fix(jr, jsp + 1, &v.y);
         }
+        *pv = v;
       }
     }
     if (tid < 3 * G::H0) {
       const int h = tid / G::H0, jr = tid - h * G::H0;
-      const int je = h == 0 ? 0 : G::HC + h;
-      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-      if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2)
-        item(je, jr, QH[(G::H1 + jr) * 4 + h]);
+      const int js = h == 0 ? -1 : G::HC + h - 1;
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 + 2 * js;
+      if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) {
+        T* p = VE + (2 * jr) * G::VP + G::V0 + js;
+        T v = FP<T>::add(*p, FP<T>::mul(code_value(QH[(G::H1 + jr) * 4 + h], T()), twoeb));
+        if (has0) fix(jr, js, &v);
+        *p = v;
+      }
     }
     __syncthreads();
   }
 
-  // Phase 2: sweep 1 on the odd rows, columns [C0-2, C1+2].
+  // Phase 2: sweep 1 on the odd rows, columns [C0-2, C1+2]; pairs of
+  // columns as in phase 1, the four row neighbours kept in registers.
   {
     const bool has1 = S1.out_end > S1.out_begin;
     auto value = [&](T a, T bb, T cc, T d, int c1, int c2, uint32_t n) {
@@ -839,15 +896,23 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       return v;
     };
     if (S1.present) {
-      const int js = tid, c2 = c.C0 + 2 * js;
-      if (c2 < M2) {
-        T* col = VE + js + 1;
-        T a = col[0], bb = col[2 * G::VP], cc = col[4 * G::VP];
-        for (int jr = 0; jr < G::H1; ++jr) {
+      if (pa) {
+        typedef typename Vec2<T>::type V2;
+        const int jr0 = tid < 128 ? 0 : H1A, jr1 = tid < 128 ? H1A : G::H1;
+        T* col = VE + G::V0 + jsp;
+        V2 a = *reinterpret_cast<const V2*>(col + (2 * jr0) * G::VP);
+        V2 bb = *reinterpret_cast<const V2*>(col + (2 * jr0 + 2) * G::VP);
+        V2 cc = *reinterpret_cast<const V2*>(col + (2 * jr0 + 4) * G::VP);
+        for (int jr = jr0; jr < jr1; ++jr) {
           const int c1 = c.R0 + 1 + 2 * jr;
           if (c1 >= c.R1) break;
-          const T d = col[(2 * jr + 6) * G::VP];
-          col[(2 * jr + 3) * G::VP] = value(a, bb, cc, d, c1, c2, code_at(Q1 + jr * G::QP + qoff<W16>(js), wb));
+          const V2 d = *reinterpret_cast<const V2*>(col + (2 * jr + 6) * G::VP);
+          uint32_t n[2];
+          code_pair(Q1 + jr * G::QP + qoff<W16>(jsp), wb, n);
+          V2 v;
+          v.x = value(a.x, bb.x, cc.x, d.x, c1, c2p, n[0]);
+          v.y = value(a.y, bb.y, cc.y, d.y, c1, c2p + 2, n[1]);
+          *reinterpret_cast<V2*>(col + (2 * jr + 3) * G::VP) = v;
           a = bb;
           bb = cc;
           cc = d;
@@ -855,11 +920,11 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       }
       if (tid < 3 * G::H1) {
         const int h = tid / G::H1, jr = tid - h * G::H1;
-        const int je = h == 0 ? 0 : G::HC + h;
-        const int c1 = c.R0 + 1 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
+        const int js = h == 0 ? -1 : G::HC + h - 1;
+        const int c1 = c.R0 + 1 + 2 * jr, c2 = c.C0 + 2 * js;
         if (c1 < c.R1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) {
-          const T* col = VE + je;
-          VE[(2 * jr + 3) * G::VP + je] =
+          const T* col = VE + G::V0 + js;
+          VE[(2 * jr + 3) * G::VP + G::V0 + js] =
               value(col[(2 * jr) * G::VP], col[(2 * jr + 2) * G::VP], col[(2 * jr + 4) * G::VP],
                     col[(2 * jr + 6) * G::VP], c1, c2, QH[jr * 4 + h]);
         }
@@ -887,8 +952,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       for (int lr = rq; lr < BR; lr += 4) {
         const int c1 = c.R0 + lr;
         if (c1 >= c.R1) break;
-        T w[8];
-        lds8<T>(VE + (lr + 2) * G::VP + 4 * g, w);
+        T w[9];
+        lds9<T>(VE + (lr + 2) * G::VP + G::V0 + 4 * g, w);
         uint32_t qa[4];
         load4(Q2 + lr * G::QP + qoff<W16>(4 * g), wb, qa);
         T val[4];
