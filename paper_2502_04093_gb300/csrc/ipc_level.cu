@@ -998,25 +998,32 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
 }
 
 // 16-bit code rows leave room for four CTAs per SM, 32-bit ones for three.
+// Persistent: the grid holds as many CTAs as fit at once; CTA i takes tiles
+// i, i + grid, ... (neighbouring CTAs stay on neighbouring tiles).
+template <bool W16> constexpr int retrieve_ctas_per_sm() { return W16 ? 4 : 3; }
+
 template <class T, int BR, int BC, bool W16>
 __global__ void __launch_bounds__(256, W16 ? 4 : 3) k_level_retrieve(
     LevelArgs L, T* out, T twoeb, int b, const uint32_t* __restrict__ cap,
     const uint32_t* __restrict__ bm, const uint64_t* __restrict__ oidx,
-    const double* __restrict__ oval, LevelDescs D) {
+    const double* __restrict__ oval, LevelDescs D, uint64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem[];
-  level_retrieve_body<T, BR, BC, W16>(L, out, twoeb, b, cap, bm, oidx, oval, D, blockIdx.x, smem);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    level_retrieve_body<T, BR, BC, W16>(L, out, twoeb, b, cap, bm, oidx, oval, D, t, smem);
+    __syncthreads();  // the next tile reuses shared memory
+  }
 }
 
 // Batched kernels: one grid covers the level's CTAs of every field of a
 // batch; entry i owns CTAs [cta_begin_i, cta_begin_{i+1}).
 template <class E>
-__device__ __forceinline__ const E& find_entry(const E* __restrict__ ents, int n) {
+__device__ __forceinline__ const E& find_entry(const E* __restrict__ ents, int n, uint64_t tile) {
   __shared__ int sel;
   if (threadIdx.x == 0) {
     int lo = 0, hi = n;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
-      if (ents[mid].cta_begin <= blockIdx.x) lo = mid;
+      if (ents[mid].cta_begin <= tile) lo = mid;
       else hi = mid;
     }
     sel = lo;
@@ -1029,7 +1036,7 @@ template <class T, int BR, int BC>
 __global__ void __launch_bounds__(256, 3) k_level_compress_batch(
     const CompressEntry* __restrict__ ents, int n) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const CompressEntry& e = find_entry(ents, n);
+  const CompressEntry& e = find_entry(ents, n, blockIdx.x);
   level_compress_body<T, BR, BC>(e.L, (const T*)e.x, (T*)e.xh, e.write_xh,
                                  *reinterpret_cast<const QuantArgs<T>*>(e.quant), e.o, e.D,
                                  blockIdx.x - e.cta_begin, smem);
@@ -1037,11 +1044,14 @@ __global__ void __launch_bounds__(256, 3) k_level_compress_batch(
 
 template <class T, int BR, int BC, bool W16>
 __global__ void __launch_bounds__(256, W16 ? 4 : 3) k_level_retrieve_batch(
-    const RetrieveEntry* __restrict__ ents, int n) {
+    const RetrieveEntry* __restrict__ ents, int n, uint64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const RetrieveEntry& e = find_entry(ents, n);
-  level_retrieve_body<T, BR, BC, W16>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx,
-                                      e.oval, e.D, blockIdx.x - e.cta_begin, smem);
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const RetrieveEntry& e = find_entry(ents, n, t);
+    level_retrieve_body<T, BR, BC, W16>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx,
+                                        e.oval, e.D, t - e.cta_begin, smem);
+    __syncthreads();  // the next tile reuses shared memory (and the entry index)
+  }
 }
 
 template <class T, int BR, int BC>
@@ -1085,17 +1095,35 @@ cudaError_t setup_once() {
   return e;
 }
 
+// CTAs of a persistent launch over `tiles` tiles: all that fit on the
+// device at once (SM count of the current device, looked up once).
+template <bool W16>
+unsigned persistent_grid(uint64_t tiles) {
+  static int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 152;
+    }
+    return n;
+  }();
+  const uint64_t cap = (uint64_t)sms * retrieve_ctas_per_sm<W16>();
+  return (unsigned)(tiles < cap ? tiles : cap);
+}
+
 template <class T, int BR, int BC, bool W16>
 void retrieve_kernel(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
                      const uint32_t* bm, const uint64_t* oidx, const double* oval,
-                     const LevelDescs& d, uint64_t grid, cudaStream_t st) {
-  k_level_retrieve<T, BR, BC, W16><<<(unsigned)grid, 256, smem_retrieve<T, BR, BC, W16>(), st>>>(
-      L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval, d);
+                     const LevelDescs& d, uint64_t tiles, cudaStream_t st) {
+  k_level_retrieve<T, BR, BC, W16>
+      <<<persistent_grid<W16>(tiles), 256, smem_retrieve<T, BR, BC, W16>(), st>>>(
+          L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval, d, tiles);
 }
 template <class T, int BR, int BC, bool W16>
-void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t ctas, cudaStream_t st) {
+void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t tiles, cudaStream_t st) {
   k_level_retrieve_batch<T, BR, BC, W16>
-      <<<(unsigned)ctas, 256, smem_retrieve<T, BR, BC, W16>(), st>>>(ents, n);
+      <<<persistent_grid<W16>(tiles), 256, smem_retrieve<T, BR, BC, W16>(), st>>>(ents, n, tiles);
 }
 
 }  // namespace
