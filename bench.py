@@ -266,29 +266,60 @@ def run_ours(args, rank, world, local_rank):
 def e2e_measure(ipc, x, args, world):
     """Same step through the public API with host buffers: pinned input ->
     device, compress, export of the container to host, every reconstruction
-    copied back to pinned host memory; all inside the timed region."""
+    copied back to pinned host memory; all inside the timed region. Two
+    device output buffers alternate so that the copy of one reconstruction
+    (on a copy stream) overlaps the computation of the next."""
     import torch
     hx = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
     hx.copy_(x.cpu())
-    hout = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    houts = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for _ in range(2)]
     dx = torch.empty_like(x)
-    out = torch.empty_like(x)
+    outs = [torch.empty_like(x) for _ in range(2)]
     nbytes = x.numel() * x.element_size()
     n_recon = len(EB_SWEEP) + len(BITRATES)
+    main = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    hblob = None  # pinned host buffer of the exported container (sized on first use)
 
     def step():
         dx.copy_(hx, non_blocking=True)
+        nonlocal hblob
         f = ipc.ipc_compress(dx, EB, ipc.IPC_EB_ABS, ipc.IPC_CUBIC, ipc.IPC_BOUND_STRICT)
-        blob = ipc.ipc_export(f)
-        v = ipc.ipc_retrieve(f, ipc.IPC_TARGET_EB, EB_SWEEP[0], out)
-        hout.copy_(out, non_blocking=True)
-        for E in EB_SWEEP[1:]:
-            ipc.ipc_refine(v, ipc.IPC_TARGET_EB, E, out)
-            hout.copy_(out, non_blocking=True)
-        ipc.ipc_free(v)
-        for br in BITRATES:
-            ipc.ipc_retrieve(f, ipc.IPC_TARGET_BITRATE, br, out, want_view=False)
-            hout.copy_(out, non_blocking=True)
+        need = ipc.ipc_export_size(f)
+        if hblob is None or hblob.numel() < need:
+            hblob = torch.empty(need + (need >> 4), dtype=torch.uint8, pin_memory=True)
+        blob = ipc.ipc_export(f, hblob.numpy())
+        freed = [None, None]  # copy-stream events: buffer i may be rewritten
+        view = None
+        cur = 0  # buffer holding the view's latest reconstruction
+        for i in range(n_recon):
+            k = i % 2
+            o = outs[k]
+            if freed[k] is not None:
+                main.wait_event(freed[k])
+            if i == 0:
+                view = ipc.ipc_retrieve(f, ipc.IPC_TARGET_EB, EB_SWEEP[0], o)
+                cur = k
+            elif i < len(EB_SWEEP):
+                before = ipc.ipc_selection(view)[0]
+                ipc.ipc_refine(view, ipc.IPC_TARGET_EB, EB_SWEEP[i], o)
+                if ipc.ipc_selection(view)[0] != before:
+                    cur = k  # else the target was already met: same data as before
+            else:
+                if view is not None:
+                    ipc.ipc_free(view)
+                    view = None
+                ipc.ipc_retrieve(f, ipc.IPC_TARGET_BITRATE, BITRATES[i - len(EB_SWEEP)], o,
+                                 want_view=False)
+                cur = k
+            done = torch.cuda.Event()
+            done.record(main)
+            copy.wait_event(done)
+            with torch.cuda.stream(copy):
+                houts[k].copy_(outs[cur], non_blocking=True)
+                outs[cur].record_stream(copy)
+            freed[cur] = torch.cuda.Event()
+            freed[cur].record(copy)
         torch.cuda.synchronize()
         ipc.ipc_free(f)
         return len(blob)
@@ -303,7 +334,8 @@ def e2e_measure(ipc, x, args, world):
     t1 = time.perf_counter()
     sec = max_over_ranks((t1 - t0) / steps, x.device, world)
     return {"value": round(job_gbs(world, nbytes * (1 + n_recon), 1, sec), 2), "unit": "GB/s",
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": blen + n_recon * nbytes}
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": blen + n_recon * nbytes,
+            "overlap": "two device output buffers; device->host copies on a second stream"}
 
 
 # ---------------------------------------------------------------------------

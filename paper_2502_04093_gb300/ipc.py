@@ -208,12 +208,28 @@ def ipc_compressed_size(field) -> int:
     return n.value
 
 
-def ipc_export(field) -> bytes:
+def ipc_export_size(field) -> int:
     n = C.c_uint64()
     _check(lib().ipc_export(field, None, C.byref(n)), "ipc_export")
-    buf = (C.c_uint8 * max(n.value, 1))()
-    _check(lib().ipc_export(field, buf, C.byref(n)), "ipc_export")
-    return bytes(buf)[:n.value]
+    return n.value
+
+
+def ipc_export(field, out=None):
+    """The container as bytes; or, when `out` is a writable host array (e.g.
+    a numpy view of pinned memory) of at least ipc_export_size bytes, the
+    container is written into it and a memoryview of its bytes returned."""
+    n = C.c_uint64(ipc_export_size(field))
+    if out is None:
+        buf = (C.c_uint8 * max(n.value, 1))()
+        _check(lib().ipc_export(field, buf, C.byref(n)), "ipc_export")
+        return bytes(buf)[:n.value]
+    mv = memoryview(out).cast("B")
+    if mv.readonly or len(mv) < n.value:
+        raise ValueError("export buffer must be writable and hold %d bytes" % n.value)
+    addr = C.addressof(C.c_uint8.from_buffer(mv))
+    n = C.c_uint64(len(mv))
+    _check(lib().ipc_export(field, C.c_void_p(addr), C.byref(n)), "ipc_export")
+    return mv[:n.value]
 
 
 def ipc_import(data: bytes, stream=None) -> C.c_void_p:

@@ -202,3 +202,17 @@ def test_multi_tile_rows(shape):
     assert g.export() == o.export()
     for E in (1e-5, 1e-3):
         check_retrieve(g, o, oracle.EB, E)
+
+
+def test_export_into_host_buffer():
+    """ipc_export into a caller's (pinned) buffer gives the same container."""
+    x = synth.random_field((33, 40, 50), seed=21)
+    g, o = both(x, 1e-4)
+    raw = o.export()
+    n = ipc.ipc_export_size(g.h)
+    assert n == len(raw)
+    buf = torch.empty(n + 7, dtype=torch.uint8, pin_memory=True)
+    mv = ipc.ipc_export(g.h, buf.numpy())
+    assert bytes(mv) == raw
+    with pytest.raises(ValueError):
+        ipc.ipc_export(g.h, bytearray(n - 1))
