@@ -39,18 +39,6 @@ template <class T> struct Vec2;
 template <> struct Vec2<float> { typedef float2 type; };
 template <> struct Vec2<double> { typedef double2 type; };
 
-template <int BR, int BC>
-struct Tile {
-  static constexpr int HC = BC / 2;       // lattice columns of one parity
-  static constexpr int CWD = BC / 64;     // words per row of a full tile
-  static constexpr int PITCH = HC + CWD;  // code-row pitch (33 words per 32 codes)
-  static constexpr int VR = BR + 5;       // VE rows: c1 in [R0-2, R0+BR+2]
-  static constexpr int VEC = HC + 3;      // VE columns: even c2 in [C0-2, C0+BC+2]
-};
-
-// Swizzled index of code column lc in a code row (one pad word per 32).
-__device__ __forceinline__ int sw(int lc) { return lc + (lc >> 5); }
-
 struct CtaPos {
   int P, R0, R1, C0, C1;
   uint64_t rb, ct;
@@ -74,10 +62,6 @@ __device__ __forceinline__ CtaPos cta_pos(const LevelArgs& L, uint64_t cta, int 
   return c;
 }
 
-// Element index of lattice point (P, c1, c2) of the CTA's plane.
-__device__ __forceinline__ int64_t eidx(const LevelArgs& L, const CtaPos& c, int c1, int c2) {
-  return c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s;
-}
 
 // Prediction from four lattice neighbours along one dimension (Eq. 1/2 with
 // the boundary rule): i is the target's lattice coordinate, M the extent.
@@ -145,246 +129,6 @@ __device__ __forceinline__ bool find_outlier(const LevelStage& S, const uint64_t
     return true;
   }
   return false;
-}
-
-// Writes the plane tile's lattice values (rows [R0, R1), columns [C0, C1))
-// to the natural-layout array: the known values of the next level (compress)
-// or the reconstruction (retrieve). At stride 1 a (even, odd) pair is one
-// vector store; at stride 2 each value is stored twice so that whole sectors
-// are written -- the element in between is a target of the next level and is
-// never read as a known value.
-template <class T, int BR, int HC, int VEC>
-__device__ __forceinline__ void store_tile(const LevelArgs& L, const CtaPos& c, const T* VE,
-                                           const T* VO, T* dst) {
-  typedef typename Vec2<T>::type V2;
-  const int ncol = c.C1 - c.C0;
-  for (int it = threadIdx.x; it < BR * HC; it += 256) {
-    const int lr = it / HC, jp = it - lr * HC;
-    const int c1 = c.R0 + lr, c2 = c.C0 + 2 * jp;
-    if (c1 >= c.R1 || 2 * jp >= ncol) continue;
-    const T ve = VE[(lr + 2) * VEC + jp + 1];
-    const int64_t e = eidx(L, c, c1, c2);
-    const bool hasodd = 2 * jp + 1 < ncol;
-    const T vo = hasodd ? VO[lr * HC + jp] : ve;
-    if (L.vec && L.s == 1 && hasodd && (e & 1) == 0) {
-      V2 v2;
-      v2.x = ve;
-      v2.y = vo;
-      *reinterpret_cast<V2*>(dst + e) = v2;
-    } else if (L.s == 2) {
-      V2 v2;
-      if (L.vec && (e & 1) == 0 && 2 * (int64_t)c2 + 1 < L.N[2]) {
-        v2.x = ve;
-        v2.y = ve;
-        *reinterpret_cast<V2*>(dst + e) = v2;
-      } else {
-        dst[e] = ve;
-      }
-      if (hasodd) {
-        if (L.vec && ((e + 2) & 1) == 0 && 2 * (int64_t)c2 + 3 < L.N[2]) {
-          v2.x = vo;
-          v2.y = vo;
-          *reinterpret_cast<V2*>(dst + e + 2) = v2;
-        } else {
-          dst[e + 2] = vo;
-        }
-      }
-    } else {
-      dst[e] = ve;
-      if (hasodd) dst[e + L.s] = vo;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Compression of one level.
-// ---------------------------------------------------------------------------
-template <class T, int BR, int BC>
-__device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T* __restrict__ x,
-                                                    T* xh, int write_xh, const QuantArgs<T>& qa,
-                                                    const SweepOut& o, const LevelDescs& D,
-                                                    uint64_t cta, unsigned char* smem) {
-  typedef Tile<BR, BC> G;
-  T* VE = reinterpret_cast<T*>(smem);                     // [VR][VEC]
-  T* VO = VE + G::VR * G::VEC;                            // [BR][HC]
-  uint32_t* E2 = reinterpret_cast<uint32_t*>(VO + BR * G::HC);  // [BR][PITCH]
-  uint32_t* E1 = E2 + BR * G::PITCH;                      // [BR/2][PITCH]
-  uint32_t* E0 = E1 + (BR / 2) * G::PITCH;                // [BR/2][PITCH]
-
-  const CtaPos c = cta_pos(L, cta, BR, BC);
-  const bool podd = (c.P & 1) != 0;
-  const int tid = threadIdx.x;
-  const int cubic = L.cubic;
-  const int M0 = (int)L.M[0], M1 = (int)L.M[1], M2 = (int)L.M[2];
-  uint32_t orN[3] = {0, 0, 0}, qmx[3] = {0, 0, 0};
-
-  // codes outside the grid (edge tiles) must read as zero in phase 4
-  if (c.R1 - c.R0 < BR || c.C1 - c.C0 < BC)
-    for (int i = tid; i < 2 * BR * G::PITCH; i += 256) E2[i] = 0;  // E2, E1, E0
-  __syncthreads();
-
-  // Phase 1: even rows of VE.
-  const LevelStage& S0 = L.st[0];
-  const int64_t so = L.s * L.stride[0];
-  const bool r1 = c.P + 1 <= M0 - 1;
-  const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
-#pragma unroll 2
-  for (int it = tid; it < (BR / 2 + 3) * G::VEC; it += 256) {
-    const int jr = it / G::VEC, je = it - jr * G::VEC;
-    const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-    if (c1 < 0 || c1 >= M1 || c2 < 0 || c2 >= M2 || c2 > c.C1 + 2) continue;
-    const int64_t e = eidx(L, c, c1, c2);
-    T v;
-    if (!podd) {
-      v = __ldg(xh + e);
-    } else {
-      const T b = __ldg(xh + e - so);
-      const T cc = r1 ? __ldg(xh + e + so) : b;
-      const T a = r3 ? __ldg(xh + e - 3 * so) : b;
-      const T d = r3 ? __ldg(xh + e + 3 * so) : b;
-      const T xv = __ldg(x + e);
-      const T pred = pred4<T>(a, b, cc, d, c.P, M0, cubic);
-      bool outl;
-      T rec;
-      const int32_t q = quantize<T>(xv, pred, qa, &rec, &outl);
-      v = rec;
-      if (c1 >= c.R0 && c1 < c.R1 && c2 >= c.C0 && c2 < c.C1) {
-        const uint32_t N = negabinary(q);
-        orN[0] |= N;
-        qmx[0] = max(qmx[0], (uint32_t)(q < 0 ? -q : q));
-        E0[((c1 - c.R0) >> 1) * G::PITCH + sw((c2 - c.C0) >> 1)] = N;
-        if (outl)
-          record_outlier(o, S0.t,
-                         ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
-                             (uint64_t)(c2 >> 1),
-                         (double)xv);
-      }
-    }
-    VE[(2 * jr) * G::VEC + je] = v;
-  }
-  __syncthreads();
-
-  // Phase 2: sweep 1 on the odd rows of the CTA, columns [C0-2, C1+2].
-  const LevelStage& S1 = L.st[1];
-#pragma unroll 2
-  for (int it = tid; it < (BR / 2) * G::VEC; it += 256) {
-    const int jr = it / G::VEC, je = it - jr * G::VEC;
-    const int c1 = c.R0 + 1 + 2 * jr, c2 = c.C0 - 2 + 2 * je;
-    if (c1 >= c.R1 || c2 < 0 || c2 >= M2 || c2 > c.C1 + 2) continue;
-    const T xv = __ldg(x + eidx(L, c, c1, c2));
-    const T b = VE[(2 * jr + 2) * G::VEC + je];
-    const T cc = VE[(2 * jr + 4) * G::VEC + je];
-    const T a = VE[(2 * jr) * G::VEC + je];
-    const T d = VE[(2 * jr + 6) * G::VEC + je];
-    const T pred = pred4<T>(a, b, cc, d, c1, M1, cubic);
-    bool outl;
-    T rec;
-    const int32_t q = quantize<T>(xv, pred, qa, &rec, &outl);
-    VE[(2 * jr + 3) * G::VEC + je] = rec;
-    if (c2 >= c.C0 && c2 < c.C1) {
-      const uint32_t N = negabinary(q);
-      orN[1] |= N;
-      qmx[1] = max(qmx[1], (uint32_t)(q < 0 ? -q : q));
-      E1[jr * G::PITCH + sw((c2 - c.C0) >> 1)] = N;
-      if (outl)
-        record_outlier(o, S1.t,
-                       ((uint64_t)c.P * S1.m1 + (uint64_t)((c1 - 1) >> 1)) * S1.m2 +
-                           (uint64_t)(c2 >> 1),
-                       (double)xv);
-    }
-  }
-  __syncthreads();
-
-  // Phase 3: sweep 2 on the odd columns of the CTA's rows.
-  const LevelStage& S2 = L.st[2];
-#pragma unroll 4
-  for (int it = tid; it < BR * G::HC; it += 256) {
-    const int lr = it / G::HC, jo = it - lr * G::HC;
-    const int c1 = c.R0 + lr, c2 = c.C0 + 1 + 2 * jo;
-    if (c1 >= c.R1 || c2 >= c.C1) continue;
-    const T xv = __ldg(x + eidx(L, c, c1, c2));
-    const T* row = VE + (lr + 2) * G::VEC;
-    const T pred = pred4<T>(row[jo], row[jo + 1], row[jo + 2], row[jo + 3], c2, M2, cubic);
-    bool outl;
-    T rec;
-    const int32_t q = quantize<T>(xv, pred, qa, &rec, &outl);
-    VO[lr * G::HC + jo] = rec;
-    const uint32_t N = negabinary(q);
-    orN[2] |= N;
-    qmx[2] = max(qmx[2], (uint32_t)(q < 0 ? -q : q));
-    E2[lr * G::PITCH + sw(jo)] = N;
-    if (outl)
-      record_outlier(o, S2.t,
-                     ((uint64_t)c.P * S2.m1 + (uint64_t)c1) * S2.m2 + (uint64_t)((c2 - 1) >> 1),
-                     (double)xv);
-  }
-  __syncthreads();
-
-  // Phase 3b: the level's values for the next level (known points there).
-  if (write_xh) store_tile<T, BR, G::HC, G::VEC>(L, c, VE, VO, xh);
-
-  // Phase 4: bitplane transpose and compaction of the three segments.
-  // Threads [0,128) words of stage 2, [128,192) stage 1, [192,256) stage 0.
-  const int lane = tid & 31;
-  int sidx, li;
-  if (tid < 128) { sidx = 2; li = tid; }
-  else if (tid < 192) { sidx = 1; li = tid - 128; }
-  else { sidx = 0; li = tid - 192; }
-  const LevelStage& S = L.st[sidx];
-  int nrows;  // rows of this stage owned by the CTA
-  if (sidx == 2) nrows = c.R1 - c.R0;
-  else if (sidx == 1) nrows = (c.R1 - c.R0) >> 1;
-  else nrows = podd ? (c.R1 - c.R0 + 1) >> 1 : 0;
-  const int RB = sidx == 2 ? BR : BR / 2;
-  const int CW = (int)S.CW;
-  const bool active = S.present && nrows > 0 && c.rb < S.nrb && c.ct < S.nct;
-  const int nwords = RB * CW;
-  const bool mine = active && li < nwords;
-  uint32_t pw[32];
-  {
-    const uint32_t* Eb = sidx == 2 ? E2 : (sidx == 1 ? E1 : E0);
-    const int lr = mine ? li / CW : 0, lj = mine ? li - lr * CW : 0;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) pw[i] = mine ? Eb[lr * G::PITCH + lj * 33 + i] : 0u;
-  }
-  transpose32(pw);
-  xor_encode_planes(pw);
-  const uint64_t pi = sidx == 0 ? (uint64_t)((c.P - 1) >> 1) : (uint64_t)c.P;
-  const uint64_t g = active ? seg_id(S, pi, c.rb, c.ct) : 0;
-  const uint32_t bwords = (uint32_t)((nwords + 31) / 32);
-  const PlaneDesc* pds = D.s[sidx].p;
-  const int wl = li >> 5;  // 32-word group of the segment (one warp)
-  const bool wact = active && wl < (int)bwords;
-  __shared__ uint32_t scnt[3][32];
-  if (tid < 96) scnt[tid >> 5][tid & 31] = 0;
-#pragma unroll
-  for (int st = 0; st < 3; ++st) {
-    const uint32_t a = __reduce_or_sync(~0u, orN[st]);
-    const uint32_t m = __reduce_max_sync(~0u, qmx[st]);
-    if (lane == 0) {
-      if (a) atomicOr(o.stat + 2 * L.st[st].t, a);
-      if (m) atomicMax(o.stat + 2 * L.st[st].t + 1, m);
-    }
-  }
-  __syncthreads();
-  const uint32_t lt = lanemask_lt();
-  const uint64_t capg = g * (uint64_t)nwords + (uint64_t)wl * 32;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    const uint32_t mk = __ballot_sync(~0u, pw[k] != 0);
-    if (wact) {
-      if (lane == k) {
-        o.bm[pds[k].bm_off + g * S.bw + wl] = mk;
-        if (mk) atomicAdd(&scnt[sidx][k], (uint32_t)__popc(mk));
-      }
-      if (pw[k]) o.cap[pds[k].cap_off + capg + __popc(mk & lt)] = pw[k];
-    }
-  }
-  __syncthreads();
-  if (tid < 96) {
-    const uint32_t n = scnt[tid >> 5][tid & 31];
-    if (n) atomicAdd(o.nnz + 32 * L.st[tid >> 5].t + (tid & 31), n);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -988,6 +732,379 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Compression of one level.
+//
+// Same tile and thread mappings as the reconstruction: value rows (even rows
+// first, then the odd rows) hold the reconstructed values x^ of the tile and
+// its halo; halo targets are recomputed exactly as their owner computes
+// them. Codes of the CTA's own points go to code rows (32-bit, blocked).
+// Phase 1: even value rows: sweep 0 of an odd plane (quantized against the
+//   prediction from the known planes P +- 1, P +- 3) or the known points.
+// Phase 2: odd value rows (sweep 1).
+// Phase 3: sweep 2, four odd columns per thread; when the next level needs
+//   them, the level's values are stored as runs of eight elements.
+// Phase 4: per 32-code word, the bitplane transpose (two 16x16 transposes
+//   when the warp's codes fit in 16 bits), the predictive XOR on the plane
+//   words, and per 32-word group the zero-word bitmap and the compacted
+//   nonzero words of every plane.
+// ---------------------------------------------------------------------------
+template <int BR, int BC>
+struct CTile {
+  static constexpr int HC = BC / 2;
+  static constexpr int CWD = BC / 64;
+  static constexpr int QP = CWD * 36;    // code-row pitch (32-bit codes, blocked)
+  static constexpr int H0 = BR / 2 + 3;  // even value rows: c1 = R0-2+2j
+  static constexpr int H1 = BR / 2;      // odd value rows: c1 = R0+1+2j
+  static constexpr int V0 = 4;           // value column of code column 0
+  static constexpr int VP = HC + 8;      // value-row pitch
+  __device__ static int even_row(int j) { return j * VP; }
+  __device__ static int odd_row(int j) { return (H0 + j) * VP; }
+  // value row of lattice row c1 = R0 + lr (own rows)
+  __device__ static int own_row(int lr) {
+    return (lr & 1) ? odd_row((lr - 1) >> 1) : even_row((lr >> 1) + 1);
+  }
+};
+
+template <class T, int BR, int BC>
+__device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T* __restrict__ x,
+                                                    T* xh, int write_xh, const QuantArgs<T>& qa,
+                                                    const SweepOut& o, const LevelDescs& D,
+                                                    uint64_t cta, unsigned char* smem) {
+  typedef CTile<BR, BC> G;
+  typedef typename Vec2<T>::type V2;
+  static_assert(G::HC == 256, "one thread per code column of a tile row");
+  T* VE = reinterpret_cast<T*>(smem);                                // [H0 + H1][VP]
+  uint32_t* E2 = reinterpret_cast<uint32_t*>(VE + (G::H0 + G::H1) * G::VP);  // [BR][QP]
+  uint32_t* E1 = E2 + BR * G::QP;                                    // [H1][QP]
+  uint32_t* E0 = E1 + G::H1 * G::QP;                                 // [BR/2][QP]
+
+  const CtaPos c = cta_pos(L, cta, BR, BC);
+  const bool podd = (c.P & 1) != 0;
+  const int tid = threadIdx.x;
+  const int cubic = L.cubic;
+  const int M0 = (int)L.M[0], M1 = (int)L.M[1], M2 = (int)L.M[2];
+  const LevelStage &S0 = L.st[0], &S1 = L.st[1], &S2 = L.st[2];
+  uint32_t orN[3] = {0, 0, 0}, qmx[3] = {0, 0, 0};
+  auto stat = [&](int st, int32_t q) {
+    orN[st] |= negabinary(q);
+    qmx[st] = max(qmx[st], (uint32_t)(q < 0 ? -q : q));
+  };
+
+  // codes outside the grid (edge tiles) must read as zero in phase 4
+  if (c.R1 - c.R0 < BR || c.C1 - c.C0 < BC)
+    for (int i = tid; i < (BR + G::H1 + BR / 2) * G::QP; i += 256) E2[i] = 0;
+  __syncthreads();
+
+  const int pp = tid & 127, jsp = 2 * pp;  // code-column pair of the thread
+  const int c2p = c.C0 + 2 * jsp;
+  const bool pa = c2p < M2, pb = c2p + 2 < M2;
+  constexpr int H0A = (G::H0 + 1) / 2, H1A = G::H1 / 2;
+  // 16-byte loads of x / x^ rows: float, stride 1, four elements inside the
+  // row, rows and planes multiples of four elements apart
+  const int64_t so = L.s * L.stride[0];
+  const bool vec = sizeof(T) == 4 && L.s == 1 && c2p + 3 < M2 && (so & 3) == 0 &&
+                   (c.rs & 3) == 0 && ((uintptr_t)(x + c.pbase + c2p) & 15) == 0 &&
+                   ((uintptr_t)(xh + c.pbase + c2p) & 15) == 0;
+
+  // Phase 1: even value rows.
+  {
+    const bool r1 = c.P + 1 <= M0 - 1;
+    const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
+    // one point: value (quantized for an odd plane), code and bookkeeping
+    auto point = [&](T pred, T xv, int c1, int c2, bool own, T* v) {
+      bool outl;
+      T rec;
+      const int32_t q = quantize<T>(xv, pred, qa, &rec, &outl);
+      *v = rec;
+      if (own) {
+        stat(0, q);
+        E0[((c1 - c.R0) >> 1) * G::QP + qoff<false>((c2 - c.C0) >> 1)] = negabinary(q);
+        if (outl)
+          record_outlier(o, S0.t,
+                         ((uint64_t)((c.P - 1) >> 1) * S0.m1 + (uint64_t)(c1 >> 1)) * S0.m2 +
+                             (uint64_t)(c2 >> 1),
+                         (double)xv);
+      }
+    };
+    auto one = [&](int c1, int c2, bool own) -> T {
+      const int64_t e = c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s;
+      if (!podd) return __ldg(xh + e);
+      const T bb = __ldg(xh + e - so);
+      const T cc = r1 ? __ldg(xh + e + so) : bb;
+      const T a = r3 ? __ldg(xh + e - 3 * so) : bb;
+      const T d = r3 ? __ldg(xh + e + 3 * so) : bb;
+      T v;
+      point(pred4<T>(a, bb, cc, d, c.P, M0, cubic), __ldg(x + e), c1, c2, own, &v);
+      return v;
+    };
+    if (pa) {
+      const int jr0 = tid < 128 ? 0 : H0A, jr1 = tid < 128 ? H0A : G::H0;
+#pragma unroll
+      for (int q = 0; q < H0A; ++q) {
+        const int jr = jr0 + q;
+        if (jr >= jr1) break;
+        const int c1 = c.R0 - 2 + 2 * jr;
+        if (c1 < 0 || c1 >= M1) continue;
+        const bool ownr = c1 >= c.R0 && c1 < c.R1;
+        T va, vb;
+        if (vec) {
+          const int64_t e = c.pbase + (int64_t)c1 * c.rs + c2p;
+          const float* xf = reinterpret_cast<const float*>(xh) + e;
+          if (!podd) {
+            const float4 k = __ldg(reinterpret_cast<const float4*>(xf));
+            va = (T)k.x;
+            vb = (T)k.z;
+          } else {
+            const float4 bb = __ldg(reinterpret_cast<const float4*>(xf - so));
+            const float4 cc = r1 ? __ldg(reinterpret_cast<const float4*>(xf + so)) : bb;
+            const float4 a = r3 ? __ldg(reinterpret_cast<const float4*>(xf - 3 * so)) : bb;
+            const float4 d = r3 ? __ldg(reinterpret_cast<const float4*>(xf + 3 * so)) : bb;
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e));
+            point((T)pred4<float>(a.x, bb.x, cc.x, d.x, c.P, M0, cubic), (T)xv.x, c1, c2p, ownr, &va);
+            point((T)pred4<float>(a.z, bb.z, cc.z, d.z, c.P, M0, cubic), (T)xv.z, c1, c2p + 2,
+                  ownr, &vb);
+          }
+        } else {
+          va = one(c1, c2p, ownr);
+          vb = pb ? one(c1, c2p + 2, ownr) : va;
+        }
+        V2 v2;
+        v2.x = va;
+        v2.y = vb;
+        *reinterpret_cast<V2*>(VE + G::even_row(jr) + G::V0 + jsp) = v2;
+      }
+    }
+    if (tid < 3 * G::H0) {
+      const int h = tid / G::H0, jr = tid - h * G::H0;
+      const int js = h == 0 ? -1 : G::HC + h - 1;
+      const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 + 2 * js;
+      if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2)
+        VE[G::even_row(jr) + G::V0 + js] = one(c1, c2, false);
+    }
+  }
+  __syncthreads();
+
+  // Phase 2: sweep 1 on the odd rows, columns [C0-2, C1+2].
+  if (S1.present) {
+    auto point = [&](T a, T bb, T cc, T d, int c1, int c2, bool own, T xv) -> T {
+      const T pred = pred4<T>(a, bb, cc, d, c1, M1, cubic);
+      bool outl;
+      T rec;
+      const int32_t q = quantize<T>(xv, pred, qa, &rec, &outl);
+      if (own) {
+        stat(1, q);
+        E1[((c1 - c.R0 - 1) >> 1) * G::QP + qoff<false>((c2 - c.C0) >> 1)] = negabinary(q);
+        if (outl)
+          record_outlier(o, S1.t,
+                         ((uint64_t)c.P * S1.m1 + (uint64_t)((c1 - 1) >> 1)) * S1.m2 +
+                             (uint64_t)(c2 >> 1),
+                         (double)xv);
+      }
+      return rec;
+    };
+    if (pa) {
+      const int jr0 = tid < 128 ? 0 : H1A, jr1 = tid < 128 ? H1A : G::H1;
+      const T* col = VE + G::V0 + jsp;
+      V2 a = *reinterpret_cast<const V2*>(col + G::even_row(jr0));
+      V2 bb = *reinterpret_cast<const V2*>(col + G::even_row(jr0 + 1));
+      V2 cc = *reinterpret_cast<const V2*>(col + G::even_row(jr0 + 2));
+#pragma unroll
+      for (int q = 0; q < (G::H1 + 1) / 2; ++q) {
+        const int jr = jr0 + q;
+        if (jr >= jr1) break;
+        const int c1 = c.R0 + 1 + 2 * jr;
+        if (c1 >= c.R1) break;
+        const V2 d = *reinterpret_cast<const V2*>(col + G::even_row(jr + 3));
+        const int64_t e = c.pbase + (int64_t)c1 * c.rs + (int64_t)c2p * L.s;
+        T xa, xb;
+        if (vec) {
+          const float4 xv = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e));
+          xa = (T)xv.x;
+          xb = (T)xv.z;
+        } else {
+          xa = __ldg(x + e);
+          xb = pb ? __ldg(x + e + 2 * L.s) : xa;
+        }
+        V2 v;
+        v.x = point(a.x, bb.x, cc.x, d.x, c1, c2p, true, xa);
+        v.y = pb ? point(a.y, bb.y, cc.y, d.y, c1, c2p + 2, true, xb) : v.x;
+        *reinterpret_cast<V2*>(VE + G::odd_row(jr) + G::V0 + jsp) = v;
+        a = bb;
+        bb = cc;
+        cc = d;
+      }
+    }
+    if (tid < 3 * G::H1) {
+      const int h = tid / G::H1, jr = tid - h * G::H1;
+      const int js = h == 0 ? -1 : G::HC + h - 1;
+      const int c1 = c.R0 + 1 + 2 * jr, c2 = c.C0 + 2 * js;
+      if (c1 < c.R1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) {
+        const T* col = VE + G::V0 + js;
+        VE[G::odd_row(jr) + G::V0 + js] =
+            point(col[G::even_row(jr)], col[G::even_row(jr + 1)], col[G::even_row(jr + 2)],
+                  col[G::even_row(jr + 3)], c1, c2, false,
+                  __ldg(x + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s));
+      }
+    }
+  }
+  __syncthreads();
+
+  // Phase 3: sweep 2 (four odd columns per thread) and the level's values.
+  {
+    const int g = tid & 63, rq = tid >> 6;
+    const int c2e = c.C0 + 8 * g;
+    uint32_t rule = 0u;  // per odd column: 2 cubic, 1 linear, 0 copy
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = c2e + 2 * k + 1;
+      const uint32_t r = i + 1 > M2 - 1 ? 0u : ((cubic && i - 3 >= 0 && i + 3 <= M2 - 1) ? 2u : 1u);
+      rule |= r << (2 * k);
+    }
+    const bool vec8 = vec && c2e + 8 <= M2 && ((uintptr_t)(x + c.pbase + c2e) & 15) == 0;
+    if (c2e < c.C1) {
+      for (int lr = rq; lr < BR; lr += 4) {
+        const int c1 = c.R0 + lr;
+        if (c1 >= c.R1) break;
+        T w[9];
+        lds9<T>(VE + G::own_row(lr) + G::V0 + 4 * g, w);
+        const int64_t e = c.pbase + (int64_t)c1 * c.rs;
+        T xo[4];
+        if (vec8) {
+          const float4* xp = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e + c2e);
+          const float4 u = __ldg(xp), v = __ldg(xp + 1);
+          xo[0] = (T)u.y;
+          xo[1] = (T)u.w;
+          xo[2] = (T)v.y;
+          xo[3] = (T)v.w;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int c2o = c2e + 2 * k + 1;
+            xo[k] = c2o < c.C1 ? __ldg(x + e + (int64_t)c2o * L.s) : (T)0;
+          }
+        }
+        T v[8];
+        uint32_t n[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c2o = c2e + 2 * k + 1;
+          const T u = FP<T>::add(w[k + 1], w[k + 2]);
+          const T cub = FP<T>::mul(FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])),
+                                   (T)0.0625);
+          const T lin = FP<T>::mul(u, (T)0.5);
+          const uint32_t r = rule >> (2 * k) & 3u;
+          const T pred = r == 2u ? cub : (r == 1u ? lin : w[k + 1]);
+          bool outl;
+          T rec;
+          const int32_t q = quantize<T>(xo[k], pred, qa, &rec, &outl);
+          v[2 * k] = w[k + 1];
+          v[2 * k + 1] = rec;
+          n[k] = 0u;
+          if (c2o < c.C1) {
+            n[k] = negabinary(q);
+            stat(2, q);
+            if (outl)
+              record_outlier(o, S2.t,
+                             ((uint64_t)c.P * S2.m1 + (uint64_t)c1) * S2.m2 + (uint64_t)((c2o - 1) >> 1),
+                             (double)xo[k]);
+          }
+        }
+        *reinterpret_cast<uint4*>(E2 + lr * G::QP + qoff<false>(4 * g)) = make_uint4(n[0], n[1], n[2], n[3]);
+        if (write_xh) store_run<T>(xh + e, L, c2e, c.C1, v);
+      }
+    }
+  }
+  __syncthreads();
+
+  // Phase 4: bitplane transpose and compaction of the three segments.
+  // Threads [0,128) words of stage 2, [128,192) stage 1, [192,256) stage 0.
+  const int lane = tid & 31;
+  int sidx, li;
+  if (tid < 128) { sidx = 2; li = tid; }
+  else if (tid < 192) { sidx = 1; li = tid - 128; }
+  else { sidx = 0; li = tid - 192; }
+  const LevelStage& S = L.st[sidx];
+  int nrows;  // rows of this stage owned by the CTA
+  if (sidx == 2) nrows = c.R1 - c.R0;
+  else if (sidx == 1) nrows = (c.R1 - c.R0) >> 1;
+  else nrows = podd ? (c.R1 - c.R0 + 1) >> 1 : 0;
+  const int RB = sidx == 2 ? BR : BR / 2;
+  const int CW = (int)S.CW;
+  const bool active = S.present && nrows > 0 && c.rb < S.nrb && c.ct < S.nct;
+  const int nwords = RB * CW;
+  const bool mine = active && li < nwords;
+  uint32_t cd[32];  // the word's codes, then its plane words
+  uint32_t cor = 0u;
+  {
+    const uint32_t* Eb = sidx == 2 ? E2 : (sidx == 1 ? E1 : E0);
+    const int lr = mine ? li / CW : 0, lj = mine ? li - lr * CW : 0;
+    const uint4* src = reinterpret_cast<const uint4*>(Eb + lr * G::QP + lj * 36);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const uint4 u = mine ? src[m] : make_uint4(0u, 0u, 0u, 0u);
+      cd[4 * m] = u.x;
+      cd[4 * m + 1] = u.y;
+      cd[4 * m + 2] = u.z;
+      cd[4 * m + 3] = u.w;
+      cor |= u.x | u.y | u.z | u.w;
+    }
+  }
+  const uint32_t wor = __reduce_or_sync(~0u, cor);  // top plane of the warp's words
+  if ((wor >> 16) == 0u) {
+    // codes below 2^16: planes 16..31 are zero
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w[i] = cd[i] | (cd[16 + i] << 16);
+    transpose16x2(w);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) cd[k] = w[k];
+#pragma unroll
+    for (int k = 16; k < 32; ++k) cd[k] = 0u;
+  } else {
+    transpose32(cd);
+  }
+  xor_encode_planes(cd);
+  const uint64_t pi = sidx == 0 ? (uint64_t)((c.P - 1) >> 1) : (uint64_t)c.P;
+  const uint64_t gseg = active ? seg_id(S, pi, c.rb, c.ct) : 0;
+  const uint32_t bwords = (uint32_t)((nwords + 31) / 32);
+  const PlaneDesc* pds = D.s[sidx].p;
+  const int wl = li >> 5;  // 32-word group of the segment (one warp)
+  const bool wact = active && wl < (int)bwords;
+  __shared__ uint32_t scnt[3][32];
+  if (tid < 96) scnt[tid >> 5][tid & 31] = 0;
+#pragma unroll
+  for (int st = 0; st < 3; ++st) {
+    const uint32_t a = __reduce_or_sync(~0u, orN[st]);
+    const uint32_t m = __reduce_max_sync(~0u, qmx[st]);
+    if (lane == 0) {
+      if (a) atomicOr(o.stat + 2 * L.st[st].t, a);
+      if (m) atomicMax(o.stat + 2 * L.st[st].t + 1, m);
+    }
+  }
+  __syncthreads();
+  const uint32_t lt = lanemask_lt();
+  const uint64_t capg = gseg * (uint64_t)nwords + (uint64_t)wl * 32;
+  const int ktop = wor ? 31 - __clz((int)wor) : -1;  // XOR encoding keeps the top plane
+  uint32_t mybm = 0u;  // the bitmap word of plane `lane`
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k > ktop) break;
+    const uint32_t mk = __ballot_sync(~0u, cd[k] != 0u);
+    if (lane == k) mybm = mk;
+    if (wact && cd[k]) o.cap[pds[k].cap_off + capg + __popc(mk & lt)] = cd[k];
+  }
+  if (wact) {
+    o.bm[pds[lane].bm_off + gseg * S.bw + wl] = mybm;
+    if (mybm) atomicAdd(&scnt[sidx][lane], (uint32_t)__popc(mybm));
+  }
+  __syncthreads();
+  if (tid < 96) {
+    const uint32_t n = scnt[tid >> 5][tid & 31];
+    if (n) atomicAdd(o.nnz + 32 * L.st[tid >> 5].t + (tid & 31), n);
+  }
+}
+
 // Single-field kernels: arguments in the parameter space.
 template <class T, int BR, int BC>
 __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T* __restrict__ x,
@@ -1056,8 +1173,8 @@ __global__ void __launch_bounds__(256, W16 ? 4 : 3) k_level_retrieve_batch(
 
 template <class T, int BR, int BC>
 size_t smem_compress() {
-  typedef Tile<BR, BC> G;
-  return sizeof(T) * (G::VR * G::VEC + BR * G::HC) + 4 * (2 * BR * G::PITCH);
+  typedef CTile<BR, BC> G;
+  return sizeof(T) * (G::H0 + G::H1) * G::VP + 4 * (BR + G::H1 + BR / 2) * G::QP;
 }
 template <class T, int BR, int BC, bool W16>
 size_t smem_retrieve() {
