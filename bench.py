@@ -8,7 +8,10 @@ model. One step = one compression of the field + a progressive retrieval
 sweep: retrieve at eb 1e-1 and refine to 1e-2 ... 1e-6 (Algorithm 2), then
 independent retrievals at 0.5, 1, 2, 4, 8 and 16 bits/value. The metric is
 the bytes of field data the step moves through the codec -- the input of the
-compression plus the output of every reconstruction -- per second.
+compression plus the output of every reconstruction computed -- per second.
+A refine whose target the view already meets (with eb 1e-6, the refine
+from 1e-5 to 1e-6: the 1e-5 selection loads every plane) computes nothing
+and is not counted.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -143,17 +146,23 @@ def job_gbs(world: int, bytes_per_rank_step: float, steps: int, seconds: float) 
 # The GPU step (through the C ABI)
 # ---------------------------------------------------------------------------
 def gpu_step(ipc, x, out, ev=None):
-    """compress + refine chain + bitrate retrievals; returns the field handle."""
+    """compress + refine chain + bitrate retrievals; returns the field handle
+    and the number of reconstructions computed (a refine whose target the
+    view already meets computes nothing and is not counted)."""
     f = ipc.ipc_compress(x, EB, ipc.IPC_EB_ABS, ipc.IPC_CUBIC, ipc.IPC_BOUND_STRICT)
     if ev is not None:
         ev[1].record()
     v = ipc.ipc_retrieve(f, ipc.IPC_TARGET_EB, EB_SWEEP[0], out)
+    n = 1
     for E in EB_SWEEP[1:]:
+        before = ipc.ipc_selection(v)[0]
         ipc.ipc_refine(v, ipc.IPC_TARGET_EB, E, out)
+        n += ipc.ipc_selection(v)[0] != before
     ipc.ipc_free(v)
     for br in BITRATES:
         ipc.ipc_retrieve(f, ipc.IPC_TARGET_BITRATE, br, out, want_view=False)
-    return f
+        n += 1
+    return f, n
 
 
 def run_ours(args, rank, world, local_rank):
@@ -170,19 +179,20 @@ def run_ours(args, rank, world, local_rank):
     out = torch.empty_like(x)
     torch.cuda.synchronize()
     nbytes = x.numel() * x.element_size()
-    n_recon = len(EB_SWEEP) + len(BITRATES)
-    step_bytes = nbytes * (1 + n_recon)
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    # warm-up
-    for _ in range(args.warmup):
-        f = gpu_step(ipc, x, out)
+    # warm-up (also counts the reconstructions a step computes: the
+    # selections, and so the no-op refines, are the same every step)
+    n_recon = 0
+    for _ in range(max(1, args.warmup)):
+        f, n_recon = gpu_step(ipc, x, out)
         torch.cuda.synchronize()
         ipc.ipc_free(f)
+    step_bytes = nbytes * (1 + n_recon)
 
     # timed region (device time, CUDA events on the working stream)
     st = torch.cuda.current_stream()
@@ -197,7 +207,7 @@ def run_ours(args, rank, world, local_rank):
         e_start.record(st)
         fields = []
         for _ in range(args.steps):
-            f = gpu_step(ipc, x, out)
+            f, _ = gpu_step(ipc, x, out)
             fields.append((f, None))
             if len(fields) > 1:
                 # compress of this step synchronised the stream, so the
@@ -222,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(3):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(st)
-        f = gpu_step(ipc, x, out, ev)
+        f, _ = gpu_step(ipc, x, out, ev)
         ev[2].record(st)
         torch.cuda.synchronize()
         cm.append(ev[0].elapsed_time(ev[1]))
@@ -276,7 +286,7 @@ def e2e_measure(ipc, x, args, world):
     dx = torch.empty_like(x)
     outs = [torch.empty_like(x) for _ in range(2)]
     nbytes = x.numel() * x.element_size()
-    n_recon = len(EB_SWEEP) + len(BITRATES)
+    n_recon = len(EB_SWEEP) + len(BITRATES)  # outputs copied to the host per step
     main = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
     hblob = None  # pinned host buffer of the exported container (sized on first use)
@@ -292,6 +302,7 @@ def e2e_measure(ipc, x, args, world):
         freed = [None, None]  # copy-stream events: buffer i may be rewritten
         view = None
         cur = 0  # buffer holding the view's latest reconstruction
+        computed = 0
         for i in range(n_recon):
             k = i % 2
             o = outs[k]
@@ -300,11 +311,13 @@ def e2e_measure(ipc, x, args, world):
             if i == 0:
                 view = ipc.ipc_retrieve(f, ipc.IPC_TARGET_EB, EB_SWEEP[0], o)
                 cur = k
+                computed += 1
             elif i < len(EB_SWEEP):
                 before = ipc.ipc_selection(view)[0]
                 ipc.ipc_refine(view, ipc.IPC_TARGET_EB, EB_SWEEP[i], o)
                 if ipc.ipc_selection(view)[0] != before:
                     cur = k  # else the target was already met: same data as before
+                    computed += 1
             else:
                 if view is not None:
                     ipc.ipc_free(view)
@@ -312,6 +325,7 @@ def e2e_measure(ipc, x, args, world):
                 ipc.ipc_retrieve(f, ipc.IPC_TARGET_BITRATE, BITRATES[i - len(EB_SWEEP)], o,
                                  want_view=False)
                 cur = k
+                computed += 1
             done = torch.cuda.Event()
             done.record(main)
             copy.wait_event(done)
@@ -322,7 +336,7 @@ def e2e_measure(ipc, x, args, world):
             freed[cur].record(copy)
         torch.cuda.synchronize()
         ipc.ipc_free(f)
-        return len(blob)
+        return len(blob), computed
 
     for _ in range(max(1, args.warmup)):
         step()
@@ -330,10 +344,10 @@ def e2e_measure(ipc, x, args, world):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        blen = step()
+        blen, computed = step()
     t1 = time.perf_counter()
     sec = max_over_ranks((t1 - t0) / steps, x.device, world)
-    return {"value": round(job_gbs(world, nbytes * (1 + n_recon), 1, sec), 2), "unit": "GB/s",
+    return {"value": round(job_gbs(world, nbytes * (1 + computed), 1, sec), 2), "unit": "GB/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": blen + n_recon * nbytes,
             "overlap": "two device output buffers; device->host copies on a second stream"}
 
@@ -573,14 +587,19 @@ SAMPLE_SHAPE = (32, 256, 256)
 
 
 def oracle_step(oracle, xs):
+    """(seconds, reconstructions computed) of one step of the oracle."""
     t0 = time.perf_counter()
     f = oracle.compress(xs, EB, oracle.ABS, oracle.CUBIC, oracle.STRICT)
     y, v = f.retrieve(oracle.EB, EB_SWEEP[0])
+    n = 1
     for E in EB_SWEEP[1:]:
+        before = v.selection()[0]
         v.refine(oracle.EB, E)
+        n += v.selection()[0] != before
     for br in BITRATES:
         f.retrieve(oracle.BITRATE, br)
-    return time.perf_counter() - t0
+        n += 1
+    return time.perf_counter() - t0, n
 
 
 def oracle_sample():
@@ -596,9 +615,9 @@ def cpu_baseline(steps=1):
     from oracle import oracle
     oracle.build()
     xs = oracle_sample()
-    secs = [oracle_step(oracle, xs) for _ in range(steps)]
-    sec = statistics.median(secs)
-    n_recon = len(EB_SWEEP) + len(BITRATES)
+    runs = [oracle_step(oracle, xs) for _ in range(steps)]
+    sec = statistics.median(r[0] for r in runs)
+    n_recon = runs[-1][1]
     return {"value": round(xs.nbytes * (1 + n_recon) / sec / 1e9, 5), "unit": "GB/s",
             "cores": 1, "kind": "oracle",
             "sample": "%dx%dx%d corner slab of the same field, same step (compress + refine "
@@ -614,9 +633,8 @@ def run_reference(args):
         oracle_step(oracle, xs)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_step(oracle, xs)
+        _, n_recon = oracle_step(oracle, xs)
     sec = (time.perf_counter() - t0) / args.steps
-    n_recon = len(EB_SWEEP) + len(BITRATES)
     value = xs.nbytes * (1 + n_recon) / sec / 1e9
     sample = "%dx%dx%d corner slab of the 512^3 field, same step" % SAMPLE_SHAPE
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GB/s",
@@ -666,6 +684,7 @@ def main():
             "compress_ms": round(r["compress_ms"], 3),
             "retrieve_ms_avg": round(r["retrieve_ms"], 3),
             "compression_ratio": round(r["nbytes"] / r["csize"], 3),
+            "reconstructions_per_step": r["n_recon"],
             "roofline": r["roofline"],
             "kernels": r["kernels"],
             "gpu_launches": r["launches"],
