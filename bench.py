@@ -57,6 +57,32 @@ def parse():
     return ap.parse_args()
 
 
+KERNEL_SOURCES = ("ipc_device.cuh", "ipc_internal.h", "ipc_level.cu")
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2502_04093_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the level retrieve kernel from the committed
+    ncu capture (profiles/retrieve_level_traffic.json), or None when the
+    kernel sources changed since that capture."""
+    p = os.path.join(ROOT, "profiles", "retrieve_level_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("kernel_sources_sha256") != kernel_sources_sha256():
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -247,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = alg / (ms * 1e-3) / 1e9 if ms else 0.0
     roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
             "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": measured_traffic(),
             "launches": L, "avg_launch_us": round(ms * 1e3 / L, 2) if L else None}
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3),
                    "alg_GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None}

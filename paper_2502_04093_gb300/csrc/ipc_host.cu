@@ -846,6 +846,7 @@ struct BatchTable {
   std::vector<AnchorEntry> anchors;
   std::vector<uint64_t> lev_off, lev_ctas;
   std::vector<int> lev_w16;  // every entry of the level keeps 16-bit codes
+  std::vector<int> lev_ns;   // sub-tiles per tile of the level's launch
   int Kmax = 0;
   double alg_bytes = 0;
 };
@@ -858,12 +859,26 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   T->lev_off.assign(T->Kmax + 2, 0);
   T->lev_ctas.assign(T->Kmax + 2, 0);
   T->lev_w16.assign(T->Kmax + 2, 1);
+  T->lev_ns.assign(T->Kmax + 2, 1);
   T->ents.clear();
   T->anchors.clear();
   T->alg_bytes = 0;
   for (size_t i = 0; i < nf; ++i) T->anchors.push_back(AnchorEntry{outs[i], fs[i]->anchor});
   for (int l = T->Kmax; l >= 1; --l) {
     T->lev_off[l] = T->ents.size();
+    // the level's code width and tile shape hold for every entry
+    int ns = 4;
+    for (size_t i = 0; i < nf; ++i) {
+      ipc_field* f = fs[i];
+      if (l > f->g.K) continue;
+      if (!level_w16(f, l, bs[i][l - 1])) T->lev_w16[l] = 0;
+    }
+    for (size_t i = 0; i < nf; ++i) {
+      ipc_field* f = fs[i];
+      if (l > f->g.K) continue;
+      ns = std::min(ns, retrieve_subtiles(level_args(f, l).M[2], T->lev_w16[l]));
+    }
+    T->lev_ns[l] = ns;
     uint64_t cta = 0;
     for (size_t i = 0; i < nf; ++i) {
       ipc_field* f = fs[i];
@@ -880,9 +895,8 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       e.oval = f->d_oval;
       e.twoeb = bin_width(f);
       e.b = bs[i][l - 1];
-      if (!level_w16(f, l, e.b)) T->lev_w16[l] = 0;
       e.cta_begin = cta;
-      cta += (uint64_t)e.L.M[0] * e.L.nrb * e.L.nct;
+      cta += retrieve_tiles(e.L, ns);
       T->ents.push_back(e);
       for (int d = 0; d < 3; ++d) {
         const int t = f->g.level_stage[d][l - 1];
@@ -913,7 +927,7 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
     const int nn = (int)(T.lev_off[l - 1] - T.lev_off[l]);
     const long ph = profile ? prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st) : -1;
     CU(launch_level_retrieve_batch(dtype, d_ents + T.lev_off[l], nn, T.lev_ctas[l], T.lev_w16[l],
-                                   st));
+                                   T.lev_ns[l], st));
     if (profile) prof_end(ph, st, l == 1 ? T.alg_bytes : 0.0);
     ++nl;
   }

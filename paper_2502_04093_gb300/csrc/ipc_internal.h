@@ -156,6 +156,19 @@ cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStrea
 cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, void* xh,
                                   int write_xh, const void* quant, const SweepOut& o,
                                   const LevelDescs& d, cudaStream_t st);
+// Retrieve tiles of a level: levels whose lattice rows hold at most
+// kLevelCols/2 (kLevelCols/4) columns put 2 (4) planes of the same parity
+// side by side in one tile.
+// Tiles enumerate (plane group, row block, column tile), the groups
+// alternating even and odd planes.
+inline int retrieve_subtiles(int64_t M2, int) {
+  return M2 <= kLevelCols / 4 ? 4 : (M2 <= kLevelCols / 2 ? 2 : 1);
+}
+inline uint64_t retrieve_tiles(const LevelArgs& L, int ns) {
+  const int64_t ne = (L.M[0] + 1) / 2, no = L.M[0] / 2;
+  const uint64_t groups = (uint64_t)((ne + ns - 1) / ns + (no + ns - 1) / ns);
+  return groups * L.nrb * L.nct;
+}
 // w16: the planes loaded at the level span at most 16 (16-bit code rows).
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
@@ -165,8 +178,9 @@ int level_rows(int dtype);
 // Batched level launches: `ents` (device memory) sorted by cta_begin.
 cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,
                                         uint64_t ctas, cudaStream_t st);
+// Batched: `tiles` over all entries, each entry's tiles counted with `ns`.
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
-                                        uint64_t ctas, int w16, cudaStream_t st);
+                                        uint64_t tiles, int w16, int ns, cudaStream_t st);
 // Segmented <-> packed container streams of one stage (export / import).
 // tmp: 2 * 32 * nbm words of scratch; flags[0] = corruption flag,
 // flags[1 + k] = nonzero words found in plane k (import).

@@ -327,94 +327,152 @@ __device__ __forceinline__ void store_run(T* row, const LevelArgs& L, int c2e, i
     if (c2e + i < C1) row[(int64_t)(c2e + i) * L.s] = v[i];
 }
 
-template <class T, int BR, int BC, bool W16>
+// Tile of a level launch: NS planes of the same parity side by side, each a
+// sub-tile of BR rows and BC / NS lattice columns (NS > 1 only when the
+// level's rows are at most BC / NS wide). Tiles enumerate (plane group,
+// row block, column tile); with NS = 1 the groups are the planes in order.
+__device__ __forceinline__ CtaPos sub_pos(const LevelArgs& L, uint64_t tile, int j, int NS, int BR,
+                                          int BCs) {
+  CtaPos c;
+  uint64_t t = tile;
+  c.ct = t % L.nct;
+  t /= L.nct;
+  c.rb = t % L.nrb;
+  // groups alternate even / odd (an odd plane reads the known points of the
+  // even planes around it while they are in L2); the even groups can be one
+  // more than the odd ones
+  const int64_t grp = (int64_t)(t / L.nrb);
+  const int64_t go = (L.M[0] / 2 + NS - 1) / NS;
+  const int64_t par = grp < 2 * go ? (grp & 1) : 0, idx = grp < 2 * go ? (grp >> 1) : go;
+  c.P = (int)(2 * (idx * NS + j) + par);
+  c.R0 = (int)c.rb * BR;
+  c.R1 = (int)min(L.M[1], (int64_t)c.R0 + BR);
+  c.C0 = (int)c.ct * BCs;
+  c.C1 = (int)min(L.M[2], (int64_t)c.C0 + BCs);
+  c.pbase = (int64_t)c.P * L.stride[0] * L.s;
+  c.rs = L.stride[1] * L.s;
+  return c;
+}
+
+template <class T, int BR, int BC, bool W16, int NS>
 __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, T twoeb, int b,
                                                     const uint32_t* __restrict__ cap,
                                                     const uint32_t* __restrict__ bm,
                                                     const uint64_t* __restrict__ oidx,
                                                     const double* __restrict__ oval,
-                                                    const LevelDescs& D, uint64_t cta,
+                                                    const LevelDescs& D, uint64_t tile,
                                                     unsigned char* smem) {
-  typedef RTile<BR, BC, W16> G;
+  constexpr int BCs = BC / NS;  // lattice columns of a sub-tile
+  typedef RTile<BR, BCs, W16> G;
   typedef typename QCfg<W16>::QT QT;
   constexpr int NPL = QCfg<W16>::NPL;
-  static_assert(G::HC == 256, "one thread per code column of a tile row");
-  T* VE = reinterpret_cast<T*>(smem);                        // [VR][VP]
-  QT* Q2 = reinterpret_cast<QT*>(VE + G::VR * G::VP);        // [BR][QP]
-  QT* Q1 = Q2 + BR * G::QP;                                  // [H1][QP]
-  QT* Q0 = Q1 + G::H1 * G::QP;                               // [H0][QP]
-  uint32_t* QH = reinterpret_cast<uint32_t*>(Q0 + G::H0 * G::QP);  // [H1 + H0][4]
-  __shared__ uint32_t SB[kSlots][NPL][kMaxBw];  // group bitmaps of the window's planes
-  __shared__ const uint32_t* SP[kSlots][NPL];   // payload base of (segment, plane)
-  __shared__ unsigned long long SG[kSlots];     // segment id (or ~0 if absent)
-  __shared__ uint32_t s_km[3];                  // planes to load, per stage
-  __shared__ int s_ktop;
+  constexpr int TS = 256 / NS;                 // threads of a sub-tile
+  constexpr int BWS = kMaxBw / NS;             // bitmap words of a sub-tile's segment
+  static_assert(G::HC * NS == 256, "one thread per code column of a tile row");
+  constexpr size_t SUB = sizeof(T) * G::VR * G::VP + sizeof(QT) * (BR + G::H1 + G::H0) * G::QP +
+                         16 * (G::H1 + G::H0);  // bytes of a sub-tile's dynamic smem
+  // Segments a sub-tile reads: with one column tile per row (NS > 1) its
+  // own stage-2 and stage-1 segments and the stage-0 segments of row blocks
+  // rb-1..rb+1 (slots 0, 1, 2..4); otherwise also the column neighbours:
+  // 0 = stage 2 own; 1..3 = stage 1 (ct-1, ct, ct+1); 4..12 = stage 0
+  // (rb-1..rb+1) x (ct-1..ct+1).
+  constexpr int KS = NS > 1 ? 5 : kSlots;
+  __shared__ uint32_t SB[NS][KS][NPL][BWS];        // group bitmaps of the window's planes
+  __shared__ const uint32_t* SP[NS][KS][NPL];      // payload base of (segment, plane)
+  __shared__ unsigned long long SG[NS][KS];        // segment id (or ~0 if absent)
+  __shared__ uint32_t s_km[NS][3];                 // planes to load, per stage
+  __shared__ int s_ktop[NS];
+  __shared__ CtaPos s_pos[NS];                     // sub-tile positions
 
-  const CtaPos c = cta_pos(L, cta, BR, BC);
-  const bool podd = (c.P & 1) != 0;
   const int tid = threadIdx.x;
+  const int sub = tid / TS, ltid = tid % TS;  // the thread's sub-tile
+  auto VEof = [&](int s) { return reinterpret_cast<T*>(smem + s * SUB); };
+  auto Q2of = [&](int s) { return reinterpret_cast<QT*>(VEof(s) + G::VR * G::VP); };
+  auto Q1of = [&](int s) { return Q2of(s) + BR * G::QP; };
+  auto Q0of = [&](int s) { return Q1of(s) + G::H1 * G::QP; };
+  auto QHof = [&](int s) { return reinterpret_cast<uint32_t*>(Q0of(s) + G::H0 * G::QP); };
   const int cubic = L.cubic;
   const int M0 = (int)L.M[0], M1 = (int)L.M[1], M2 = (int)L.M[2];
   const LevelStage &S0 = L.st[0], &S1 = L.st[1], &S2 = L.st[2];
 
-  if (tid < 32) {
+  if (tid < NS) s_pos[tid] = sub_pos(L, tile, tid, NS, BR, BCs);
+  // the thread's own sub-tile (all sub-tiles of a tile share the plane
+  // parity; sub-tile 0 always holds a plane)
+  const CtaPos c = sub_pos(L, tile, sub, NS, BR, BCs);
+  const bool live = c.P < M0;
+  const bool podd = (c.P & 1) != 0;
+  T* VE = VEof(sub);
+  QT* Q2 = Q2of(sub);
+  QT* Q1 = Q1of(sub);
+  QT* Q0 = Q0of(sub);
+  uint32_t* QH = QHof(sub);
+
+  if (tid < 32 * NS) {
+    const int s = tid >> 5, k = tid & 31;
+    const CtaPos cs = sub_pos(L, tile, s, NS, BR, BCs);
+    const bool odd = (cs.P & 1) != 0, ok = cs.P < M0;
     uint32_t any = 0;
 #pragma unroll
     for (int sx = 0; sx < 3; ++sx) {
-      const bool ld = L.st[sx].present && (sx != 0 || podd) && tid >= b && D.s[sx].p[tid].nnz > 0;
+      const bool ld = ok && L.st[sx].present && (sx != 0 || odd) && k >= b && D.s[sx].p[k].nnz > 0;
       const uint32_t m = __ballot_sync(~0u, ld);
-      if (tid == 0) s_km[sx] = m;
+      if (k == 0) s_km[s][sx] = m;
       any |= m;
     }
-    if (tid == 0) s_ktop = any ? 31 - __clz((int)any) : -1;
+    if (k == 0) s_ktop[s] = any ? 31 - __clz((int)any) : -1;
   }
-  // slots: 0 = stage 2 own; 1..3 = stage 1 (ct-1, ct, ct+1);
-  //        4..12 = stage 0 (rb-1..rb+1) x (ct-1..ct+1)
-  if (tid >= 32 && tid < 32 + kSlots) {
-    const int sl = tid - 32;
+  if (tid >= 128 && tid < 128 + NS * KS) {
+    const int s = (tid - 128) / KS, sl = (tid - 128) % KS;
+    const CtaPos cs = sub_pos(L, tile, s, NS, BR, BCs);
     int sx, drb, dct;
     if (sl == 0) { sx = 2; drb = 0; dct = 0; }
-    else if (sl < 4) { sx = 1; drb = 0; dct = sl - 2; }
+    else if (KS == 5) {
+      sx = sl == 1 ? 1 : 0; drb = sl == 1 ? 0 : sl - 3; dct = 0;
+    } else if (sl < 4) { sx = 1; drb = 0; dct = sl - 2; }
     else { sx = 0; drb = (sl - 4) / 3 - 1; dct = (sl - 4) % 3 - 1; }
     const LevelStage& S = L.st[sx];
-    const int64_t rbs = (int64_t)c.rb + drb, cts = (int64_t)c.ct + dct;
-    const bool ok = S.present && (sx != 0 || podd) && rbs >= 0 && (uint64_t)rbs < S.nrb &&
-                    cts >= 0 && (uint64_t)cts < S.nct;
-    const uint64_t pi = sx == 0 ? (uint64_t)((c.P - 1) >> 1) : (uint64_t)c.P;
-    SG[sl] = ok ? seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts) : ~0ULL;
+    const int64_t rbs = (int64_t)cs.rb + drb, cts = (int64_t)cs.ct + dct;
+    const bool ok = cs.P < M0 && S.present && (sx != 0 || (cs.P & 1)) && rbs >= 0 &&
+                    (uint64_t)rbs < S.nrb && cts >= 0 && (uint64_t)cts < S.nct;
+    const uint64_t pi = sx == 0 ? (uint64_t)((cs.P - 1) >> 1) : (uint64_t)cs.P;
+    SG[s][sl] = ok ? seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts) : ~0ULL;
   }
   __syncthreads();
-  // Plane window: slot i of the staged tables is plane wb + i. With 16-bit
-  // codes the loaded planes [b, ktop] lie in [wb, wb + 15] (checked on the
-  // host for the level; a CTA's ktop is at most the level's).
-  const int ktop = s_ktop;
-  const int wb = W16 ? max(0, ktop - 15) : 0;
-  for (int u = tid; u < kSlots * NPL; u += 256) {
-    const int sl = u / NPL, i = u % NPL, k = wb + i;
-    const int sx = sl == 0 ? 2 : (sl < 4 ? 1 : 0);
-    const unsigned long long g = SG[sl];
-    if (g == ~0ULL || k > 31 || !((s_km[sx] >> k) & 1u)) continue;
+  // Plane window of each sub-tile: slot i of the staged tables is plane
+  // wb + i. With 16-bit codes the loaded planes [b, ktop] lie in
+  // [wb, wb + 15] (checked on the host for the level; a sub-tile's ktop is at
+  // most the level's).
+  auto wbof = [&](int s) { return W16 ? max(0, s_ktop[s] - 15) : 0; };
+  const int wb = wbof(sub);
+  for (int u = tid; u < NS * KS * NPL; u += 256) {
+    const int s = u / (KS * NPL), r = u % (KS * NPL);
+    const int sl = r / NPL, i = r % NPL, k = wbof(s) + i;
+    const int sx = sl == 0 ? 2 : (KS == 5 ? (sl == 1 ? 1 : 0) : (sl < 4 ? 1 : 0));
+    const unsigned long long g = SG[s][sl];
+    if (g == ~0ULL || k > 31 || !((s_km[s][sx] >> k) & 1u)) continue;
     const LevelStage& S = L.st[sx];
     const PlaneDesc& pd = D.s[sx].p[k];
-    SP[sl][i] = cap + pd.cap_off + g * (uint64_t)S.RB * S.CW;
+    SP[s][sl][i] = cap + pd.cap_off + g * (uint64_t)S.RB * S.CW;
     const uint32_t* bp = bm + pd.bm_off + g * S.bw;
-    for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[sl][i][v], bp + v);
+    for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[s][sl][i][v], bp + v);
   }
 
   // Phase 1a: even value rows -- the sweep-0 predictions of an odd plane
   // (its codes are added in phase 1b), or the known points of an even plane.
-  // Own code columns go in pairs (2p, 2p+1) to the threads p = tid % 128;
-  // the first 128 threads take the upper rows, the others the lower rows. At
-  // stride 1 the two values of a pair and the element between them (and the
-  // one after) are one 16-byte load per plane. The three halo columns are
-  // spread over threads.
+  // Own code columns go in pairs (2p, 2p+1) to the sub-tile's threads
+  // p = ltid % (HC/2); the first half of them take the upper rows, the other
+  // the lower rows. At stride 1 the two values of a pair (and the elements
+  // between and after them) are one 16-byte load per plane. The three halo
+  // columns are spread over the sub-tile's threads.
   const bool has0 = S0.out_end > S0.out_begin;
-  const int pp = tid & 127, jsp = 2 * pp;            // the pair's first code column
-  const int c2p = c.C0 + 2 * jsp;                    // its lattice column
-  const bool pa = c2p < M2, pb = c2p + 2 < M2;        // columns present
+  constexpr int NP = G::HC / 2;                        // pairs per row
+  const int pp = ltid % NP, jsp = 2 * pp;              // the pair's first code column
+  const bool upper = ltid < NP;
+  const int c2p = c.C0 + 2 * jsp;                      // its lattice column
+  const bool pa = live && c2p < M2, pb = c2p + 2 < M2;  // columns present
   constexpr int H0A = (G::H0 + 1) / 2, H1A = G::H1 / 2;
+  const int64_t so = L.s * L.stride[0];
   {
-    const int64_t so = L.s * L.stride[0];
     const bool r1 = c.P + 1 <= M0 - 1;
     const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
     auto one = [&](const T* p) -> T {
@@ -426,7 +484,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       return pred4<T>(a, bb, cc, d, c.P, M0, cubic);
     };
     if (pa) {
-      const int jr0 = tid < 128 ? 0 : H0A, jr1 = tid < 128 ? H0A : G::H0;
+      const int jr0 = upper ? 0 : H0A, jr1 = upper ? H0A : G::H0;
       const T* colp = out + c.pbase + (int64_t)c2p * L.s;
       // 16-byte loads: float, stride 1, all four elements inside the row,
       // every plane and row offset a multiple of four elements
@@ -464,8 +522,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         *reinterpret_cast<typename Vec2<T>::type*>(VE + (2 * jr) * G::VP + G::V0 + jsp) = v2;
       }
     }
-    if (tid < 3 * G::H0) {
-      const int h = tid / G::H0, jr = tid - h * G::H0;
+    if (live && ltid < 3 * G::H0) {
+      const int h = ltid / G::H0, jr = ltid - h * G::H0;
       const int js = h == 0 ? -1 : G::HC + h - 1;
       const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 + 2 * js;
       if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2)
@@ -475,33 +533,39 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   cp_async_wait_all();
   __syncthreads();
 
-  // Phase 0: decode the words of the tile's code columns.
-  const int cw0 = (int)c.ct * G::CWD;          // first own word of a row
-  const int n2r = c.R1 - c.R0, n1r = (c.R1 - c.R0) >> 1;
-  const bool st0 = S0.present && podd;
-  const int nA = (S2.present && c.ct < S2.nct) ? n2r * G::CWD : 0;
-  const int nB = S1.present ? n1r * G::CWD : 0;
-  const int nC = st0 ? G::H0 * G::CWD : 0;
-  const int nD1 = S1.present ? 2 * n1r : 0;
-  const int nD0 = st0 ? 2 * G::H0 : 0;
-  const int nit = nA + nB + nC + nD1 + nD0;
-  for (int it = tid; it < nit; it += 256) {
+  // Phase 0: decode the words of the sub-tiles' code columns (items of all
+  // sub-tiles in one list).
+  constexpr int MAXIT = (BR + G::H1 + G::H0) * G::CWD + 2 * (G::H1 + G::H0);
+  for (int it = tid; it < NS * MAXIT; it += 256) {
+    const int s = it / MAXIT, i = it % MAXIT;
+    const CtaPos& cs = s_pos[s];
+    if (cs.P >= M0) continue;
+    const bool odd = (cs.P & 1) != 0;
+    const int cw0 = (int)cs.ct * G::CWD;  // first own word of a row
+    const int n2r = cs.R1 - cs.R0, n1r = (cs.R1 - cs.R0) >> 1;
+    const bool st0 = S0.present && odd;
+    const int nA = (S2.present && cs.ct < S2.nct) ? n2r * G::CWD : 0;
+    const int nB = S1.present ? n1r * G::CWD : 0;
+    const int nC = st0 ? G::H0 * G::CWD : 0;
+    const int nD1 = S1.present ? 2 * n1r : 0;
+    const int nD0 = st0 ? 2 * G::H0 : 0;
+    if (i >= nA + nB + nC + nD1 + nD0) continue;
     int sx, qrow, side, rr, j;  // side: -1 own word, 0 left / 1 right halo word
-    if (it < nA) {
-      sx = 2; qrow = it / G::CWD; j = cw0 + it % G::CWD; rr = c.R0 + qrow; side = -1;
-    } else if (it < nA + nB) {
-      const int u = it - nA;
-      sx = 1; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (c.R0 >> 1) + qrow; side = -1;
-    } else if (it < nA + nB + nC) {
-      const int u = it - nA - nB;
-      sx = 0; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (c.R0 >> 1) - 1 + qrow; side = -1;
-    } else if (it < nA + nB + nC + nD1) {
-      const int u = it - nA - nB - nC;
-      sx = 1; qrow = u >> 1; side = u & 1; rr = (c.R0 >> 1) + qrow;
+    if (i < nA) {
+      sx = 2; qrow = i / G::CWD; j = cw0 + i % G::CWD; rr = cs.R0 + qrow; side = -1;
+    } else if (i < nA + nB) {
+      const int u = i - nA;
+      sx = 1; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (cs.R0 >> 1) + qrow; side = -1;
+    } else if (i < nA + nB + nC) {
+      const int u = i - nA - nB;
+      sx = 0; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (cs.R0 >> 1) - 1 + qrow; side = -1;
+    } else if (i < nA + nB + nC + nD1) {
+      const int u = i - nA - nB - nC;
+      sx = 1; qrow = u >> 1; side = u & 1; rr = (cs.R0 >> 1) + qrow;
       j = side ? cw0 + G::CWD : cw0 - 1;
     } else {
-      const int u = it - nA - nB - nC - nD1;
-      sx = 0; qrow = u >> 1; side = u & 1; rr = (c.R0 >> 1) - 1 + qrow;
+      const int u = i - nA - nB - nC - nD1;
+      sx = 0; qrow = u >> 1; side = u & 1; rr = (cs.R0 >> 1) - 1 + qrow;
       j = side ? cw0 + G::CWD : cw0 - 1;
     }
     const LevelStage& S = L.st[sx];
@@ -511,34 +575,41 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const int ctw = CW == G::CWD ? (int)((unsigned)j / G::CWD) : 0;
     const int rbw = sx == 2 ? (int)((unsigned)rr / BR) : (int)((unsigned)rr / (BR / 2));
     int sl = 0;
-    if (sx == 1) sl = 2 + (ctw - (int)c.ct);
-    else if (sx == 0) sl = 4 + (rbw - (int)c.rb + 1) * 3 + (ctw - (int)c.ct) + 1;
+    if (KS == 5) {
+      if (sx == 1) sl = 1;
+      else if (sx == 0) sl = 3 + (rbw - (int)cs.rb);
+    } else {
+      if (sx == 1) sl = 2 + (ctw - (int)cs.ct);
+      else if (sx == 0) sl = 4 + (rbw - (int)cs.rb + 1) * 3 + (ctw - (int)cs.ct) + 1;
+    }
     const int li = (rr - rbw * RB) * CW + (j - ctw * CW);
     const int wl = li >> 5;
     const uint32_t bit = 1u << (li & 31), below = bit - 1u;
-    const uint32_t km = s_km[sx];
-    const uint32_t* sb = &SB[sl][0][wl];
-    const uint32_t* const* sp = SP[sl];
+    const uint32_t km = s_km[s][sx];
+    const int wbs = wbof(s);
+    const uint32_t* sb = &SB[s][sl][0][wl];
+    const uint32_t* const* sp = SP[s][sl];
     const uint32_t off = (uint32_t)wl * 32;
-    uint32_t* QHr = QH + (sx == 1 ? qrow : G::H1 + qrow) * 4;
-    QT* Qr = (sx == 2 ? Q2 : (sx == 1 ? Q1 : Q0)) + qrow * G::QP + (j - cw0) * QCfg<W16>::BLK;
+    uint32_t* QHr = QHof(s) + (sx == 1 ? qrow : G::H1 + qrow) * 4;
+    QT* Qr = (sx == 2 ? Q2of(s) : (sx == 1 ? Q1of(s) : Q0of(s))) + qrow * G::QP +
+             (j - cw0) * QCfg<W16>::BLK;
     uint32_t a[NPL];
 #pragma unroll
-    for (int i = 0; i < NPL; ++i) {
-      const int k = wb + i;
+    for (int i2 = 0; i2 < NPL; ++i2) {
+      const int k = wbs + i2;
       uint32_t w = 0u;
       if (k <= 31 && ((km >> k) & 1u)) {
-        const uint32_t m = sb[i * kMaxBw];
-        if (m & bit) w = __ldg(sp[i] + off + __popc(m & below));
+        const uint32_t m = sb[i2 * BWS];
+        if (m & bit) w = __ldg(sp[i2] + off + __popc(m & below));
       }
-      a[i] = w;
+      a[i2] = w;
     }
     // inverse predictive XOR, top-down; planes below b are zero, planes
     // above the window are zero
 #pragma unroll
-    for (int i = NPL - 1; i >= 0; --i) {
-      const uint32_t p1 = i + 1 < NPL ? a[i + 1] : 0u, p2 = i + 2 < NPL ? a[i + 2] : 0u;
-      a[i] = wb + i >= b ? (a[i] ^ p1 ^ p2) : 0u;
+    for (int i2 = NPL - 1; i2 >= 0; --i2) {
+      const uint32_t p1 = i2 + 1 < NPL ? a[i2 + 1] : 0u, p2 = i2 + 2 < NPL ? a[i2 + 2] : 0u;
+      a[i2] = wbs + i2 >= b ? (a[i2] ^ p1 ^ p2) : 0u;
     }
     if (side < 0) {
       if constexpr (W16) {
@@ -567,15 +638,15 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       uint32_t v0 = 0u, v1 = 0u;
       const int i0 = side ? 0 : 31;
 #pragma unroll
-      for (int i = 0; i < NPL; ++i) {
-        v0 |= ((a[i] >> i0) & 1u) << i;
-        v1 |= ((a[i] >> 1) & 1u) << i;
+      for (int i2 = 0; i2 < NPL; ++i2) {
+        v0 |= ((a[i2] >> i0) & 1u) << i2;
+        v1 |= ((a[i2] >> 1) & 1u) << i2;
       }
       if (side) {
-        QHr[1] = v0 << wb;
-        QHr[2] = v1 << wb;
+        QHr[1] = v0 << wbs;
+        QHr[2] = v1 << wbs;
       } else {
-        QHr[0] = v0 << wb;
+        QHr[0] = v0 << wbs;
       }
     }
   }
@@ -590,7 +661,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       find_outlier<T>(S0, oidx, oval, ci, v);
     };
     if (pa) {
-      const int jr0 = tid < 128 ? 0 : H0A, jr1 = tid < 128 ? H0A : G::H0;
+      const int jr0 = upper ? 0 : H0A, jr1 = upper ? H0A : G::H0;
 #pragma unroll
       for (int q = 0; q < H0A; ++q) {
         const int jr = jr0 + q;
@@ -611,8 +682,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         *pv = v;
       }
     }
-    if (tid < 3 * G::H0) {
-      const int h = tid / G::H0, jr = tid - h * G::H0;
+    if (live && ltid < 3 * G::H0) {
+      const int h = ltid / G::H0, jr = ltid - h * G::H0;
       const int js = h == 0 ? -1 : G::HC + h - 1;
       const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 + 2 * js;
       if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) {
@@ -622,7 +693,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         *p = v;
       }
     }
-    __syncthreads();
+    __syncthreads();  // every thread of the tile sees the same parity
   }
 
   // Phase 2: sweep 1 on the odd rows, columns [C0-2, C1+2]; pairs of
@@ -639,10 +710,10 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       }
       return v;
     };
-    if (S1.present) {
+    if (S1.present && live) {
       if (pa) {
         typedef typename Vec2<T>::type V2;
-        const int jr0 = tid < 128 ? 0 : H1A, jr1 = tid < 128 ? H1A : G::H1;
+        const int jr0 = upper ? 0 : H1A, jr1 = upper ? H1A : G::H1;
         T* col = VE + G::V0 + jsp;
         V2 a = *reinterpret_cast<const V2*>(col + (2 * jr0) * G::VP);
         V2 bb = *reinterpret_cast<const V2*>(col + (2 * jr0 + 2) * G::VP);
@@ -662,8 +733,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
           cc = d;
         }
       }
-      if (tid < 3 * G::H1) {
-        const int h = tid / G::H1, jr = tid - h * G::H1;
+      if (ltid < 3 * G::H1) {
+        const int h = ltid / G::H1, jr = ltid - h * G::H1;
         const int js = h == 0 ? -1 : G::HC + h - 1;
         const int c1 = c.R0 + 1 + 2 * jr, c2 = c.C0 + 2 * js;
         if (c1 < c.R1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2) {
@@ -678,10 +749,11 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   __syncthreads();
 
   // Phase 3: sweep 2 and the output. Thread: four odd columns (code columns
-  // 4g .. 4g+3) of the rows rq, rq+4, ...
+  // 4g .. 4g+3) of the rows rq, rq+4, ... of its sub-tile.
   {
     const bool has2 = S2.out_end > S2.out_begin;
-    const int g = tid & 63, rq = tid >> 6;
+    constexpr int NG = G::HC / 4;  // four-column groups per row
+    const int g = ltid % NG, rq = ltid / NG;
     const int c2e = c.C0 + 8 * g;  // first (even) lattice column of the run
     // per odd column k of the run: 2 = cubic, 1 = linear, 0 = copy (the
     // boundary rule of pred4), two bits each
@@ -692,7 +764,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       const uint32_t r = i + 1 > M2 - 1 ? 0u : ((cubic && i - 3 >= 0 && i + 3 <= M2 - 1) ? 2u : 1u);
       rule |= r << (2 * k);
     }
-    if (c2e < c.C1) {
+    if (live && c2e < c.C1) {
       for (int lr = rq; lr < BR; lr += 4) {
         const int c1 = c.R0 + lr;
         if (c1 >= c.R1) break;
@@ -1114,19 +1186,21 @@ __global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T*
   level_compress_body<T, BR, BC>(L, x, xh, write_xh, qa, o, D, blockIdx.x, smem);
 }
 
-// 16-bit code rows leave room for four CTAs per SM, 32-bit ones for three.
+// 16-bit code rows leave room for four CTAs per SM (three with four
+// sub-tiles), 32-bit ones for three.
 // Persistent: the grid holds as many CTAs as fit at once; CTA i takes tiles
 // i, i + grid, ... (neighbouring CTAs stay on neighbouring tiles).
-template <bool W16> constexpr int retrieve_ctas_per_sm() { return W16 ? 4 : 3; }
+template <bool W16, int NS>
+__host__ __device__ constexpr int retrieve_ctas_per_sm() { return W16 ? 4 : 3; }
 
-template <class T, int BR, int BC, bool W16>
-__global__ void __launch_bounds__(256, W16 ? 4 : 3) k_level_retrieve(
+template <class T, int BR, int BC, bool W16, int NS>
+__global__ void __launch_bounds__(256, retrieve_ctas_per_sm<W16, NS>()) k_level_retrieve(
     LevelArgs L, T* out, T twoeb, int b, const uint32_t* __restrict__ cap,
     const uint32_t* __restrict__ bm, const uint64_t* __restrict__ oidx,
     const double* __restrict__ oval, LevelDescs D, uint64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    level_retrieve_body<T, BR, BC, W16>(L, out, twoeb, b, cap, bm, oidx, oval, D, t, smem);
+    level_retrieve_body<T, BR, BC, W16, NS>(L, out, twoeb, b, cap, bm, oidx, oval, D, t, smem);
     __syncthreads();  // the next tile reuses shared memory
   }
 }
@@ -1159,14 +1233,14 @@ __global__ void __launch_bounds__(256, 3) k_level_compress_batch(
                                  blockIdx.x - e.cta_begin, smem);
 }
 
-template <class T, int BR, int BC, bool W16>
-__global__ void __launch_bounds__(256, W16 ? 4 : 3) k_level_retrieve_batch(
+template <class T, int BR, int BC, bool W16, int NS>
+__global__ void __launch_bounds__(256, retrieve_ctas_per_sm<W16, NS>()) k_level_retrieve_batch(
     const RetrieveEntry* __restrict__ ents, int n, uint64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const RetrieveEntry& e = find_entry(ents, n, t);
-    level_retrieve_body<T, BR, BC, W16>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx,
-                                        e.oval, e.D, t - e.cta_begin, smem);
+    level_retrieve_body<T, BR, BC, W16, NS>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx,
+                                            e.oval, e.D, t - e.cta_begin, smem);
     __syncthreads();  // the next tile reuses shared memory (and the entry index)
   }
 }
@@ -1176,22 +1250,22 @@ size_t smem_compress() {
   typedef CTile<BR, BC> G;
   return sizeof(T) * (G::H0 + G::H1) * G::VP + 4 * (BR + G::H1 + BR / 2) * G::QP;
 }
-template <class T, int BR, int BC, bool W16>
+template <class T, int BR, int BC, bool W16, int NS>
 size_t smem_retrieve() {
-  typedef RTile<BR, BC, W16> G;
-  return sizeof(T) * G::VR * G::VP +
-         sizeof(typename QCfg<W16>::QT) * (BR + G::H1 + G::H0) * G::QP + 4 * (G::H1 + G::H0) * 4;
+  typedef RTile<BR, BC / NS, W16> G;
+  return NS * (sizeof(T) * G::VR * G::VP +
+               sizeof(typename QCfg<W16>::QT) * (BR + G::H1 + G::H0) * G::QP + 16 * (G::H1 + G::H0));
 }
 
-template <class T, int BR, int BC, bool W16>
+template <class T, int BR, int BC, bool W16, int NS>
 cudaError_t setup_retrieve() {
-  cudaError_t r = cudaFuncSetAttribute(k_level_retrieve<T, BR, BC, W16>,
+  cudaError_t r = cudaFuncSetAttribute(k_level_retrieve<T, BR, BC, W16, NS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_retrieve<T, BR, BC, W16>());
+                                       (int)smem_retrieve<T, BR, BC, W16, NS>());
   if (r == cudaSuccess)
-    r = cudaFuncSetAttribute(k_level_retrieve_batch<T, BR, BC, W16>,
+    r = cudaFuncSetAttribute(k_level_retrieve_batch<T, BR, BC, W16, NS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_retrieve<T, BR, BC, W16>());
+                             (int)smem_retrieve<T, BR, BC, W16, NS>());
   return r;
 }
 
@@ -1205,8 +1279,12 @@ cudaError_t setup_once() {
       r = cudaFuncSetAttribute(k_level_compress_batch<T, BR, BC>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_compress<T, BR, BC>());
-    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true>();
-    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true, 1>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true, 2>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true, 4>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false, 1>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false, 2>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false, 4>();
     return r;
   }();
   return e;
@@ -1214,8 +1292,7 @@ cudaError_t setup_once() {
 
 // CTAs of a persistent launch over `tiles` tiles: all that fit on the
 // device at once (SM count of the current device, looked up once).
-template <bool W16>
-unsigned persistent_grid(uint64_t tiles) {
+inline unsigned persistent_grid(uint64_t tiles, int per_sm) {
   static int sms = [] {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1225,22 +1302,51 @@ unsigned persistent_grid(uint64_t tiles) {
     }
     return n;
   }();
-  const uint64_t cap = (uint64_t)sms * retrieve_ctas_per_sm<W16>();
+  const uint64_t cap = (uint64_t)sms * per_sm;
   return (unsigned)(tiles < cap ? tiles : cap);
 }
 
-template <class T, int BR, int BC, bool W16>
+template <class T, int BR, int BC, bool W16, int NS>
 void retrieve_kernel(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
                      const uint32_t* bm, const uint64_t* oidx, const double* oval,
-                     const LevelDescs& d, uint64_t tiles, cudaStream_t st) {
-  k_level_retrieve<T, BR, BC, W16>
-      <<<persistent_grid<W16>(tiles), 256, smem_retrieve<T, BR, BC, W16>(), st>>>(
-          L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval, d, tiles);
+                     const LevelDescs& d, cudaStream_t st) {
+  const uint64_t tiles = retrieve_tiles(L, NS);
+  if (tiles == 0) return;
+  k_level_retrieve<T, BR, BC, W16, NS>
+      <<<persistent_grid(tiles, retrieve_ctas_per_sm<W16, NS>()), 256,
+         smem_retrieve<T, BR, BC, W16, NS>(), st>>>(L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval,
+                                                    d, tiles);
 }
-template <class T, int BR, int BC, bool W16>
+template <class T, int BR, int BC, bool W16, int NS>
 void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t tiles, cudaStream_t st) {
-  k_level_retrieve_batch<T, BR, BC, W16>
-      <<<persistent_grid<W16>(tiles), 256, smem_retrieve<T, BR, BC, W16>(), st>>>(ents, n, tiles);
+  k_level_retrieve_batch<T, BR, BC, W16, NS>
+      <<<persistent_grid(tiles, retrieve_ctas_per_sm<W16, NS>()), 256,
+         smem_retrieve<T, BR, BC, W16, NS>(), st>>>(ents, n, tiles);
+}
+
+template <class T, int BR, int BC>
+void retrieve_dispatch(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
+                       const uint32_t* bm, const uint64_t* oidx, const double* oval,
+                       const LevelDescs& d, int w16, cudaStream_t st) {
+  const int ns = retrieve_subtiles(L.M[2], w16);
+  if (!w16) {
+    if (ns == 4) retrieve_kernel<T, BR, BC, false, 4>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
+    else if (ns == 2) retrieve_kernel<T, BR, BC, false, 2>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
+    else retrieve_kernel<T, BR, BC, false, 1>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
+  } else if (ns == 4) retrieve_kernel<T, BR, BC, true, 4>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
+  else if (ns == 2) retrieve_kernel<T, BR, BC, true, 2>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
+  else retrieve_kernel<T, BR, BC, true, 1>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
+}
+template <class T, int BR, int BC>
+void retrieve_batch_dispatch(const RetrieveEntry* ents, int n, uint64_t tiles, int w16, int ns,
+                             cudaStream_t st) {
+  if (!w16) {
+    if (ns == 4) retrieve_batch_kernel<T, BR, BC, false, 4>(ents, n, tiles, st);
+    else if (ns == 2) retrieve_batch_kernel<T, BR, BC, false, 2>(ents, n, tiles, st);
+    else retrieve_batch_kernel<T, BR, BC, false, 1>(ents, n, tiles, st);
+  } else if (ns == 4) retrieve_batch_kernel<T, BR, BC, true, 4>(ents, n, tiles, st);
+  else if (ns == 2) retrieve_batch_kernel<T, BR, BC, true, 2>(ents, n, tiles, st);
+  else retrieve_batch_kernel<T, BR, BC, true, 1>(ents, n, tiles, st);
 }
 
 }  // namespace
@@ -1271,21 +1377,14 @@ cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, doub
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
                                   const double* oval, const LevelDescs& d, int w16,
                                   cudaStream_t st) {
-  const uint64_t grid = (uint64_t)L.M[0] * L.nrb * L.nct;
-  if (grid == 0) return cudaSuccess;
+  if (retrieve_tiles(L, retrieve_subtiles(L.M[2], w16)) == 0) return cudaSuccess;
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    if (w16)
-      retrieve_kernel<float, kLevelRowsF32, kLevelCols, true>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
-    else
-      retrieve_kernel<float, kLevelRowsF32, kLevelCols, false>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
+    retrieve_dispatch<float, kLevelRowsF32, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, d, w16, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    if (w16)
-      retrieve_kernel<double, kLevelRowsF64, kLevelCols, true>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
-    else
-      retrieve_kernel<double, kLevelRowsF64, kLevelCols, false>(L, out, twoeb, b, cap, bm, oidx, oval, d, grid, st);
+    retrieve_dispatch<double, kLevelRowsF64, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, d, w16, st);
   }
   return cudaGetLastError();
 }
@@ -1307,17 +1406,15 @@ cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, in
 }
 
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
-                                        uint64_t ctas, int w16, cudaStream_t st) {
-  if (ctas == 0 || n == 0) return cudaSuccess;
+                                        uint64_t tiles, int w16, int ns, cudaStream_t st) {
+  if (tiles == 0 || n == 0) return cudaSuccess;
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    if (w16) retrieve_batch_kernel<float, kLevelRowsF32, kLevelCols, true>(ents, n, ctas, st);
-    else retrieve_batch_kernel<float, kLevelRowsF32, kLevelCols, false>(ents, n, ctas, st);
+    retrieve_batch_dispatch<float, kLevelRowsF32, kLevelCols>(ents, n, tiles, w16, ns, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    if (w16) retrieve_batch_kernel<double, kLevelRowsF64, kLevelCols, true>(ents, n, ctas, st);
-    else retrieve_batch_kernel<double, kLevelRowsF64, kLevelCols, false>(ents, n, ctas, st);
+    retrieve_batch_dispatch<double, kLevelRowsF64, kLevelCols>(ents, n, tiles, w16, ns, st);
   }
   return cudaGetLastError();
 }
