@@ -806,20 +806,64 @@ bool level_w16(const ipc_field* f, int l, int b) {
   return ktop - b <= 15;
 }
 
+// Reconstruction scratch: level l >= 2 writes its whole lattice densely (row
+// major over its extents) to a scratch array, which holds the known points
+// of level l - 1; level K + 1 is the anchor alone. Only level 1 writes the
+// caller's array (its lattice is the grid). Returns the scratch bytes and
+// the byte offset of each level's array (256-byte aligned).
+uint64_t lattice_elems(const Geo& g, int l) {
+  uint64_t n = 1;
+  for (int e = 0; e < 3; ++e) n *= (uint64_t)(((g.N[e] - 1) >> (l - 1)) + 1);
+  return n;
+}
+uint64_t ladder(const Geo& g, size_t esz, std::vector<uint64_t>* off) {
+  off->assign(g.K + 2, 0);
+  uint64_t tot = 0;
+  for (int l = 2; l <= g.K + 1; ++l) {
+    (*off)[l] = tot;
+    tot += (lattice_elems(g, l) * esz + 255) & ~uint64_t(255);
+  }
+  return tot;
+}
+// Level l's layout in a reconstruction: dense lattice strides for its
+// output, the known points read from level l + 1's dense lattice `kin`.
+void retrieve_layout(LevelArgs* L, const void* kin) {
+  for (int e = 0; e < 3; ++e) L->N[e] = L->M[e];
+  L->stride[2] = 1;
+  L->stride[1] = L->M[2];
+  L->stride[0] = L->M[1] * L->M[2];
+  L->s = 1;
+  L->kin = kin;
+  L->kst1 = ((L->M[2] - 1) >> 1) + 1;
+  L->kst0 = (((L->M[1] - 1) >> 1) + 1) * L->kst1;
+}
+
 // Algorithm 1 on the device: the anchor, then one fused launch per level
 // (coarse to fine); outliers are applied inside the level kernels.
 int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream_t st) {
   const Geo& g = f->g;
+  const size_t esz = f->dtype == 0 ? 4 : 8;
+  std::vector<uint64_t> off;
+  uint8_t* scr = nullptr;
+  if (g.K > 0) {
+    int rc = dalloc((void**)&scr, ladder(g, esz, &off), st);
+    if (rc) return rc;
+  }
+  struct Free {  // stream-ordered after the launches
+    uint8_t* p;
+    cudaStream_t s;
+    ~Free() { if (p) cudaFreeAsync(p, s); }
+  } guard{scr, st};
   {
     const long ph = prof_begin(IPC_KERNEL_ANCHOR, st);
-    CU(launch_set_anchor(f->dtype, d_out, f->anchor, st));
+    CU(launch_set_anchor(f->dtype, g.K > 0 ? (void*)(scr + off[g.K + 1]) : d_out, f->anchor, st));
     prof_end(ph, st, 8);
   }
   const double twoeb = bin_width(f);
-  const size_t esz = f->dtype == 0 ? 4 : 8;
   for (int l = g.K; l >= 1; --l) {
     LevelArgs L = level_args(f, l);
-    L.vec = ((uintptr_t)d_out % (2 * esz)) == 0;
+    retrieve_layout(&L, scr + off[l + 1]);
+    void* o = l == 1 ? d_out : (void*)(scr + off[l]);
     const LevelDescs D = level_descs(f, l);
     double by = 0;
     uint64_t nc = 0;
@@ -830,7 +874,7 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
       for (int k = b[l - 1]; k < 32; ++k) by += (double)f->st[t].size[k];
     }
     const long ph = prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st);
-    CU(launch_level_retrieve(f->dtype, L, d_out, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
+    CU(launch_level_retrieve(f->dtype, L, o, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
                              f->d_oval, D, level_w16(f, l, b[l - 1]) ? 1 : 0, st));
     prof_end(ph, st, by + (double)(nc * esz));
   }
@@ -839,14 +883,18 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
 
 // Batched reconstruction of fields of one element type: the anchors in one
 // launch, then ONE launch per level over that level's CTAs of every field.
-// The entry table is copied to `tab` (device) first. When `plan` is set the
-// launches go to a capturing stream and no profiler events are recorded.
+// The entry table and the fields' scratch ladders are one device allocation
+// (`tab`); the entries carry scratch offsets until upload_table turns them
+// into pointers. When `plan` is set the launches go to a capturing stream
+// and no profiler events are recorded.
 struct BatchTable {
   std::vector<RetrieveEntry> ents;
   std::vector<AnchorEntry> anchors;
+  std::vector<int64_t> kin_off, out_off, anch_off;  // scratch offsets (-1: caller's array)
   std::vector<uint64_t> lev_off, lev_ctas;
   std::vector<int> lev_w16;  // every entry of the level keeps 16-bit codes
   std::vector<int> lev_ns;   // sub-tiles per tile of the level's launch
+  uint64_t scratch = 0;      // bytes of the fields' scratch ladders
   int Kmax = 0;
   double alg_bytes = 0;
 };
@@ -862,8 +910,24 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   T->lev_ns.assign(T->Kmax + 2, 1);
   T->ents.clear();
   T->anchors.clear();
+  T->kin_off.clear();
+  T->out_off.clear();
+  T->anch_off.clear();
   T->alg_bytes = 0;
-  for (size_t i = 0; i < nf; ++i) T->anchors.push_back(AnchorEntry{outs[i], fs[i]->anchor});
+  // each field's scratch ladder, one after the other
+  std::vector<uint64_t> base(nf, 0);
+  std::vector<std::vector<uint64_t>> off(nf);
+  T->scratch = 0;
+  for (size_t i = 0; i < nf; ++i) {
+    const size_t esz = fs[i]->dtype == 0 ? 4 : 8;
+    base[i] = T->scratch;
+    if (fs[i]->g.K > 0) T->scratch += ladder(fs[i]->g, esz, &off[i]);
+  }
+  for (size_t i = 0; i < nf; ++i) {
+    T->anchors.push_back(AnchorEntry{outs[i], fs[i]->anchor});
+    const int K = fs[i]->g.K;
+    T->anch_off.push_back(K > 0 ? (int64_t)(base[i] + off[i][K + 1]) : -1);
+  }
   for (int l = T->Kmax; l >= 1; --l) {
     T->lev_off[l] = T->ents.size();
     // the level's code width and tile shape hold for every entry
@@ -886,7 +950,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       const size_t esz = f->dtype == 0 ? 4 : 8;
       RetrieveEntry e{};
       e.L = level_args(f, l);
-      e.L.vec = ((uintptr_t)outs[i] % (2 * esz)) == 0;
+      retrieve_layout(&e.L, nullptr);
       e.D = level_descs(f, l);
       e.out = outs[i];
       e.cap = f->d_cap;
@@ -898,6 +962,8 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       e.cta_begin = cta;
       cta += retrieve_tiles(e.L, ns);
       T->ents.push_back(e);
+      T->kin_off.push_back((int64_t)(base[i] + off[i][l + 1]));
+      T->out_off.push_back(l == 1 ? -1 : (int64_t)(base[i] + off[i][l]));
       for (int d = 0; d < 3; ++d) {
         const int t = f->g.level_stage[d][l - 1];
         if (t < 0) continue;
@@ -910,10 +976,14 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   T->lev_off[0] = T->ents.size();
 }
 
+// Table layout: [scratch ladders | entries | anchors]; the scratch comes
+// first so that it keeps the allocation's alignment.
+uint64_t table_scratch(const BatchTable& T) { return (T.scratch + 255) & ~uint64_t(255); }
+
 int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_t st,
                           bool profile, uint64_t* launches) {
-  RetrieveEntry* d_ents = (RetrieveEntry*)tab;
-  AnchorEntry* d_anch = (AnchorEntry*)((uint8_t*)tab + T.ents.size() * sizeof(RetrieveEntry));
+  RetrieveEntry* d_ents = (RetrieveEntry*)((uint8_t*)tab + table_scratch(T));
+  AnchorEntry* d_anch = (AnchorEntry*)((uint8_t*)d_ents + T.ents.size() * sizeof(RetrieveEntry));
   uint64_t nl = 0;
   {
     const long ph = profile ? prof_begin(IPC_KERNEL_ANCHOR, st) : -1;
@@ -937,20 +1007,30 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
 }
 
 int upload_table(const BatchTable& T, void** tab, cudaStream_t st, bool pooled) {
+  const uint64_t sb = table_scratch(T);
   const size_t bytes = T.ents.size() * sizeof(RetrieveEntry) + T.anchors.size() * sizeof(AnchorEntry);
   int rc;
   if (pooled) {
-    if ((rc = dalloc(tab, bytes, st))) return rc;
-  } else if (cudaMalloc(tab, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    if ((rc = dalloc(tab, sb + bytes, st))) return rc;
+  } else if (cudaMalloc(tab, std::max<size_t>(sb + bytes, 16)) != cudaSuccess) {
     cudaGetLastError();
     return fail(IPC_ENOMEM, "device allocation failed");
   }
+  uint8_t* base = (uint8_t*)*tab;
+  std::vector<RetrieveEntry> ents = T.ents;
+  std::vector<AnchorEntry> anch = T.anchors;
+  for (size_t i = 0; i < ents.size(); ++i) {
+    ents[i].L.kin = base + T.kin_off[i];
+    if (T.out_off[i] >= 0) ents[i].out = base + T.out_off[i];
+  }
+  for (size_t i = 0; i < anch.size(); ++i)
+    if (T.anch_off[i] >= 0) anch[i].out = base + T.anch_off[i];
   std::vector<uint8_t> h(bytes);
-  std::memcpy(h.data(), T.ents.data(), T.ents.size() * sizeof(RetrieveEntry));
-  std::memcpy(h.data() + T.ents.size() * sizeof(RetrieveEntry), T.anchors.data(),
-              T.anchors.size() * sizeof(AnchorEntry));
+  std::memcpy(h.data(), ents.data(), ents.size() * sizeof(RetrieveEntry));
+  std::memcpy(h.data() + ents.size() * sizeof(RetrieveEntry), anch.data(),
+              anch.size() * sizeof(AnchorEntry));
   // pageable source: the copy is staged before the call returns
-  CU(cudaMemcpyAsync(*tab, h.data(), bytes, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(base + sb, h.data(), bytes, cudaMemcpyHostToDevice, st));
   if (!pooled) CU(cudaStreamSynchronize(st));
   return IPC_OK;
 }

@@ -57,6 +57,10 @@ struct LevelArgs {
   int vec;            // output base aligned to two elements (paired stores allowed)
   uint64_t nrb, nct;  // CTA row blocks per plane, column tiles
   LevelStage st[3];
+  // reconstruction: the known points of the level, the next coarser
+  // level's lattice stored densely (plane and row strides in elements)
+  const void* kin;
+  int64_t kst0, kst1;
 };
 
 // Kernel-side view of a stage's word grid and segments (pack / unpack).

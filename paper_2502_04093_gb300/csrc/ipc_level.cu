@@ -471,55 +471,58 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   const int c2p = c.C0 + 2 * jsp;                      // its lattice column
   const bool pa = live && c2p < M2, pb = c2p + 2 < M2;  // columns present
   constexpr int H0A = (G::H0 + 1) / 2, H1A = G::H1 / 2;
-  const int64_t so = L.s * L.stride[0];
   {
+    // Known points come from the next coarser level's lattice, stored
+    // densely: point (P', c1, c2) (all even) is kin[(P'/2) k0 + (c1/2) k1 +
+    // c2/2]. `p` below points at plane P (even plane) or P - 1 (odd plane);
+    // planes P + 1, P - 3, P + 3 are k0, -k0, 2 k0 away.
+    typedef typename Vec2<T>::type V2;
+    const T* kin = reinterpret_cast<const T*>(L.kin);
+    const int64_t k0 = L.kst0, k1 = L.kst1;
     const bool r1 = c.P + 1 <= M0 - 1;
     const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
     auto one = [&](const T* p) -> T {
       if (!podd) return __ldg(p);
-      const T bb = __ldg(p - so);
-      const T cc = r1 ? __ldg(p + so) : bb;
-      const T a = r3 ? __ldg(p - 3 * so) : bb;
-      const T d = r3 ? __ldg(p + 3 * so) : bb;
+      const T bb = __ldg(p);
+      const T cc = r1 ? __ldg(p + k0) : bb;
+      const T a = r3 ? __ldg(p - k0) : bb;
+      const T d = r3 ? __ldg(p + 2 * k0) : bb;
       return pred4<T>(a, bb, cc, d, c.P, M0, cubic);
     };
+    const T* kplane = kin + (int64_t)(c.P >> 1) * k0;
     if (pa) {
       const int jr0 = upper ? 0 : H0A, jr1 = upper ? H0A : G::H0;
-      const T* colp = out + c.pbase + (int64_t)c2p * L.s;
-      // 16-byte loads: float, stride 1, all four elements inside the row,
-      // every plane and row offset a multiple of four elements
-      const bool vec = sizeof(T) == 4 && L.s == 1 && c2p + 3 < M2 && (so & 3) == 0 &&
-                       (c.rs & 3) == 0 && ((uintptr_t)colp & 15) == 0;
+      const T* colp = kplane + (c2p >> 1);
+      // the pair's two known points are consecutive elements: one 8-byte
+      // (16-byte for double) load per plane when every row and plane offset
+      // keeps that alignment
+      const bool vec = pb && (k1 & 1) == 0 && (k0 & 1) == 0 &&
+                       ((uintptr_t)colp % (2 * sizeof(T))) == 0;
 #pragma unroll
       for (int q = 0; q < H0A; ++q) {
         const int jr = jr0 + q;
         if (jr >= jr1) break;
         const int c1 = c.R0 - 2 + 2 * jr;
         if (c1 < 0 || c1 >= M1) continue;
-        const T* p = colp + (int64_t)c1 * c.rs;
-        T va, vb;
+        const T* p = colp + (int64_t)(c1 >> 1) * k1;
+        V2 v2;
         if (vec) {
-          const float* pf = reinterpret_cast<const float*>(p);
+          const V2* p2 = reinterpret_cast<const V2*>(p);
           if (!podd) {
-            const float4 k = __ldg(reinterpret_cast<const float4*>(pf));
-            va = (T)k.x;
-            vb = (T)k.z;
+            v2 = __ldg(p2);
           } else {
-            const float4 bb = __ldg(reinterpret_cast<const float4*>(pf - so));
-            const float4 cc = r1 ? __ldg(reinterpret_cast<const float4*>(pf + so)) : bb;
-            const float4 a = r3 ? __ldg(reinterpret_cast<const float4*>(pf - 3 * so)) : bb;
-            const float4 d = r3 ? __ldg(reinterpret_cast<const float4*>(pf + 3 * so)) : bb;
-            va = (T)pred4<float>(a.x, bb.x, cc.x, d.x, c.P, M0, cubic);
-            vb = (T)pred4<float>(a.z, bb.z, cc.z, d.z, c.P, M0, cubic);
+            const V2 bb = __ldg(p2);
+            const V2 cc = r1 ? __ldg(reinterpret_cast<const V2*>(p + k0)) : bb;
+            const V2 a = r3 ? __ldg(reinterpret_cast<const V2*>(p - k0)) : bb;
+            const V2 d = r3 ? __ldg(reinterpret_cast<const V2*>(p + 2 * k0)) : bb;
+            v2.x = pred4<T>(a.x, bb.x, cc.x, d.x, c.P, M0, cubic);
+            v2.y = pred4<T>(a.y, bb.y, cc.y, d.y, c.P, M0, cubic);
           }
         } else {
-          va = one(p);
-          vb = pb ? one(p + 2 * L.s) : va;
+          v2.x = one(p);
+          v2.y = pb ? one(p + 1) : v2.x;
         }
-        typename Vec2<T>::type v2;
-        v2.x = va;
-        v2.y = vb;
-        *reinterpret_cast<typename Vec2<T>::type*>(VE + (2 * jr) * G::VP + G::V0 + jsp) = v2;
+        *reinterpret_cast<V2*>(VE + (2 * jr) * G::VP + G::V0 + jsp) = v2;
       }
     }
     if (live && ltid < 3 * G::H0) {
@@ -527,7 +530,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       const int js = h == 0 ? -1 : G::HC + h - 1;
       const int c1 = c.R0 - 2 + 2 * jr, c2 = c.C0 + 2 * js;
       if (c1 >= 0 && c1 < M1 && c2 >= 0 && c2 < M2 && c2 <= c.C1 + 2)
-        VE[(2 * jr) * G::VP + G::V0 + js] = one(out + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s);
+        VE[(2 * jr) * G::VP + G::V0 + js] = one(kplane + (int64_t)(c1 >> 1) * k1 + (c2 >> 1));
     }
   }
   cp_async_wait_all();
