@@ -220,35 +220,46 @@ def run_ours(args, rank, world, local_rank):
         ipc.ipc_free(f)
     step_bytes = nbytes * (1 + n_recon)
 
-    # timed region (device time, CUDA events on the working stream)
+    # timed region (device time, CUDA events on the working stream). The
+    # per-kernel profiler (two events and host bookkeeping per launch) stays
+    # off here; the roofline's per-launch times come from a second timed
+    # pass of the same steps with it on.
     st = torch.cuda.current_stream()
-    ipc.ipc_profile_enable(True)
-    ipc.ipc_profile_reset()
-    barrier()
-    torch.cuda.synchronize()
-    launches0 = ipc.ipc_launch_count()
-    with ClockSampler(local_rank) as clk:
-        e_start = torch.cuda.Event(enable_timing=True)
-        e_end = torch.cuda.Event(enable_timing=True)
-        e_start.record(st)
-        fields = []
-        for _ in range(args.steps):
-            f, _ = gpu_step(ipc, x, out)
-            fields.append((f, None))
-            if len(fields) > 1:
-                # compress of this step synchronised the stream, so the
-                # previous field has no pending work
-                ipc.ipc_free(fields.pop(0)[0])
-        e_end.record(st)
-        torch.cuda.synchronize()
-        barrier()
-    launches = ipc.ipc_launch_count() - launches0
-    elapsed_ms = e_start.elapsed_time(e_end)
-    ipc.ipc_profile_enable(False)
-    prof = {ipc.IPC_KERNEL_NAMES[k]: ipc.ipc_profile_read(k) for k in range(len(ipc.IPC_KERNEL_NAMES))}
-    csize = ipc.ipc_compressed_size(fields[-1][0])
-    ipc.ipc_free(fields[-1][0])
 
+    def timed(profile):
+        if profile:
+            ipc.ipc_profile_enable(True)
+            ipc.ipc_profile_reset()
+        barrier()
+        torch.cuda.synchronize()
+        l0 = ipc.ipc_launch_count()
+        with ClockSampler(local_rank) as clk:
+            e_start = torch.cuda.Event(enable_timing=True)
+            e_end = torch.cuda.Event(enable_timing=True)
+            e_start.record(st)
+            fields = []
+            for _ in range(args.steps):
+                f, _ = gpu_step(ipc, x, out)
+                fields.append(f)
+                if len(fields) > 1:
+                    # compress of this step synchronised the stream, so the
+                    # previous field has no pending work
+                    ipc.ipc_free(fields.pop(0))
+            e_end.record(st)
+            torch.cuda.synchronize()
+            barrier()
+        launches = ipc.ipc_launch_count() - l0
+        prof = None
+        if profile:
+            ipc.ipc_profile_enable(False)
+            prof = {ipc.IPC_KERNEL_NAMES[k]: ipc.ipc_profile_read(k)
+                    for k in range(len(ipc.IPC_KERNEL_NAMES))}
+        csize = ipc.ipc_compressed_size(fields[-1])
+        ipc.ipc_free(fields[-1])
+        return e_start.elapsed_time(e_end), launches, clk, prof, csize
+
+    elapsed_ms, launches, clk, _, csize = timed(False)
+    prof_ms, _, _, prof, _ = timed(True)
     elapsed_ms = max_over_ranks(elapsed_ms, dev, world)
     ms_per_step = elapsed_ms / args.steps
     value = job_gbs(world, step_bytes, args.steps, elapsed_ms * 1e-3)
@@ -274,7 +285,10 @@ def run_ours(args, rank, world, local_rank):
     roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1),
             "peak": peak, "peak_source": peak_src, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": measured_traffic(),
-            "launches": L, "avg_launch_us": round(ms * 1e3 / L, 2) if L else None}
+            "launches": L, "avg_launch_us": round(ms * 1e3 / L, 2) if L else None,
+            "timing": "CUDA events around each launch on the library's stream, in a second "
+                      "timed pass of the same %d steps (%.3f ms/step with the events)"
+                      % (args.steps, prof_ms / args.steps)}
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3),
                    "alg_GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None}
                for k, v in prof.items() if v[0]}
