@@ -528,6 +528,50 @@ void quant_args(double eb, double xmaxabs, void* out) {
 // every level from the coarsest, ONE launch covering that level's CTAs of
 // every field (entry table in device memory); one sync to read the
 // per-stage statistics, plane populations and outliers back.
+// Level ladders: level l >= 2 of a reconstruction (of a compression) writes
+// its whole lattice densely (row major over its extents) to a scratch array,
+// which holds the known points of level l - 1; level K + 1 is the anchor
+// alone. Only level 1 writes the caller's array (compression: nothing).
+// ladder() returns the scratch bytes and the byte offset of each level's
+// array (256-byte aligned).
+uint64_t lattice_elems(const Geo& g, int l) {
+  uint64_t n = 1;
+  for (int e = 0; e < 3; ++e) n *= (uint64_t)(((g.N[e] - 1) >> (l - 1)) + 1);
+  return n;
+}
+uint64_t ladder(const Geo& g, size_t esz, std::vector<uint64_t>* off) {
+  off->assign(g.K + 2, 0);
+  uint64_t tot = 0;
+  for (int l = 2; l <= g.K + 1; ++l) {
+    (*off)[l] = tot;
+    tot += (lattice_elems(g, l) * esz + 255) & ~uint64_t(255);
+  }
+  return tot;
+}
+// Level l's layout in a reconstruction: dense lattice strides for its
+// output, the known points read from level l + 1's dense lattice `kin`.
+void retrieve_layout(LevelArgs* L, const void* kin) {
+  for (int e = 0; e < 3; ++e) L->N[e] = L->M[e];
+  L->stride[2] = 1;
+  L->stride[1] = L->M[2];
+  L->stride[0] = L->M[1] * L->M[2];
+  L->s = 1;
+  L->kin = kin;
+  L->kst1 = ((L->M[2] - 1) >> 1) + 1;
+  L->kst0 = (((L->M[1] - 1) >> 1) + 1) * L->kst1;
+}
+
+// Level l's layout in a compression: x is read in its natural layout, the
+// known points from level l + 1's dense lattice `kin`, and the level's own
+// values go densely to its ladder array.
+void compress_layout(LevelArgs* L, const void* kin) {
+  L->kin = kin;
+  L->kst1 = ((L->M[2] - 1) >> 1) + 1;
+  L->kst0 = (((L->M[1] - 1) >> 1) + 1) * L->kst1;
+  L->ost1 = L->M[2];
+  L->ost0 = L->M[1] * L->M[2];
+}
+
 int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>& ins,
                     cudaStream_t st) {
   int dev = 0;
@@ -542,10 +586,12 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
   const int dtype = fs[0]->dtype;
   const size_t esz = dtype == 0 ? 4 : 8;
   // per-field offsets into the shared scratch
+  // per field: its level ladder of reconstructed values (byte offsets)
   std::vector<uint64_t> xo(nf + 1, 0), so(nf + 1, 0);
+  std::vector<std::vector<uint64_t>> xl(nf);
   int Kmax = 0;
   for (size_t i = 0; i < nf; ++i) {
-    xo[i + 1] = xo[i] + ((fs[i]->g.n * esz + 255) / 256) * 256;
+    xo[i + 1] = xo[i] + ladder(fs[i]->g, esz, &xl[i]);
     so[i + 1] = so[i] + std::max<size_t>(fs[i]->g.stages.size(), 1);
     Kmax = std::max(Kmax, fs[i]->g.K);
   }
@@ -617,8 +663,10 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     if (dtype == 0) quant_args<float>(eb, f->xmaxabs, quant[i].data());
     else quant_args<double>(eb, f->xmaxabs, quant[i].data());
     if ((rc = plan_field(f, st))) return rc;
-    // the anchor is stored exactly: xh[0] = x[0]
-    CU(cudaMemcpyAsync((uint8_t*)ws.xh + xo[i], ins[i], esz, cudaMemcpyDeviceToDevice, st));
+    // the anchor is stored exactly: the origin of level K + 1 is x[0]
+    if (f->g.K > 0)
+      CU(cudaMemcpyAsync((uint8_t*)ws.xh + xo[i] + xl[i][f->g.K + 1], ins[i], esz,
+                         cudaMemcpyDeviceToDevice, st));
   }
 
   // entry table of every level (coarsest first)
@@ -640,8 +688,9 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
         e.D = level_descs(f, l);
         e.o = SweepOut{f->d_cap, f->d_bm, ws.nnz + 32 * so[i], ws.okey, ws.oval, ocount,
                        ws.ocap, ws.stat + 2 * so[i], (uint32_t)i};
+        compress_layout(&e.L, (uint8_t*)ws.xh + xo[i] + xl[i][l + 1]);
         e.x = ins[i];
-        e.xh = (uint8_t*)ws.xh + xo[i];
+        e.xh = l > 1 ? (uint8_t*)ws.xh + xo[i] + xl[i][l] : nullptr;
         std::memcpy(e.quant, quant[i].data(), 32);
         e.write_xh = l > 1;  // the finest level's values are never read again
         e.cta_begin = cta;
@@ -804,38 +853,6 @@ bool level_w16(const ipc_field* f, int l, int b) {
       }
   }
   return ktop - b <= 15;
-}
-
-// Reconstruction scratch: level l >= 2 writes its whole lattice densely (row
-// major over its extents) to a scratch array, which holds the known points
-// of level l - 1; level K + 1 is the anchor alone. Only level 1 writes the
-// caller's array (its lattice is the grid). Returns the scratch bytes and
-// the byte offset of each level's array (256-byte aligned).
-uint64_t lattice_elems(const Geo& g, int l) {
-  uint64_t n = 1;
-  for (int e = 0; e < 3; ++e) n *= (uint64_t)(((g.N[e] - 1) >> (l - 1)) + 1);
-  return n;
-}
-uint64_t ladder(const Geo& g, size_t esz, std::vector<uint64_t>* off) {
-  off->assign(g.K + 2, 0);
-  uint64_t tot = 0;
-  for (int l = 2; l <= g.K + 1; ++l) {
-    (*off)[l] = tot;
-    tot += (lattice_elems(g, l) * esz + 255) & ~uint64_t(255);
-  }
-  return tot;
-}
-// Level l's layout in a reconstruction: dense lattice strides for its
-// output, the known points read from level l + 1's dense lattice `kin`.
-void retrieve_layout(LevelArgs* L, const void* kin) {
-  for (int e = 0; e < 3; ++e) L->N[e] = L->M[e];
-  L->stride[2] = 1;
-  L->stride[1] = L->M[2];
-  L->stride[0] = L->M[1] * L->M[2];
-  L->s = 1;
-  L->kin = kin;
-  L->kst1 = ((L->M[2] - 1) >> 1) + 1;
-  L->kst0 = (((L->M[1] - 1) >> 1) + 1) * L->kst1;
 }
 
 // Algorithm 1 on the device: the anchor, then one fused launch per level

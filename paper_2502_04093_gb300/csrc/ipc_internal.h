@@ -57,10 +57,13 @@ struct LevelArgs {
   int vec;            // output base aligned to two elements (paired stores allowed)
   uint64_t nrb, nct;  // CTA row blocks per plane, column tiles
   LevelStage st[3];
-  // reconstruction: the known points of the level, the next coarser
-  // level's lattice stored densely (plane and row strides in elements)
+  // the known points of the level: the next coarser level's lattice stored
+  // densely (plane and row strides in elements)
   const void* kin;
   int64_t kst0, kst1;
+  // compression: plane and row strides of the level's own dense lattice
+  // (its reconstructed values, the next finer level's known points)
+  int64_t ost0, ost1;
 };
 
 // Kernel-side view of a stage's word grid and segments (pack / unpack).

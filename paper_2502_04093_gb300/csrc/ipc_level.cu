@@ -269,10 +269,10 @@ __device__ __forceinline__ void code_pair(const uint32_t* p, int, uint32_t (&n)[
 // whole sectors are written (the element in between is a target of the next
 // level and is never read as a known value); larger strides store singly.
 template <class T>
-__device__ __forceinline__ void store_run(T* row, const LevelArgs& L, int c2e, int C1,
+__device__ __forceinline__ void store_run(T* row, int64_t s, int64_t n2, int c2e, int C1,
                                           const T (&v)[8]) {
   typedef typename Vec2<T>::type V2;
-  if (L.s == 1) {
+  if (s == 1) {
     T* p = row + c2e;
     if (c2e + 8 <= C1 && ((uintptr_t)p & 15) == 0) {
       if (sizeof(T) == 4) {
@@ -296,9 +296,9 @@ __device__ __forceinline__ void store_run(T* row, const LevelArgs& L, int c2e, i
       if (c2e + i < C1) p[i] = v[i];
     return;
   }
-  if (L.s == 2) {
+  if (s == 2) {
     T* p = row + 2 * (int64_t)c2e;
-    if (c2e + 8 <= C1 && 2 * (int64_t)(c2e + 7) + 1 < L.N[2] && ((uintptr_t)p & 15) == 0) {
+    if (c2e + 8 <= C1 && 2 * (int64_t)(c2e + 7) + 1 < n2 && ((uintptr_t)p & 15) == 0) {
       if (sizeof(T) == 4) {
         float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
@@ -324,7 +324,7 @@ __device__ __forceinline__ void store_run(T* row, const LevelArgs& L, int c2e, i
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i)
-    if (c2e + i < C1) row[(int64_t)(c2e + i) * L.s] = v[i];
+    if (c2e + i < C1) row[(int64_t)(c2e + i) * s] = v[i];
 }
 
 // Tile of a level launch: NS planes of the same parity side by side, each a
@@ -801,7 +801,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
             }
           }
         }
-        store_run<T>(out + c.pbase + (int64_t)c1 * c.rs, L, c2e, c.C1, v);
+        store_run<T>(out + c.pbase + (int64_t)c1 * c.rs, L.s, L.N[2], c2e, c.C1, v);
       }
     }
   }
@@ -879,8 +879,16 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
   // row, rows and planes multiples of four elements apart
   const int64_t so = L.s * L.stride[0];
   const bool vec = sizeof(T) == 4 && L.s == 1 && c2p + 3 < M2 && (so & 3) == 0 &&
-                   (c.rs & 3) == 0 && ((uintptr_t)(x + c.pbase + c2p) & 15) == 0 &&
-                   ((uintptr_t)(xh + c.pbase + c2p) & 15) == 0;
+                   (c.rs & 3) == 0 && ((uintptr_t)(x + c.pbase + c2p) & 15) == 0;
+  // Known points: the next coarser level's lattice stored densely, point
+  // (P', c1, c2) (all even) at kin[(P'/2) k0 + (c1/2) k1 + c2/2]; `kp` points
+  // at plane P (even plane) or P - 1 (odd plane) -- planes P + 1, P - 3,
+  // P + 3 are k0, -k0, 2 k0 away.
+  const T* kin = reinterpret_cast<const T*>(L.kin);
+  const int64_t k0 = L.kst0, k1 = L.kst1;
+  const T* kplane = kin + (int64_t)(c.P >> 1) * k0;
+  const bool veck = pb && (k1 & 1) == 0 && (k0 & 1) == 0 &&
+                    ((uintptr_t)(kplane + (c2p >> 1)) % (2 * sizeof(T))) == 0;
 
   // Phase 1: even value rows.
   {
@@ -903,14 +911,15 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
       }
     };
     auto one = [&](int c1, int c2, bool own) -> T {
-      const int64_t e = c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s;
-      if (!podd) return __ldg(xh + e);
-      const T bb = __ldg(xh + e - so);
-      const T cc = r1 ? __ldg(xh + e + so) : bb;
-      const T a = r3 ? __ldg(xh + e - 3 * so) : bb;
-      const T d = r3 ? __ldg(xh + e + 3 * so) : bb;
+      const T* p = kplane + (int64_t)(c1 >> 1) * k1 + (c2 >> 1);
+      if (!podd) return __ldg(p);
+      const T bb = __ldg(p);
+      const T cc = r1 ? __ldg(p + k0) : bb;
+      const T a = r3 ? __ldg(p - k0) : bb;
+      const T d = r3 ? __ldg(p + 2 * k0) : bb;
       T v;
-      point(pred4<T>(a, bb, cc, d, c.P, M0, cubic), __ldg(x + e), c1, c2, own, &v);
+      point(pred4<T>(a, bb, cc, d, c.P, M0, cubic),
+            __ldg(x + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s), c1, c2, own, &v);
       return v;
     };
     if (pa) {
@@ -923,22 +932,31 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
         if (c1 < 0 || c1 >= M1) continue;
         const bool ownr = c1 >= c.R0 && c1 < c.R1;
         T va, vb;
-        if (vec) {
-          const int64_t e = c.pbase + (int64_t)c1 * c.rs + c2p;
-          const float* xf = reinterpret_cast<const float*>(xh) + e;
+        if (veck) {
+          // the pair's known points: consecutive elements (one 8-byte load
+          // per plane for float); x: one 16-byte load at stride 1
+          const V2* p2 = reinterpret_cast<const V2*>(kplane + (int64_t)(c1 >> 1) * k1 + (c2p >> 1));
           if (!podd) {
-            const float4 k = __ldg(reinterpret_cast<const float4*>(xf));
-            va = (T)k.x;
-            vb = (T)k.z;
+            const V2 k = __ldg(p2);
+            va = k.x;
+            vb = k.y;
           } else {
-            const float4 bb = __ldg(reinterpret_cast<const float4*>(xf - so));
-            const float4 cc = r1 ? __ldg(reinterpret_cast<const float4*>(xf + so)) : bb;
-            const float4 a = r3 ? __ldg(reinterpret_cast<const float4*>(xf - 3 * so)) : bb;
-            const float4 d = r3 ? __ldg(reinterpret_cast<const float4*>(xf + 3 * so)) : bb;
-            const float4 xv = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e));
-            point((T)pred4<float>(a.x, bb.x, cc.x, d.x, c.P, M0, cubic), (T)xv.x, c1, c2p, ownr, &va);
-            point((T)pred4<float>(a.z, bb.z, cc.z, d.z, c.P, M0, cubic), (T)xv.z, c1, c2p + 2,
-                  ownr, &vb);
+            const V2 bb = __ldg(p2);
+            const V2 cc = r1 ? __ldg(p2 + k0 / 2) : bb;
+            const V2 a = r3 ? __ldg(p2 - k0 / 2) : bb;
+            const V2 d = r3 ? __ldg(p2 + k0) : bb;
+            const int64_t e = c.pbase + (int64_t)c1 * c.rs + (int64_t)c2p * L.s;
+            T xa, xb;
+            if (vec) {
+              const float4 xv = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e));
+              xa = (T)xv.x;
+              xb = (T)xv.z;
+            } else {
+              xa = __ldg(x + e);
+              xb = __ldg(x + e + 2 * L.s);
+            }
+            point(pred4<T>(a.x, bb.x, cc.x, d.x, c.P, M0, cubic), xa, c1, c2p, ownr, &va);
+            point(pred4<T>(a.y, bb.y, cc.y, d.y, c.P, M0, cubic), xb, c1, c2p + 2, ownr, &vb);
           }
         } else {
           va = one(c1, c2p, ownr);
@@ -1086,7 +1104,7 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
           }
         }
         *reinterpret_cast<uint4*>(E2 + lr * G::QP + qoff<false>(4 * g)) = make_uint4(n[0], n[1], n[2], n[3]);
-        if (write_xh) store_run<T>(xh + e, L, c2e, c.C1, v);
+        if (write_xh) store_run<T>(xh + (int64_t)c.P * L.ost0 + (int64_t)c1 * L.ost1, 1, 0, c2e, c.C1, v);
       }
     }
   }
