@@ -520,7 +520,7 @@ def serve_stream(ipc, fields, reqs, plain, rate, live_cap=8):
     import numpy as np
     srv = ipc.ipc_server_create(48 << 30, max_batch=1 if plain else 0,
                                 max_inflight=1 if plain else 3, nstreams=1 if plain else 3,
-                                plain=plain)
+                                plain=plain, max_batch_values=0 if plain else 1 << 26)
     rng = np.random.default_rng(77)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
     live = []  # (view_id, field index, current E)

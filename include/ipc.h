@@ -191,6 +191,9 @@ typedef struct {
   int max_inflight;      /* batches on the device at once (>= 1)                */
   int nstreams;          /* streams the batches rotate over (1..16)             */
   int plain;             /* 1: single-field launches per request (a baseline)   */
+  uint64_t max_batch_values; /* values (output elements) per batch; a request past
+                                the limit waits for the next batch, a larger one
+                                runs alone (0: unlimited)                        */
 } ipc_server_cfg;
 enum { IPC_REQ_RETRIEVE = 0, IPC_REQ_REFINE = 1, IPC_REQ_RELEASE = 2 };
 /* RETRIEVE(field, target): a new view with a server-owned output buffer.
@@ -216,8 +219,9 @@ typedef struct {
 
 /* ipc_server_create -- starts a server on the current device: a worker
  * thread admits submitted requests in arrival order while output memory
- * (mem_budget, and free HBM above hbm_reserve) allows, groups everything it
- * admitted into one batched reconstruction (ipc_retrieve_batch's launches)
+ * (mem_budget, and free HBM above hbm_reserve) and the batch limits allow,
+ * groups everything it admitted into one batched reconstruction
+ * (ipc_retrieve_batch's launches; a batch of one takes ipc_retrieve's)
  * and rotates batches over `nstreams` streams, so requests that arrive
  * while others run are launched and overlap on the device. A request's
  * reconstruction is bitwise equal to the same request served alone. A

@@ -137,6 +137,8 @@ void admit_and_launch(ipc_server* s) {
   std::vector<int> status;
   std::deque<Pending> keep;
   bool blocked = false;
+  uint64_t values = 0;  // output elements of the batch so far
+  const uint64_t maxv = s->cfg.max_batch_values;
   std::vector<uint64_t> touched;
   size_t free_hbm = 0, total_hbm = 0;
   cudaMemGetInfo(&free_hbm, &total_hbm);
@@ -148,6 +150,22 @@ void admit_and_launch(ipc_server* s) {
     if ((blocked && p.req.kind == IPC_REQ_RETRIEVE) || (int)take.size() >= maxb) {
       keep.push_back(p);
       continue;
+    }
+    // the batch's size limit: a request that would pass it waits (and keeps
+    // its place) for the next batch; the first request of a batch always goes
+    if (maxv && !take.empty() && p.req.kind != IPC_REQ_RELEASE) {
+      uint64_t nv = 0;
+      int dt = 0;
+      if (p.req.kind == IPC_REQ_RETRIEVE && p.req.field) ipc_internal_field_shape(p.req.field, &nv, &dt);
+      if (p.req.kind == IPC_REQ_REFINE) {
+        auto it = s->views.find(p.req.view_id);
+        if (it != s->views.end()) ipc_internal_field_shape(it->second.f, &nv, &dt);
+      }
+      if (values + nv > maxv) {
+        blocked = true;  // later retrieves keep arrival order behind it
+        keep.push_back(p);
+        continue;
+      }
     }
     const Clock::time_point now = Clock::now();
     const ipc_request& r = p.req;
@@ -197,6 +215,12 @@ void admit_and_launch(ipc_server* s) {
       v.b = nb;
       v.bytes = nbytes;
       v.bound = nbound;
+      {
+        uint64_t nv = 0;
+        int dt = 0;
+        ipc_internal_field_shape(v.f, &nv, &dt);
+        values += nv;
+      }
       take.push_back(p);
       vid.push_back(r.view_id);
       sel.push_back(nb);
@@ -255,6 +279,7 @@ void admit_and_launch(ipc_server* s) {
     sel.push_back(nb);
     status.push_back(IPC_OK);
     touched.push_back(id);
+    values += n;
   }
   s->pending = std::move(keep);
   if (take.empty()) return;
@@ -276,7 +301,8 @@ void admit_and_launch(ipc_server* s) {
     outs.push_back(v.out);
   }
   int rc;
-  if (s->cfg.plain) rc = ipc_internal_reconstruct_each(fs, sel, outs, st);
+  // a batch of one takes the single-field path (no entry table to upload)
+  if (s->cfg.plain || take.size() == 1) rc = ipc_internal_reconstruct_each(fs, sel, outs, st);
   else rc = ipc_internal_reconstruct_batch(fs, sel, outs, st, &fl.tabs);
   if (rc)
     for (auto& x : fl.status) x = rc;

@@ -40,7 +40,8 @@ class ipc_batch_item(C.Structure):
 
 class ipc_server_cfg(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("hbm_reserve", C.c_uint64), ("max_batch", C.c_int),
-                ("max_inflight", C.c_int), ("nstreams", C.c_int), ("plain", C.c_int)]
+                ("max_inflight", C.c_int), ("nstreams", C.c_int), ("plain", C.c_int),
+                ("max_batch_values", C.c_uint64)]
 
 
 class ipc_request(C.Structure):
@@ -308,9 +309,9 @@ def ipc_plan_launch(plan, stream=None):
 
 
 def ipc_server_create(mem_budget, max_batch=0, max_inflight=2, nstreams=2, plain=False,
-                      hbm_reserve=1 << 30):
+                      hbm_reserve=1 << 30, max_batch_values=0):
     cfg = ipc_server_cfg(int(mem_budget), int(hbm_reserve), int(max_batch), int(max_inflight),
-                         int(nstreams), 1 if plain else 0)
+                         int(nstreams), 1 if plain else 0, int(max_batch_values))
     h = C.c_void_p()
     _check(lib().ipc_server_create(C.byref(cfg), C.byref(h)), "ipc_server_create")
     return h

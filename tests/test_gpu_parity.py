@@ -216,3 +216,52 @@ def test_export_into_host_buffer():
     assert bytes(mv) == raw
     with pytest.raises(ValueError):
         ipc.ipc_export(g.h, bytearray(n - 1))
+
+
+@pytest.mark.parametrize("shape,dtype", [
+    ((9, 257, 257), np.float32),   # level 1 one plane per tile, level 2 two, level 3 four
+    ((5, 20, 513), np.float32),    # two column tiles at level 1
+    ((17, 40, 129), np.float32),   # 129 / 65 / 33 columns: sub-tile edges
+    ((12, 33, 256), np.float64),   # f64 tiles of 8 rows with two and four planes
+    ((7, 64, 100), np.float64),
+])
+def test_planes_per_tile_and_dense_levels(shape, dtype):
+    """Levels whose rows are narrow put two or four planes in a tile; levels
+    above 1 read their known points from the next level's dense lattice."""
+    x = synth.random_field(shape, seed=sum(shape), dtype=dtype)
+    g, o = both(x, 1e-5)
+    assert g.export() == o.export()
+    for E in (1e-5, 1e-3, 1e-1):
+        check_retrieve(g, o, oracle.EB, E)
+    for br in (2.0, 8.0):
+        check_retrieve(g, o, oracle.BITRATE, br)
+
+
+def test_outliers_on_narrow_levels():
+    x = synth.random_field((24, 100, 120), seed=31, kind="spiky")
+    x[3, 50, 60] = np.inf
+    g, o = both(x, 1e-4, ipc.IPC_EB_ABS)
+    assert g.export() == o.export()
+    for E in (1e-4, 1e-2, 1.0):
+        check_retrieve(g, o, oracle.EB, E)
+
+
+def test_batch_mixed_widths_and_repeats():
+    """One batched retrieval over fields whose levels take different tile
+    shapes (the launch uses the smallest planes-per-tile of the batch) and
+    over the same field several times."""
+    shapes = [(10, 40, 600), (12, 30, 100), (8, 64, 250)]
+    xs = [synth.random_field(s, seed=40 + i) for i, s in enumerate(shapes)]
+    gs = [ipc.Field.compress(to_dev(x), 1e-5) for x in xs]
+    os_ = [oracle.compress(x, 1e-5) for x in xs]
+    fields = [gs[0].h, gs[1].h, gs[2].h, gs[1].h, gs[1].h]
+    srcs = [0, 1, 2, 1, 1]
+    # (bitrates well above the small fields' mandatory tables)
+    targets = [(ipc.IPC_TARGET_EB, 1e-3), (ipc.IPC_TARGET_BITRATE, 8.0), (ipc.IPC_TARGET_EB, 1e-5),
+               (ipc.IPC_TARGET_EB, 1e-2), (ipc.IPC_TARGET_BITRATE, 16.0)]
+    outs = [torch.empty(shapes[i], dtype=torch.float32, device="cuda") for i in srcs]
+    ipc.ipc_retrieve_batch(fields, targets, outs)
+    torch.cuda.synchronize()
+    for j, (i, (k, v)) in enumerate(zip(srcs, targets)):
+        oy, _ = os_[i].retrieve(oracle.EB if k == ipc.IPC_TARGET_EB else oracle.BITRATE, v)
+        assert np.array_equal(outs[j].cpu().numpy().view(np.uint8), oy.view(np.uint8)), j

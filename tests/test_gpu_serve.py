@@ -38,11 +38,13 @@ def fields():
     return xs, fs
 
 
-@pytest.mark.parametrize("plain", [False, True])
-def test_results_same_alone_and_in_the_mix(fields, plain):
+@pytest.mark.parametrize("plain,maxv", [(False, 0), (True, 0), (False, 150000)])
+def test_results_same_alone_and_in_the_mix(fields, plain, maxv):
+    """maxv: batch size limit in values (150000 splits the mix into batches
+    of one to a few fields; the 128x129 field fits alone)."""
     xs, fs = fields
     srv = ipc.ipc_server_create(8 << 30, max_inflight=3, nstreams=3, plain=plain,
-                                max_batch=1 if plain else 0)
+                                max_batch=1 if plain else 0, max_batch_values=maxv)
     try:
         rng = np.random.default_rng(3)
         reqs = []
