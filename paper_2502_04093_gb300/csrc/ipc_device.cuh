@@ -157,6 +157,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// floor(n / d) from m = div_magic(d): the high 64 bits of the 96-bit n * m.
+__device__ __forceinline__ uint32_t div_by(uint32_t n, uint64_t m) {
+  if (m == 0) return n;
+  const uint64_t lo = (uint64_t)n * (uint32_t)m;
+  const uint64_t hi = (uint64_t)n * (uint32_t)(m >> 32) + (lo >> 32);
+  return (uint32_t)(hi >> 32);
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -372,6 +373,8 @@ void keep_pool(int dev) {
 
 // Segmented layout of the device streams (independent of the data): per
 // stage and plane, nseg segments of RB*CW capacity words and bw bitmap words.
+// The planes of a stage follow one another at a fixed stride (the level
+// kernels address plane k from plane 0 and that stride).
 int plan_field(ipc_field* f, cudaStream_t st) {
   const Geo& g = f->g;
   f->desc.assign(g.stages.size(), StageDescs{});
@@ -414,6 +417,8 @@ LevelArgs level_args(const ipc_field* f, int l) {
   const int BR = level_rows(f->dtype);
   L.nrb = ((uint64_t)L.M[1] + BR - 1) / BR;
   L.nct = ((uint64_t)L.M[2] + kLevelCols - 1) / kLevelCols;
+  L.mrb = div_magic(L.nrb);
+  L.mct = div_magic(L.nct);
   for (int d = 0; d < 3; ++d) {
     LevelStage& S = L.st[d];
     const int t = g.level_stage[d][l - 1];
@@ -435,6 +440,24 @@ LevelArgs level_args(const ipc_field* f, int l) {
     }
   }
   return L;
+}
+
+// Reconstruction view of level l's plane streams with b_l = b: where plane
+// 0 of each stage lies, the plane strides, and the planes to load.
+void retrieve_planes(const ipc_field* f, int l, int b, LevelArgs* L) {
+  for (int d = 0; d < 3; ++d) {
+    const int t = f->g.level_stage[d][l - 1];
+    LevelStage& S = L->st[d];
+    S.kmask = 0;
+    if (t < 0) continue;
+    const StageGeo& sg = f->g.stages[t];
+    S.cap0 = f->desc[t].p[0].cap_off;
+    S.bm0 = f->desc[t].p[0].bm_off;
+    S.pcap = sg.nseg * (uint64_t)sg.RB * sg.CW;
+    S.pbm = sg.nseg * sg.bw;
+    for (int k = std::max(b, 0); k < 32; ++k)
+      if (f->st[t].nnz[k]) S.kmask |= 1u << k;
+  }
 }
 
 LevelDescs level_descs(const ipc_field* f, int l) {
@@ -852,7 +875,9 @@ bool level_w16(const ipc_field* f, int l, int b) {
         break;
       }
   }
-  return ktop - b <= 15;
+  // 16-bit rows scale 2eb by up to 2^16 (the product must stay finite)
+  const double lim = f->dtype == 0 ? (double)FLT_MAX : DBL_MAX;
+  return ktop - b <= 15 && bin_width(f) * 65536.0 <= lim;
 }
 
 // Algorithm 1 on the device: the anchor, then one fused launch per level
@@ -880,8 +905,8 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
   for (int l = g.K; l >= 1; --l) {
     LevelArgs L = level_args(f, l);
     retrieve_layout(&L, scr + off[l + 1]);
+    retrieve_planes(f, l, b[l - 1], &L);
     void* o = l == 1 ? d_out : (void*)(scr + off[l]);
-    const LevelDescs D = level_descs(f, l);
     double by = 0;
     uint64_t nc = 0;
     for (int d = 0; d < 3; ++d) {
@@ -892,7 +917,7 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
     }
     const long ph = prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st);
     CU(launch_level_retrieve(f->dtype, L, o, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
-                             f->d_oval, D, level_w16(f, l, b[l - 1]) ? 1 : 0, st));
+                             f->d_oval, level_w16(f, l, b[l - 1]) ? 1 : 0, st));
     prof_end(ph, st, by + (double)(nc * esz));
   }
   return IPC_OK;
@@ -968,7 +993,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       RetrieveEntry e{};
       e.L = level_args(f, l);
       retrieve_layout(&e.L, nullptr);
-      e.D = level_descs(f, l);
+      retrieve_planes(f, l, bs[i][l - 1], &e.L);
       e.out = outs[i];
       e.cap = f->d_cap;
       e.bm = f->d_bm;

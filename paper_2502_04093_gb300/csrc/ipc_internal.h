@@ -49,6 +49,11 @@ struct LevelStage {
   uint64_t nrb, nct, bw;
   uint64_t m1, m2, wr;  // stage lattice: rows per plane, codes per row, words per row
   uint64_t out_begin, out_end;  // outlier range of the stage (reconstruction)
+  // reconstruction: word offsets of plane 0's capacity array and bitmap and
+  // the per-plane strides (plane k lies k strides further), and the planes
+  // to load (bit k: k >= b and the plane has nonzero words)
+  uint64_t cap0, pcap, bm0, pbm;
+  uint32_t kmask;
 };
 struct LevelArgs {
   int64_t N[3], stride[3], M[3];  // extents, element strides, lattice extents
@@ -56,6 +61,7 @@ struct LevelArgs {
   int cubic;
   int vec;            // output base aligned to two elements (paired stores allowed)
   uint64_t nrb, nct;  // CTA row blocks per plane, column tiles
+  uint64_t mrb, mct;  // div_magic(nrb), div_magic(nct): tile -> (plane, row block, column tile)
   LevelStage st[3];
   // the known points of the level: the next coarser level's lattice stored
   // densely (plane and row strides in elements)
@@ -65,6 +71,11 @@ struct LevelArgs {
   // (its reconstructed values, the next finer level's known points)
   int64_t ost0, ost1;
 };
+
+// Division of a 32-bit n by a divisor 1 <= d < 2^32 as the high half of n * m,
+// m = ceil(2^64 / d) (0 for d = 1): n m / 2^64 exceeds n / d by less than
+// 2^-32 < 1/d, which never carries it past the next integer.
+inline uint64_t div_magic(uint64_t d) { return d <= 1 ? 0 : UINT64_MAX / d + 1; }
 
 // Kernel-side view of a stage's word grid and segments (pack / unpack).
 struct StageArgs {
@@ -138,7 +149,6 @@ struct CompressEntry {
 };
 struct RetrieveEntry {
   LevelArgs L;
-  LevelDescs D;
   void* out;
   const uint32_t* cap;
   const uint32_t* bm;
@@ -179,8 +189,7 @@ inline uint64_t retrieve_tiles(const LevelArgs& L, int ns) {
 // w16: the planes loaded at the level span at most 16 (16-bit code rows).
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
-                                  const double* oval, const LevelDescs& d, int w16,
-                                  cudaStream_t st);
+                                  const double* oval, int w16, cudaStream_t st);
 int level_rows(int dtype);
 // Batched level launches: `ents` (device memory) sorted by cta_begin.
 cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,

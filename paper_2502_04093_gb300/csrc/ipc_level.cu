@@ -48,11 +48,10 @@ struct CtaPos {
 
 __device__ __forceinline__ CtaPos cta_pos(const LevelArgs& L, uint64_t cta, int BR, int BC) {
   CtaPos c;
-  uint64_t b = cta;
-  c.ct = b % L.nct;
-  b /= L.nct;
-  c.rb = b % L.nrb;
-  c.P = (int)(b / L.nrb);
+  const uint32_t b = (uint32_t)cta, b1 = div_by(b, L.mct), p = div_by(b1, L.mrb);
+  c.ct = b - b1 * (uint32_t)L.nct;
+  c.rb = b1 - p * (uint32_t)L.nrb;
+  c.P = (int)p;
   c.R0 = (int)c.rb * BR;
   c.R1 = (int)min(L.M[1], (int64_t)c.R0 + BR);
   c.C0 = (int)c.ct * BC;
@@ -194,14 +193,7 @@ struct RTile {
 template <bool W16>
 __device__ __forceinline__ int qoff(int e) { return (e >> 5) * QCfg<W16>::BLK + (e & 31); }
 
-// Four consecutive codes (negabinary, window shift applied).
-__device__ __forceinline__ void load4(const uint16_t* p, int wb, uint32_t (&n)[4]) {
-  const uint2 v = *reinterpret_cast<const uint2*>(p);
-  n[0] = (v.x & 0xFFFFu) << wb;
-  n[1] = (v.x >> 16) << wb;
-  n[2] = (v.y & 0xFFFFu) << wb;
-  n[3] = (v.y >> 16) << wb;
-}
+// Four consecutive 32-bit codes.
 __device__ __forceinline__ void load4(const uint32_t* p, int, uint32_t (&n)[4]) {
   const uint4 v = *reinterpret_cast<const uint4*>(p);
   n[0] = v.x;
@@ -251,16 +243,61 @@ __device__ __forceinline__ void lds9<double>(const double* p, double (&w)[9]) {
   }
 }
 
-// Two consecutive codes (negabinary, window shift applied).
-__device__ __forceinline__ void code_pair(const uint16_t* p, int wb, uint32_t (&n)[2]) {
-  const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
-  n[0] = (v & 0xFFFFu) << wb;
-  n[1] = (v >> 16) << wb;
+// Products code value x 2eb of the codes of a code row. A 16-bit row entry v
+// holds the negabinary digits wb .. wb+15 of a code, whose value is then
+// (-2)^wb times the 16-digit value of v. That sign is folded into the digit
+// mask: swapping the masks of the odd and the even positions negates a digit
+// string's value, so the code's value is 2^wb * z with z = (v ^ mask) - mask.
+// z is exact in float (|z| < 2^16) and is formed by placing v ^ mask under
+// the exponent of 1.5 * 2^23 and subtracting 1.5 * 2^23 + mask. The product
+// z * (2eb 2^wb) is the same real number as value * 2eb, rounded once, so it
+// is the same result (2eb 2^wb is exact: the host keeps it finite).
+template <class T>
+struct CodeScale {
+  uint32_t zmask;  // digit mask in both 16-bit halves
+  float zbias;     // 1.5 * 2^23 + the 16-bit mask
+  T tw;            // 2eb * 2^wb (16-bit rows) or 2eb (32-bit rows)
+};
+template <class T>
+__device__ __forceinline__ CodeScale<T> code_scale(T twoeb, int wb) {
+  CodeScale<T> c;
+  c.zmask = (wb & 1) ? 0x55555555u : 0xAAAAAAAAu;
+  c.zbias = (wb & 1) ? 12604757.0f : 12626602.0f;
+  c.tw = FP<T>::mul(twoeb, (T)(1u << wb));
+  return c;
 }
-__device__ __forceinline__ void code_pair(const uint32_t* p, int, uint32_t (&n)[2]) {
-  const uint2 v = *reinterpret_cast<const uint2*>(p);
-  n[0] = v.x;
-  n[1] = v.y;
+template <class T>
+__device__ __forceinline__ void scaled_word(uint32_t x, const CodeScale<T>& cs, T* v) {
+  const uint32_t t = x ^ cs.zmask;
+  const float z0 = __fsub_rn(__int_as_float(__byte_perm(t, 0x4B40u, 0x5410)), cs.zbias);
+  const float z1 = __fsub_rn(__int_as_float(__byte_perm(t, 0x4B40u, 0x5432)), cs.zbias);
+  v[0] = FP<T>::mul((T)z0, cs.tw);
+  v[1] = FP<T>::mul((T)z1, cs.tw);
+}
+template <class T>
+__device__ __forceinline__ void scaled_pair(const uint16_t* p, const CodeScale<T>& cs, T (&v)[2]) {
+  scaled_word(*reinterpret_cast<const uint32_t*>(p), cs, v);
+}
+template <class T>
+__device__ __forceinline__ void scaled_pair(const uint32_t* p, const CodeScale<T>& cs, T (&v)[2]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  v[0] = FP<T>::mul(code_value(u.x, T()), cs.tw);
+  v[1] = FP<T>::mul(code_value(u.y, T()), cs.tw);
+}
+template <class T>
+__device__ __forceinline__ void scaled_quad(const uint16_t* p, const CodeScale<T>& cs, T (&v)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  scaled_word(u.x, cs, v);
+  scaled_word(u.y, cs, v + 2);
+}
+template <class T>
+__device__ __forceinline__ void scaled_quad(const uint32_t* p, const CodeScale<T>& cs, T (&v)[4]) {
+  uint32_t n[4];
+  load4(p, 0, n);
+  T c[4];
+  code_values4(n, c);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = FP<T>::mul(c[k], cs.tw);
 }
 
 // Stores the values v[0..7] of lattice columns c2e .. c2e+7 of one row
@@ -334,15 +371,14 @@ __device__ __forceinline__ void store_run(T* row, int64_t s, int64_t n2, int c2e
 __device__ __forceinline__ CtaPos sub_pos(const LevelArgs& L, uint64_t tile, int j, int NS, int BR,
                                           int BCs) {
   CtaPos c;
-  uint64_t t = tile;
-  c.ct = t % L.nct;
-  t /= L.nct;
-  c.rb = t % L.nrb;
+  const uint32_t t = (uint32_t)tile, t1 = div_by(t, L.mct), g = div_by(t1, L.mrb);
+  c.ct = t - t1 * (uint32_t)L.nct;
+  c.rb = t1 - g * (uint32_t)L.nrb;
   // groups alternate even / odd (an odd plane reads the known points of the
   // even planes around it while they are in L2); the even groups can be one
   // more than the odd ones
-  const int64_t grp = (int64_t)(t / L.nrb);
-  const int64_t go = (L.M[0] / 2 + NS - 1) / NS;
+  const int64_t grp = g;
+  const int64_t go = ((int)(L.M[0] >> 1) + NS - 1) / NS;
   const int64_t par = grp < 2 * go ? (grp & 1) : 0, idx = grp < 2 * go ? (grp >> 1) : go;
   c.P = (int)(2 * (idx * NS + j) + par);
   c.R0 = (int)c.rb * BR;
@@ -360,8 +396,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
                                                     const uint32_t* __restrict__ bm,
                                                     const uint64_t* __restrict__ oidx,
                                                     const double* __restrict__ oval,
-                                                    const LevelDescs& D, uint64_t tile,
-                                                    unsigned char* smem) {
+                                                    uint64_t tile, unsigned char* smem) {
   constexpr int BCs = BC / NS;  // lattice columns of a sub-tile
   typedef RTile<BR, BCs, W16> G;
   typedef typename QCfg<W16>::QT QT;
@@ -379,10 +414,6 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   constexpr int KS = NS > 1 ? 5 : kSlots;
   __shared__ uint32_t SB[NS][KS][NPL][BWS];        // group bitmaps of the window's planes
   __shared__ const uint32_t* SP[NS][KS][NPL];      // payload base of (segment, plane)
-  __shared__ unsigned long long SG[NS][KS];        // segment id (or ~0 if absent)
-  __shared__ uint32_t s_km[NS][3];                 // planes to load, per stage
-  __shared__ int s_ktop[NS];
-  __shared__ CtaPos s_pos[NS];                     // sub-tile positions
 
   const int tid = threadIdx.x;
   const int sub = tid / TS, ltid = tid % TS;  // the thread's sub-tile
@@ -395,10 +426,11 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   const int M0 = (int)L.M[0], M1 = (int)L.M[1], M2 = (int)L.M[2];
   const LevelStage &S0 = L.st[0], &S1 = L.st[1], &S2 = L.st[2];
 
-  if (tid < NS) s_pos[tid] = sub_pos(L, tile, tid, NS, BR, BCs);
-  // the thread's own sub-tile (all sub-tiles of a tile share the plane
-  // parity; sub-tile 0 always holds a plane)
+  // The thread's own sub-tile. The sub-tiles of a tile share rows, columns
+  // and plane parity: sub-tile j holds plane P0 + 2j (sub-tile 0 always
+  // holds a plane).
   const CtaPos c = sub_pos(L, tile, sub, NS, BR, BCs);
+  const int P0 = c.P - 2 * sub;
   const bool live = c.P < M0;
   const bool podd = (c.P & 1) != 0;
   T* VE = VEof(sub);
@@ -407,53 +439,35 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   QT* Q0 = Q0of(sub);
   uint32_t* QH = QHof(sub);
 
-  if (tid < 32 * NS) {
-    const int s = tid >> 5, k = tid & 31;
-    const CtaPos cs = sub_pos(L, tile, s, NS, BR, BCs);
-    const bool odd = (cs.P & 1) != 0, ok = cs.P < M0;
-    uint32_t any = 0;
-#pragma unroll
-    for (int sx = 0; sx < 3; ++sx) {
-      const bool ld = ok && L.st[sx].present && (sx != 0 || odd) && k >= b && D.s[sx].p[k].nnz > 0;
-      const uint32_t m = __ballot_sync(~0u, ld);
-      if (k == 0) s_km[s][sx] = m;
-      any |= m;
-    }
-    if (k == 0) s_ktop[s] = any ? 31 - __clz((int)any) : -1;
-  }
-  if (tid >= 128 && tid < 128 + NS * KS) {
-    const int s = (tid - 128) / KS, sl = (tid - 128) % KS;
-    const CtaPos cs = sub_pos(L, tile, s, NS, BR, BCs);
+  // Planes to load per stage (k >= b with nonzero words, from the host) and
+  // the plane window: slot i of the staged tables is plane wb + i. With
+  // 16-bit codes the loaded planes [b, ktop] lie in [wb, wb + 15] (checked
+  // on the host for the level).
+  const uint32_t km0 = podd ? S0.kmask : 0u, km1 = S1.kmask, km2 = S2.kmask;
+  const int ktop = 31 - __clz((int)(km0 | km1 | km2));
+  const int wb = W16 ? max(0, ktop - 15) : 0;
+  const CodeScale<T> sc = code_scale<T>(twoeb, wb);
+  // Staging, one (sub-tile, segment slot, window plane) per thread: the
+  // payload base and asynchronous copies of the group bitmap words.
+  for (int u = tid; u < NS * KS * NPL; u += 256) {
+    const int s = u / (KS * NPL), r = u % (KS * NPL);
+    const int sl = r / NPL, i = r % NPL, k = wb + i;
     int sx, drb, dct;
     if (sl == 0) { sx = 2; drb = 0; dct = 0; }
     else if (KS == 5) {
       sx = sl == 1 ? 1 : 0; drb = sl == 1 ? 0 : sl - 3; dct = 0;
     } else if (sl < 4) { sx = 1; drb = 0; dct = sl - 2; }
     else { sx = 0; drb = (sl - 4) / 3 - 1; dct = (sl - 4) % 3 - 1; }
+    const uint32_t km = sx == 0 ? km0 : (sx == 1 ? km1 : km2);
+    const int Ps = P0 + 2 * s;
+    if (Ps >= M0 || k > 31 || !((km >> k) & 1u)) continue;
     const LevelStage& S = L.st[sx];
-    const int64_t rbs = (int64_t)cs.rb + drb, cts = (int64_t)cs.ct + dct;
-    const bool ok = cs.P < M0 && S.present && (sx != 0 || (cs.P & 1)) && rbs >= 0 &&
-                    (uint64_t)rbs < S.nrb && cts >= 0 && (uint64_t)cts < S.nct;
-    const uint64_t pi = sx == 0 ? (uint64_t)((cs.P - 1) >> 1) : (uint64_t)cs.P;
-    SG[s][sl] = ok ? seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts) : ~0ULL;
-  }
-  __syncthreads();
-  // Plane window of each sub-tile: slot i of the staged tables is plane
-  // wb + i. With 16-bit codes the loaded planes [b, ktop] lie in
-  // [wb, wb + 15] (checked on the host for the level; a sub-tile's ktop is at
-  // most the level's).
-  auto wbof = [&](int s) { return W16 ? max(0, s_ktop[s] - 15) : 0; };
-  const int wb = wbof(sub);
-  for (int u = tid; u < NS * KS * NPL; u += 256) {
-    const int s = u / (KS * NPL), r = u % (KS * NPL);
-    const int sl = r / NPL, i = r % NPL, k = wbof(s) + i;
-    const int sx = sl == 0 ? 2 : (KS == 5 ? (sl == 1 ? 1 : 0) : (sl < 4 ? 1 : 0));
-    const unsigned long long g = SG[s][sl];
-    if (g == ~0ULL || k > 31 || !((s_km[s][sx] >> k) & 1u)) continue;
-    const LevelStage& S = L.st[sx];
-    const PlaneDesc& pd = D.s[sx].p[k];
-    SP[s][sl][i] = cap + pd.cap_off + g * (uint64_t)S.RB * S.CW;
-    const uint32_t* bp = bm + pd.bm_off + g * S.bw;
+    const int64_t rbs = (int64_t)c.rb + drb, cts = (int64_t)c.ct + dct;
+    if (rbs < 0 || (uint64_t)rbs >= S.nrb || cts < 0 || (uint64_t)cts >= S.nct) continue;
+    const uint64_t pi = sx == 0 ? (uint64_t)((Ps - 1) >> 1) : (uint64_t)Ps;
+    const uint64_t g = seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts);
+    SP[s][sl][i] = cap + S.cap0 + (uint64_t)k * S.pcap + g * (uint64_t)S.RB * S.CW;
+    const uint32_t* bp = bm + S.bm0 + (uint64_t)k * S.pbm + g * S.bw;
     for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[s][sl][i][v], bp + v);
   }
 
@@ -541,13 +555,11 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   constexpr int MAXIT = (BR + G::H1 + G::H0) * G::CWD + 2 * (G::H1 + G::H0);
   for (int it = tid; it < NS * MAXIT; it += 256) {
     const int s = it / MAXIT, i = it % MAXIT;
-    const CtaPos& cs = s_pos[s];
-    if (cs.P >= M0) continue;
-    const bool odd = (cs.P & 1) != 0;
-    const int cw0 = (int)cs.ct * G::CWD;  // first own word of a row
-    const int n2r = cs.R1 - cs.R0, n1r = (cs.R1 - cs.R0) >> 1;
-    const bool st0 = S0.present && odd;
-    const int nA = (S2.present && cs.ct < S2.nct) ? n2r * G::CWD : 0;
+    if (P0 + 2 * s >= M0) continue;
+    const int cw0 = (int)c.ct * G::CWD;  // first own word of a row
+    const int n2r = c.R1 - c.R0, n1r = (c.R1 - c.R0) >> 1;
+    const bool st0 = S0.present && podd;
+    const int nA = (S2.present && c.ct < S2.nct) ? n2r * G::CWD : 0;
     const int nB = S1.present ? n1r * G::CWD : 0;
     const int nC = st0 ? G::H0 * G::CWD : 0;
     const int nD1 = S1.present ? 2 * n1r : 0;
@@ -555,20 +567,20 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     if (i >= nA + nB + nC + nD1 + nD0) continue;
     int sx, qrow, side, rr, j;  // side: -1 own word, 0 left / 1 right halo word
     if (i < nA) {
-      sx = 2; qrow = i / G::CWD; j = cw0 + i % G::CWD; rr = cs.R0 + qrow; side = -1;
+      sx = 2; qrow = i / G::CWD; j = cw0 + i % G::CWD; rr = c.R0 + qrow; side = -1;
     } else if (i < nA + nB) {
       const int u = i - nA;
-      sx = 1; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (cs.R0 >> 1) + qrow; side = -1;
+      sx = 1; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (c.R0 >> 1) + qrow; side = -1;
     } else if (i < nA + nB + nC) {
       const int u = i - nA - nB;
-      sx = 0; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (cs.R0 >> 1) - 1 + qrow; side = -1;
+      sx = 0; qrow = u / G::CWD; j = cw0 + u % G::CWD; rr = (c.R0 >> 1) - 1 + qrow; side = -1;
     } else if (i < nA + nB + nC + nD1) {
       const int u = i - nA - nB - nC;
-      sx = 1; qrow = u >> 1; side = u & 1; rr = (cs.R0 >> 1) + qrow;
+      sx = 1; qrow = u >> 1; side = u & 1; rr = (c.R0 >> 1) + qrow;
       j = side ? cw0 + G::CWD : cw0 - 1;
     } else {
       const int u = i - nA - nB - nC - nD1;
-      sx = 0; qrow = u >> 1; side = u & 1; rr = (cs.R0 >> 1) - 1 + qrow;
+      sx = 0; qrow = u >> 1; side = u & 1; rr = (c.R0 >> 1) - 1 + qrow;
       j = side ? cw0 + G::CWD : cw0 - 1;
     }
     const LevelStage& S = L.st[sx];
@@ -580,16 +592,16 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     int sl = 0;
     if (KS == 5) {
       if (sx == 1) sl = 1;
-      else if (sx == 0) sl = 3 + (rbw - (int)cs.rb);
+      else if (sx == 0) sl = 3 + (rbw - (int)c.rb);
     } else {
-      if (sx == 1) sl = 2 + (ctw - (int)cs.ct);
-      else if (sx == 0) sl = 4 + (rbw - (int)cs.rb + 1) * 3 + (ctw - (int)cs.ct) + 1;
+      if (sx == 1) sl = 2 + (ctw - (int)c.ct);
+      else if (sx == 0) sl = 4 + (rbw - (int)c.rb + 1) * 3 + (ctw - (int)c.ct) + 1;
     }
     const int li = (rr - rbw * RB) * CW + (j - ctw * CW);
     const int wl = li >> 5;
     const uint32_t bit = 1u << (li & 31), below = bit - 1u;
-    const uint32_t km = s_km[s][sx];
-    const int wbs = wbof(s);
+    const uint32_t kmw = (sx == 0 ? km0 : (sx == 1 ? km1 : km2)) >> wb;  // bit i2: plane wb + i2 loaded
+    const int bws = b - wb;  // window planes below bws are dropped
     const uint32_t* sb = &SB[s][sl][0][wl];
     const uint32_t* const* sp = SP[s][sl];
     const uint32_t off = (uint32_t)wl * 32;
@@ -599,9 +611,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     uint32_t a[NPL];
 #pragma unroll
     for (int i2 = 0; i2 < NPL; ++i2) {
-      const int k = wbs + i2;
       uint32_t w = 0u;
-      if (k <= 31 && ((km >> k) & 1u)) {
+      if ((kmw >> i2) & 1u) {
         const uint32_t m = sb[i2 * BWS];
         if (m & bit) w = __ldg(sp[i2] + off + __popc(m & below));
       }
@@ -612,7 +623,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
 #pragma unroll
     for (int i2 = NPL - 1; i2 >= 0; --i2) {
       const uint32_t p1 = i2 + 1 < NPL ? a[i2 + 1] : 0u, p2 = i2 + 2 < NPL ? a[i2 + 2] : 0u;
-      a[i2] = wbs + i2 >= b ? (a[i2] ^ p1 ^ p2) : 0u;
+      a[i2] = i2 >= bws ? (a[i2] ^ p1 ^ p2) : 0u;
     }
     if (side < 0) {
       if constexpr (W16) {
@@ -646,10 +657,10 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         v1 |= ((a[i2] >> 1) & 1u) << i2;
       }
       if (side) {
-        QHr[1] = v0 << wbs;
-        QHr[2] = v1 << wbs;
+        QHr[1] = v0 << wb;
+        QHr[2] = v1 << wb;
       } else {
-        QHr[0] = v0 << wbs;
+        QHr[0] = v0 << wb;
       }
     }
   }
@@ -674,10 +685,10 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         typedef typename Vec2<T>::type V2;
         V2* pv = reinterpret_cast<V2*>(VE + (2 * jr) * G::VP + G::V0 + jsp);
         V2 v = *pv;
-        uint32_t n[2];
-        code_pair(Q0 + jr * G::QP + qoff<W16>(jsp), wb, n);
-        v.x = FP<T>::add(v.x, FP<T>::mul(code_value(n[0], T()), twoeb));
-        v.y = FP<T>::add(v.y, FP<T>::mul(code_value(n[1], T()), twoeb));
+        T cv[2];
+        scaled_pair(Q0 + jr * G::QP + qoff<W16>(jsp), sc, cv);
+        v.x = FP<T>::add(v.x, cv[0]);
+        v.y = FP<T>::add(v.y, cv[1]);
         if (has0) {
           fix(jr, jsp, &v.x);
           if (pb) fix(jr, jsp + 1, &v.y);
@@ -703,9 +714,9 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   // columns as in phase 1, the four row neighbours kept in registers.
   {
     const bool has1 = S1.out_end > S1.out_begin;
-    auto value = [&](T a, T bb, T cc, T d, int c1, int c2, uint32_t n) {
+    auto value = [&](T a, T bb, T cc, T d, int c1, int c2, T cv) {
       const T pred = pred4<T>(a, bb, cc, d, c1, M1, cubic);
-      T v = FP<T>::add(pred, FP<T>::mul(code_value(n, T()), twoeb));
+      T v = FP<T>::add(pred, cv);
       if (has1) {
         const uint64_t ci = ((uint64_t)c.P * S1.m1 + (uint64_t)((c1 - 1) >> 1)) * S1.m2 +
                             (uint64_t)(c2 >> 1);
@@ -725,11 +736,11 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
           const int c1 = c.R0 + 1 + 2 * jr;
           if (c1 >= c.R1) break;
           const V2 d = *reinterpret_cast<const V2*>(col + (2 * jr + 6) * G::VP);
-          uint32_t n[2];
-          code_pair(Q1 + jr * G::QP + qoff<W16>(jsp), wb, n);
+          T cv[2];
+          scaled_pair(Q1 + jr * G::QP + qoff<W16>(jsp), sc, cv);
           V2 v;
-          v.x = value(a.x, bb.x, cc.x, d.x, c1, c2p, n[0]);
-          v.y = value(a.y, bb.y, cc.y, d.y, c1, c2p + 2, n[1]);
+          v.x = value(a.x, bb.x, cc.x, d.x, c1, c2p, cv[0]);
+          v.y = value(a.y, bb.y, cc.y, d.y, c1, c2p + 2, cv[1]);
           *reinterpret_cast<V2*>(col + (2 * jr + 3) * G::VP) = v;
           a = bb;
           bb = cc;
@@ -744,7 +755,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
           const T* col = VE + G::V0 + js;
           VE[(2 * jr + 3) * G::VP + G::V0 + js] =
               value(col[(2 * jr) * G::VP], col[(2 * jr + 2) * G::VP], col[(2 * jr + 4) * G::VP],
-                    col[(2 * jr + 6) * G::VP], c1, c2, QH[jr * 4 + h]);
+                    col[(2 * jr + 6) * G::VP], c1, c2,
+                    FP<T>::mul(code_value(QH[jr * 4 + h], T()), twoeb));
         }
       }
     }
@@ -773,10 +785,8 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         if (c1 >= c.R1) break;
         T w[9];
         lds9<T>(VE + (lr + 2) * G::VP + G::V0 + 4 * g, w);
-        uint32_t qa[4];
-        load4(Q2 + lr * G::QP + qoff<W16>(4 * g), wb, qa);
-        T val[4];
-        code_values4(qa, val);
+        T cv[4];
+        scaled_quad(Q2 + lr * G::QP + qoff<W16>(4 * g), sc, cv);
         T v[8];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -786,9 +796,10 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
           const T cub = FP<T>::mul(FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])),
                                    (T)0.0625);
           const T lin = FP<T>::mul(u, (T)0.5);
-          const T pred = (rule >> (2 * k) & 3u) == 2u ? cub : ((rule >> (2 * k) & 3u) == 1u ? lin : w[k + 1]);
+          const uint32_t r = rule >> (2 * k) & 3u;
+          const T pred = r == 2u ? cub : (r == 1u ? lin : w[k + 1]);
           v[2 * k] = w[k + 1];
-          v[2 * k + 1] = FP<T>::add(pred, FP<T>::mul(val[k], twoeb));
+          v[2 * k + 1] = FP<T>::add(pred, cv[k]);
         }
         if (has2) {
 #pragma unroll
@@ -1218,10 +1229,10 @@ template <class T, int BR, int BC, bool W16, int NS>
 __global__ void __launch_bounds__(256, retrieve_ctas_per_sm<W16, NS>()) k_level_retrieve(
     LevelArgs L, T* out, T twoeb, int b, const uint32_t* __restrict__ cap,
     const uint32_t* __restrict__ bm, const uint64_t* __restrict__ oidx,
-    const double* __restrict__ oval, LevelDescs D, uint64_t ntiles) {
+    const double* __restrict__ oval, uint64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    level_retrieve_body<T, BR, BC, W16, NS>(L, out, twoeb, b, cap, bm, oidx, oval, D, t, smem);
+    level_retrieve_body<T, BR, BC, W16, NS>(L, out, twoeb, b, cap, bm, oidx, oval, t, smem);
     __syncthreads();  // the next tile reuses shared memory
   }
 }
@@ -1261,7 +1272,7 @@ __global__ void __launch_bounds__(256, retrieve_ctas_per_sm<W16, NS>()) k_level_
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const RetrieveEntry& e = find_entry(ents, n, t);
     level_retrieve_body<T, BR, BC, W16, NS>(e.L, (T*)e.out, (T)e.twoeb, e.b, e.cap, e.bm, e.oidx,
-                                            e.oval, e.D, t - e.cta_begin, smem);
+                                            e.oval, t - e.cta_begin, smem);
     __syncthreads();  // the next tile reuses shared memory (and the entry index)
   }
 }
@@ -1330,13 +1341,13 @@ inline unsigned persistent_grid(uint64_t tiles, int per_sm) {
 template <class T, int BR, int BC, bool W16, int NS>
 void retrieve_kernel(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
                      const uint32_t* bm, const uint64_t* oidx, const double* oval,
-                     const LevelDescs& d, cudaStream_t st) {
+                     cudaStream_t st) {
   const uint64_t tiles = retrieve_tiles(L, NS);
   if (tiles == 0) return;
   k_level_retrieve<T, BR, BC, W16, NS>
       <<<persistent_grid(tiles, retrieve_ctas_per_sm<W16, NS>()), 256,
          smem_retrieve<T, BR, BC, W16, NS>(), st>>>(L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval,
-                                                    d, tiles);
+                                                    tiles);
 }
 template <class T, int BR, int BC, bool W16, int NS>
 void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t tiles, cudaStream_t st) {
@@ -1347,16 +1358,16 @@ void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t tiles, cud
 
 template <class T, int BR, int BC>
 void retrieve_dispatch(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
-                       const uint32_t* bm, const uint64_t* oidx, const double* oval,
-                       const LevelDescs& d, int w16, cudaStream_t st) {
+                       const uint32_t* bm, const uint64_t* oidx, const double* oval, int w16,
+                       cudaStream_t st) {
   const int ns = retrieve_subtiles(L.M[2], w16);
   if (!w16) {
-    if (ns == 4) retrieve_kernel<T, BR, BC, false, 4>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
-    else if (ns == 2) retrieve_kernel<T, BR, BC, false, 2>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
-    else retrieve_kernel<T, BR, BC, false, 1>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
-  } else if (ns == 4) retrieve_kernel<T, BR, BC, true, 4>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
-  else if (ns == 2) retrieve_kernel<T, BR, BC, true, 2>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
-  else retrieve_kernel<T, BR, BC, true, 1>(L, out, twoeb, b, cap, bm, oidx, oval, d, st);
+    if (ns == 4) retrieve_kernel<T, BR, BC, false, 4>(L, out, twoeb, b, cap, bm, oidx, oval, st);
+    else if (ns == 2) retrieve_kernel<T, BR, BC, false, 2>(L, out, twoeb, b, cap, bm, oidx, oval, st);
+    else retrieve_kernel<T, BR, BC, false, 1>(L, out, twoeb, b, cap, bm, oidx, oval, st);
+  } else if (ns == 4) retrieve_kernel<T, BR, BC, true, 4>(L, out, twoeb, b, cap, bm, oidx, oval, st);
+  else if (ns == 2) retrieve_kernel<T, BR, BC, true, 2>(L, out, twoeb, b, cap, bm, oidx, oval, st);
+  else retrieve_kernel<T, BR, BC, true, 1>(L, out, twoeb, b, cap, bm, oidx, oval, st);
 }
 template <class T, int BR, int BC>
 void retrieve_batch_dispatch(const RetrieveEntry* ents, int n, uint64_t tiles, int w16, int ns,
@@ -1379,6 +1390,7 @@ cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, 
                                   const LevelDescs& d, cudaStream_t st) {
   const uint64_t grid = (uint64_t)L.M[0] * L.nrb * L.nct;
   if (grid == 0) return cudaSuccess;
+  if (grid >= (1ULL << 31)) return cudaErrorInvalidValue;  // grid x limit (tile ids are 32-bit)
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
@@ -1396,16 +1408,17 @@ cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, 
 
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
-                                  const double* oval, const LevelDescs& d, int w16,
-                                  cudaStream_t st) {
-  if (retrieve_tiles(L, retrieve_subtiles(L.M[2], w16)) == 0) return cudaSuccess;
+                                  const double* oval, int w16, cudaStream_t st) {
+  const uint64_t tiles = retrieve_tiles(L, retrieve_subtiles(L.M[2], w16));
+  if (tiles == 0) return cudaSuccess;
+  if (tiles >= (1ULL << 32)) return cudaErrorInvalidValue;  // tile ids are 32-bit
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_dispatch<float, kLevelRowsF32, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, d, w16, st);
+    retrieve_dispatch<float, kLevelRowsF32, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_dispatch<double, kLevelRowsF64, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, d, w16, st);
+    retrieve_dispatch<double, kLevelRowsF64, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, st);
   }
   return cudaGetLastError();
 }
@@ -1413,6 +1426,7 @@ cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, doub
 cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,
                                         uint64_t ctas, cudaStream_t st) {
   if (ctas == 0 || n == 0) return cudaSuccess;
+  if (ctas >= (1ULL << 31)) return cudaErrorInvalidValue;
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
@@ -1429,6 +1443,7 @@ cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, in
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
                                         uint64_t tiles, int w16, int ns, cudaStream_t st) {
   if (tiles == 0 || n == 0) return cudaSuccess;
+  if (tiles >= (1ULL << 32)) return cudaErrorInvalidValue;
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;

@@ -265,3 +265,18 @@ def test_batch_mixed_widths_and_repeats():
     for j, (i, (k, v)) in enumerate(zip(srcs, targets)):
         oy, _ = os_[i].retrieve(oracle.EB if k == ipc.IPC_TARGET_EB else oracle.BITRATE, v)
         assert np.array_equal(outs[j].cpu().numpy().view(np.uint8), oy.view(np.uint8)), j
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_window_bases(dtype):
+    """Codes up to ~2^21 (noise at eb 1e-6 of its scale): retrievals that drop
+    0..21 low planes keep 16-plane windows at many bases, odd and even,
+    across the levels (the code value is scaled by the window base)."""
+    x = synth.random_field((20, 37, 140), seed=77, dtype=dtype, kind="noise")
+    x = (x * np.linspace(0.2, 3.0, 140)).astype(dtype)  # code sizes vary along the rows
+    g, o = both(x, 1e-6, ipc.IPC_EB_ABS)
+    assert g.export() == o.export()
+    for j in range(0, 22):
+        check_retrieve(g, o, oracle.EB, 1e-6 * 2.0 ** j * 1.3)
+    for br in (3.0, 6.0, 9.0, 12.0):
+        check_retrieve(g, o, oracle.BITRATE, br)
