@@ -108,9 +108,41 @@ __device__ __forceinline__ void tround(uint32_t (&a)[NW]) {
     }
   }
 }
+// The 16- and 8-bit rounds move whole half-words and bytes: one byte
+// permute per output word. (Round 16: a[i] takes the low halves of a[i] and
+// a[i+16], a[i+16] the high halves; round 8: a[i] takes bytes 0 and 2 of
+// a[i] and a[i+8] interleaved, a[i+8] bytes 1 and 3.)
+template <int NW>
+__device__ __forceinline__ void tround16(uint32_t (&a)[NW]) {
+#pragma unroll
+  for (int i = 0; i < NW; ++i)
+    if ((i & 16) == 0) {
+      const uint32_t x = a[i], y = a[i + 16];
+      a[i] = __byte_perm(x, y, 0x5410);
+      a[i + 16] = __byte_perm(x, y, 0x7632);
+    }
+}
+template <int NW>
+__device__ __forceinline__ void tround8(uint32_t (&a)[NW]) {
+#pragma unroll
+  for (int i = 0; i < NW; ++i)
+    if ((i & 8) == 0) {
+      const uint32_t x = a[i], y = a[i + 8];
+      a[i] = __byte_perm(x, y, 0x6240);
+      a[i + 8] = __byte_perm(x, y, 0x7351);
+    }
+}
+// BP: the byte-permute forms of the 16- and 8-bit rounds (fewer operations;
+// the shift forms keep fewer values live at once).
+template <bool BP = true>
 __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
-  tround<16, 0x0000FFFFu>(a);
-  tround<8, 0x00FF00FFu>(a);
+  if constexpr (BP) {
+    tround16(a);
+    tround8(a);
+  } else {
+    tround<16, 0x0000FFFFu>(a);
+    tround<8, 0x00FF00FFu>(a);
+  }
   tround<4, 0x0F0F0F0Fu>(a);
   tround<2, 0x33333333u>(a);
   tround<1, 0x55555555u>(a);
@@ -121,8 +153,10 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
 // half of a[i] is column i of the left matrix and the high half column i of
 // the right one. With a[k] = plane k of 32 codes (planes >= 16 all zero),
 // code i is the low half of a[i] and code 16 + i the high half.
+template <bool BP = true>
 __device__ __forceinline__ void transpose16x2(uint32_t (&a)[16]) {
-  tround<8, 0x00FF00FFu>(a);
+  if constexpr (BP) tround8(a);
+  else tround<8, 0x00FF00FFu>(a);
   tround<4, 0x0F0F0F0Fu>(a);
   tround<2, 0x33333333u>(a);
   tround<1, 0x55555555u>(a);

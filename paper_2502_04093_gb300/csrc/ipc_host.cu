@@ -447,7 +447,7 @@ LevelArgs level_args(const ipc_field* f, int l) {
 void retrieve_planes(const ipc_field* f, int l, int b, LevelArgs* L) {
   for (int d = 0; d < 3; ++d) {
     const int t = f->g.level_stage[d][l - 1];
-    LevelStage& S = L->st[d];
+    StagePlanes& S = L->sp[d];
     S.kmask = 0;
     if (t < 0) continue;
     const StageGeo& sg = f->g.stages[t];

@@ -49,9 +49,12 @@ struct LevelStage {
   uint64_t nrb, nct, bw;
   uint64_t m1, m2, wr;  // stage lattice: rows per plane, codes per row, words per row
   uint64_t out_begin, out_end;  // outlier range of the stage (reconstruction)
-  // reconstruction: word offsets of plane 0's capacity array and bitmap and
-  // the per-plane strides (plane k lies k strides further), and the planes
-  // to load (bit k: k >= b and the plane has nonzero words)
+};
+// Reconstruction view of a sweep's plane streams: word offsets of plane 0's
+// capacity array and bitmap, the per-plane strides (plane k lies k strides
+// further), and the planes to load (bit k: k >= b and the plane has nonzero
+// words).
+struct StagePlanes {
   uint64_t cap0, pcap, bm0, pbm;
   uint32_t kmask;
 };
@@ -70,6 +73,7 @@ struct LevelArgs {
   // compression: plane and row strides of the level's own dense lattice
   // (its reconstructed values, the next finer level's known points)
   int64_t ost0, ost1;
+  StagePlanes sp[3];  // reconstruction only
 };
 
 // Division of a 32-bit n by a divisor 1 <= d < 2^32 as the high half of n * m,

@@ -443,7 +443,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   // the plane window: slot i of the staged tables is plane wb + i. With
   // 16-bit codes the loaded planes [b, ktop] lie in [wb, wb + 15] (checked
   // on the host for the level).
-  const uint32_t km0 = podd ? S0.kmask : 0u, km1 = S1.kmask, km2 = S2.kmask;
+  const uint32_t km0 = podd ? L.sp[0].kmask : 0u, km1 = L.sp[1].kmask, km2 = L.sp[2].kmask;
   const int ktop = 31 - __clz((int)(km0 | km1 | km2));
   const int wb = W16 ? max(0, ktop - 15) : 0;
   const CodeScale<T> sc = code_scale<T>(twoeb, wb);
@@ -466,8 +466,9 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     if (rbs < 0 || (uint64_t)rbs >= S.nrb || cts < 0 || (uint64_t)cts >= S.nct) continue;
     const uint64_t pi = sx == 0 ? (uint64_t)((Ps - 1) >> 1) : (uint64_t)Ps;
     const uint64_t g = seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts);
-    SP[s][sl][i] = cap + S.cap0 + (uint64_t)k * S.pcap + g * (uint64_t)S.RB * S.CW;
-    const uint32_t* bp = bm + S.bm0 + (uint64_t)k * S.pbm + g * S.bw;
+    const StagePlanes& SQ = L.sp[sx];
+    SP[s][sl][i] = cap + SQ.cap0 + (uint64_t)k * SQ.pcap + g * (uint64_t)S.RB * S.CW;
+    const uint32_t* bp = bm + SQ.bm0 + (uint64_t)k * SQ.pbm + g * S.bw;
     for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[s][sl][i][v], bp + v);
   }
 
@@ -1160,13 +1161,13 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
     uint32_t w[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) w[i] = cd[i] | (cd[16 + i] << 16);
-    transpose16x2(w);
+    transpose16x2<false>(w);
 #pragma unroll
     for (int k = 0; k < 16; ++k) cd[k] = w[k];
 #pragma unroll
     for (int k = 16; k < 32; ++k) cd[k] = 0u;
   } else {
-    transpose32(cd);
+    transpose32<false>(cd);
   }
   xor_encode_planes(cd);
   const uint64_t pi = sidx == 0 ? (uint64_t)((c.P - 1) >> 1) : (uint64_t)c.P;
