@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the batched and serving measurements")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the reconstruction's launch shapes before the warm-up "
+                         "(measured no faster than the defaults on this workload)")
     ap.add_argument("--serving-small", action="store_true",
                     help="serving with 40 fields up to 448^3 and 400 requests (quick)")
     return ap.parse_args()
@@ -172,6 +175,18 @@ def job_gbs(world: int, bytes_per_rank_step: float, steps: int, seconds: float) 
 # ---------------------------------------------------------------------------
 # The GPU step (through the C ABI)
 # ---------------------------------------------------------------------------
+def launch_shapes(tuned):
+    """Summary of the launch shapes the timed steps used."""
+    if tuned is None:
+        return "defaults"
+    other = ["%s%s M=%s: %d planes/tile, %d CTAs/SM" % ("f32" if dt == 0 else "f64",
+                                                          " 16-bit" if w else " 32-bit",
+                                                          "x".join(map(str, M)), ns, psm)
+             for dt, w, M, ns, psm in tuned if ns or psm]
+    return "tuned before the warm-up: %d level shapes, %d not the default%s" % (
+        len(tuned), len(other), (" (" + "; ".join(other) + ")") if other else "")
+
+
 def gpu_step(ipc, x, out, ev=None, outs_br=None):
     """compress + refine chain + bitrate retrievals; returns the field handle
     and the number of reconstructions computed (a refine whose target the
@@ -220,6 +235,19 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
+
+    # launch-shape tuning of the reconstruction levels (untimed): the
+    # retrievals of a step, on a field compressed like the step's
+    tuned = None
+    if args.autotune:
+        f = ipc.ipc_compress(x, EB, ipc.IPC_EB_ABS, ipc.IPC_CUBIC, ipc.IPC_BOUND_STRICT)
+        targets = [(ipc.IPC_TARGET_EB, E) for E in EB_SWEEP] + \
+                  [(ipc.IPC_TARGET_BITRATE, br) for br in BITRATES]
+        for kind, v in targets:
+            ipc.ipc_autotune_retrieve(f, kind, v, out, reps=5)
+        tuned = [e for e in ipc.ipc_autotune_entries()]
+        ipc.ipc_free(f)
+        torch.cuda.synchronize()
 
     # warm-up (also counts the reconstructions a step computes: the
     # selections, and so the no-op refines, are the same every step)
@@ -320,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
     return dict(value=value, ms_per_step=ms_per_step, compress_ms=compress_ms,
                 retrieve_ms=retrieve_ms, roofline=roof, kernels=kernels, launches=launches,
                 clocks=clk.summary(), csize=csize, nbytes=nbytes, n_recon=n_recon, e2e=e2e,
-                step_bytes=step_bytes, extra=extra)
+                step_bytes=step_bytes, extra=extra, tuned=tuned)
 
 
 def e2e_measure(ipc, x, args, world):
@@ -728,7 +756,8 @@ def main():
                             "at 0.5,1,2,4,8,16 bits/value (one batched call, one output each)"
                             % args.edge,
                 "l2": "inputs larger than L2 (512 MiB field vs 129 MB L2)",
-                "parallelism": "one field per GPU" if world > 1 else "single GPU"},
+                "parallelism": "one field per GPU" if world > 1 else "single GPU",
+                "launch_shapes": launch_shapes(r["tuned"])},
             "compress_gbs": round(r["nbytes"] / (r["compress_ms"] * 1e-3) / 1e9, 1),
             "retrieve_gbs": round(r["nbytes"] / (r["retrieve_ms"] * 1e-3) / 1e9, 1),
             "compress_ms": round(r["compress_ms"], 3),

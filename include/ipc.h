@@ -95,6 +95,30 @@ int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims,
 int ipc_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream,
                  ipc_view** out);
 
+/* ipc_autotune_retrieve -- launch-shape tuning of the reconstruction kernel
+ * (no counterpart in the paper; the values it computes do not depend on the
+ * shape). Selects as ipc_retrieve does, then reconstructs level by level,
+ * timing every shape of each level's launch -- planes per tile 1, 2 or 4
+ * where the level's rows allow, persistent grids of 1 .. the most CTAs per
+ * SM that fit -- `reps` times each (1..100) with CUDA events on `stream`,
+ * each time right after the next coarser level ran again, and records per
+ * (element type, code width, level lattice extents) the shape with the
+ * smallest median time (the default one unless another is faster by more
+ * than 3 %) in a process-wide table. Later ipc_retrieve / ipc_refine calls, and batched
+ * retrievals whose fields share a level's extents, launch with the recorded
+ * shapes. d_out (device, prod(dims) elements) receives the reconstruction.
+ * nshapes (optional) receives the table's size. Synchronizes `stream`.
+ * Errors: those of ipc_retrieve, IPC_EINVAL for reps out of range. */
+int ipc_autotune_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream, int reps,
+                          int* nshapes);
+/* ipc_autotune_clear -- empties the table (default shapes again). */
+int ipc_autotune_clear(void);
+/* ipc_autotune_entry -- entry i (0 .. size-1) of the table: element type,
+ * code width (1: 16-bit), level lattice extents M[3], planes per tile and
+ * CTAs per SM (0, 0: the default shape measured fastest). IPC_EINVAL when i
+ * is out of range. Any output pointer may be NULL. */
+int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* per_sm);
+
 /* ipc_refine -- Algorithm 2 (incremental reconstruction). The new selection
  * only adds planes (b'_l <= b_l at every level) and minimises the added
  * bytes; d_out (normally the array of the earlier retrieve) is rewritten with

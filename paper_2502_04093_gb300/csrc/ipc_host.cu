@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -880,6 +881,32 @@ bool level_w16(const ipc_field* f, int l, int b) {
   return ktop - b <= 15 && bin_width(f) * 65536.0 <= lim;
 }
 
+// Launch shapes chosen by measurement (ipc_autotune_retrieve), per element
+// type, code width and level lattice extents; process-wide.
+struct ShapeKey {
+  int dtype, w16;
+  int64_t M0, M1, M2;
+  bool operator<(const ShapeKey& o) const {
+    if (dtype != o.dtype) return dtype < o.dtype;
+    if (w16 != o.w16) return w16 < o.w16;
+    if (M0 != o.M0) return M0 < o.M0;
+    if (M1 != o.M1) return M1 < o.M1;
+    return M2 < o.M2;
+  }
+};
+std::mutex g_shape_mu;
+std::map<ShapeKey, RetrieveShape> g_shapes;
+
+ShapeKey shape_key(int dtype, int w16, const LevelArgs& L) {
+  return ShapeKey{dtype, w16 ? 1 : 0, L.M[0], L.M[1], L.M[2]};
+}
+// The tuned shape of a level launch, or the default (ns = per_sm = 0).
+RetrieveShape tuned_shape(const ShapeKey& k) {
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  auto it = g_shapes.find(k);
+  return it == g_shapes.end() ? RetrieveShape{} : it->second;
+}
+
 // Algorithm 1 on the device: the anchor, then one fused launch per level
 // (coarse to fine); outliers are applied inside the level kernels.
 int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream_t st) {
@@ -915,9 +942,10 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
       nc += g.stages[t].ncodes;
       for (int k = b[l - 1]; k < 32; ++k) by += (double)f->st[t].size[k];
     }
+    const int w16 = level_w16(f, l, b[l - 1]) ? 1 : 0;
     const long ph = prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st);
     CU(launch_level_retrieve(f->dtype, L, o, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
-                             f->d_oval, level_w16(f, l, b[l - 1]) ? 1 : 0, st));
+                             f->d_oval, w16, tuned_shape(shape_key(f->dtype, w16, L)), st));
     prof_end(ph, st, by + (double)(nc * esz));
   }
   return IPC_OK;
@@ -936,6 +964,7 @@ struct BatchTable {
   std::vector<uint64_t> lev_off, lev_ctas;
   std::vector<int> lev_w16;  // every entry of the level keeps 16-bit codes
   std::vector<int> lev_ns;   // sub-tiles per tile of the level's launch
+  std::vector<int> lev_psm;  // CTAs per SM of the level's launch (0: as many as fit)
   uint64_t scratch = 0;      // bytes of the fields' scratch ladders
   int Kmax = 0;
   double alg_bytes = 0;
@@ -950,6 +979,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   T->lev_ctas.assign(T->Kmax + 2, 0);
   T->lev_w16.assign(T->Kmax + 2, 1);
   T->lev_ns.assign(T->Kmax + 2, 1);
+  T->lev_psm.assign(T->Kmax + 2, 0);
   T->ents.clear();
   T->anchors.clear();
   T->kin_off.clear();
@@ -979,10 +1009,23 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       if (l > f->g.K) continue;
       if (!level_w16(f, l, bs[i][l - 1])) T->lev_w16[l] = 0;
     }
+    // a tuned shape applies when every entry's level has the same key
+    bool same = true;
+    ShapeKey key{};
+    int seen = 0;
     for (size_t i = 0; i < nf; ++i) {
       ipc_field* f = fs[i];
       if (l > f->g.K) continue;
-      ns = std::min(ns, retrieve_subtiles(level_args(f, l).M[2], T->lev_w16[l]));
+      const LevelArgs La = level_args(f, l);
+      ns = std::min(ns, retrieve_subtiles(La.M[2], T->lev_w16[l]));
+      const ShapeKey k = shape_key(f->dtype, T->lev_w16[l], La);
+      if (seen++ && (k < key || key < k)) same = false;
+      key = k;
+    }
+    if (seen && same) {
+      const RetrieveShape sh = tuned_shape(key);
+      if (sh.ns && sh.ns <= ns) ns = sh.ns;
+      T->lev_psm[l] = sh.per_sm;
     }
     T->lev_ns[l] = ns;
     uint64_t cta = 0;
@@ -1039,7 +1082,7 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
     const int nn = (int)(T.lev_off[l - 1] - T.lev_off[l]);
     const long ph = profile ? prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st) : -1;
     CU(launch_level_retrieve_batch(dtype, d_ents + T.lev_off[l], nn, T.lev_ctas[l], T.lev_w16[l],
-                                   T.lev_ns[l], st));
+                                   T.lev_ns[l], T.lev_psm[l], st));
     if (profile) prof_end(ph, st, l == 1 ? T.alg_bytes : 0.0);
     ++nl;
   }
@@ -1257,6 +1300,126 @@ int ipc_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream, ipc
     v->bound = bound;
     *out = v;
   }
+  return IPC_OK;
+}
+
+int ipc_autotune_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream, int reps,
+                          int* nshapes) {
+  g_err.clear();
+  if (!f || f->tag != kFieldTag || !d_out) return fail(IPC_EINVAL, "null or invalid argument");
+  if (reps < 1 || reps > 100) return fail(IPC_EINVAL, "reps must be 1..100");
+  DeviceGuard dg(f->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> b;
+  uint64_t bytes = 0;
+  double bound = 0;
+  int rc = select(f, target, nullptr, &b, &bytes, &bound);
+  if (rc) return rc;
+  const Geo& g = f->g;
+  const size_t esz = f->dtype == 0 ? 4 : 8;
+  std::vector<uint64_t> off;
+  uint8_t* scr = nullptr;
+  if (g.K > 0 && (rc = dalloc((void**)&scr, ladder(g, esz, &off), st))) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  struct Guard {
+    uint8_t* p;
+    cudaStream_t s;
+    cudaEvent_t& a;
+    cudaEvent_t& b;
+    ~Guard() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      if (p) cudaFreeAsync(p, s);
+    }
+  } guard{scr, st, e0, e1};
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(launch_set_anchor(f->dtype, g.K > 0 ? (void*)(scr + off[g.K + 1]) : d_out, f->anchor, st));
+  const double twoeb = bin_width(f);
+  // level l's launch with shape sh (its inputs: level l + 1's output)
+  std::vector<LevelArgs> La(g.K + 2);
+  std::vector<int> W(g.K + 2, 0);
+  std::vector<RetrieveShape> chosen(g.K + 2);
+  for (int l = g.K; l >= 1; --l) {
+    La[l] = level_args(f, l);
+    retrieve_layout(&La[l], scr + off[l + 1]);
+    retrieve_planes(f, l, b[l - 1], &La[l]);
+    W[l] = level_w16(f, l, b[l - 1]) ? 1 : 0;
+  }
+  auto run = [&](int l, RetrieveShape sh) {
+    void* o = l == 1 ? d_out : (void*)(scr + off[l]);
+    return launch_level_retrieve(f->dtype, La[l], o, twoeb, b[l - 1], f->d_cap, f->d_bm,
+                                 f->d_oidx, f->d_oval, W[l], sh, st);
+  };
+  for (int l = g.K; l >= 1; --l) {
+    // Each shape is timed `reps` times, each time right after level l + 1
+    // ran again (as in a reconstruction, level l reads what level l + 1 just
+    // wrote); the median decides. A shape replaces the default only when it
+    // is faster by more than 3 %. Every shape gives the same values, so the
+    // level's output is right after any of the launches.
+    std::vector<float> t(reps);
+    auto timed = [&](RetrieveShape sh, float* med) -> int {
+      CU(run(l, sh));  // warm-up
+      for (int r = 0; r < reps; ++r) {
+        if (l < g.K) CU(run(l + 1, chosen[l + 1]));
+        CU(cudaEventRecord(e0, st));
+        CU(run(l, sh));
+        CU(cudaEventRecord(e1, st));
+        CU(cudaEventSynchronize(e1));
+        CU(cudaEventElapsedTime(&t[r], e0, e1));
+      }
+      std::sort(t.begin(), t.end());
+      *med = t[reps / 2];
+      return IPC_OK;
+    };
+    float def_ms = 0, best_ms = 0;
+    if ((rc = timed(RetrieveShape{}, &def_ms))) return rc;
+    RetrieveShape best{};
+    best_ms = def_ms;
+    for (int ns : {1, 2, 4}) {
+      if (!retrieve_ns_ok(La[l].M[2], ns)) continue;
+      for (int psm = 1; psm <= retrieve_max_per_sm(W[l]); ++psm) {
+        float ms = 0;
+        if ((rc = timed(RetrieveShape{ns, psm}, &ms))) return rc;
+        if (ms < best_ms && ms < 0.97f * def_ms) {
+          best = RetrieveShape{ns, psm};
+          best_ms = ms;
+        }
+      }
+    }
+    chosen[l] = best;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_shapes[shape_key(f->dtype, W[l], La[l])] = best;
+  }
+  CU(cudaStreamSynchronize(st));
+  if (nshapes) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    *nshapes = (int)g_shapes.size();
+  }
+  return IPC_OK;
+}
+
+int ipc_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  g_shapes.clear();
+  return IPC_OK;
+}
+
+int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* per_sm) {
+  g_err.clear();
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  if (i < 0 || i >= (int)g_shapes.size()) return fail(IPC_EINVAL, "no such entry");
+  auto it = g_shapes.begin();
+  std::advance(it, i);
+  if (dtype) *dtype = it->first.dtype;
+  if (w16) *w16 = it->first.w16;
+  if (M) {
+    M[0] = it->first.M0;
+    M[1] = it->first.M1;
+    M[2] = it->first.M2;
+  }
+  if (ns) *ns = it->second.ns;
+  if (per_sm) *per_sm = it->second.per_sm;
   return IPC_OK;
 }
 

@@ -190,17 +190,31 @@ inline uint64_t retrieve_tiles(const LevelArgs& L, int ns) {
   const uint64_t groups = (uint64_t)((ne + ns - 1) / ns + (no + ns - 1) / ns);
   return groups * L.nrb * L.nct;
 }
+// Launch shape of a level reconstruction (results do not depend on it):
+// planes per tile (1, 2 or 4; 0 = the most the level's rows allow) and CTAs
+// per SM of the persistent grid (0 = as many as fit).
+struct RetrieveShape {
+  int ns = 0;
+  int per_sm = 0;
+};
+inline bool retrieve_ns_ok(int64_t M2, int ns) {
+  return ns == 1 || (ns == 2 && M2 <= kLevelCols / 2) || (ns == 4 && M2 <= kLevelCols / 4);
+}
+// Most CTAs of a level reconstruction resident per SM (16-bit / 32-bit codes).
+inline int retrieve_max_per_sm(int w16) { return w16 ? 4 : 3; }
 // w16: the planes loaded at the level span at most 16 (16-bit code rows).
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
-                                  const double* oval, int w16, cudaStream_t st);
+                                  const double* oval, int w16, RetrieveShape shape,
+                                  cudaStream_t st);
 int level_rows(int dtype);
 // Batched level launches: `ents` (device memory) sorted by cta_begin.
 cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,
                                         uint64_t ctas, cudaStream_t st);
 // Batched: `tiles` over all entries, each entry's tiles counted with `ns`.
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
-                                        uint64_t tiles, int w16, int ns, cudaStream_t st);
+                                        uint64_t tiles, int w16, int ns, int per_sm,
+                                        cudaStream_t st);
 // Segmented <-> packed container streams of one stage (export / import).
 // tmp: 2 * 32 * nbm words of scratch; flags[0] = corruption flag,
 // flags[1 + k] = nonzero words found in plane k (import).

@@ -1338,48 +1338,50 @@ inline unsigned persistent_grid(uint64_t tiles, int per_sm) {
   const uint64_t cap = (uint64_t)sms * per_sm;
   return (unsigned)(tiles < cap ? tiles : cap);
 }
+// CTAs per SM of a persistent grid: the shape's, within what fits.
+inline int grid_per_sm(int want, int most) { return want > 0 && want < most ? want : most; }
 
 template <class T, int BR, int BC, bool W16, int NS>
 void retrieve_kernel(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
-                     const uint32_t* bm, const uint64_t* oidx, const double* oval,
+                     const uint32_t* bm, const uint64_t* oidx, const double* oval, int per_sm,
                      cudaStream_t st) {
   const uint64_t tiles = retrieve_tiles(L, NS);
   if (tiles == 0) return;
   k_level_retrieve<T, BR, BC, W16, NS>
-      <<<persistent_grid(tiles, retrieve_ctas_per_sm<W16, NS>()), 256,
+      <<<persistent_grid(tiles, grid_per_sm(per_sm, retrieve_ctas_per_sm<W16, NS>())), 256,
          smem_retrieve<T, BR, BC, W16, NS>(), st>>>(L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval,
                                                     tiles);
 }
 template <class T, int BR, int BC, bool W16, int NS>
-void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t tiles, cudaStream_t st) {
+void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t tiles, int per_sm,
+                           cudaStream_t st) {
   k_level_retrieve_batch<T, BR, BC, W16, NS>
-      <<<persistent_grid(tiles, retrieve_ctas_per_sm<W16, NS>()), 256,
+      <<<persistent_grid(tiles, grid_per_sm(per_sm, retrieve_ctas_per_sm<W16, NS>())), 256,
          smem_retrieve<T, BR, BC, W16, NS>(), st>>>(ents, n, tiles);
 }
 
 template <class T, int BR, int BC>
 void retrieve_dispatch(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
                        const uint32_t* bm, const uint64_t* oidx, const double* oval, int w16,
-                       cudaStream_t st) {
-  const int ns = retrieve_subtiles(L.M[2], w16);
+                       int ns, int per_sm, cudaStream_t st) {
   if (!w16) {
-    if (ns == 4) retrieve_kernel<T, BR, BC, false, 4>(L, out, twoeb, b, cap, bm, oidx, oval, st);
-    else if (ns == 2) retrieve_kernel<T, BR, BC, false, 2>(L, out, twoeb, b, cap, bm, oidx, oval, st);
-    else retrieve_kernel<T, BR, BC, false, 1>(L, out, twoeb, b, cap, bm, oidx, oval, st);
-  } else if (ns == 4) retrieve_kernel<T, BR, BC, true, 4>(L, out, twoeb, b, cap, bm, oidx, oval, st);
-  else if (ns == 2) retrieve_kernel<T, BR, BC, true, 2>(L, out, twoeb, b, cap, bm, oidx, oval, st);
-  else retrieve_kernel<T, BR, BC, true, 1>(L, out, twoeb, b, cap, bm, oidx, oval, st);
+    if (ns == 4) retrieve_kernel<T, BR, BC, false, 4>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
+    else if (ns == 2) retrieve_kernel<T, BR, BC, false, 2>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
+    else retrieve_kernel<T, BR, BC, false, 1>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
+  } else if (ns == 4) retrieve_kernel<T, BR, BC, true, 4>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
+  else if (ns == 2) retrieve_kernel<T, BR, BC, true, 2>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
+  else retrieve_kernel<T, BR, BC, true, 1>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
 }
 template <class T, int BR, int BC>
 void retrieve_batch_dispatch(const RetrieveEntry* ents, int n, uint64_t tiles, int w16, int ns,
-                             cudaStream_t st) {
+                             int per_sm, cudaStream_t st) {
   if (!w16) {
-    if (ns == 4) retrieve_batch_kernel<T, BR, BC, false, 4>(ents, n, tiles, st);
-    else if (ns == 2) retrieve_batch_kernel<T, BR, BC, false, 2>(ents, n, tiles, st);
-    else retrieve_batch_kernel<T, BR, BC, false, 1>(ents, n, tiles, st);
-  } else if (ns == 4) retrieve_batch_kernel<T, BR, BC, true, 4>(ents, n, tiles, st);
-  else if (ns == 2) retrieve_batch_kernel<T, BR, BC, true, 2>(ents, n, tiles, st);
-  else retrieve_batch_kernel<T, BR, BC, true, 1>(ents, n, tiles, st);
+    if (ns == 4) retrieve_batch_kernel<T, BR, BC, false, 4>(ents, n, tiles, per_sm, st);
+    else if (ns == 2) retrieve_batch_kernel<T, BR, BC, false, 2>(ents, n, tiles, per_sm, st);
+    else retrieve_batch_kernel<T, BR, BC, false, 1>(ents, n, tiles, per_sm, st);
+  } else if (ns == 4) retrieve_batch_kernel<T, BR, BC, true, 4>(ents, n, tiles, per_sm, st);
+  else if (ns == 2) retrieve_batch_kernel<T, BR, BC, true, 2>(ents, n, tiles, per_sm, st);
+  else retrieve_batch_kernel<T, BR, BC, true, 1>(ents, n, tiles, per_sm, st);
 }
 
 }  // namespace
@@ -1409,17 +1411,20 @@ cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, 
 
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
-                                  const double* oval, int w16, cudaStream_t st) {
-  const uint64_t tiles = retrieve_tiles(L, retrieve_subtiles(L.M[2], w16));
+                                  const double* oval, int w16, RetrieveShape shape,
+                                  cudaStream_t st) {
+  const int ns = shape.ns ? shape.ns : retrieve_subtiles(L.M[2], w16);
+  if (!retrieve_ns_ok(L.M[2], ns)) return cudaErrorInvalidValue;
+  const uint64_t tiles = retrieve_tiles(L, ns);
   if (tiles == 0) return cudaSuccess;
   if (tiles >= (1ULL << 32)) return cudaErrorInvalidValue;  // tile ids are 32-bit
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_dispatch<float, kLevelRowsF32, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, st);
+    retrieve_dispatch<float, kLevelRowsF32, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_dispatch<double, kLevelRowsF64, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, st);
+    retrieve_dispatch<double, kLevelRowsF64, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
   }
   return cudaGetLastError();
 }
@@ -1442,16 +1447,17 @@ cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, in
 }
 
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
-                                        uint64_t tiles, int w16, int ns, cudaStream_t st) {
+                                        uint64_t tiles, int w16, int ns, int per_sm,
+                                        cudaStream_t st) {
   if (tiles == 0 || n == 0) return cudaSuccess;
   if (tiles >= (1ULL << 32)) return cudaErrorInvalidValue;
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_batch_dispatch<float, kLevelRowsF32, kLevelCols>(ents, n, tiles, w16, ns, st);
+    retrieve_batch_dispatch<float, kLevelRowsF32, kLevelCols>(ents, n, tiles, w16, ns, per_sm, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_batch_dispatch<double, kLevelRowsF64, kLevelCols>(ents, n, tiles, w16, ns, st);
+    retrieve_batch_dispatch<double, kLevelRowsF64, kLevelCols>(ents, n, tiles, w16, ns, per_sm, st);
   }
   return cudaGetLastError();
 }

@@ -85,6 +85,9 @@ def lib() -> C.CDLL:
                                C.c_int, vp, C.POINTER(vp)]
     L.ipc_retrieve.argtypes = [vp, ipc_target, vp, vp, C.POINTER(vp)]
     L.ipc_refine.argtypes = [vp, ipc_target, vp, vp]
+    L.ipc_autotune_retrieve.argtypes = [vp, ipc_target, vp, vp, C.c_int, C.POINTER(C.c_int)]
+    L.ipc_autotune_entry.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p,
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.ipc_free.argtypes = [vp]
     L.ipc_selection.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
                                 C.POINTER(C.c_double)]
@@ -166,6 +169,35 @@ def ipc_retrieve(field, kind: int, value: float, out, stream=None, want_view=Tru
                               C.c_void_p(out.data_ptr()), _stream(stream),
                               C.byref(v) if want_view else None), "ipc_retrieve")
     return v if want_view else None
+
+
+def ipc_autotune_retrieve(field, kind: int, value: float, out, stream=None, reps: int = 3) -> int:
+    """Time the launch shapes of each level of this retrieval and record the
+    fastest (process-wide); `out` receives the reconstruction. Returns the
+    number of recorded shapes."""
+    _require_cuda(out, "out")
+    n = C.c_int()
+    _check(lib().ipc_autotune_retrieve(field, ipc_target(int(kind), float(value)),
+                                       C.c_void_p(out.data_ptr()), _stream(stream), int(reps),
+                                       C.byref(n)), "ipc_autotune_retrieve")
+    return n.value
+
+
+def ipc_autotune_clear() -> None:
+    _check(lib().ipc_autotune_clear(), "ipc_autotune_clear")
+
+
+def ipc_autotune_entries():
+    """The recorded shapes: [(dtype, w16, (M0, M1, M2), ns, per_sm)]."""
+    out, i = [], 0
+    while True:
+        dt, w, ns, ps = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        M = (C.c_int64 * 3)()
+        rc = lib().ipc_autotune_entry(i, C.byref(dt), C.byref(w), M, C.byref(ns), C.byref(ps))
+        if rc != IPC_OK:
+            return out
+        out.append((dt.value, w.value, tuple(M), ns.value, ps.value))
+        i += 1
 
 
 def ipc_refine(view, kind: int, value: float, out, stream=None) -> None:

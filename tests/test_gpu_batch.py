@@ -89,3 +89,44 @@ def test_batch_retrieve_and_plan_equal_single():
             assert torch.equal(o, o2)
     finally:
         ipc.ipc_free(plan)
+
+
+def test_autotuned_shapes_keep_results():
+    """ipc_autotune_retrieve times every launch shape of each level and
+    records the fastest; reconstructions with the recorded shapes (single,
+    batched, planned) stay bitwise equal to the oracle's."""
+    x = synth.random_field((24, 70, 300), seed=88)  # rows 300/150/75/38/..: 1, 2, 4 planes per tile
+    o = oracle.compress(x, 1e-5)
+    g = ipc.Field.compress(torch.from_numpy(x).cuda(), 1e-5)
+    try:
+        ipc.ipc_autotune_clear()
+        out = torch.empty(x.shape, dtype=torch.float32, device="cuda")
+        n = ipc.ipc_autotune_retrieve(g.h, ipc.IPC_TARGET_EB, 1e-4, out, reps=1)
+        ents = ipc.ipc_autotune_entries()
+        assert n == len(ents) >= 1
+        for dt, w16, M, ns, psm in ents:
+            assert dt == 0 and w16 in (0, 1) and ns in (0, 1, 2, 4) and 0 <= psm <= 4
+            assert ns == 0 or ns == 1 or M[2] <= 512 // ns
+        oy, _ = o.retrieve(oracle.EB, 1e-4)
+        assert np.array_equal(out.cpu().numpy().view(np.uint8), oy.view(np.uint8))
+        for E in (1e-4, 1e-3):
+            oy, _ = o.retrieve(oracle.EB, E)
+            y, _ = g.retrieve(ipc.IPC_TARGET_EB, E)
+            torch.cuda.synchronize()
+            assert np.array_equal(y.cpu().numpy().view(np.uint8), oy.view(np.uint8)), E
+        outs = [torch.empty_like(out) for _ in range(3)]
+        tg = [(ipc.IPC_TARGET_EB, 1e-4)] * 3
+        ipc.ipc_retrieve_batch([g.h] * 3, tg, outs)
+        plan = ipc.ipc_plan_retrieve_batch([g.h] * 3, tg, outs)
+        try:
+            ipc.ipc_plan_launch(plan)
+        finally:
+            torch.cuda.synchronize()
+            ipc.ipc_free(plan)
+        oy, _ = o.retrieve(oracle.EB, 1e-4)
+        for y in outs:
+            assert np.array_equal(y.cpu().numpy().view(np.uint8), oy.view(np.uint8))
+        with pytest.raises(ipc.IpcError):
+            ipc.ipc_autotune_retrieve(g.h, ipc.IPC_TARGET_EB, 1e-4, out, reps=0)
+    finally:
+        ipc.ipc_autotune_clear()
