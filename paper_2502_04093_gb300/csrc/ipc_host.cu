@@ -933,6 +933,7 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
     LevelArgs L = level_args(f, l);
     retrieve_layout(&L, scr + off[l + 1]);
     retrieve_planes(f, l, b[l - 1], &L);
+    L.stream_out = l == 1;
     void* o = l == 1 ? d_out : (void*)(scr + off[l]);
     double by = 0;
     uint64_t nc = 0;
@@ -1037,6 +1038,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       e.L = level_args(f, l);
       retrieve_layout(&e.L, nullptr);
       retrieve_planes(f, l, bs[i][l - 1], &e.L);
+      e.L.stream_out = l == 1;
       e.out = outs[i];
       e.cap = f->d_cap;
       e.bm = f->d_bm;
@@ -1344,6 +1346,7 @@ int ipc_autotune_retrieve(ipc_field* f, ipc_target target, void* d_out, void* st
     La[l] = level_args(f, l);
     retrieve_layout(&La[l], scr + off[l + 1]);
     retrieve_planes(f, l, b[l - 1], &La[l]);
+    La[l].stream_out = l == 1;
     W[l] = level_w16(f, l, b[l - 1]) ? 1 : 0;
   }
   auto run = [&](int l, RetrieveShape sh) {

@@ -63,6 +63,8 @@ struct LevelArgs {
   int64_t s;
   int cubic;
   int vec;            // output base aligned to two elements (paired stores allowed)
+  int stream_out;     // reconstruction: the output is the caller's array, written
+                      // with evict-first stores (kept out of L2's way)
   uint64_t nrb, nct;  // CTA row blocks per plane, column tiles
   uint64_t mrb, mct;  // div_magic(nrb), div_magic(nct): tile -> (plane, row block, column tile)
   LevelStage st[3];

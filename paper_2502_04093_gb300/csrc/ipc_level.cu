@@ -305,17 +305,25 @@ __device__ __forceinline__ void scaled_quad(const uint32_t* p, const CodeScale<T
 // are consecutive elements; at stride 2 each value is written twice so that
 // whole sectors are written (the element in between is a target of the next
 // level and is never read as a known value); larger strides store singly.
+// cs: evict-first ("streaming") stores for the runs at stride 1.
 template <class T>
 __device__ __forceinline__ void store_run(T* row, int64_t s, int64_t n2, int c2e, int C1,
-                                          const T (&v)[8]) {
+                                          const T (&v)[8], bool cs = false) {
   typedef typename Vec2<T>::type V2;
   if (s == 1) {
     T* p = row + c2e;
     if (c2e + 8 <= C1 && ((uintptr_t)p & 15) == 0) {
       if (sizeof(T) == 4) {
         float4* q = reinterpret_cast<float4*>(p);
-        q[0] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
-        q[1] = make_float4((float)v[4], (float)v[5], (float)v[6], (float)v[7]);
+        const float4 a = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+        const float4 b = make_float4((float)v[4], (float)v[5], (float)v[6], (float)v[7]);
+        if (cs) {
+          __stcs(q, a);
+          __stcs(q + 1, b);
+        } else {
+          q[0] = a;
+          q[1] = b;
+        }
       } else {
         V2* q = reinterpret_cast<V2*>(p);
 #pragma unroll
@@ -323,7 +331,8 @@ __device__ __forceinline__ void store_run(T* row, int64_t s, int64_t n2, int c2e
           V2 t;
           t.x = v[2 * i];
           t.y = v[2 * i + 1];
-          q[i] = t;
+          if (cs) __stcs(q + i, t);
+          else q[i] = t;
         }
       }
       return;
@@ -615,7 +624,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       uint32_t w = 0u;
       if ((kmw >> i2) & 1u) {
         const uint32_t m = sb[i2 * BWS];
-        if (m & bit) w = __ldg(sp[i2] + off + __popc(m & below));
+        if (m & bit) w = __ldcs(sp[i2] + off + __popc(m & below));  // read once: evict-first
       }
       a[i2] = w;
     }
@@ -813,7 +822,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
             }
           }
         }
-        store_run<T>(out + c.pbase + (int64_t)c1 * c.rs, L.s, L.N[2], c2e, c.C1, v);
+        store_run<T>(out + c.pbase + (int64_t)c1 * c.rs, L.s, L.N[2], c2e, c.C1, v, L.stream_out);
       }
     }
   }
