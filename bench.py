@@ -73,18 +73,24 @@ def kernel_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
+def measured_traffic(with_time=False):
     """DRAM bytes per launch of the level retrieve kernel from the committed
     ncu capture (profiles/retrieve_level_traffic.json), or None when the
-    kernel sources changed since that capture."""
+    kernel sources changed since that capture; with_time: also the average
+    launch duration under ncu (us)."""
     p = os.path.join(ROOT, "profiles", "retrieve_level_traffic.json")
     if not os.path.exists(p):
-        return None
+        return (None, None) if with_time else None
     with open(p) as fh:
         d = json.load(fh)
     if d.get("kernel_sources_sha256") != kernel_sources_sha256():
-        return None
+        return (None, None) if with_time else None
+    if with_time:
+        return float(d["dram_bytes_per_launch"]), float(d["avg_launch_us_under_ncu"])
     return float(d["dram_bytes_per_launch"])
+
+
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
 def load_peaks():
@@ -327,6 +333,11 @@ def run_ours(args, rank, world, local_rank):
             "timing": "CUDA events around each launch on the library's stream, in a second "
                       "timed pass of the same %d steps (%.3f ms/step with the events)"
                       % (args.steps, prof_ms / args.steps)}
+    roof["frac_of_nominal"] = round(achieved / NOMINAL_HBM_GBS, 4)
+    tb, tus = measured_traffic(with_time=True)
+    if tb is not None and tus:
+        # the capture's own DRAM throughput (cold caches, serialised launches)
+        roof["dram_frac_under_ncu"] = round(tb / (tus * 1e-6) / 1e9 / peak, 4)
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3),
                    "alg_GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None}
                for k, v in prof.items() if v[0]}
@@ -340,6 +351,8 @@ def run_ours(args, rank, world, local_rank):
         del x
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(ipc, synth, torch)
+        if rank == 0 and not args.no_cpu_baseline:
+            extra["batched"]["cpu_baseline"] = batched_cpu_baseline()
         torch.cuda.empty_cache()
         extra["batched_f64"] = measure_f64(ipc, synth, torch)
         torch.cuda.empty_cache()
@@ -490,6 +503,54 @@ def measure_batched(ipc, synth, torch):
             "retrieve_batched_ms": round(rb, 3), "retrieve_per_field_ms": round(rs, 3),
             "retrieve_graph_ms": round(rg, 3), "retrieve_batched_gbs": gbs(rb),
             "retrieve_per_field_gbs": gbs(rs), "retrieve_graph_gbs": gbs(rg)}
+
+
+def _oracle_field(task):
+    """Pool task: one field of the batched workload through the oracle --
+    compression at rel eb 1e-4 and one retrieval at the field's eb; returns
+    the seconds spent."""
+    x, E = task
+    from oracle import oracle
+    t0 = time.perf_counter()
+    f = oracle.compress(x, 1e-4, oracle.REL)
+    f.retrieve(oracle.EB, E)
+    return time.perf_counter() - t0
+
+
+def _oracle_ready(_):
+    from oracle import oracle
+    oracle.lib()
+    return os.getpid()
+
+
+def batched_cpu_baseline():
+    """The oracle on a bounded sample of the batched workload -- its 24
+    smallest fields (450x900), each compressed and retrieved at its eb --
+    single-threaded, and on all host cores with one field per task in a pool
+    of spawned processes (started, and the oracle loaded, before the timed
+    region). Value: field bytes compressed plus bytes retrieved per second."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import oracle
+    from paper_2502_04093_gb300 import synth
+    oracle.build()
+    shapes, seeds = synth.zonal_batch(seed=1300)
+    rng = np.random.default_rng(1303)
+    targets = [float(10 ** rng.uniform(-4, -1)) for _ in shapes]
+    tasks = [(synth.zonal2d(s, seed=sd), E) for s, sd, E in zip(shapes, seeds, targets)
+             if tuple(s) == (450, 900)]
+    nbytes = 2 * sum(t[0].nbytes for t in tasks)
+    one = sum(_oracle_field(t) for t in tasks)
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_ready, range(cores))
+        t0 = time.perf_counter()
+        pool.map(_oracle_field, tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+    return {"kind": "oracle", "unit": "GB/s", "sample": "the 24 fields of 450x900 (compress + one "
+            "retrieve each); all cores: one field per task, spawned pool",
+            "value_one_core": round(nbytes / one / 1e9, 4),
+            "value_all_cores": round(nbytes / wall / 1e9, 4), "cores": cores}
 
 
 def measure_f64(ipc, synth, torch):
