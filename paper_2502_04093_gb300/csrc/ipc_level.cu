@@ -1219,9 +1219,11 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
   }
 }
 
-// Single-field kernels: arguments in the parameter space.
+// Single-field kernels: arguments in the parameter space. Four CTAs of the
+// compression fit per SM (64 registers, all of the SM's shared memory); the
+// batched kernel, whose arguments come from global memory, keeps three.
 template <class T, int BR, int BC>
-__global__ void __launch_bounds__(256, 3) k_level_compress(LevelArgs L, const T* __restrict__ x,
+__global__ void __launch_bounds__(256, 4) k_level_compress(LevelArgs L, const T* __restrict__ x,
                                                            T* xh, int write_xh, QuantArgs<T> qa,
                                                            SweepOut o, LevelDescs D) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1317,6 +1319,10 @@ cudaError_t setup_once() {
     cudaError_t r = cudaFuncSetAttribute(k_level_compress<T, BR, BC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_compress<T, BR, BC>());
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_level_compress<T, BR, BC>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(k_level_compress_batch<T, BR, BC>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
