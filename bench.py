@@ -816,7 +816,9 @@ def main():
                             "step = compress + retrieve 1e-1 refined to 1e-2..1e-6 + retrieve "
                             "at 0.5,1,2,4,8,16 bits/value (one batched call, one output each)"
                             % args.edge,
-                "l2": "inputs larger than L2 (512 MiB field vs 129 MB L2)",
+                "l2": ("inputs larger than L2 (%d MiB field vs 129 MB L2)" % (r["nbytes"] >> 20))
+                      if r["nbytes"] > 129e6 else
+                      "field smaller than L2 (%d MiB): timings include L2 reuse" % (r["nbytes"] >> 20),
                 "parallelism": "one field per GPU" if world > 1 else "single GPU",
                 "launch_shapes": launch_shapes(r["tuned"])},
             "compress_gbs": round(r["nbytes"] / (r["compress_ms"] * 1e-3) / 1e9, 1),
