@@ -339,7 +339,8 @@ def run_ours(args, rank, world, local_rank):
         # the capture's own DRAM throughput (cold caches, serialised launches)
         roof["dram_frac_under_ncu"] = round(tb / (tus * 1e-6) / 1e9 / peak, 4)
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3),
-                   "alg_GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None}
+                   "alg_GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None,
+                   "frac": round(v[2] / (v[1] * 1e-3) / 1e9 / peak, 4) if v[1] else None}
                for k, v in prof.items() if v[0]}
 
     e2e = None
