@@ -159,6 +159,12 @@ def test_errors():
     with pytest.raises(ipc.IpcError) as e:
         ipc.ipc_compress(x, 0.0)
     assert e.value.rc == ipc.IPC_EINVAL
+    # empty extents are rejected (every extent >= 1), as the oracle does
+    for shape in [(0,), (3, 0, 5)]:
+        with pytest.raises(ipc.IpcError) as e:
+            ipc.ipc_compress(torch.empty(shape, device="cuda"), 1e-3)
+        assert e.value.rc == ipc.IPC_EINVAL
+        assert oracle.compress_rc(np.zeros(shape, np.float32), 1e-3) == e.value.rc
     f = ipc.Field.compress(x, 1e-3)
     with pytest.raises(ipc.IpcError) as e:
         f.retrieve(ipc.IPC_TARGET_EB, 1e-4)
