@@ -116,19 +116,28 @@ class ClockSampler:
         self.thread = None
 
     def __enter__(self):
+        # nvidia-smi's start (NVML initialisation) slows the GPU work running
+        # beside it: wait for its first sample, outside the timed region, and
+        # keep only the samples taken after that
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.ready = threading.Event()
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            self.ready.wait(timeout=10)
+            self.lines = []
         except OSError:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
+            if not self.ready.is_set():
+                self.ready.set()
+                continue
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
