@@ -679,7 +679,7 @@ def measure_serving(ipc, synth, torch, full=False):
     U[1, 12]), 25% refine of a live view to E * 10^-U[1, 2], at 0.7x the
     measured capacity of the plain (one request per launch) server."""
     import numpy as np
-    nf, hi, nreq = (128, 768, 2000) if full else (40, 448, 400)
+    nf, hi, nreq = (128, 768, 4000) if full else (40, 448, 400)
     edges = synth.serving_edges(nfields=nf, hi=hi)
     fields = []
     for j, e in enumerate(edges):
