@@ -962,10 +962,18 @@ struct BatchTable {
   std::vector<RetrieveEntry> ents;
   std::vector<AnchorEntry> anchors;
   std::vector<int64_t> kin_off, out_off, anch_off;  // scratch offsets (-1: caller's array)
-  std::vector<uint64_t> lev_off, lev_ctas;
-  std::vector<int> lev_w16;  // every entry of the level keeps 16-bit codes
-  std::vector<int> lev_ns;   // sub-tiles per tile of the level's launch
-  std::vector<int> lev_psm;  // CTAs per SM of the level's launch (0: as many as fit)
+  // One launch per (level, code width): a level's entries whose loaded
+  // planes span at most 16 go to the 16-bit kernel, the others to the
+  // 32-bit one, coarse levels first.
+  struct Launch {
+    uint64_t off = 0;   // first entry
+    int n = 0;          // entries
+    uint64_t ctas = 0;  // tiles over the entries
+    int w16 = 1;        // 16-bit code rows
+    int ns = 1;         // sub-tiles per tile
+    int psm = 0;        // CTAs per SM (0: as many as fit)
+  };
+  std::vector<Launch> launches;
   uint64_t scratch = 0;      // bytes of the fields' scratch ladders
   int Kmax = 0;
   double alg_bytes = 0;
@@ -976,11 +984,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   const size_t nf = fs.size();
   T->Kmax = 0;
   for (auto* f : fs) T->Kmax = std::max(T->Kmax, f->g.K);
-  T->lev_off.assign(T->Kmax + 2, 0);
-  T->lev_ctas.assign(T->Kmax + 2, 0);
-  T->lev_w16.assign(T->Kmax + 2, 1);
-  T->lev_ns.assign(T->Kmax + 2, 1);
-  T->lev_psm.assign(T->Kmax + 2, 0);
+  T->launches.clear();
   T->ents.clear();
   T->anchors.clear();
   T->kin_off.clear();
@@ -1002,65 +1006,66 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
     T->anch_off.push_back(K > 0 ? (int64_t)(base[i] + off[i][K + 1]) : -1);
   }
   for (int l = T->Kmax; l >= 1; --l) {
-    T->lev_off[l] = T->ents.size();
-    // the level's code width and tile shape hold for every entry
-    int ns = 4;
-    for (size_t i = 0; i < nf; ++i) {
-      ipc_field* f = fs[i];
-      if (l > f->g.K) continue;
-      if (!level_w16(f, l, bs[i][l - 1])) T->lev_w16[l] = 0;
-    }
-    // a tuned shape applies when every entry's level has the same key
-    bool same = true;
-    ShapeKey key{};
-    int seen = 0;
-    for (size_t i = 0; i < nf; ++i) {
-      ipc_field* f = fs[i];
-      if (l > f->g.K) continue;
-      const LevelArgs La = level_args(f, l);
-      ns = std::min(ns, retrieve_subtiles(La.M[2], T->lev_w16[l]));
-      const ShapeKey k = shape_key(f->dtype, T->lev_w16[l], La);
-      if (seen++ && (k < key || key < k)) same = false;
-      key = k;
-    }
-    if (seen && same) {
-      const RetrieveShape sh = tuned_shape(key);
-      if (sh.ns && sh.ns <= ns) ns = sh.ns;
-      T->lev_psm[l] = sh.per_sm;
-    }
-    T->lev_ns[l] = ns;
-    uint64_t cta = 0;
-    for (size_t i = 0; i < nf; ++i) {
-      ipc_field* f = fs[i];
-      if (l > f->g.K) continue;
-      const size_t esz = f->dtype == 0 ? 4 : 8;
-      RetrieveEntry e{};
-      e.L = level_args(f, l);
-      retrieve_layout(&e.L, nullptr);
-      retrieve_planes(f, l, bs[i][l - 1], &e.L);
-      e.L.stream_out = l == 1;
-      e.out = outs[i];
-      e.cap = f->d_cap;
-      e.bm = f->d_bm;
-      e.oidx = f->d_oidx;
-      e.oval = f->d_oval;
-      e.twoeb = bin_width(f);
-      e.b = bs[i][l - 1];
-      e.cta_begin = cta;
-      cta += retrieve_tiles(e.L, ns);
-      T->ents.push_back(e);
-      T->kin_off.push_back((int64_t)(base[i] + off[i][l + 1]));
-      T->out_off.push_back(l == 1 ? -1 : (int64_t)(base[i] + off[i][l]));
-      for (int d = 0; d < 3; ++d) {
-        const int t = f->g.level_stage[d][l - 1];
-        if (t < 0) continue;
-        T->alg_bytes += (double)(f->g.stages[t].ncodes * esz);
-        for (int k = e.b; k < 32; ++k) T->alg_bytes += (double)f->st[t].size[k];
+    std::vector<size_t> group[2];  // the level's fields by code width (index: w16)
+    for (size_t i = 0; i < nf; ++i)
+      if (l <= fs[i]->g.K) group[level_w16(fs[i], l, bs[i][l - 1]) ? 1 : 0].push_back(i);
+    for (int w16 : {1, 0}) {
+      if (group[w16].empty()) continue;
+      BatchTable::Launch ln;
+      ln.off = T->ents.size();
+      ln.n = (int)group[w16].size();
+      ln.w16 = w16;
+      // the tile shape holds for every entry; a tuned shape applies when
+      // every entry's level has the same key
+      int ns = 4;
+      bool same = true;
+      ShapeKey key{};
+      int seen = 0;
+      for (size_t i : group[w16]) {
+        const LevelArgs La = level_args(fs[i], l);
+        ns = std::min(ns, retrieve_subtiles(La.M[2], w16));
+        const ShapeKey k = shape_key(fs[i]->dtype, w16, La);
+        if (seen++ && (k < key || key < k)) same = false;
+        key = k;
       }
+      if (same) {
+        const RetrieveShape sh = tuned_shape(key);
+        if (sh.ns && sh.ns <= ns) ns = sh.ns;
+        ln.psm = sh.per_sm;
+      }
+      ln.ns = ns;
+      uint64_t cta = 0;
+      for (size_t i : group[w16]) {
+        ipc_field* f = fs[i];
+        const size_t esz = f->dtype == 0 ? 4 : 8;
+        RetrieveEntry e{};
+        e.L = level_args(f, l);
+        retrieve_layout(&e.L, nullptr);
+        retrieve_planes(f, l, bs[i][l - 1], &e.L);
+        e.L.stream_out = l == 1;
+        e.out = outs[i];
+        e.cap = f->d_cap;
+        e.bm = f->d_bm;
+        e.oidx = f->d_oidx;
+        e.oval = f->d_oval;
+        e.twoeb = bin_width(f);
+        e.b = bs[i][l - 1];
+        e.cta_begin = cta;
+        cta += retrieve_tiles(e.L, ns);
+        T->ents.push_back(e);
+        T->kin_off.push_back((int64_t)(base[i] + off[i][l + 1]));
+        T->out_off.push_back(l == 1 ? -1 : (int64_t)(base[i] + off[i][l]));
+        for (int d = 0; d < 3; ++d) {
+          const int t = f->g.level_stage[d][l - 1];
+          if (t < 0) continue;
+          T->alg_bytes += (double)(f->g.stages[t].ncodes * esz);
+          for (int k = e.b; k < 32; ++k) T->alg_bytes += (double)f->st[t].size[k];
+        }
+      }
+      ln.ctas = cta;
+      T->launches.push_back(ln);
     }
-    T->lev_ctas[l] = cta;
   }
-  T->lev_off[0] = T->ents.size();
 }
 
 // Table layout: [scratch ladders | entries | anchors]; the scratch comes
@@ -1078,14 +1083,13 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
     if (profile) prof_end(ph, st, 16.0 * T.anchors.size());
     ++nl;
   }
-  // the per-level share of the algorithmic bytes is reported for the batch
-  for (int l = T.Kmax; l >= 1; --l) {
-    // level l's entries: [lev_off[l], lev_off[l-1]) with lev_off[0] = size
-    const int nn = (int)(T.lev_off[l - 1] - T.lev_off[l]);
+  // the algorithmic bytes of the whole batch are reported with its last launch
+  for (size_t j = 0; j < T.launches.size(); ++j) {
+    const BatchTable::Launch& ln = T.launches[j];
     const long ph = profile ? prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st) : -1;
-    CU(launch_level_retrieve_batch(dtype, d_ents + T.lev_off[l], nn, T.lev_ctas[l], T.lev_w16[l],
-                                   T.lev_ns[l], T.lev_psm[l], st));
-    if (profile) prof_end(ph, st, l == 1 ? T.alg_bytes : 0.0);
+    CU(launch_level_retrieve_batch(dtype, d_ents + ln.off, ln.n, ln.ctas, ln.w16, ln.ns, ln.psm,
+                                   st));
+    if (profile) prof_end(ph, st, j + 1 == T.launches.size() ? T.alg_bytes : 0.0);
     ++nl;
   }
   if (!profile) g_launches.fetch_add(nl, std::memory_order_relaxed);
