@@ -443,6 +443,14 @@ LevelArgs level_args(const ipc_field* f, int l) {
   return L;
 }
 
+// Row blocks of a level's reconstruction tiles (their rows depend on the
+// code width, see retrieve_rows).
+void retrieve_tiling(LevelArgs* L, int dtype, int w16, int ns) {
+  const int R = retrieve_rows(dtype, w16, ns);
+  L->nrb = ((uint64_t)L->M[1] + R - 1) / R;
+  L->mrb = div_magic(L->nrb);
+}
+
 // Reconstruction view of level l's plane streams with b_l = b: where plane
 // 0 of each stage lies, the plane strides, and the planes to load.
 void retrieve_planes(const ipc_field* f, int l, int b, LevelArgs* L) {
@@ -944,9 +952,12 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
       for (int k = b[l - 1]; k < 32; ++k) by += (double)f->st[t].size[k];
     }
     const int w16 = level_w16(f, l, b[l - 1]) ? 1 : 0;
+    RetrieveShape sh = tuned_shape(shape_key(f->dtype, w16, L));
+    if (!sh.ns) sh.ns = retrieve_subtiles(L.M[2], w16);
+    retrieve_tiling(&L, f->dtype, w16, sh.ns);
     const long ph = prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st);
     CU(launch_level_retrieve(f->dtype, L, o, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
-                             f->d_oval, w16, tuned_shape(shape_key(f->dtype, w16, L)), st));
+                             f->d_oval, w16, sh, st));
     prof_end(ph, st, by + (double)(nc * esz));
   }
   return IPC_OK;
@@ -1042,6 +1053,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
         e.L = level_args(f, l);
         retrieve_layout(&e.L, nullptr);
         retrieve_planes(f, l, bs[i][l - 1], &e.L);
+        retrieve_tiling(&e.L, f->dtype, w16, ns);
         e.L.stream_out = l == 1;
         e.out = outs[i];
         e.cap = f->d_cap;
@@ -1355,7 +1367,10 @@ int ipc_autotune_retrieve(ipc_field* f, ipc_target target, void* d_out, void* st
   }
   auto run = [&](int l, RetrieveShape sh) {
     void* o = l == 1 ? d_out : (void*)(scr + off[l]);
-    return launch_level_retrieve(f->dtype, La[l], o, twoeb, b[l - 1], f->d_cap, f->d_bm,
+    if (!sh.ns) sh.ns = retrieve_subtiles(La[l].M[2], W[l]);
+    LevelArgs Lt = La[l];
+    retrieve_tiling(&Lt, f->dtype, W[l], sh.ns);
+    return launch_level_retrieve(f->dtype, Lt, o, twoeb, b[l - 1], f->d_cap, f->d_bm,
                                  f->d_oidx, f->d_oval, W[l], sh, st);
   };
   for (int l = g.K; l >= 1; --l) {
@@ -1385,7 +1400,7 @@ int ipc_autotune_retrieve(ipc_field* f, ipc_target target, void* d_out, void* st
     best_ms = def_ms;
     for (int ns : {1, 2, 4}) {
       if (!retrieve_ns_ok(La[l].M[2], ns)) continue;
-      for (int psm = 1; psm <= retrieve_max_per_sm(W[l]); ++psm) {
+      for (int psm = 1; psm <= retrieve_max_per_sm(f->dtype, W[l], ns); ++psm) {
         float ms = 0;
         if ((rc = timed(RetrieveShape{ns, psm}, &ms))) return rc;
         if (ms < best_ms && ms < 0.97f * def_ms) {

@@ -202,8 +202,18 @@ struct RetrieveShape {
 inline bool retrieve_ns_ok(int64_t M2, int ns) {
   return ns == 1 || (ns == 2 && M2 <= kLevelCols / 2) || (ns == 4 && M2 <= kLevelCols / 4);
 }
-// Most CTAs of a level reconstruction resident per SM (16-bit / 32-bit codes).
-inline int retrieve_max_per_sm(int w16) { return w16 ? 4 : 3; }
+// Rows of a reconstruction tile: the compressed segment's rows, except for
+// f32 tiles of several planes (ns > 1) with 32-bit code rows, which take half
+// a segment (8 rows) so that four CTAs fit per SM. (One-plane tiles keep 16
+// rows: with 8, the halo rows' share of the work costs more than the fourth
+// CTA gains.)
+inline int retrieve_rows(int dtype, int w16, int ns) {
+  return dtype == 0 ? (w16 || ns == 1 ? kLevelRowsF32 : kLevelRowsF32 / 2) : kLevelRowsF64;
+}
+// Most CTAs of a level reconstruction resident per SM.
+inline int retrieve_max_per_sm(int dtype, int w16, int ns) {
+  return w16 || (dtype == 0 && ns > 1) ? 4 : 3;
+}
 // w16: the planes loaded at the level span at most 16 (16-bit code rows).
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,

@@ -440,6 +440,11 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   // holds a plane).
   const CtaPos c = sub_pos(L, tile, sub, NS, BR, BCs);
   const int P0 = c.P - 2 * sub;
+  // Segments (the compression's tiles) are SR rows of stage 2 and SR / 2 of
+  // stages 1 and 0; a tile of BR <= SR rows lies in segment row block rbseg.
+  constexpr int SR = sizeof(T) == 4 ? kLevelRowsF32 : kLevelRowsF64;
+  static_assert(SR % BR == 0, "a tile's rows lie in one segment");
+  const int rbseg = c.R0 / SR;
   const bool live = c.P < M0;
   const bool podd = (c.P & 1) != 0;
   T* VE = VEof(sub);
@@ -471,7 +476,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const int Ps = P0 + 2 * s;
     if (Ps >= M0 || k > 31 || !((km >> k) & 1u)) continue;
     const LevelStage& S = L.st[sx];
-    const int64_t rbs = (int64_t)c.rb + drb, cts = (int64_t)c.ct + dct;
+    const int64_t rbs = (int64_t)rbseg + drb, cts = (int64_t)c.ct + dct;
     if (rbs < 0 || (uint64_t)rbs >= S.nrb || cts < 0 || (uint64_t)cts >= S.nct) continue;
     const uint64_t pi = sx == 0 ? (uint64_t)((Ps - 1) >> 1) : (uint64_t)Ps;
     const uint64_t g = seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts);
@@ -595,17 +600,17 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     }
     const LevelStage& S = L.st[sx];
     if (rr < 0 || (uint64_t)rr >= S.m1 || j < 0 || (uint64_t)j >= S.wr) continue;
-    const int RB = sx == 2 ? BR : BR / 2;
+    const int RB = sx == 2 ? SR : SR / 2;  // the segment's rows
     const int CW = (int)S.CW;  // G::CWD, or the whole (short) row when nct == 1
     const int ctw = CW == G::CWD ? (int)((unsigned)j / G::CWD) : 0;
-    const int rbw = sx == 2 ? (int)((unsigned)rr / BR) : (int)((unsigned)rr / (BR / 2));
+    const int rbw = sx == 2 ? (int)((unsigned)rr / SR) : (int)((unsigned)rr / (SR / 2));
     int sl = 0;
     if (KS == 5) {
       if (sx == 1) sl = 1;
-      else if (sx == 0) sl = 3 + (rbw - (int)c.rb);
+      else if (sx == 0) sl = 3 + (rbw - rbseg);
     } else {
       if (sx == 1) sl = 2 + (ctw - (int)c.ct);
-      else if (sx == 0) sl = 4 + (rbw - (int)c.rb + 1) * 3 + (ctw - (int)c.ct) + 1;
+      else if (sx == 0) sl = 4 + (rbw - rbseg + 1) * 3 + (ctw - (int)c.ct) + 1;
     }
     const int li = (rr - rbw * RB) * CW + (j - ctw * CW);
     const int wl = li >> 5;
@@ -1234,11 +1239,13 @@ __global__ void __launch_bounds__(256, 4) k_level_compress(LevelArgs L, const T*
 // sub-tiles), 32-bit ones for three.
 // Persistent: the grid holds as many CTAs as fit at once; CTA i takes tiles
 // i, i + grid, ... (neighbouring CTAs stay on neighbouring tiles).
-template <bool W16, int NS>
-__host__ __device__ constexpr int retrieve_ctas_per_sm() { return W16 ? 4 : 3; }
+template <class T, int BR, bool W16>
+__host__ __device__ constexpr int retrieve_ctas_per_sm() {
+  return W16 || sizeof(T) * BR <= 32 ? 4 : 3;
+}
 
 template <class T, int BR, int BC, bool W16, int NS>
-__global__ void __launch_bounds__(256, retrieve_ctas_per_sm<W16, NS>()) k_level_retrieve(
+__global__ void __launch_bounds__(256, retrieve_ctas_per_sm<T, BR, W16>()) k_level_retrieve(
     LevelArgs L, T* out, T twoeb, int b, const uint32_t* __restrict__ cap,
     const uint32_t* __restrict__ bm, const uint64_t* __restrict__ oidx,
     const double* __restrict__ oval, uint64_t ntiles) {
@@ -1278,7 +1285,7 @@ __global__ void __launch_bounds__(256, 3) k_level_compress_batch(
 }
 
 template <class T, int BR, int BC, bool W16, int NS>
-__global__ void __launch_bounds__(256, retrieve_ctas_per_sm<W16, NS>()) k_level_retrieve_batch(
+__global__ void __launch_bounds__(256, retrieve_ctas_per_sm<T, BR, W16>()) k_level_retrieve_batch(
     const RetrieveEntry* __restrict__ ents, int n, uint64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem[];
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1330,9 +1337,10 @@ cudaError_t setup_once() {
     if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true, 1>();
     if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true, 2>();
     if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, true, 4>();
+    constexpr int BR32 = sizeof(T) == 4 ? BR / 2 : BR;  // rows of 32-bit-code tiles, ns > 1
     if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false, 1>();
-    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false, 2>();
-    if (r == cudaSuccess) r = setup_retrieve<T, BR, BC, false, 4>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR32, BC, false, 2>();
+    if (r == cudaSuccess) r = setup_retrieve<T, BR32, BC, false, 4>();
     return r;
   }();
   return e;
@@ -1363,7 +1371,7 @@ void retrieve_kernel(const LevelArgs& L, void* out, double twoeb, int b, const u
   const uint64_t tiles = retrieve_tiles(L, NS);
   if (tiles == 0) return;
   k_level_retrieve<T, BR, BC, W16, NS>
-      <<<persistent_grid(tiles, grid_per_sm(per_sm, retrieve_ctas_per_sm<W16, NS>())), 256,
+      <<<persistent_grid(tiles, grid_per_sm(per_sm, retrieve_ctas_per_sm<T, BR, W16>())), 256,
          smem_retrieve<T, BR, BC, W16, NS>(), st>>>(L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval,
                                                     tiles);
 }
@@ -1371,32 +1379,38 @@ template <class T, int BR, int BC, bool W16, int NS>
 void retrieve_batch_kernel(const RetrieveEntry* ents, int n, uint64_t tiles, int per_sm,
                            cudaStream_t st) {
   k_level_retrieve_batch<T, BR, BC, W16, NS>
-      <<<persistent_grid(tiles, grid_per_sm(per_sm, retrieve_ctas_per_sm<W16, NS>())), 256,
+      <<<persistent_grid(tiles, grid_per_sm(per_sm, retrieve_ctas_per_sm<T, BR, W16>())), 256,
          smem_retrieve<T, BR, BC, W16, NS>(), st>>>(ents, n, tiles);
 }
 
-template <class T, int BR, int BC>
+// BR16 / BR32: tile rows with 16-bit code rows / with 32-bit code rows and
+// several planes per tile (one-plane 32-bit tiles keep BR16 rows).
+template <class T, int BR16, int BR32, int BC>
 void retrieve_dispatch(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
                        const uint32_t* bm, const uint64_t* oidx, const double* oval, int w16,
                        int ns, int per_sm, cudaStream_t st) {
+#define IPC_RK(R, W, N) retrieve_kernel<T, R, BC, W, N>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st)
   if (!w16) {
-    if (ns == 4) retrieve_kernel<T, BR, BC, false, 4>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
-    else if (ns == 2) retrieve_kernel<T, BR, BC, false, 2>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
-    else retrieve_kernel<T, BR, BC, false, 1>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
-  } else if (ns == 4) retrieve_kernel<T, BR, BC, true, 4>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
-  else if (ns == 2) retrieve_kernel<T, BR, BC, true, 2>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
-  else retrieve_kernel<T, BR, BC, true, 1>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st);
+    if (ns == 4) IPC_RK(BR32, false, 4);
+    else if (ns == 2) IPC_RK(BR32, false, 2);
+    else IPC_RK(BR16, false, 1);
+  } else if (ns == 4) IPC_RK(BR16, true, 4);
+  else if (ns == 2) IPC_RK(BR16, true, 2);
+  else IPC_RK(BR16, true, 1);
+#undef IPC_RK
 }
-template <class T, int BR, int BC>
+template <class T, int BR16, int BR32, int BC>
 void retrieve_batch_dispatch(const RetrieveEntry* ents, int n, uint64_t tiles, int w16, int ns,
                              int per_sm, cudaStream_t st) {
+#define IPC_RB(R, W, N) retrieve_batch_kernel<T, R, BC, W, N>(ents, n, tiles, per_sm, st)
   if (!w16) {
-    if (ns == 4) retrieve_batch_kernel<T, BR, BC, false, 4>(ents, n, tiles, per_sm, st);
-    else if (ns == 2) retrieve_batch_kernel<T, BR, BC, false, 2>(ents, n, tiles, per_sm, st);
-    else retrieve_batch_kernel<T, BR, BC, false, 1>(ents, n, tiles, per_sm, st);
-  } else if (ns == 4) retrieve_batch_kernel<T, BR, BC, true, 4>(ents, n, tiles, per_sm, st);
-  else if (ns == 2) retrieve_batch_kernel<T, BR, BC, true, 2>(ents, n, tiles, per_sm, st);
-  else retrieve_batch_kernel<T, BR, BC, true, 1>(ents, n, tiles, per_sm, st);
+    if (ns == 4) IPC_RB(BR32, false, 4);
+    else if (ns == 2) IPC_RB(BR32, false, 2);
+    else IPC_RB(BR16, false, 1);
+  } else if (ns == 4) IPC_RB(BR16, true, 4);
+  else if (ns == 2) IPC_RB(BR16, true, 2);
+  else IPC_RB(BR16, true, 1);
+#undef IPC_RB
 }
 
 }  // namespace
@@ -1436,10 +1450,10 @@ cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, doub
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_dispatch<float, kLevelRowsF32, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
+    retrieve_dispatch<float, kLevelRowsF32, kLevelRowsF32 / 2, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_dispatch<double, kLevelRowsF64, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
+    retrieve_dispatch<double, kLevelRowsF64, kLevelRowsF64, kLevelCols>(L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
   }
   return cudaGetLastError();
 }
@@ -1469,10 +1483,10 @@ cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, in
   cudaError_t e;
   if (dtype == 0) {
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_batch_dispatch<float, kLevelRowsF32, kLevelCols>(ents, n, tiles, w16, ns, per_sm, st);
+    retrieve_batch_dispatch<float, kLevelRowsF32, kLevelRowsF32 / 2, kLevelCols>(ents, n, tiles, w16, ns, per_sm, st);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols>()) != cudaSuccess) return e;
-    retrieve_batch_dispatch<double, kLevelRowsF64, kLevelCols>(ents, n, tiles, w16, ns, per_sm, st);
+    retrieve_batch_dispatch<double, kLevelRowsF64, kLevelRowsF64, kLevelCols>(ents, n, tiles, w16, ns, per_sm, st);
   }
   return cudaGetLastError();
 }
