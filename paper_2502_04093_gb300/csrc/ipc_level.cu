@@ -624,6 +624,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     QT* Qr = (sx == 2 ? Q2of(s) : (sx == 1 ? Q1of(s) : Q0of(s))) + qrow * G::QP +
              (j - cw0) * QCfg<W16>::BLK;
     uint32_t a[NPL];
+    uint32_t any = 0u;
 #pragma unroll
     for (int i2 = 0; i2 < NPL; ++i2) {
       uint32_t w = 0u;
@@ -632,6 +633,22 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         if (m & bit) w = __ldcs(sp[i2] + off + __popc(m & below));  // read once: evict-first
       }
       a[i2] = w;
+      any |= w;
+    }
+    if (any == 0u) {
+      // every loaded plane word is zero (common when few low planes are
+      // loaded): the 32 codes are zero, with no XOR or transpose to undo
+      if (side < 0) {
+        uint4* q = reinterpret_cast<uint4*>(Qr);
+#pragma unroll
+        for (int m = 0; m < (W16 ? 4 : 8); ++m) q[m] = make_uint4(0u, 0u, 0u, 0u);
+      } else if (side) {
+        QHr[1] = 0u;
+        QHr[2] = 0u;
+      } else {
+        QHr[0] = 0u;
+      }
+      continue;
     }
     // inverse predictive XOR, top-down; planes below b are zero, planes
     // above the window are zero
