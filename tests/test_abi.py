@@ -57,3 +57,20 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ipc, "_lib", None)
     with pytest.raises(ipc.LibraryMissing):
         ipc.lib()
+
+
+def test_autotune_table_without_gpu(libipc):
+    """The shape table's host API: empty after a clear, out-of-range entries
+    rejected, and a tuning call with bad arguments refused before any CUDA
+    work."""
+    assert libipc.ipc_autotune_clear() == 0
+    ns = ctypes.c_int(-7)
+    assert libipc.ipc_autotune_entry(0, None, None, None, ctypes.byref(ns), None) == -1
+    assert libipc.ipc_autotune_entry(-1, None, None, None, None, None) == -1
+    assert ns.value == -7  # untouched on failure
+
+    class Target(ctypes.Structure):
+        _fields_ = [("kind", ctypes.c_int), ("value", ctypes.c_double)]
+    n = ctypes.c_int()
+    rc = libipc.ipc_autotune_retrieve(None, Target(0, 1e-3), None, None, 3, ctypes.byref(n))
+    assert rc == -1
