@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the batched and serving measurements")
+    ap.add_argument("--bound-study", action="store_true",
+                    help="instead of the bench: strict against paper error model on three "
+                         "workloads (loaded bytes, guaranteed bound, measured max error)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the reconstruction's launch shapes before the warm-up "
                          "(measured no faster than the defaults on this workload)")
@@ -817,8 +820,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bound_study(args):
+    """The error models side by side (Sec. 5.1, Theorem 1): for each workload
+    and eb target, with the strict model (stage amplification and rounding
+    margin) and the paper's (one factor p per level, no margin), the loaded
+    bytes, the guaranteed bound and the measured max |x - y| (FP64, on the
+    GPU), all absolute. One JSON line."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_04093_gb300 import ipc, synth
+    cases = [
+        ("grf_k53 512^3 f32, eb 1e-6 abs", lambda: synth.grf_k53((512,) * 3, seed=SEED,
+                                                                  device="cuda"),
+         1e-6, ipc.IPC_EB_ABS, [1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6]),
+        ("8 gaussians + noise 64^3 f32, eb 1e-3 of the range",
+         lambda: torch.from_numpy(synth.gaussians3d((64,) * 3, seed=1001)).cuda(),
+         1e-3, ipc.IPC_EB_REL, [1e-1, 1e-2, 1e-3]),
+        ("sinusoids 384x384x256 f64, eb 1e-8 of the range",
+         lambda: synth.sinusoids3d_torch((384, 384, 256), seed=1400),
+         1e-8, ipc.IPC_EB_REL, [1e-2, 1e-4, 1e-6, 1e-8]),
+    ]
+    out = []
+    for name, make, eb, mode, targets in cases:
+        x = make()
+        torch.cuda.synchronize()
+        xd = x.double()
+        rng = float(xd.max() - xd.min())
+        scale = rng if mode == ipc.IPC_EB_REL else 1.0
+        rows = []
+        fields = {bd: ipc.Field.compress(x, eb, mode, ipc.IPC_CUBIC, bd)
+                  for bd in (ipc.IPC_BOUND_STRICT, ipc.IPC_BOUND_PAPER)}
+        for E in targets:
+            row = {"target": E * scale}
+            for bd, tag in ((ipc.IPC_BOUND_STRICT, "strict"), (ipc.IPC_BOUND_PAPER, "paper")):
+                y, view = fields[bd].retrieve(ipc.IPC_TARGET_EB, E)
+                b, nbytes, bound = view.selection()
+                err = float((y.double() - xd).abs().max())
+                row[tag] = {"bytes": nbytes, "bound": bound, "max_err": err,
+                            "within_target": err <= E * scale}
+                del y, view
+            rows.append(row)
+        out.append({"workload": name, "compressed_bytes": fields[0].size(), "rows": rows})
+        del fields, x, xd
+        torch.cuda.empty_cache()
+    print(json.dumps({"study": "error models: strict against paper", "cases": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.bound_study:
+        bound_study(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
