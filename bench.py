@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--bound-study", action="store_true",
                     help="instead of the bench: strict against paper error model on three "
                          "workloads (loaded bytes, guaranteed bound, measured max error)")
+    ap.add_argument("--entropy-study", action="store_true",
+                    help="instead of the bench: the exported container of the bench field "
+                         "through host-side entropy coders (zlib; zstd when libzstd loads)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the reconstruction's launch shapes before the warm-up "
                          "(measured no faster than the defaults on this workload)")
@@ -868,8 +871,69 @@ def bound_study(args):
     print(json.dumps({"study": "error models: strict against paper", "cases": out}), flush=True)
 
 
+def _zstd():
+    """libzstd through ctypes (its public one-shot API), or None."""
+    import ctypes
+    for name in ("libzstd.so.1", "libzstd.so"):
+        try:
+            L = ctypes.CDLL(name)
+        except OSError:
+            continue
+        L.ZSTD_compressBound.restype = ctypes.c_size_t
+        L.ZSTD_compressBound.argtypes = [ctypes.c_size_t]
+        L.ZSTD_compress.restype = ctypes.c_size_t
+        L.ZSTD_compress.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_int]
+        L.ZSTD_isError.restype = ctypes.c_uint
+        L.ZSTD_isError.argtypes = [ctypes.c_size_t]
+        return L
+    return None
+
+
+def entropy_study(args):
+    """How much a host-side lossless coder would add to the container of the
+    bench field (the paper runs zstd over its plane streams; this build's
+    GPU format stops at zero-word compaction). One JSON line."""
+    import ctypes
+    import zlib
+
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2502_04093_gb300 import ipc, synth
+    x = synth.grf_k53((args.edge,) * 3, seed=SEED, device="cuda")
+    raw = x.numel() * x.element_size()
+    f = ipc.Field.compress(x, EB)
+    blob = f.export()
+    res = {"workload": "grf_k53 %d^3 f32, eb 1e-6 abs, cubic, strict" % args.edge,
+           "field_bytes": raw, "container_bytes": len(blob),
+           "container_ratio": round(raw / len(blob), 3), "coders": []}
+    for lvl in (1, 6):
+        t0 = time.perf_counter()
+        n = len(zlib.compress(blob, lvl))
+        res["coders"].append({"coder": "zlib-%d" % lvl, "bytes": n, "ratio": round(raw / n, 3),
+                              "host_s": round(time.perf_counter() - t0, 2)})
+    Z = _zstd()
+    if Z is not None:
+        cap = Z.ZSTD_compressBound(len(blob))
+        dst = ctypes.create_string_buffer(cap)
+        for lvl in (1, 3, 9):
+            t0 = time.perf_counter()
+            n = Z.ZSTD_compress(dst, cap, blob, len(blob), lvl)
+            if Z.ZSTD_isError(n):
+                continue
+            res["coders"].append({"coder": "zstd-%d" % lvl, "bytes": n,
+                                  "ratio": round(raw / n, 3),
+                                  "host_s": round(time.perf_counter() - t0, 2)})
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
+    if args.entropy_study:
+        entropy_study(args)
+        return
     if args.bound_study:
         bound_study(args)
         return
