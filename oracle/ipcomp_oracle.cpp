@@ -190,8 +190,9 @@ uint64_t uncertainty(int d) {
 
 /* Half bin width of the quantizer. Reading of Sec. 4.2.2: |y - yhat| <= eb
  * must hold for the value reconstructed in the element type, whose two
- * roundings (q*bin and pred + r) add up to about 3u(max|x| + eb); the bin is
- * shrunk by 4u(max|x| + eb), but never below eb. */
+ * roundings (q*bin and pred + r) add up to about 3u(max|x| + eb); the half
+ * bin is eb shrunk by 4u(max|x| + eb), but never below eb/2 (where the
+ * shrink would pass eb/2, the outlier check takes over). */
 double half_bin(double eb, double xmaxabs, int dtype) {
   const double u = dtype == 0 ? Prec<float>::unit() : Prec<double>::unit();
   double eq = eb - 4.0 * u * (xmaxabs + eb);
@@ -516,6 +517,18 @@ void option_tables(const ipco_field* f, double A, Options* o) {
   double twoeb_T = f->dtype == 0 ? (double)(float)(2.0 * eq) : 2.0 * eq;
   double bin = twoeb_T / f->eb;
   double u = f->dtype == 0 ? Prec<float>::unit() : Prec<double>::unit();
+  /* kappa bounds the rounding of one stage, in units of u * A, summed over
+   * the two computations whose difference it covers (compressor and
+   * retriever). With |a|,|b|,|c|,|d| <= A: u = b + c and v = a + d round by
+   * at most 2A u each, w = 9u by 18A u, z = w - v by 20A u; the u-error
+   * enters w nine times. pred = z / 16 is exact, so the stencil's rounding
+   * reaches pred divided by 16: (9*2 + 2 + 18 + 20) A u / 16 < 3.7 A u. The
+   * scaled code r = q * bin (|r| <= 2.25A, x - pred with |pred| <= 1.25A)
+   * and xhat = pred + r (|xhat| <= A) add 2.25 A u and A u: 6.9 A u per
+   * computation, 13.8 A u for the two. kappa = 24 keeps a 1.7x headroom.
+   * Linear: b + c rounds by 2A u, halved by the exact * 0.5, then r (2A u)
+   * and xhat (A u): 4A u per computation, 8A u for two; kappa = 12 keeps a
+   * 1.5x headroom. */
   double kappa = cubic ? 24.0 : 12.0;
   o->cost.assign((size_t)K * 33, 0);
   o->bytes.assign((size_t)K * 33, 0);
