@@ -272,21 +272,23 @@ int ipc_field_info(const ipc_field* f, int* dtype, int* ndim, int64_t* dims,
 
 /* ---- allocation-free range reduction -------------------------------------- */
 /* No counterpart in the paper: an entry point for callers that must not
- * allocate memory -- code inside a CUDA graph capture, a process whose
- * device memory is all owned by another pool, or a loop that must keep a
- * fixed footprint. It computes, for each of nfields device arrays of n[i]
- * elements of `dtype`, the minimum, maximum and maximum |x| over the finite
- * values and their count (the range step of ipc_compress), writing
- * out[4*i + 0..3] = {min, max, max|x|, count} (host array; all zero when an
- * array has no finite value). It allocates nothing: the reduction's
- * accumulators are a fixed 32 KiB device array inside the library, sized for
- * IPC_NOALLOC_MAX_FIELDS arrays per call; more arrays are rejected with
- * IPC_EINVAL. Every GPU that loads the library holds that array until the
- * process exits. The first call on a device looks up the array's address
- * (with that device current), so make that first call before any stream
- * capture. Calls share the array: this process serialises them, and the
- * call synchronises `stream` before returning, but calls from other threads
- * of work that overlap on the GPU through other means would race on it. */
+ * allocate device memory -- a process whose device memory is all owned by
+ * another pool or allocator, or a loop that must keep a fixed footprint. It
+ * computes, for each of nfields device arrays of n[i] elements of `dtype`,
+ * the minimum, maximum and maximum |x| over the finite values and their
+ * count (the range step of ipc_compress), writing out[4*i + 0..3] = {min,
+ * max, max|x|, count} (host array; all zero when an array has no finite
+ * value; max|x| of signed zeros is +0). It allocates nothing: the
+ * reduction's accumulators are a fixed 32 KiB device array inside the
+ * library, sized for IPC_NOALLOC_MAX_FIELDS arrays per call; more arrays
+ * are rejected with IPC_EINVAL. Every GPU that loads the library holds that
+ * array until the process exits. Each call looks up the array's address for
+ * the current device before it queues any work. The results are decoded on
+ * the host, so the call waits for `stream` before it returns; a stream that
+ * is being captured is refused with IPC_EINVAL before anything is queued.
+ * Calls share the array: this process serialises them, but work that
+ * overlaps on the GPU through other means (another process loading the
+ * library runs on its own copy) would race on it. */
 #define IPC_NOALLOC_MAX_FIELDS 1024
 int ipc_range_noalloc(int nfields, const void* const* d_in, const uint64_t* n, int dtype,
                       void* stream, double* out);

@@ -1251,6 +1251,10 @@ int parse_head(const uint8_t* p, uint64_t len, ipc_field* f, uint64_t* pos_out,
   return IPC_OK;
 }
 
+namespace ipc {
+void set_last_error(const char* what) { g_err = what; }
+}  // namespace ipc
+
 // ===========================================================================
 extern "C" {
 

@@ -236,4 +236,7 @@ cudaError_t launch_unpack(const StageArgs& a, const StageDescs& d, uint64_t nseg
                           const uint32_t* blob, uint32_t* tmp, uint32_t* cap, uint32_t* bm,
                           unsigned int* flags, cudaStream_t st);
 
+// Sets the message ipc_last_error() returns on the calling thread.
+void set_last_error(const char* what);
+
 }  // namespace ipc

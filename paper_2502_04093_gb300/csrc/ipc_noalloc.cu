@@ -1,13 +1,14 @@
 // Allocation-free variant of the range reduction (min, max, max|x| and the
-// finite count of device arrays), for callers that may not allocate memory:
-// code running inside a CUDA graph capture, in a process whose memory is all
-// handed out by another pool, or in a loop with a fixed memory footprint.
+// finite count of device arrays), for callers that may not allocate device
+// memory: a process whose device memory is all handed out by another pool or
+// allocator, or a loop that must keep a fixed memory footprint.
 //
 // The reduction's accumulators live in one fixed device array of this file
 // (kMaxFields sets of 4 words, 32 KiB). Every GPU that loads the library
 // holds it until the process exits. Host code cannot use the array's name as
-// a device address, so the address is looked up once per device (the first
-// call on that device, with it current) and passed to the kernel.
+// a device address, so every call looks the address up (with the calling
+// thread's current device, before any work is queued) and passes it to the
+// kernels; a looked-up address therefore never outlives a context reset.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,6 +16,7 @@
 #include <mutex>
 
 #include "ipc.h"
+#include "ipc_internal.h"
 
 namespace {
 
@@ -26,7 +28,6 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned long long g_range_scratch[4 * kMaxFields];
 
 std::mutex g_mu;  // one call at a time in this process (they share the array)
-unsigned long long* g_addr[kMaxDevices] = {};
 
 __device__ __forceinline__ unsigned long long okey(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) k_range_noalloc(const T* __restrict__ x, 
   for (uint64_t i = tid; i < n; i += nth) {
     const T v = __ldg(x + i);
     if (!isfinite(v)) continue;
-    const T a = v < 0 ? -v : v;
+    const T a = fabs(v);  // +0 for -0: the bits of max|x| are compared as integers
     mn = cnt ? (v < mn ? v : mn) : v;
     mx = cnt ? (v > mx ? v : mx) : v;
     ma = cnt ? (a > ma ? a : ma) : a;
@@ -89,28 +90,55 @@ __global__ void __launch_bounds__(256) k_range_noalloc(const T* __restrict__ x, 
 
 extern "C" int ipc_range_noalloc(int nfields, const void* const* d_in, const uint64_t* n,
                                  int dtype, void* stream, double* out) {
-  if (nfields < 0 || (nfields > 0 && (!d_in || !n || !out))) return IPC_EINVAL;
-  if (nfields > kMaxFields) return IPC_EINVAL;  // beyond the fixed scratch
-  if (dtype != IPC_F32 && dtype != IPC_F64) return IPC_EINVAL;
+  using ipc::set_last_error;
+  if (nfields < 0 || (nfields > 0 && (!d_in || !n || !out))) {
+    set_last_error("ipc_range_noalloc: null argument or negative count");
+    return IPC_EINVAL;
+  }
+  if (nfields > kMaxFields) {  // beyond the fixed scratch
+    set_last_error("ipc_range_noalloc: more arrays than IPC_NOALLOC_MAX_FIELDS");
+    return IPC_EINVAL;
+  }
+  if (dtype != IPC_F32 && dtype != IPC_F64) {
+    set_last_error("ipc_range_noalloc: dtype must be IPC_F32 or IPC_F64");
+    return IPC_EINVAL;
+  }
   if (nfields == 0) return IPC_OK;
   for (int i = 0; i < nfields; ++i)
-    if (!d_in[i] && n[i]) return IPC_EINVAL;
+    if (!d_in[i] && n[i]) {
+      set_last_error("ipc_range_noalloc: null array with a nonzero size");
+      return IPC_EINVAL;
+    }
+  cudaStream_t st = (cudaStream_t)stream;
+  // The call ends with a host wait on `stream`, which a capturing stream
+  // does not allow: refuse before anything is queued, so the caller's
+  // capture stays intact.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("ipc_range_noalloc: cudaStreamIsCapturing failed");
+    return IPC_ECUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) {
+    set_last_error("ipc_range_noalloc: the stream is being captured; the call waits on it");
+    return IPC_EINVAL;
+  }
   std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
+    set_last_error("ipc_range_noalloc: no current device");
     return IPC_ECUDA;
   }
-  if (!g_addr[dev]) {  // set-up, once per device, with that device current
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_range_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return IPC_ECUDA;
-    }
-    g_addr[dev] = (unsigned long long*)p;
+  // The array's device address, with this device current (a host-side
+  // lookup; it allocates nothing).
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_range_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    set_last_error("ipc_range_noalloc: cudaGetSymbolAddress failed");
+    return IPC_ECUDA;
   }
-  unsigned long long* acc = g_addr[dev];
-  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* acc = (unsigned long long*)p;
   // the array keeps the previous call's contents: reset the used part
   k_range_init<<<(nfields + 127) / 128, 128, 0, st>>>(acc, nfields);
   for (int i = 0; i < nfields; ++i) {
@@ -128,7 +156,10 @@ extern "C" int ipc_range_noalloc(int nfields, const void* const* d_in, const uin
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, acc, 32 * (size_t)nfields, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return IPC_ECUDA;
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return IPC_ECUDA;
+  }
   for (int i = 0; i < nfields; ++i) {
     unsigned long long w[4];
     std::memcpy(w, out + 4 * i, 32);

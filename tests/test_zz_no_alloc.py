@@ -1,8 +1,9 @@
 """ipc_range_noalloc: the range reduction for callers that cannot allocate
-(graph capture, externally owned memory pools, fixed-footprint loops).
-Through the C ABI, on two calls in a row, its results must equal what the
-allocating path computes (ipc_compress's range, read back with
-ipc_field_info) and the exact numpy values. This file is collected last."""
+device memory (a process whose memory is owned by another pool or allocator,
+a loop with a fixed footprint). Through the C ABI, on two calls in a row, its
+results must equal what the allocating path computes (ipc_compress's range,
+read back with ipc_field_info) and the exact numpy values; a warm call must
+leave the device's free memory unchanged. This file is collected last."""
 import ctypes as C
 
 import numpy as np
@@ -82,3 +83,56 @@ def test_rejects_more_arrays_than_the_scratch_holds(lib):
     assert rc == ipc.IPC_EINVAL
     rc, got = call(lib, [t] * 3, 0)
     assert rc == 0 and (got[:, :3] == 1.0).all() and (got[:, 3] == 4).all()
+
+
+def test_signed_zeros(lib):
+    """max|x| of signed zeros is +0 (an all -0.0 array, and a mixed one)."""
+    for dt, code in ((np.float32, 0), (np.float64, 1)):
+        neg = np.full(3000, -0.0, dtype=dt)
+        mixed = np.zeros(5000, dtype=dt)
+        mixed[::3] = -0.0
+        mixed[1::7] = dt(-2.5)
+        mixed[2::11] = dt(1.25)
+        ts = [torch.from_numpy(neg).cuda(), torch.from_numpy(mixed).cuda()]
+        rc, got = call(lib, ts, code)
+        assert rc == 0
+        assert got[0, 2] == 0.0 and not np.signbit(got[0, 2])
+        assert got[0, 0] == 0.0 and got[0, 1] == 0.0 and got[0, 3] == 3000
+        fin = mixed.astype(np.float64)
+        assert got[1, 0] == fin.min() and got[1, 1] == fin.max()
+        assert got[1, 2] == np.abs(fin).max() == 2.5 and got[1, 3] == 5000
+
+
+def test_warm_call_allocates_nothing(lib):
+    xs = make_batch(3, np.float32)
+    ts = [torch.from_numpy(x).cuda() for x in xs]
+    rc, first = call(lib, ts, 0)
+    assert rc == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rc, again = call(lib, ts, 0)
+        assert rc == 0 and np.array_equal(first, again)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_capturing_stream_is_refused_and_capture_survives(lib):
+    from paper_2502_04093_gb300 import ipc
+    a = torch.arange(64, device="cuda", dtype=torch.float32)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        b = a * 2.0  # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b = a * 2.0
+        rc, _ = call(lib, [a], 0)
+    assert rc == ipc.IPC_EINVAL
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b, a * 2.0)
+    rc, got = call(lib, [a], 0)  # usable again outside the capture
+    assert rc == 0 and got[0, 1] == 63.0 and got[0, 3] == 64
