@@ -304,6 +304,13 @@ struct ipco_view {
   std::vector<int> b; /* b[l-1] */
   uint64_t bytes;
   double bound;
+  /* State of Algorithm 2: per stage, the loaded negabinary digits of every
+   * code (planes >= b_l, the others zero), and the rounding allowance, in
+   * units of eb * 2^-16, that the current reconstruction carries against the
+   * compressor's values (the rounding margins of a fresh selection, plus
+   * the margin of every incremental step since). */
+  std::vector<std::vector<uint32_t>> N;
+  uint64_t racc = 0;
 };
 
 namespace {
@@ -503,6 +510,7 @@ uint64_t stage_M(const StageData& sd, int b) {
 struct Options {
   std::vector<uint64_t> cost;  /* K x 33 */
   std::vector<uint64_t> bytes; /* K x 33 */
+  std::vector<uint64_t> rho;   /* K: the rounding margin in cost(l, b > 0) */
 };
 
 void option_tables(const ipco_field* f, double A, Options* o) {
@@ -532,12 +540,14 @@ void option_tables(const ipco_field* f, double A, Options* o) {
   double kappa = cubic ? 24.0 : 12.0;
   o->cost.assign((size_t)K * 33, 0);
   o->bytes.assign((size_t)K * 33, 0);
+  o->rho.assign((size_t)K, 0);
   for (int l = 1; l <= K; ++l) {
     /* rounding margin: every stage at this level or finer recomputes. */
     double asum = 0;
     for (int t = 0; t < S; ++t)
       if (g.stages[t].level <= l) asum += (f->bound == 0 && cubic) ? P[S - 1 - t] : 1.0;
     uint64_t rho = ceil_units(kappa * u * (A / f->eb) * 65536.0 * asum);
+    o->rho[l - 1] = f->bound == 0 ? rho : 0;
     for (int b = 0; b <= 32; ++b) {
       uint64_t c = 0, y = 0;
       uint64_t mmax = 0;
@@ -627,9 +637,18 @@ double range_of(const ipco_field* f) { return f->xmax - f->xmin; }
 
 /* Choose a selection for a target. Returns the selection, bytes and the
  * guaranteed L-inf bound (absolute). upper != null constrains b'_l <= b_l. */
+uint64_t rounding_part(const Options& o, const std::vector<int>& b) {
+  uint64_t r = 0;
+  for (size_t l = 0; l < b.size(); ++l)
+    if (b[l] > 0) r = sat_add(r, o.rho[l]);
+  return r;
+}
+
+/* rparts (optional): [0] = the rounding margins in the selection's cost
+ * (sum of rho_l over levels with b_l > 0), [1] = the rest (truncation). */
 int choose(const ipco_field* f, int kind, double value,
            const std::vector<int>* upper, std::vector<int>* b,
-           uint64_t* bytes, double* bound) {
+           uint64_t* bytes, double* bound, uint64_t* rparts = nullptr) {
   const int K = f->g.K;
   if (!std::isfinite(value)) return IPCO_EINVAL;
   Options o;
@@ -645,6 +664,7 @@ int choose(const ipco_field* f, int kind, double value,
     if (rc) return rc;
     *bytes = loaded_bytes(f, *b);
     *bound = f->eb + (double)total_cost(o, *b) * f->eb / 65536.0;
+    if (rparts) { rparts[0] = rounding_part(o, *b); rparts[1] = total_cost(o, *b) - rparts[0]; }
     return IPCO_OK;
   }
   if (kind == 1) {
@@ -666,6 +686,7 @@ int choose(const ipco_field* f, int kind, double value,
       G = f->eb + (double)total_cost(o, *b) * f->eb / 65536.0;
     }
     *bound = G;
+    if (rparts) { rparts[0] = rounding_part(o, *b); rparts[1] = total_cost(o, *b) - rparts[0]; }
     return IPCO_OK;
   }
   return IPCO_EINVAL;
@@ -729,6 +750,159 @@ int reconstruct_t(const ipco_field* f, const std::vector<int>& bsel, T* out) {
 int reconstruct(const ipco_field* f, const std::vector<int>& b, void* out) {
   if (f->dtype == 0) return reconstruct_t<float>(f, b, (float*)out);
   return reconstruct_t<double>(f, b, (double*)out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Incremental reconstruction (Algorithm 2, Sec. 4.3).                       */
+/* Reading: a refinement loads only the encoded planes b'_l .. b_l - 1 of   */
+/* each level. Each new digit is decoded from its encoded bit and the two   */
+/* more significant digits (Sec. 4.4.1); for the top two new planes those   */
+/* are the lowest two loaded digits, which the view keeps. The increment of */
+/* a code, dq, is the value of its new digits; it is dequantized            */
+/* (dq * 2e_q) and interpolated level by level from zero -- the Delta of    */
+/* Algorithm 2, zero at outliers, whose values are exact already -- and     */
+/* x^new = x^old + Delta wherever Delta is not zero.                        */
+/* ------------------------------------------------------------------------ */
+
+/* The loaded digits (planes >= b) of every code of stage t. */
+int loaded_digits(const ipco_field* f, size_t t, int b, std::vector<uint32_t>* N) {
+  const StageGeom& sg = f->g.stages[t];
+  const StageData& sd = f->st[t];
+  const uint64_t m = (uint64_t)sg.m[2];
+  std::vector<uint32_t> E(sg.ncodes, 0), words;
+  for (int k = 31; k >= b; --k) {
+    if (!decode_stream(f->bytes.data() + sd.offset[k], sd.size[k], sg.words, &words))
+      return IPCO_ECORRUPT;
+    for (uint64_t r = 0; r < sg.rows; ++r)
+      for (uint64_t j = 0; j < sg.wr; ++j)
+        for (uint64_t i = 0; i < 32 && 32 * j + i < m; ++i)
+          E[r * m + 32 * j + i] |= ((words[r * sg.wr + j] >> i) & 1u) << k;
+  }
+  N->assign(sg.ncodes, 0);
+  for (uint64_t ci = 0; ci < sg.ncodes; ++ci) (*N)[ci] = xor_decode(E[ci]) & plane_mask(b);
+  return IPCO_OK;
+}
+
+int all_loaded_digits(const ipco_field* f, const std::vector<int>& b,
+                      std::vector<std::vector<uint32_t>>* N) {
+  N->assign(f->g.stages.size(), {});
+  for (size_t t = 0; t < f->g.stages.size(); ++t) {
+    int rc = loaded_digits(f, t, b[f->g.stages[t].level - 1], &(*N)[t]);
+    if (rc) return rc;
+  }
+  return IPCO_OK;
+}
+
+/* Digits bn .. bo-1 of one code, from its encoded bits e (only those planes
+ * are read) and its loaded digits nold (planes >= bo, the rest zero),
+ * decoded top-down. Returns the new digits alone. */
+uint32_t decode_window(uint32_t e, uint32_t nold, int bn, int bo) {
+  uint32_t n = nold;
+  for (int k = bo - 1; k >= bn; --k) {
+    const uint32_t ek = (e >> k) & 1u;
+    const uint32_t p1 = k + 1 <= 31 ? (n >> (k + 1)) & 1u : 0u;
+    const uint32_t p2 = k + 2 <= 31 ? (n >> (k + 2)) & 1u : 0u;
+    n |= (ek ^ p1 ^ p2) << k;
+  }
+  return n & plane_mask(bn) & ~plane_mask(bo);
+}
+
+/* Algorithm 2 on the host: Delta from the new planes, then out += Delta.
+ * On success N holds the digits of the new selection. */
+template <class T>
+int delta_t(const ipco_field* f, const std::vector<int>& bold, const std::vector<int>& bnew,
+            std::vector<std::vector<uint32_t>>* N, T* out) {
+  const Geometry& g = f->g;
+  const T twoeb = (T)(2.0 * half_bin(f->eb, f->xmaxabs, f->dtype));
+  const bool cubic = f->interp == 1;
+  const int64_t stride[3] = {g.N[1] * g.N[2], g.N[2], 1};
+  std::vector<T> D(g.n, (T)0);  /* Delta; the anchor never changes */
+  std::vector<std::vector<uint32_t>> Nn = *N;
+  std::vector<uint32_t> words;
+  for (size_t t = 0; t < g.stages.size(); ++t) {
+    const StageGeom& sg = g.stages[t];
+    const StageData& sd = f->st[t];
+    const int bo = bold[sg.level - 1], bn = bnew[sg.level - 1];
+    const uint64_t m = (uint64_t)sg.m[2];
+    /* the encoded bits of the new planes only */
+    std::vector<uint32_t> E(sg.ncodes, 0);
+    for (int k = bo - 1; k >= bn; --k) {
+      if (!decode_stream(f->bytes.data() + sd.offset[k], sd.size[k], sg.words, &words))
+        return IPCO_ECORRUPT;
+      for (uint64_t r = 0; r < sg.rows; ++r)
+        for (uint64_t j = 0; j < sg.wr; ++j)
+          for (uint64_t i = 0; i < 32 && 32 * j + i < m; ++i)
+            E[r * m + 32 * j + i] |= ((words[r * sg.wr + j] >> i) & 1u) << k;
+    }
+    const int d = sg.dim3;
+    const int64_t s = (int64_t)1 << (sg.level - 1);
+    size_t oi = 0;
+    uint64_t ci = 0;
+    for (int64_t c0 = 0; c0 < sg.m[0]; ++c0)
+      for (int64_t c1 = 0; c1 < sg.m[1]; ++c1)
+        for (int64_t c2 = 0; c2 < sg.m[2]; ++c2, ++ci) {
+          int64_t i[3] = {sg.start[0] + c0 * sg.step[0],
+                          sg.start[1] + c1 * sg.step[1],
+                          sg.start[2] + c2 * sg.step[2]};
+          int64_t idx = i[0] * stride[0] + i[1] * stride[1] + i[2];
+          if (oi < sd.outliers.size() && sd.outliers[oi].first == ci) {
+            D[idx] = (T)0;  /* an outlier's value is exact: no increment */
+            ++oi;
+            continue;
+          }
+          int64_t base = idx - i[d] * stride[d];
+          T pred = predict<T>(D.data(), base, stride[d], i[d], s, g.N[d], cubic);
+          uint32_t nd = bn < bo ? decode_window(E[ci], (*N)[t][ci], bn, bo) : 0u;
+          int64_t dq = negabinary_inv(nd);  /* value of the new digits */
+          T r = (T)dq * twoeb;
+          D[idx] = pred + r;
+          Nn[t][ci] |= nd;
+        }
+  }
+  for (uint64_t i = 0; i < g.n; ++i)
+    if (D[i] != (T)0) out[i] = out[i] + D[i];
+  *N = std::move(Nn);
+  return IPCO_OK;
+}
+
+/* Guaranteed bound of an incremental result (strict mode). Relative to the
+ * compressor's values, x^old + Delta differs from the truncated exact
+ * reconstruction of the new selection by the old result's rounding (the
+ * view's allowance), the rounding of Delta and that of the final addition.
+ * Delta is interpolated from zero, so it is exactly zero above the coarsest
+ * changed level l_c; below, each stage rounds by at most (kappa / 2) u D in
+ * the worst case (the per-computation share of the margin kappa, with D =
+ * G_old + G_new bounding |Delta|), amplified like any stage error (a_t).
+ * The addition rounds by u (max|x| + 2D) at most. Paper mode carries no
+ * rounding model: the bound is the selection's. */
+void delta_bound(const ipco_field* f, const ipco_view* v, const std::vector<int>& b,
+                 double Gnew, const uint64_t* rparts, double* Gd, uint64_t* racc) {
+  if (f->bound != 0) { *Gd = Gnew; *racc = 0; return; }
+  const Geometry& g = f->g;
+  const int S = (int)g.stages.size();
+  const bool cubic = f->interp == 1;
+  int lc = 0;
+  for (int l = 1; l <= g.K; ++l)
+    if (b[l - 1] < v->b[l - 1]) lc = l;
+  std::vector<double> P(S + 1);
+  P[0] = 1.0;
+  for (int i = 1; i <= S; ++i) P[i] = P[i - 1] * (cubic ? 1.25 : 1.0);
+  double asum = 0;
+  for (int t = 0; t < S; ++t)
+    if (g.stages[t].level <= lc) asum += P[S - 1 - t];
+  const double u = f->dtype == 0 ? Prec<float>::unit() : Prec<double>::unit();
+  const double D = v->bound + Gnew;
+  const double half_kappa = cubic ? 12.0 : 6.0;
+  const uint64_t eps = sat_add(ceil_units(half_kappa * u * (D / f->eb) * 65536.0 * asum),
+                               ceil_units(u * ((f->xmaxabs + 2.0 * D) / f->eb) * 65536.0));
+  *racc = sat_add(v->racc, eps);
+  *Gd = f->eb + (double)sat_add(rparts[1], *racc) * f->eb / 65536.0;
+}
+
+/* Absolute error target of an eb-mode request. */
+double target_abs(const ipco_field* f, double value) {
+  if (f->eb_mode == 1) { double r = range_of(f); return r > 0 ? value * r : value; }
+  return value;
 }
 
 /* Parse a container (import) and rebuild the per-stage tables. */
@@ -870,7 +1044,8 @@ int ipco_retrieve(const ipco_field* f, int kind, double value, void* out,
   std::vector<int> b;
   uint64_t bytes = 0;
   double bound = 0;
-  int rc = choose(f, kind, value, nullptr, &b, &bytes, &bound);
+  uint64_t rp[2] = {0, 0};
+  int rc = choose(f, kind, value, nullptr, &b, &bytes, &bound, rp);
   if (rc) return rc;
   rc = reconstruct(f, b, out);
   if (rc) return rc;
@@ -878,6 +1053,9 @@ int ipco_retrieve(const ipco_field* f, int kind, double value, void* out,
     ipco_view* v = new (std::nothrow) ipco_view();
     if (!v) return IPCO_ENOMEM;
     v->f = f; v->b = b; v->bytes = bytes; v->bound = bound;
+    v->racc = rp[0];
+    rc = all_loaded_digits(f, b, &v->N);
+    if (rc) { delete v; return rc; }
     *view = v;
   }
   return IPCO_OK;
@@ -888,7 +1066,8 @@ int ipco_refine(ipco_view* v, int kind, double value, void* out) {
   std::vector<int> b;
   uint64_t bytes = 0;
   double bound = 0;
-  int rc = choose(v->f, kind, value, &v->b, &b, &bytes, &bound);
+  uint64_t rp[2] = {0, 0};
+  int rc = choose(v->f, kind, value, &v->b, &b, &bytes, &bound, rp);
   /* A target that the current selection already meets (or, in bitrate
    * mode, one below what is already loaded) leaves the view unchanged. */
   if (rc == IPCO_EBUDGET && kind == 1) return IPCO_OK;
@@ -896,8 +1075,55 @@ int ipco_refine(ipco_view* v, int kind, double value, void* out) {
   if (b == v->b) return IPCO_OK;
   rc = reconstruct(v->f, b, out);
   if (rc) return rc;
+  std::vector<std::vector<uint32_t>> N;
+  rc = all_loaded_digits(v->f, b, &N);
+  if (rc) return rc;
   v->b = b; v->bytes = bytes; v->bound = bound;
+  v->N = std::move(N);
+  v->racc = rp[0];
   return IPCO_OK;
+}
+
+int ipco_refine_delta(ipco_view* v, int kind, double value, void* out, int* incremental) {
+  if (!v || !out) return IPCO_EINVAL;
+  if (incremental) *incremental = 0;
+  const ipco_field* f = v->f;
+  std::vector<int> b;
+  uint64_t bytes = 0;
+  double bound = 0;
+  uint64_t rp[2] = {0, 0};
+  int rc = choose(f, kind, value, &v->b, &b, &bytes, &bound, rp);
+  if (rc == IPCO_EBUDGET && kind == 1) return IPCO_OK;
+  if (rc) return rc;
+  if (b == v->b) return IPCO_OK;
+  double Gd = 0;
+  uint64_t racc = 0;
+  delta_bound(f, v, b, bound, rp, &Gd, &racc);
+  /* the incremental result is taken when its bound meets the target (an
+   * error target) or always (a bitrate target); otherwise the refinement
+   * reconstructs from scratch */
+  if (kind == 1 || Gd <= target_abs(f, value)) {
+    rc = f->dtype == 0 ? delta_t<float>(f, v->b, b, &v->N, (float*)out)
+                       : delta_t<double>(f, v->b, b, &v->N, (double*)out);
+    if (rc) return rc;
+    v->b = b; v->bytes = bytes; v->bound = Gd; v->racc = racc;
+    if (incremental) *incremental = 1;
+    return IPCO_OK;
+  }
+  rc = reconstruct(f, b, out);
+  if (rc) return rc;
+  std::vector<std::vector<uint32_t>> N;
+  rc = all_loaded_digits(f, b, &N);
+  if (rc) return rc;
+  v->b = b; v->bytes = bytes; v->bound = bound;
+  v->N = std::move(N);
+  v->racc = rp[0];
+  return IPCO_OK;
+}
+
+uint32_t ipco_decode_window(uint32_t e, uint32_t nold, int bn, int bo) {
+  if (bn < 0 || bo > 32 || bn > bo) return 0;
+  return decode_window(e, nold, bn, bo);
 }
 
 int ipco_reconstruct(const ipco_field* f, const int* b, void* out) {

@@ -45,6 +45,16 @@ int ipco_retrieve(const ipco_field* f, int kind, double value, void* out,
                   ipco_view** view);
 /* Canonical refinement: selection constrained to b'_l <= b_l. */
 int ipco_refine(ipco_view* v, int kind, double value, void* out);
+/* Incremental refinement (Algorithm 2): `out` must hold the view's current
+ * reconstruction. The same constrained selection as ipco_refine; only the
+ * new planes are read, and out += Delta. The incremental result is used when
+ * its guaranteed bound (which adds the rounding of the increment) meets an
+ * error target, or for a bitrate target; otherwise the refinement
+ * reconstructs from scratch. *incremental (optional) tells which ran. */
+int ipco_refine_delta(ipco_view* v, int kind, double value, void* out, int* incremental);
+/* The digits bn..bo-1 of a code from its encoded bits e and its loaded
+ * digits nold (planes >= bo), decoded top-down (for the coding pins). */
+uint32_t ipco_decode_window(uint32_t e, uint32_t nold, int bn, int bo);
 /* Reconstruction for an explicit per-level selection b[0..K-1]
  * (b[l-1] = planes dropped at level l). */
 int ipco_reconstruct(const ipco_field* f, const int* b, void* out);

@@ -55,6 +55,9 @@ def lib() -> C.CDLL:
         L.ipco_free_view.argtypes = [vp]
         L.ipco_retrieve.argtypes = [vp, C.c_int, C.c_double, vp, C.POINTER(vp)]
         L.ipco_refine.argtypes = [vp, C.c_int, C.c_double, vp]
+        L.ipco_refine_delta.argtypes = [vp, C.c_int, C.c_double, vp, C.POINTER(C.c_int)]
+        L.ipco_decode_window.argtypes = [C.c_uint32, C.c_uint32, C.c_int, C.c_int]
+        L.ipco_decode_window.restype = C.c_uint32
         L.ipco_reconstruct.argtypes = [vp, C.POINTER(C.c_int), vp]
         L.ipco_selection.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
                                      C.POINTER(C.c_double)]
@@ -186,6 +189,14 @@ class View:
                "ipco_refine")
         return self.out
 
+    def refine_delta(self, kind: int, value: float):
+        """Algorithm 2 on the view's output array (updated in place); returns
+        (output, whether the incremental path ran)."""
+        inc = C.c_int()
+        _check(lib().ipco_refine_delta(self.h, kind, float(value), self.out.ctypes.data,
+                                       C.byref(inc)), "ipco_refine_delta")
+        return self.out, bool(inc.value)
+
     def selection(self):
         K = self.field.info()["K"]
         b = (C.c_int * max(K, 1))()
@@ -264,6 +275,10 @@ def xor_encode(n: int) -> int:
 
 def xor_decode(e: int) -> int:
     return lib().ipco_xor_decode(e)
+
+
+def decode_window(e: int, nold: int, bn: int, bo: int) -> int:
+    return int(lib().ipco_decode_window(e & 0xFFFFFFFF, nold & 0xFFFFFFFF, bn, bo))
 
 
 def xor_check(start: int, count: int, step: int) -> int:

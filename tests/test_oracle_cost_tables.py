@@ -72,9 +72,16 @@ def exact_f64(v: Fr) -> float:
     return f
 
 
-def build_field(shape, codes, cubic, anchor, g):
+def exact_f32(v: Fr) -> float:
+    f = float(np.float32(float(v)))
+    assert Fr(f) == v, "not exactly representable in f32: %s" % v
+    return f
+
+
+def build_field(shape, codes, cubic, anchor, g, exact_f64=exact_f64):
     """Values whose codes are exactly `codes` (one list per stage) for bin g.
-    Checks that every intermediate of the f64 predictor is exact."""
+    Checks that every intermediate of the predictor is exact (in f64, or in
+    the type whose check is passed as exact_f64)."""
     N, K, st = stage_list(shape)
     assert len(st) == len(codes)
     xh = {(0, 0, 0): Fr(anchor)}
@@ -138,8 +145,9 @@ def M_of(H, Q, b):
     return uncert(b) if b <= H else Q
 
 
-def expected_costs(st, HQ, K, cubic, strict, bin_rel, A_over_eb):
-    """The cost table of the module docstring, in exact rationals."""
+def expected_costs(st, HQ, K, cubic, strict, bin_rel, A_over_eb, u=U53):
+    """The cost table of the module docstring, in exact rationals (u: the
+    element type's unit roundoff)."""
     S = len(st)
     p = P if cubic else Fr(1)
     kappa = 24 if cubic else 12
@@ -147,7 +155,7 @@ def expected_costs(st, HQ, K, cubic, strict, bin_rel, A_over_eb):
     for l in range(1, K + 1):
         ts = [t for t in range(S) if st[t][0] == l]
         asum = sum((p ** (S - 1 - t) if strict else 1) for t in range(S) if st[t][0] <= l)
-        rho_exact = kappa * U53 * A_over_eb * 65536 * asum
+        rho_exact = kappa * u * A_over_eb * 65536 * asum
         if strict:
             # the oracle evaluates the margin in f64: keep it off an integer
             assert abs(rho_exact - round(rho_exact)) > Fr(1, 10 ** 9)
