@@ -361,8 +361,10 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = e2e_measure(ipc, x, args, world)
-    del out, outs_br
     extra = {}
+    if not args.no_systems:
+        extra["refine_chain"] = measure_refine_chain(ipc, x, out)
+    del out, outs_br
     if not args.no_systems:
         del x
         torch.cuda.empty_cache()
@@ -463,15 +465,35 @@ def e2e_measure(ipc, x, args, world):
 
     for _ in range(max(1, args.warmup)):
         step()
-    steps = max(1, min(args.steps, 5))
+    # every step ends with a device synchronisation, so each one is timed on
+    # the host clock on its own; the value is the median step
+    per = []
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
         computed, d2h = step()
-    t1 = time.perf_counter()
-    sec = max_over_ranks((t1 - t0) / steps, x.device, world)
+        per.append(time.perf_counter() - t0)
+    sec = max_over_ranks(statistics.median(per), x.device, world)
+    # the host link as this run sees it: one field-sized pinned copy each way
+    link = {}
+    for name, src, dst in (("h2d_GBps", hx, dxs[0]), ("d2h_GBps", outs[0], houts[0])):
+        ms = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            dst.copy_(src, non_blocking=True)
+            b.record(main)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        link[name] = round(nbytes / (min(ms) * 1e-3) / 1e9, 1)
+    # what the copies alone would take at those rates (no overlap with work)
+    link["copy_bound_ms"] = round(1e3 * (nbytes / (link["h2d_GBps"] * 1e9) +
+                                         d2h / (link["d2h_GBps"] * 1e9)), 2)
     return {"value": round(job_gbs(world, nbytes * (1 + computed), 1, sec), 2), "unit": "GB/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h,
+            "steps": len(per), "ms_per_step_median": round(1e3 * statistics.median(per), 2),
+            "ms_per_step_min": round(1e3 * min(per), 2), "ms_per_step_max": round(1e3 * max(per), 2),
+            "link": link,
             "overlap": "device->host copies on a second stream under the next reconstruction; "
                        "the next step's host->device input copy on a third stream under this "
                        "step's reconstructions"}
@@ -516,6 +538,22 @@ def measure_batched(ipc, synth, torch):
 
     cb = _events_ms(torch, comp_batched)
     cs = _events_ms(torch, comp_single)
+    # where the batched compression's time goes: device time of its kernels
+    # by kind (events around each launch) and the host's wall time
+    torch.cuda.synchronize()
+    ipc.ipc_profile_enable(True)
+    ipc.ipc_profile_reset()
+    t0 = time.perf_counter()
+    comp_batched()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3
+    ipc.ipc_profile_enable(False)
+    kinds = {}
+    for k, name in enumerate(ipc.IPC_KERNEL_NAMES):
+        n, ms, _ = ipc.ipc_profile_read(k)
+        if n:
+            kinds[name] = {"launches": n, "ms": round(ms, 3)}
+    cb_split = {"wall_ms": round(wall, 3), "kernels": kinds}
     hs = ipc.ipc_compress_batch(xs, 1e-4, ipc.IPC_EB_REL)
     csize = sum(ipc.ipc_compressed_size(h) for h in hs)
     rng = np.random.default_rng(1303)
@@ -534,6 +572,7 @@ def measure_batched(ipc, synth, torch):
                         "rel eb 1e-4; retrieves at eb log-uniform [1e-4, 1e-1]",
             "bytes": nbytes, "compression_ratio": round(nbytes / csize, 2),
             "compress_batched_ms": round(cb, 3), "compress_per_field_ms": round(cs, 3),
+            "compress_batched_split": cb_split,
             "compress_batched_gbs": gbs(cb), "compress_per_field_gbs": gbs(cs),
             "retrieve_batched_ms": round(rb, 3), "retrieve_per_field_ms": round(rs, 3),
             "retrieve_graph_ms": round(rg, 3), "retrieve_batched_gbs": gbs(rb),
@@ -625,6 +664,36 @@ def measure_f64(ipc, synth, torch):
              zip(outs, xs, views))
     for v in views:
         ipc.ipc_free(v)
+
+    # the same chain in the incremental form (Algorithm 2): each field's
+    # retrieval records the view's state; refines add increments where their
+    # bound meets the target
+    def chain_inc():
+        vs = [ipc.ipc_retrieve_ex(h, ipc.IPC_TARGET_EB, 1e-2, o, ipc.IPC_REFINE_INCREMENTAL)
+              for h, o in zip(hs, outs)]
+        n_inc = 0
+        sbytes = 0
+        for E in (1e-4, 1e-6, 1e-8):
+            for v, o in zip(vs, outs):
+                ipc.ipc_refine(v, ipc.IPC_TARGET_EB, E, o)
+                inc, by = ipc.ipc_refine_info(v)
+                n_inc += inc
+                sbytes += by
+        return vs, n_inc, sbytes
+
+    for v in chain_inc()[0]:
+        ipc.ipc_free(v)
+    torch.cuda.synchronize()
+    d, e = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    d.record(st)
+    vs, n_inc, sbytes = chain_inc()
+    e.record(st)
+    torch.cuda.synchronize()
+    im = d.elapsed_time(e)
+    ok_inc = all(float((o - x).abs().max()) <= ipc.ipc_selection(v)[2] for o, x, v in
+                 zip(outs, xs, vs))
+    for v in vs:
+        ipc.ipc_free(v)
     csize = sum(ipc.ipc_compressed_size(h) for h in hs)
     for h in hs:
         ipc.ipc_free(h)
@@ -634,7 +703,44 @@ def measure_f64(ipc, synth, torch):
             "compress_ms": round(cm, 3), "compress_gbs": round(nbytes / (cm * 1e-3) / 1e9, 1),
             "refine_chain_ms": round(rm, 3),
             "refine_chain_gbs": round(4 * nbytes / (rm * 1e-3) / 1e9, 1),
-            "max_error_within_bound": bool(ok)}
+            "max_error_within_bound": bool(ok),
+            "incremental": {"refine_chain_ms": round(im, 3),
+                            "refine_chain_gbs": round(4 * nbytes / (im * 1e-3) / 1e9, 1),
+                            "refines_incremental": n_inc, "refines": 3 * len(xs),
+                            "stream_MB_read_by_refines": round(sbytes / 1e6, 1),
+                            "max_error_within_bound": bool(ok_inc)}}
+
+
+def measure_refine_chain(ipc, x, out):
+    """The bench field's refine chain (1e-1 -> 1e-2 -> ... -> 1e-5) in the
+    canonical and the incremental form: per refine its device time, whether
+    it added an increment, the plane-stream bytes it read and its bound."""
+    import torch
+    res = {}
+    st = torch.cuda.current_stream()
+    f = ipc.ipc_compress(x, EB, ipc.IPC_EB_ABS, ipc.IPC_CUBIC, ipc.IPC_BOUND_STRICT)
+    for name, mode in (("canonical", ipc.IPC_REFINE_CANONICAL),
+                       ("incremental", ipc.IPC_REFINE_INCREMENTAL)):
+        rows = None
+        for rep in range(3):
+            v = ipc.ipc_retrieve_ex(f, ipc.IPC_TARGET_EB, EB_SWEEP[0], out, mode)
+            steps = []
+            for E in EB_SWEEP[1:-1]:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                ipc.ipc_refine(v, ipc.IPC_TARGET_EB, E, out)
+                b.record(st)
+                torch.cuda.synchronize()
+                inc, by = ipc.ipc_refine_info(v)
+                steps.append({"E": E, "ms": round(a.elapsed_time(b), 4), "incremental": inc,
+                              "stream_MB": round(by / 1e6, 2),
+                              "bound": ipc.ipc_selection(v)[2]})
+            ipc.ipc_free(v)
+            rows = steps
+        res[name] = rows
+    ipc.ipc_free(f)
+    torch.cuda.synchronize()
+    return res
 
 
 def serve_stream(ipc, fields, reqs, plain, rate, live_cap=8):

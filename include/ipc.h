@@ -119,13 +119,49 @@ int ipc_autotune_clear(void);
  * is out of range. Any output pointer may be NULL. */
 int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* per_sm);
 
-/* ipc_refine -- Algorithm 2 (incremental reconstruction). The new selection
- * only adds planes (b'_l <= b_l at every level) and minimises the added
- * bytes; d_out (normally the array of the earlier retrieve) is rewritten with
- * a reconstruction bitwise equal to a fresh retrieval of the same planes. A
- * target the view already meets (or, in bitrate mode, a budget below what is
- * loaded) leaves the view and d_out unchanged and returns IPC_OK. */
+/* Refinement forms of a view (Algorithm 2, Sec. 4.3).
+ *  IPC_REFINE_CANONICAL   : a refinement reconstructs from the union of the
+ *      selected planes; the result is bitwise equal to a fresh retrieval of
+ *      the same planes (the default).
+ *  IPC_REFINE_INCREMENTAL : a refinement reads only the newly selected planes
+ *      of each level, plus a per-view state of two bits per code (the digits
+ *      at the two lowest loaded planes, the prefix that decodes the next
+ *      plane down, Sec. 4.4.1), and adds the interpolated increment to the
+ *      array that holds the view's current reconstruction: x += Delta. Its
+ *      guaranteed bound adds the increment's worst-case rounding to the
+ *      canonical one; when that bound misses an error target, the refinement
+ *      runs in the canonical form instead (ipc_refine_info tells which). */
+enum { IPC_REFINE_CANONICAL = 0, IPC_REFINE_INCREMENTAL = 1 };
+
+/* ipc_refine -- Algorithm 2. The new selection only adds planes (b'_l <= b_l
+ * at every level) and minimises the added bytes. d_out: device array of
+ * prod(dims) elements. Canonical form: d_out is rewritten with a
+ * reconstruction bitwise equal to a fresh retrieval of the same planes.
+ * Incremental form: d_out must hold the view's current reconstruction (the
+ * output of its last retrieve or refine, unmodified); it is updated in place.
+ * A target the view already meets (or, in bitrate mode, a budget below what
+ * is loaded) leaves the view and d_out unchanged and returns IPC_OK.
+ * Errors: IPC_EINVAL, IPC_EBOUND, IPC_ENOMEM, IPC_ECUDA. Asynchronous on
+ * `stream`. */
 int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream);
+
+/* ipc_retrieve_ex -- ipc_retrieve whose view refines in `refine_mode`; in the
+ * incremental form the reconstruction also records the view's state (two
+ * bits per code of device memory, held until ipc_free). Errors: those of
+ * ipc_retrieve; IPC_EINVAL for an unknown mode. */
+int ipc_retrieve_ex(ipc_field* f, ipc_target target, void* d_out, void* stream, int refine_mode,
+                    ipc_view** out);
+
+/* ipc_view_set_refine_mode -- switches a view's refinement form. A view
+ * switched to the incremental form records its state during its next
+ * refinement, which therefore runs in the canonical form. */
+int ipc_view_set_refine_mode(ipc_view* v, int refine_mode);
+
+/* ipc_refine_info -- about the view's last refinement that loaded planes:
+ * whether it added an increment (1) or reconstructed (0), and the plane-stream
+ * bytes it read (the new planes alone for an increment; every selected plane
+ * for a reconstruction). Any output pointer may be NULL. */
+int ipc_refine_info(const ipc_view* v, int* incremental, uint64_t* stream_bytes);
 
 /* ipc_free -- frees a field, a view or a plan (NULL is accepted). No work
  * that uses the handle may still be pending on any stream. */
@@ -218,6 +254,10 @@ typedef struct {
   uint64_t max_batch_values; /* values (output elements) per batch; a request past
                                 the limit waits for the next batch, a larger one
                                 runs alone (0: unlimited)                        */
+  int refine_mode;       /* IPC_REFINE_*: the form of REFINE requests; in the
+                            incremental form a view's refines run through its
+                            own increment path (single-field launches on the
+                            batch's stream), not in the batched launch      */
 } ipc_server_cfg;
 enum { IPC_REQ_RETRIEVE = 0, IPC_REQ_REFINE = 1, IPC_REQ_RELEASE = 2 };
 /* RETRIEVE(field, target): a new view with a server-owned output buffer.
@@ -259,8 +299,13 @@ int ipc_server_submit(ipc_server* s, const ipc_request* r, uint64_t* ticket);
 int ipc_server_poll(ipc_server* s, ipc_completion* out, int max, int* n, int timeout_us);
 /* ipc_server_stats -- batches launched, requests launched, output bytes held. */
 int ipc_server_stats(ipc_server* s, uint64_t* batches, uint64_t* requests, uint64_t* mem_used);
-/* ipc_server_destroy -- finishes in-flight work, completes requests that
- * can no longer be admitted with IPC_EBUSY, frees every view. */
+/* ipc_server_stop -- shuts the server down but keeps it pollable: later
+ * submissions return IPC_EBUSY; work in flight finishes; what can still be
+ * admitted runs; queued requests that cannot (e.g. a retrieve waiting for
+ * memory) complete with IPC_EBUSY. Returns when the worker has exited. */
+int ipc_server_stop(ipc_server* s);
+/* ipc_server_destroy -- ipc_server_stop, then frees every view, the streams
+ * and the server. */
 int ipc_server_destroy(ipc_server* s);
 
 /* ---- introspection ------------------------------------------------------- */
@@ -302,7 +347,9 @@ enum {
   IPC_KERNEL_ANCHOR = 3,          /* anchor store                               */
   IPC_KERNEL_PACK = 4,            /* device streams -> container (export)       */
   IPC_KERNEL_UNPACK = 5,          /* container -> device streams (import)       */
-  IPC_KERNEL_KINDS = 6
+  IPC_KERNEL_INCREMENT_LEVEL = 6, /* all sweeps of one level, increment (Alg. 2) */
+  IPC_KERNEL_COARSE = 7,          /* the coarse levels of a reconstruction, one CTA */
+  IPC_KERNEL_KINDS = 8
 };
 /* ipc_profile_enable -- when on, every later launch is bracketed by CUDA
  * events recorded on its stream. */
@@ -311,7 +358,9 @@ int ipc_profile_enable(int on);
  * kernel kind, the number of timed launches, their summed device time (ms)
  * and their summed algorithmic bytes (compress level: input values of its
  * targets + the compacted streams it produced; retrieve level: selected
- * stream bytes + its output values; range: input bytes). */
+ * stream bytes + its output values; increment level: the new planes' stream
+ * bytes + the state words read and written + its output values (at level 1
+ * read and written); range: input bytes). */
 int ipc_profile_read(int kind, uint64_t* launches, double* total_ms, double* alg_bytes);
 /* ipc_profile_reset -- clears the accumulated figures. */
 int ipc_profile_reset(void);

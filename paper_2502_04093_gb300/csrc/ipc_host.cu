@@ -230,6 +230,20 @@ struct ipc_view {
   std::vector<int> b;
   uint64_t bytes;
   double bound;
+  // Refinement form (IPC_REFINE_*). An incremental view keeps, per code word
+  // of every stage, the digits of its 32 codes at the two lowest loaded
+  // planes (`d_state`, two words per word, stage by stage), and the rounding
+  // allowance of its current reconstruction (units of eb * 2^-16).
+  int mode = IPC_REFINE_CANONICAL;
+  int state_device = 0;           // the device of d_state
+  uint32_t* d_state = nullptr;    // two buffers of state_words words each
+  uint64_t state_words = 0;
+  int state_cur = 0;              // the buffer that holds the current state
+  std::vector<uint64_t> state_off;  // per stage, word offset into a buffer
+  bool state_valid = false;
+  uint64_t racc = 0;
+  int last_incremental = 0;   // the last refinement added an increment
+  uint64_t last_stream_bytes = 0;  // plane-stream bytes that refinement read
 };
 
 struct ipc_plan {
@@ -640,14 +654,16 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     if ((rc = grow(&ws.small, &dummy, 5 * nf + 1, 8))) return rc;
     ws.small_words = 5 * nf + 1;
   }
+  // small: [range accumulators, 4 per field | first values, 1 per field | outlier count]
   if (ws.ocap == 0) {
     uint64_t oc = 0;
     if ((rc = grow(&ws.okey, &oc, 1 << 16, 8)) || (rc = grow(&ws.oval, &oc, 1 << 16, 8)))
       return rc;
     ws.ocap = 1 << 16;
   }
-  unsigned long long* acc = ws.small;         // 4 per field
-  unsigned long long* ocount = ws.small + 4 * nf;
+  unsigned long long* acc = ws.small;          // 4 per field
+  unsigned long long* x0d = ws.small + 4 * nf;  // f64 bits of each field's first value
+  unsigned long long* ocount = ws.small + 5 * nf;
 
   // a0: range over finite values, and the anchor
   {
@@ -658,19 +674,26 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     }
     CU(cudaMemcpyAsync(acc, init.data(), 32 * nf, cudaMemcpyHostToDevice, st));
   }
-  for (size_t i = 0; i < nf; ++i) {
+  // one range launch per kRangeBatch fields, one read-back of the results
+  for (size_t i0 = 0; i0 < nf; i0 += kRangeBatch) {
+    const int nb = (int)std::min<size_t>(kRangeBatch, nf - i0);
+    RangeBatch rb{};
+    uint64_t nmax = 0;
+    double by = 0;
+    for (int j = 0; j < nb; ++j) {
+      rb.x[j] = ins[i0 + j];
+      rb.n[j] = fs[i0 + j]->g.n;
+      nmax = std::max(nmax, rb.n[j]);
+      by += (double)(rb.n[j] * esz);
+    }
+    rb.acc = acc + 4 * i0;
+    rb.x0 = x0d + i0;
     const long ph = prof_begin(IPC_KERNEL_RANGE, st);
-    CU(launch_range(dtype, ins[i], fs[i]->g.n, acc + 4 * i, st));
-    prof_end(ph, st, (double)(fs[i]->g.n * esz));
+    CU(launch_range_batch(dtype, rb, nb, nmax, st));
+    prof_end(ph, st, by);
   }
-  std::vector<unsigned long long> hacc(4 * nf);
-  std::vector<double> x0(nf, 0.0);
-  std::vector<float> x0f(nf, 0.0f);
-  CU(cudaMemcpyAsync(hacc.data(), acc, 32 * nf, cudaMemcpyDeviceToHost, st));
-  for (size_t i = 0; i < nf; ++i) {
-    if (dtype == 0) CU(cudaMemcpyAsync(&x0f[i], ins[i], 4, cudaMemcpyDeviceToHost, st));
-    else CU(cudaMemcpyAsync(&x0[i], ins[i], 8, cudaMemcpyDeviceToHost, st));
-  }
+  std::vector<unsigned long long> hacc(5 * nf);
+  CU(cudaMemcpyAsync(hacc.data(), acc, 40 * nf, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   std::vector<std::array<unsigned char, 32>> quant(nf);
   for (size_t i = 0; i < nf; ++i) {
@@ -690,7 +713,7 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     }
     if (!(eb > 0) || !std::isfinite(eb)) return fail(IPC_EINVAL, "error bound must be > 0 and finite");
     f->eb = eb;
-    f->anchor = dtype == 0 ? (double)x0f[i] : x0[i];
+    std::memcpy(&f->anchor, &hacc[4 * nf + i], 8);
     quant[i].fill(0);
     if (dtype == 0) quant_args<float>(eb, f->xmaxabs, quant[i].data());
     else quant_args<double>(eb, f->xmaxabs, quant[i].data());
@@ -865,9 +888,10 @@ SelInput sel_input(const ipc_field* f) {
 }
 
 int select(const ipc_field* f, ipc_target tg, const std::vector<int>* upper, std::vector<int>* b,
-           uint64_t* bytes, double* bound) {
+           uint64_t* bytes, double* bound, uint64_t* rparts = nullptr) {
   const char* why = "";
-  const int rc = select_planes(sel_input(f), tg.kind, tg.value, upper, b, bytes, bound, &why);
+  const int rc =
+      select_planes(sel_input(f), tg.kind, tg.value, upper, b, bytes, bound, &why, rparts);
   return rc ? fail(rc, why) : IPC_OK;
 }
 
@@ -915,9 +939,89 @@ RetrieveShape tuned_shape(const ShapeKey& k) {
   return it == g_shapes.end() ? RetrieveShape{} : it->second;
 }
 
+// State of an incremental view: per stage, two words per code word.
+uint64_t state_words(const Geo& g, std::vector<uint64_t>* off) {
+  off->assign(g.stages.size(), 0);
+  uint64_t tot = 0;
+  for (size_t t = 0; t < g.stages.size(); ++t) {
+    (*off)[t] = tot;
+    tot += 2 * g.stages[t].words;
+  }
+  return tot;
+}
+
+// The coarse levels K .. Lc of a reconstruction with selection b, for one
+// CTA (ipc_coarse.cu): the smallest Lc whose lattice and codes fit its shared
+// memory. Returns false when not even level K fits.
+bool coarse_plan(const ipc_field* f, const std::vector<int>& b, void* out, CoarseArgs* a) {
+  const Geo& g = f->g;
+  if (g.K < 1) return false;
+  std::memset(a, 0, sizeof(*a));
+  a->K = g.K;
+  a->cubic = f->interp == IPC_CUBIC;
+  a->esz = f->dtype == 0 ? 4 : 8;
+  a->anchor = f->anchor;
+  a->twoeb = bin_width(f);
+  a->out = out;
+  a->cap = f->d_cap;
+  a->bm = f->d_bm;
+  a->oidx = f->d_oidx;
+  a->oval = f->d_oval;
+  int best = 0;
+  for (int Lc = g.K; Lc >= 1; --Lc) {
+    CoarseArgs t = *a;
+    t.Lc = Lc;
+    for (int e = 0; e < 3; ++e) t.ML[e] = ((g.N[e] - 1) >> (Lc - 1)) + 1;
+    int n = 0;
+    bool ok = true;
+    for (size_t s = 0; s < g.stages.size() && ok; ++s) {
+      const StageGeo& sg = g.stages[s];
+      if (sg.level < Lc) continue;
+      if (n == kCoarseMaxStages) { ok = false; break; }
+      CoarseStage& S = t.st[n++];
+      S.level = sg.level;
+      S.dim = sg.dim3;
+      S.b = b[sg.level - 1];
+      for (int e = 0; e < 3; ++e) S.m[e] = sg.m[e];
+      S.wr = sg.wr;
+      S.words = sg.words;
+      S.RB = sg.RB;
+      S.CW = sg.CW;
+      S.nrb = sg.nrb;
+      S.nct = sg.nct;
+      S.bw = sg.bw;
+      S.cap0 = f->desc[s].p[0].cap_off;
+      S.bm0 = f->desc[s].p[0].bm_off;
+      S.pcap = sg.nseg * (uint64_t)sg.RB * sg.CW;
+      S.pbm = sg.nseg * sg.bw;
+      S.kmask = 0;
+      for (int k = std::max(S.b, 0); k < 32; ++k)
+        if (f->st[s].nnz[k]) S.kmask |= 1u << k;
+      S.out_begin = f->out_off[s];
+      S.out_end = f->out_off[s + 1];
+    }
+    if (!ok) break;
+    t.nst = n;
+    uint64_t off = 0;
+    for (int i = 0; i < n; ++i) {
+      t.st[i].code_off = off;
+      off += (uint64_t)(t.st[i].m[0] * t.st[i].m[1] * t.st[i].m[2]);
+    }
+    if (coarse_smem(t) > kCoarseSmem) break;
+    *a = t;
+    best = Lc;
+  }
+  return best > 0;
+}
+
 // Algorithm 1 on the device: the anchor, then one fused launch per level
-// (coarse to fine); outliers are applied inside the level kernels.
-int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream_t st) {
+// (coarse to fine); outliers are applied inside the level kernels. The
+// coarse levels that fit one CTA's shared memory run together in one launch
+// (ipc_coarse.cu). With a view state (`state`, per-stage offsets `soff`)
+// every level takes the level kernels, which also record the digits of
+// every code at its two lowest loaded planes.
+int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream_t st,
+                uint32_t* state = nullptr, const std::vector<uint64_t>* soff = nullptr) {
   const Geo& g = f->g;
   const size_t esz = f->dtype == 0 ? 4 : 8;
   std::vector<uint64_t> off;
@@ -931,13 +1035,31 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
     cudaStream_t s;
     ~Free() { if (p) cudaFreeAsync(p, s); }
   } guard{scr, st};
+  int ltop = g.K;  // the finest level not done yet
   {
+    CoarseArgs ca;
+    if (!state && coarse_plan(f, b, nullptr, &ca)) {
+      ca.out = ca.Lc == 1 ? d_out : (void*)(scr + off[ca.Lc]);
+      double by = 0;
+      uint64_t nc = 0;
+      for (int i = 0; i < ca.nst; ++i) {
+        const int t = g.level_stage[ca.st[i].dim][ca.st[i].level - 1];
+        nc += g.stages[t].ncodes;
+        for (int k = ca.st[i].b; k < 32; ++k) by += (double)f->st[t].size[k];
+      }
+      const long ph = prof_begin(IPC_KERNEL_COARSE, st);
+      CU(launch_coarse(f->dtype, ca, st));
+      prof_end(ph, st, by + (double)(nc * esz));
+      ltop = ca.Lc - 1;
+    }
+  }
+  if (ltop == g.K) {
     const long ph = prof_begin(IPC_KERNEL_ANCHOR, st);
     CU(launch_set_anchor(f->dtype, g.K > 0 ? (void*)(scr + off[g.K + 1]) : d_out, f->anchor, st));
     prof_end(ph, st, 8);
   }
   const double twoeb = bin_width(f);
-  for (int l = g.K; l >= 1; --l) {
+  for (int l = ltop; l >= 1; --l) {
     LevelArgs L = level_args(f, l);
     retrieve_layout(&L, scr + off[l + 1]);
     retrieve_planes(f, l, b[l - 1], &L);
@@ -956,9 +1078,96 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
     if (!sh.ns) sh.ns = retrieve_subtiles(L.M[2], w16);
     retrieve_tiling(&L, f->dtype, w16, sh.ns);
     const long ph = prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st);
-    CU(launch_level_retrieve(f->dtype, L, o, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
-                             f->d_oval, w16, sh, st));
+    if (state) {
+      for (int d = 0; d < 3; ++d) {
+        const int t = g.level_stage[d][l - 1];
+        L.sp[d].carry = t >= 0 ? state + (*soff)[t] : nullptr;
+        L.sp[d].carry_in = nullptr;
+      }
+      CU(launch_level_retrieve_mode(f->dtype, L, o, twoeb, b[l - 1], f->d_cap, f->d_bm,
+                                    f->d_oidx, f->d_oval, w16, sh, 1, st));
+    } else {
+      CU(launch_level_retrieve(f->dtype, L, o, twoeb, b[l - 1], f->d_cap, f->d_bm, f->d_oidx,
+                               f->d_oval, w16, sh, st));
+    }
     prof_end(ph, st, by + (double)(nc * esz));
+  }
+  return IPC_OK;
+}
+
+// Algorithm 2 on the device: from selection bo to bn (bn <= bo), read only
+// the planes [bn_l, bo_l) of every level, decode them with the view's state
+// as prefix, interpolate the increment from zero and add it to d_out (which
+// holds the current reconstruction). Levels coarser than the coarsest one
+// that loads planes have a zero increment and are skipped: the known points
+// of that level are zeros. *stream_bytes: the plane-stream bytes read.
+// The state is read from `state_in` and written to `state_out` (whole: the
+// words of levels that load no new planes are copied).
+int reconstruct_increment(ipc_field* f, const std::vector<int>& bo, const std::vector<int>& bn,
+                          void* d_out, const uint32_t* state_in, uint32_t* state_out,
+                          const std::vector<uint64_t>& soff, cudaStream_t st,
+                          uint64_t* stream_bytes) {
+  const Geo& g = f->g;
+  const size_t esz = f->dtype == 0 ? 4 : 8;
+  *stream_bytes = 0;
+  int lc = 0;
+  for (int l = 1; l <= g.K; ++l)
+    if (bn[l - 1] < bo[l - 1]) lc = l;
+  if (lc == 0) return IPC_OK;
+  std::vector<uint64_t> off;
+  uint8_t* scr = nullptr;
+  int rc = dalloc((void**)&scr, ladder(g, esz, &off), st);
+  if (rc) return rc;
+  struct Free {  // stream-ordered after the launches
+    uint8_t* p;
+    cudaStream_t s;
+    ~Free() { if (p) cudaFreeAsync(p, s); }
+  } guard{scr, st};
+  // the increments of level lc's known points (level lc + 1, or the anchor)
+  CU(cudaMemsetAsync(scr + off[lc + 1], 0, lattice_elems(g, lc + 1) * esz, st));
+  // the state of the stages whose level loads no new planes is carried over
+  for (size_t t = 0; t < g.stages.size(); ++t) {
+    const int l = g.stages[t].level;
+    if (bn[l - 1] < bo[l - 1]) continue;
+    CU(cudaMemcpyAsync(state_out + soff[t], state_in + soff[t], 8 * g.stages[t].words,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  const double twoeb = bin_width(f);
+  const double lim = f->dtype == 0 ? (double)FLT_MAX : DBL_MAX;
+  for (int l = lc; l >= 1; --l) {
+    const int b0 = bo[l - 1], b1 = bn[l - 1];
+    LevelArgs L = level_args(f, l);
+    retrieve_layout(&L, scr + off[l + 1]);
+    retrieve_planes(f, l, b1, &L);
+    double by = 0;
+    uint64_t nc = 0, nw = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int t = g.level_stage[d][l - 1];
+      L.sp[d].carry = t >= 0 ? state_out + soff[t] : nullptr;
+      L.sp[d].carry_in = t >= 0 ? state_in + soff[t] : nullptr;
+      if (t < 0) continue;
+      // only the new planes [b1, b0)
+      L.sp[d].kmask &= b0 >= 32 ? ~0u : ((1u << b0) - 1u);
+      nc += g.stages[t].ncodes;
+      nw += g.stages[t].words;
+      for (int k = b1; k < b0; ++k) by += (double)f->st[t].size[k];
+    }
+    *stream_bytes += (uint64_t)by;
+    L.bo = b0;
+    L.stream_out = l == 1;
+    void* o = l == 1 ? d_out : (void*)(scr + off[l]);
+    const int w16 = (b0 - b1 <= 16 && bin_width(f) * 65536.0 <= lim) ? 1 : 0;
+    RetrieveShape sh = tuned_shape(shape_key(f->dtype, w16, L));
+    if (!sh.ns) sh.ns = retrieve_subtiles(L.M[2], w16);
+    retrieve_tiling(&L, f->dtype, w16, sh.ns);
+    const long ph = prof_begin(IPC_KERNEL_INCREMENT_LEVEL, st);
+    CU(launch_level_retrieve_mode(f->dtype, L, o, twoeb, b1, f->d_cap, f->d_bm, f->d_oidx,
+                                  f->d_oval, w16, sh, 2, st));
+    const double state_bytes = b0 > b1 ? 16.0 * (double)nw : 0.0;
+    // level 1 reads and writes the whole output; coarser levels write their
+    // targets' increments
+    prof_end(ph, st, by + state_bytes + (l == 1 ? 2.0 * (double)g.n * (double)esz
+                                                 : (double)(nc * esz)));
   }
   return IPC_OK;
 }
@@ -973,6 +1182,12 @@ struct BatchTable {
   std::vector<RetrieveEntry> ents;
   std::vector<AnchorEntry> anchors;
   std::vector<int64_t> kin_off, out_off, anch_off;  // scratch offsets (-1: caller's array)
+  // fields whose coarse levels run in one CTA each (ipc_coarse.cu): their
+  // arguments, where each writes its level-Lc lattice (-1: the caller's
+  // array), and the most shared memory one of them takes
+  std::vector<CoarseArgs> coarse;
+  std::vector<int64_t> coarse_off;
+  size_t coarse_smem = 0;
   // One launch per (level, code width): a level's entries whose loaded
   // planes span at most 16 go to the 16-bit kernel, the others to the
   // 32-bit one, coarse levels first.
@@ -1001,6 +1216,9 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   T->kin_off.clear();
   T->out_off.clear();
   T->anch_off.clear();
+  T->coarse.clear();
+  T->coarse_off.clear();
+  T->coarse_smem = 0;
   T->alg_bytes = 0;
   // each field's scratch ladder, one after the other
   std::vector<uint64_t> base(nf, 0);
@@ -1011,15 +1229,32 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
     base[i] = T->scratch;
     if (fs[i]->g.K > 0) T->scratch += ladder(fs[i]->g, esz, &off[i]);
   }
+  std::vector<int> ltop(nf);  // per field the finest level the level kernels start at
   for (size_t i = 0; i < nf; ++i) {
-    T->anchors.push_back(AnchorEntry{outs[i], fs[i]->anchor});
     const int K = fs[i]->g.K;
+    CoarseArgs ca;
+    if (coarse_plan(fs[i], bs[i], nullptr, &ca)) {
+      ltop[i] = ca.Lc - 1;
+      T->coarse.push_back(ca);
+      T->coarse_off.push_back(ca.Lc == 1 ? -1 : (int64_t)(base[i] + off[i][ca.Lc]));
+      if (ca.Lc == 1) T->coarse.back().out = outs[i];
+      T->coarse_smem = std::max(T->coarse_smem, coarse_smem(ca));
+      const size_t esz = fs[i]->dtype == 0 ? 4 : 8;
+      for (int j = 0; j < ca.nst; ++j) {
+        const int t = fs[i]->g.level_stage[ca.st[j].dim][ca.st[j].level - 1];
+        T->alg_bytes += (double)(fs[i]->g.stages[t].ncodes * esz);
+        for (int k = ca.st[j].b; k < 32; ++k) T->alg_bytes += (double)fs[i]->st[t].size[k];
+      }
+      continue;
+    }
+    ltop[i] = K;
+    T->anchors.push_back(AnchorEntry{outs[i], fs[i]->anchor});
     T->anch_off.push_back(K > 0 ? (int64_t)(base[i] + off[i][K + 1]) : -1);
   }
   for (int l = T->Kmax; l >= 1; --l) {
     std::vector<size_t> group[2];  // the level's fields by code width (index: w16)
     for (size_t i = 0; i < nf; ++i)
-      if (l <= fs[i]->g.K) group[level_w16(fs[i], l, bs[i][l - 1]) ? 1 : 0].push_back(i);
+      if (l <= ltop[i]) group[level_w16(fs[i], l, bs[i][l - 1]) ? 1 : 0].push_back(i);
     for (int w16 : {1, 0}) {
       if (group[w16].empty()) continue;
       BatchTable::Launch ln;
@@ -1088,11 +1323,18 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
                           bool profile, uint64_t* launches) {
   RetrieveEntry* d_ents = (RetrieveEntry*)((uint8_t*)tab + table_scratch(T));
   AnchorEntry* d_anch = (AnchorEntry*)((uint8_t*)d_ents + T.ents.size() * sizeof(RetrieveEntry));
+  CoarseArgs* d_coarse = (CoarseArgs*)((uint8_t*)d_anch + T.anchors.size() * sizeof(AnchorEntry));
   uint64_t nl = 0;
-  {
+  if (!T.anchors.empty()) {
     const long ph = profile ? prof_begin(IPC_KERNEL_ANCHOR, st) : -1;
     CU(launch_set_anchors(dtype, d_anch, (int)T.anchors.size(), st));
     if (profile) prof_end(ph, st, 16.0 * T.anchors.size());
+    ++nl;
+  }
+  if (!T.coarse.empty()) {
+    const long ph = profile ? prof_begin(IPC_KERNEL_COARSE, st) : -1;
+    CU(launch_coarse_batch(dtype, d_coarse, (int)T.coarse.size(), T.coarse_smem, st));
+    if (profile) prof_end(ph, st, 0.0);
     ++nl;
   }
   // the algorithmic bytes of the whole batch are reported with its last launch
@@ -1111,7 +1353,8 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
 
 int upload_table(const BatchTable& T, void** tab, cudaStream_t st, bool pooled) {
   const uint64_t sb = table_scratch(T);
-  const size_t bytes = T.ents.size() * sizeof(RetrieveEntry) + T.anchors.size() * sizeof(AnchorEntry);
+  const size_t eb = T.ents.size() * sizeof(RetrieveEntry) + T.anchors.size() * sizeof(AnchorEntry);
+  const size_t bytes = eb + T.coarse.size() * sizeof(CoarseArgs);
   int rc;
   if (pooled) {
     if ((rc = dalloc(tab, sb + bytes, st))) return rc;
@@ -1128,10 +1371,14 @@ int upload_table(const BatchTable& T, void** tab, cudaStream_t st, bool pooled) 
   }
   for (size_t i = 0; i < anch.size(); ++i)
     if (T.anch_off[i] >= 0) anch[i].out = base + T.anch_off[i];
+  std::vector<CoarseArgs> co = T.coarse;
+  for (size_t i = 0; i < co.size(); ++i)
+    if (T.coarse_off[i] >= 0) co[i].out = base + T.coarse_off[i];
   std::vector<uint8_t> h(bytes);
   std::memcpy(h.data(), ents.data(), ents.size() * sizeof(RetrieveEntry));
   std::memcpy(h.data() + ents.size() * sizeof(RetrieveEntry), anch.data(),
               anch.size() * sizeof(AnchorEntry));
+  if (!co.empty()) std::memcpy(h.data() + eb, co.data(), co.size() * sizeof(CoarseArgs));
   // pageable source: the copy is staged before the call returns
   CU(cudaMemcpyAsync(base + sb, h.data(), bytes, cudaMemcpyHostToDevice, st));
   if (!pooled) CU(cudaStreamSynchronize(st));
@@ -1296,30 +1543,54 @@ int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims, int
 }
 
 int ipc_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream, ipc_view** out) {
+  return ipc_retrieve_ex(f, target, d_out, stream, IPC_REFINE_CANONICAL, out);
+}
+
+int ipc_retrieve_ex(ipc_field* f, ipc_target target, void* d_out, void* stream, int refine_mode,
+                    ipc_view** out) {
   g_err.clear();
   if (!f || f->tag != kFieldTag || !d_out) return fail(IPC_EINVAL, "null or invalid argument");
+  if (refine_mode != IPC_REFINE_CANONICAL && refine_mode != IPC_REFINE_INCREMENTAL)
+    return fail(IPC_EINVAL, "unknown refine mode");
   DeviceGuard dg(f->device);
   std::vector<int> b;
   uint64_t bytes = 0;
   double bound = 0;
-  int rc = select(f, target, nullptr, &b, &bytes, &bound);
+  uint64_t rparts[2] = {0, 0};
+  int rc = select(f, target, nullptr, &b, &bytes, &bound, rparts);
   if (rc) return rc;
   ipc_view* v = nullptr;
   if (out) {
     v = new (std::nothrow) ipc_view();
     if (!v) return fail(IPC_ENOMEM, "host allocation");
+    v->tag = kViewTag;
+    v->f = f;
+    v->mode = refine_mode;
+    v->state_device = f->device;
   }
-  rc = reconstruct(f, b, d_out, (cudaStream_t)stream);
+  // the incremental form records its state during this reconstruction
+  const bool record = v && refine_mode == IPC_REFINE_INCREMENTAL;
+  if (record) {
+    v->state_words = std::max<uint64_t>(state_words(f->g, &v->state_off), 2);
+    if (cudaMalloc((void**)&v->d_state, 2 * v->state_words * 4) != cudaSuccess) {
+      cudaGetLastError();
+      delete v;
+      return fail(IPC_ENOMEM, "device allocation of the view state");
+    }
+  }
+  rc = reconstruct(f, b, d_out, (cudaStream_t)stream, record ? v->d_state : nullptr,
+                   record ? &v->state_off : nullptr);
   if (rc) {
+    if (v && v->d_state) cudaFree(v->d_state);
     delete v;
     return rc;
   }
   if (out) {
-    v->tag = kViewTag;
-    v->f = f;
     v->b = b;
     v->bytes = bytes;
     v->bound = bound;
+    v->racc = rparts[0];
+    v->state_valid = record;
     *out = v;
   }
   return IPC_OK;
@@ -1457,18 +1728,81 @@ int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream) {
   std::vector<int> b;
   uint64_t bytes = 0;
   double bound = 0;
-  int rc = select(f, target, &v->b, &b, &bytes, &bound);
+  uint64_t rparts[2] = {0, 0};
+  int rc = select(f, target, &v->b, &b, &bytes, &bound, rparts);
   if (rc == IPC_EBUDGET && target.kind == IPC_TARGET_BITRATE) {
     g_err.clear();
     return IPC_OK;
   }
   if (rc) return rc;
   if (b == v->b) return IPC_OK;
-  rc = reconstruct(f, b, d_out, (cudaStream_t)stream);
-  if (rc) return rc;
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (v->mode == IPC_REFINE_INCREMENTAL && v->state_valid) {
+    uint64_t racc = 0;
+    const double Gd =
+        incremental_bound(sel_input(f), v->b, v->bound, v->racc, b, bound, rparts, &racc);
+    double E = target.value;
+    if (f->eb_mode == IPC_EB_REL && f->xmax - f->xmin > 0) E = target.value * (f->xmax - f->xmin);
+    if (target.kind == IPC_TARGET_BITRATE || Gd <= E) {
+      uint64_t sb = 0;
+      uint32_t* cur = v->d_state + (uint64_t)v->state_cur * v->state_words;
+      uint32_t* nxt = v->d_state + (uint64_t)(1 - v->state_cur) * v->state_words;
+      rc = reconstruct_increment(f, v->b, b, d_out, cur, nxt, v->state_off, st, &sb);
+      if (rc) {
+        v->state_valid = false;  // d_out may be half updated
+        return rc;
+      }
+      v->state_cur = 1 - v->state_cur;
+      v->b = b;
+      v->bytes = bytes;
+      v->bound = Gd;
+      v->racc = racc;
+      v->last_incremental = 1;
+      v->last_stream_bytes = sb;
+      return IPC_OK;
+    }
+  }
+  // canonical form (an incremental view records its state on the way)
+  const bool record = v->mode == IPC_REFINE_INCREMENTAL;
+  if (record && !v->d_state) {
+    v->state_words = std::max<uint64_t>(state_words(f->g, &v->state_off), 2);
+    if (cudaMalloc((void**)&v->d_state, 2 * v->state_words * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(IPC_ENOMEM, "device allocation of the view state");
+    }
+  }
+  rc = reconstruct(f, b, d_out, st,
+                   record ? v->d_state + (uint64_t)v->state_cur * v->state_words : nullptr,
+                   record ? &v->state_off : nullptr);
+  if (rc) {
+    v->state_valid = false;
+    return rc;
+  }
   v->b = b;
   v->bytes = bytes;
   v->bound = bound;
+  v->racc = rparts[0];
+  v->state_valid = record;
+  v->last_incremental = 0;
+  v->last_stream_bytes = bytes - f->mandatory;
+  return IPC_OK;
+}
+
+int ipc_view_set_refine_mode(ipc_view* v, int refine_mode) {
+  g_err.clear();
+  if (!v || v->tag != kViewTag) return fail(IPC_EINVAL, "null or invalid view");
+  if (refine_mode != IPC_REFINE_CANONICAL && refine_mode != IPC_REFINE_INCREMENTAL)
+    return fail(IPC_EINVAL, "unknown refine mode");
+  if (refine_mode != v->mode) v->state_valid = false;
+  v->mode = refine_mode;
+  return IPC_OK;
+}
+
+int ipc_refine_info(const ipc_view* v, int* incremental, uint64_t* stream_bytes) {
+  g_err.clear();
+  if (!v || v->tag != kViewTag) return fail(IPC_EINVAL, "null or invalid view");
+  if (incremental) *incremental = v->last_incremental;
+  if (stream_bytes) *stream_bytes = v->last_stream_bytes;
   return IPC_OK;
 }
 
@@ -1486,6 +1820,10 @@ int ipc_free(void* handle) {
   }
   if (tag == kViewTag) {
     ipc_view* v = (ipc_view*)handle;
+    if (v->d_state) {
+      DeviceGuard dg(v->state_device);
+      cudaFree(v->d_state);
+    }
     v->tag = kDeadTag;
     delete v;
     return IPC_OK;
@@ -1701,8 +2039,30 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
 
 // ---- hooks of the serving loop (ipc_serve.cu) ---------------------------------
 int ipc_internal_select(ipc_field* f, ipc_target tg, const std::vector<int>* upper,
-                        std::vector<int>* b, uint64_t* bytes, double* bound) {
-  return select(f, tg, upper, b, bytes, bound);
+                        std::vector<int>* b, uint64_t* bytes, double* bound, uint64_t* rparts) {
+  return select(f, tg, upper, b, bytes, bound, rparts);
+}
+
+ipc_view* ipc_internal_view_make(ipc_field* f, const std::vector<int>& b, uint64_t bytes,
+                                 double bound, uint64_t racc, int mode) {
+  ipc_view* v = new (std::nothrow) ipc_view();
+  if (!v) return nullptr;
+  v->tag = kViewTag;
+  v->f = f;
+  v->b = b;
+  v->bytes = bytes;
+  v->bound = bound;
+  v->racc = racc;
+  v->mode = mode;
+  v->state_device = f->device;
+  return v;
+}
+
+void ipc_internal_view_selection(const ipc_view* v, std::vector<int>* b, uint64_t* bytes,
+                                 double* bound) {
+  *b = v->b;
+  *bytes = v->bytes;
+  *bound = v->bound;
 }
 
 void ipc_internal_field_shape(const ipc_field* f, uint64_t* n, int* dtype) {

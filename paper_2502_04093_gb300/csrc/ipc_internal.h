@@ -57,6 +57,14 @@ struct LevelStage {
 struct StagePlanes {
   uint64_t cap0, pcap, bm0, pbm;
   uint32_t kmask;
+  // State of an incremental view (Algorithm 2): per word of the stage's word
+  // grid, the digits of its 32 codes at the two lowest loaded planes (two
+  // words, word-grid order). Written (`carry`) by recording and incremental
+  // reconstructions; an incremental one reads the previous state from a
+  // second buffer (`carry_in`), since a tile reads its neighbours' words for
+  // its halo while their owners write theirs. Null otherwise.
+  uint32_t* carry;
+  const uint32_t* carry_in;
 };
 struct LevelArgs {
   int64_t N[3], stride[3], M[3];  // extents, element strides, lattice extents
@@ -76,7 +84,50 @@ struct LevelArgs {
   // (its reconstructed values, the next finer level's known points)
   int64_t ost0, ost1;
   StagePlanes sp[3];  // reconstruction only
+  int bo;             // incremental reconstruction: planes >= bo are loaded already
 };
+
+// The coarse levels K .. Lc of a reconstruction in one CTA (ipc_coarse.cu):
+// per stage of those levels (execution order), its lattice, word grid,
+// segments, the planes to load and where its codes go in shared memory.
+constexpr int kCoarseMaxStages = 32;
+constexpr size_t kCoarseSmem = 96 * 1024;  // shared memory the host may plan for
+struct CoarseStage {
+  int level, dim;          // dim: sweep dimension in the padded index space
+  int b;                   // planes dropped
+  uint32_t kmask;          // planes to load (k >= b with nonzero words)
+  int64_t m[3];            // stage lattice extents
+  uint64_t wr, words;      // words per row, words of the stage
+  uint32_t RB, CW;         // segment rows x words
+  uint64_t nrb, nct, bw;
+  uint64_t cap0, pcap, bm0, pbm;
+  uint64_t out_begin, out_end;
+  uint64_t code_off;       // first code of the stage in the shared code buffer
+};
+struct CoarseArgs {
+  int nst, K, Lc, cubic;
+  int esz;                 // element bytes
+  int64_t ML[3];           // level-Lc lattice extents
+  double anchor, twoeb;
+  void* out;               // the level-Lc lattice, dense
+  const uint32_t* cap;
+  const uint32_t* bm;
+  const uint64_t* oidx;
+  const double* oval;
+  CoarseStage st[kCoarseMaxStages];
+};
+// Shared memory of a coarse launch: the level-Lc lattice (16-byte aligned)
+// and the codes of every stage.
+inline size_t coarse_smem(const CoarseArgs& a) {
+  const size_t v = (size_t)(a.ML[0] * a.ML[1] * a.ML[2]) * (size_t)a.esz;
+  size_t c = 0;
+  for (int t = 0; t < a.nst; ++t)
+    c += (size_t)(a.st[t].m[0] * a.st[t].m[1] * a.st[t].m[2]) * 4;
+  return ((v + 15) & ~(size_t)15) + c;
+}
+cudaError_t launch_coarse(int dtype, const CoarseArgs& a, cudaStream_t st);
+cudaError_t launch_coarse_batch(int dtype, const CoarseArgs* d_args, int n, size_t smem,
+                                cudaStream_t st);
 
 // Division of a 32-bit n by a divisor 1 <= d < 2^32 as the high half of n * m,
 // m = ceil(2^64 / d) (0 for d = 1): n m / 2^64 exceeds n / d by less than
@@ -173,6 +224,17 @@ struct AnchorEntry {
 // ---- kernel launchers -------------------------------------------------------
 cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long long* acc,
                          cudaStream_t st);
+// The range of up to kRangeBatch arrays in one launch (arguments by value):
+// acc[4 j ..] as launch_range, x0[j] = the f64 bits of array j's first value.
+constexpr int kRangeBatch = 128;
+struct RangeBatch {
+  const void* x[kRangeBatch];
+  uint64_t n[kRangeBatch];
+  unsigned long long* acc;
+  unsigned long long* x0;
+};
+cudaError_t launch_range_batch(int dtype, const RangeBatch& rb, int n, uint64_t nmax,
+                               cudaStream_t st);
 cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st);
 cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStream_t st);
 // Fused level kernels (ipc_level.cu).
@@ -215,6 +277,12 @@ inline int retrieve_max_per_sm(int dtype, int w16, int ns) {
   return w16 || (dtype == 0 && ns > 1) ? 4 : 3;
 }
 // w16: the planes loaded at the level span at most 16 (16-bit code rows).
+// The recording (mode 1) and incremental (mode 2) forms of the level
+// reconstruction (single field); mode 2 reads only the planes [b, L.bo).
+cudaError_t launch_level_retrieve_mode(int dtype, const LevelArgs& L, void* out, double twoeb,
+                                       int b, const uint32_t* cap, const uint32_t* bm,
+                                       const uint64_t* oidx, const double* oval, int w16,
+                                       RetrieveShape shape, int mode, cudaStream_t st);
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,
                                   const uint32_t* cap, const uint32_t* bm, const uint64_t* oidx,
                                   const double* oval, int w16, RetrieveShape shape,

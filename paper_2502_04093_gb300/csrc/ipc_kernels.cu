@@ -87,6 +87,53 @@ __global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, uint64_t
   }
 }
 
+// The range of up to kRangeBatch arrays in one launch: blockIdx.y picks the
+// array; its blocks reduce it as k_range does, and block 0 also copies the
+// array's first value (the anchor) as f64 bits into x0[j].
+template <class T>
+__global__ void __launch_bounds__(256) k_range_batch(RangeBatch rb) {
+  const int j = blockIdx.y;
+  const T* __restrict__ x = (const T*)rb.x[j];
+  const uint64_t n = rb.n[j];
+  unsigned long long* acc = rb.acc + 4 * j;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && n)
+    rb.x0[j] = (unsigned long long)__double_as_longlong((double)__ldg(x));
+  typedef typename Vec16<T>::type V;
+  constexpr int VN = Vec16<T>::n;
+  RangeAcc<T> r{(T)0, (T)0, (T)0, 0ULL};
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t mis = ((uintptr_t)x & 15) / sizeof(T);
+  const uint64_t head = mis ? ((uint64_t)VN - mis < n ? (uint64_t)VN - mis : n) : 0;
+  if (tid < head) r.add(__ldg(x + tid));
+  const uint64_t nv = (n - head) / VN;
+  const V* xv = reinterpret_cast<const V*>(x + head);
+  for (uint64_t i = tid; i < nv; i += nth) {
+    const V v = __ldg(xv + i);
+    const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int q = 0; q < VN; ++q) r.add(e[q]);
+  }
+  for (uint64_t i = head + nv * VN + tid; i < n; i += nth) r.add(__ldg(x + i));
+  unsigned long long kmn = r.cnt ? okey((double)r.mn) : ~0ULL;
+  unsigned long long kmx = r.cnt ? okey((double)r.mx) : 0ULL;
+  unsigned long long kma = r.cnt ? (unsigned long long)__double_as_longlong((double)r.ma) : 0ULL;
+  unsigned long long cnt = r.cnt;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    kmn = min(kmn, __shfl_xor_sync(~0u, kmn, o));
+    kmx = max(kmx, __shfl_xor_sync(~0u, kmx, o));
+    kma = max(kma, __shfl_xor_sync(~0u, kma, o));
+    cnt += __shfl_xor_sync(~0u, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    atomicMin(acc + 0, kmn);
+    atomicMax(acc + 1, kmx);
+    atomicMax(acc + 2, kma);
+    atomicAdd(acc + 3, cnt);
+  }
+}
+
 template <class T>
 __global__ void k_anchor(T* out, double v) { out[0] = (T)v; }
 
@@ -313,6 +360,21 @@ cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long lon
   const unsigned grid = grid_for(n / 4 + 1, 256, 152 * 8);
   if (dtype == 0) k_range<float><<<grid, 256, 0, st>>>((const float*)x, n, acc);
   else k_range<double><<<grid, 256, 0, st>>>((const double*)x, n, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_batch(int dtype, const RangeBatch& rb, int n, uint64_t nmax,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kRangeBatch) return cudaErrorInvalidValue;
+  // about 152 * 8 blocks over the batch, at least one per array
+  uint64_t per = (152 * 8 + n - 1) / n;
+  const uint64_t need = (nmax / 4 + 255) / 256;
+  if (per > need) per = need;
+  if (per < 1) per = 1;
+  const dim3 grid((unsigned)per, (unsigned)n);
+  if (dtype == 0) k_range_batch<float><<<grid, 256, 0, st>>>(rb);
+  else k_range_batch<double><<<grid, 256, 0, st>>>(rb);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ uint64_t uncert(int b) {
 struct Tables {
   int K;
   std::vector<uint64_t> cost, bytes;
+  std::vector<uint64_t> rho;  // per level: the rounding margin inside cost(l, b > 0)
 };
 
 void build_tables(const SelInput& in, double A, Tables* T) {
@@ -50,11 +51,13 @@ void build_tables(const SelInput& in, double A, Tables* T) {
   T->K = K;
   T->cost.assign((size_t)K * 33, 0);
   T->bytes.assign((size_t)K * 33, 0);
+  T->rho.assign((size_t)K, 0);
   for (int l = 1; l <= K; ++l) {
     double asum = 0;
     for (int t = 0; t < S; ++t)
       if (in.st[t].level <= l) asum += (strict && cubic) ? pw[S - 1 - t] : 1.0;
     const uint64_t rho = units(kappa * u * (A / in.eb) * 65536.0 * asum);
+    T->rho[l - 1] = strict ? rho : 0;
     for (int b = 0; b <= 32; ++b) {
       uint64_t c = 0, y = 0, mmax = 0;
       for (int t = 0; t < S; ++t) {
@@ -254,6 +257,16 @@ int solve(const Tables& T, int kind, uint64_t limit, const std::vector<int>* upp
   return IPC_OK;
 }
 
+// The selection's cost split into its rounding margins (rho_l of every
+// level with b_l > 0) and the rest (the truncation terms).
+void cost_parts(const Tables& T, const std::vector<int>& b, uint64_t* rparts) {
+  uint64_t r = 0;
+  for (size_t l = 0; l < b.size(); ++l)
+    if (b[l] > 0) r = sadd(r, T.rho[l]);
+  rparts[0] = r;
+  rparts[1] = cost_of(T, b) - r;
+}
+
 uint64_t loaded(const SelInput& in, const std::vector<int>& b) {
   uint64_t y = in.mandatory;
   for (const SelStage& s : in.st)
@@ -264,7 +277,8 @@ uint64_t loaded(const SelInput& in, const std::vector<int>& b) {
 }  // namespace
 
 int select_planes(const SelInput& in, int kind, double value, const std::vector<int>* upper,
-                  std::vector<int>* b, uint64_t* bytes, double* bound, const char** why) {
+                  std::vector<int>* b, uint64_t* bytes, double* bound, const char** why,
+                  uint64_t* rparts) {
   *why = "";
   if (!std::isfinite(value)) {
     *why = "target must be finite";
@@ -289,6 +303,7 @@ int select_planes(const SelInput& in, int kind, double value, const std::vector<
     }
     *bytes = loaded(in, *b);
     *bound = in.eb + (double)cost_of(T, *b) * in.eb / 65536.0;
+    if (rparts) cost_parts(T, *b, rparts);
     return IPC_OK;
   }
   if (kind == IPC_TARGET_BITRATE) {
@@ -319,10 +334,39 @@ int select_planes(const SelInput& in, int kind, double value, const std::vector<
       G = in.eb + (double)cost_of(T, *b) * in.eb / 65536.0;
     }
     *bound = G;
+    if (rparts) cost_parts(T, *b, rparts);
     return IPC_OK;
   }
   *why = "unknown target kind";
   return IPC_EINVAL;
+}
+
+double incremental_bound(const SelInput& in, const std::vector<int>& bold, double Gold,
+                         uint64_t racc_old, const std::vector<int>& bnew, double Gnew,
+                         const uint64_t* rparts, uint64_t* racc_new) {
+  if (in.bound != IPC_BOUND_STRICT) {
+    *racc_new = 0;
+    return Gnew;
+  }
+  const int S = (int)in.st.size();
+  const bool cubic = in.interp == IPC_CUBIC;
+  int lc = 0;  // coarsest level that loads new planes
+  for (int l = 1; l <= in.K; ++l)
+    if (bnew[l - 1] < bold[l - 1]) lc = l;
+  // a_t = p^(S-1-t), products formed in order as in the option tables
+  std::vector<double> pw(S + 1);
+  pw[0] = 1.0;
+  for (int i = 1; i <= S; ++i) pw[i] = pw[i - 1] * (cubic ? 1.25 : 1.0);
+  double asum = 0;
+  for (int t = 0; t < S; ++t)
+    if (in.st[t].level <= lc) asum += pw[S - 1 - t];
+  const double u = in.dtype == IPC_F32 ? 1.0 / 16777216.0 : 1.0 / 9007199254740992.0;
+  const double D = Gold + Gnew;  // bounds |Delta|
+  const double half_kappa = cubic ? 12.0 : 6.0;
+  const uint64_t eps = sadd(units(half_kappa * u * (D / in.eb) * 65536.0 * asum),
+                            units(u * ((in.xmaxabs + 2.0 * D) / in.eb) * 65536.0));
+  *racc_new = sadd(racc_old, eps);
+  return in.eb + (double)sadd(rparts[1], *racc_new) * in.eb / 65536.0;
 }
 
 }  // namespace ipc

@@ -30,7 +30,24 @@ struct SelInput {
 // Selection for a target (kind 0: error bound in the field's eb mode, kind 1:
 // bitrate in bits/value). upper (optional) bounds b_l from above (refine).
 // Returns 0 or a negative IPC_* status; `why` names the failure.
+// rparts (optional): [0] = the rounding margins inside the selection's cost
+// (rho_l of each level with b_l > 0), [1] = the rest (truncation terms); both
+// in units of eb * 2^-16.
 int select_planes(const SelInput& in, int kind, double value, const std::vector<int>* upper,
-                  std::vector<int>* b, uint64_t* bytes, double* bound, const char** why);
+                  std::vector<int>* b, uint64_t* bytes, double* bound, const char** why,
+                  uint64_t* rparts = nullptr);
+
+// Guaranteed bound of an incremental refinement (Algorithm 2) from selection
+// bold (bound Gold, rounding allowance racc_old) to bnew (whose fresh
+// reconstruction would have bound Gnew and cost parts rparts). Relative to
+// the compressor's values, x^old + Delta adds to the truncation of bnew the
+// old result's rounding and the increment's: Delta is zero above the
+// coarsest changed level l_c, each stage at or below it rounds by at most
+// (kappa / 2) u D (D = Gold + Gnew bounds |Delta|), amplified like any stage
+// error, and the final addition rounds by u (max|x| + 2D). Returns the bound
+// and the new allowance (units of eb * 2^-16). Paper mode: Gnew, allowance 0.
+double incremental_bound(const SelInput& in, const std::vector<int>& bold, double Gold,
+                         uint64_t racc_old, const std::vector<int>& bnew, double Gnew,
+                         const uint64_t* rparts, uint64_t* racc_new);
 
 }  // namespace ipc

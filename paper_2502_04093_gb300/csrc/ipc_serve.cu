@@ -47,6 +47,18 @@ struct SView {
   uint64_t bytes = 0;
   double bound = 0;
   int busy = 0;  // batches in flight that write `out`
+  ipc_view* hv = nullptr;  // incremental servers: the view that refines `out`
+};
+
+// What a request's completion applies to its view: the new selection of a
+// refine (taken only once its batch has finished without error).
+struct NewSel {
+  bool refine = false;
+  bool incremental = false;  // refined through the view's own increment path
+  ipc_target target{};
+  std::vector<int> b;
+  uint64_t bytes = 0;
+  double bound = 0;
 };
 
 struct Pending {
@@ -61,6 +73,7 @@ struct Flight {
   int stream;
   std::vector<Pending> reqs;
   std::vector<uint64_t> views;  // view of each request (0 if none)
+  std::vector<NewSel> nsel;     // per request
   std::vector<int> status;
   Clock::time_point t_launch;
 };
@@ -116,9 +129,26 @@ void reap(ipc_server* s) {
     for (size_t i = 0; i < fl.reqs.size(); ++i) {
       auto it = s->views.find(fl.views[i]);
       SView* v = it == s->views.end() ? nullptr : &it->second;
-      if (v) v->busy -= 1;
-      complete(s, fl.reqs[i], q == cudaSuccess ? fl.status[i] : IPC_ECUDA, fl.views[i], v,
-               fl.t_launch, now);
+      const int st = q == cudaSuccess ? fl.status[i] : IPC_ECUDA;
+      if (v) {
+        v->busy -= 1;
+        const NewSel& ns = fl.nsel[i];
+        if (ns.refine && st == IPC_OK) {
+          if (ns.incremental) {
+            ipc_internal_view_selection(v->hv, &v->b, &v->bytes, &v->bound);
+          } else {
+            v->b = ns.b;
+            v->bytes = ns.bytes;
+            v->bound = ns.bound;
+          }
+        } else if (ns.refine && ns.incremental) {
+          // the output and the view's state may be half updated: the next
+          // refinement reconstructs (and records the state again)
+          ipc_view_set_refine_mode(v->hv, IPC_REFINE_CANONICAL);
+          ipc_view_set_refine_mode(v->hv, IPC_REFINE_INCREMENTAL);
+        }
+      }
+      complete(s, fl.reqs[i], st, fl.views[i], v, fl.t_launch, now);
     }
     for (void* t : fl.tabs) cudaFreeAsync(t, s->streams[fl.stream]);
     cudaEventDestroy(fl.done);
@@ -134,6 +164,7 @@ void admit_and_launch(ipc_server* s) {
   std::vector<Pending> take;
   std::vector<uint64_t> vid;
   std::vector<std::vector<int>> sel;
+  std::vector<NewSel> nsel;
   std::vector<int> status;
   std::deque<Pending> keep;
   bool blocked = false;
@@ -180,6 +211,7 @@ void admit_and_launch(ipc_server* s) {
         continue;
       }
       if (it->second.out) cudaFreeAsync(it->second.out, s->streams[0]);
+      if (it->second.hv) ipc_free(it->second.hv);
       s->mem_used -= it->second.out_bytes;
       s->views.erase(it);
       complete(s, p, IPC_OK, r.view_id, nullptr, now, now);
@@ -212,9 +244,14 @@ void admit_and_launch(ipc_server* s) {
         complete(s, p, IPC_OK, r.view_id, &v, now, now);  // target already met
         continue;
       }
-      v.b = nb;
-      v.bytes = nbytes;
-      v.bound = nbound;
+      NewSel ns;  // applied when the batch is done
+      ns.refine = true;
+      ns.incremental = v.hv != nullptr;
+      ns.target = r.target;
+      ns.b = nb;
+      ns.bytes = nbytes;
+      ns.bound = nbound;
+      nsel.push_back(ns);
       {
         uint64_t nv = 0;
         int dt = 0;
@@ -250,15 +287,25 @@ void admit_and_launch(ipc_server* s) {
     std::vector<int> nb;
     uint64_t nbytes = 0;
     double nbound = 0;
-    int rc = ipc_internal_select(r.field, r.target, nullptr, &nb, &nbytes, &nbound);
+    uint64_t rparts[2] = {0, 0};
+    int rc = ipc_internal_select(r.field, r.target, nullptr, &nb, &nbytes, &nbound, rparts);
     if (rc) {
       complete(s, p, rc, 0, nullptr, now, now);
       continue;
+    }
+    ipc_view* hv = nullptr;
+    if (s->cfg.refine_mode == IPC_REFINE_INCREMENTAL) {
+      hv = ipc_internal_view_make(r.field, nb, nbytes, nbound, rparts[0], IPC_REFINE_INCREMENTAL);
+      if (!hv) {
+        complete(s, p, IPC_ENOMEM, 0, nullptr, now, now);
+        continue;
+      }
     }
     void* out = nullptr;
     const int sidx = s->next_stream;
     if (cudaMallocAsync(&out, need, s->streams[sidx]) != cudaSuccess) {
       cudaGetLastError();
+      if (hv) ipc_free(hv);
       blocked = true;
       keep.push_back(p);
       continue;
@@ -273,10 +320,12 @@ void admit_and_launch(ipc_server* s) {
     v.b = nb;
     v.bytes = nbytes;
     v.bound = nbound;
+    v.hv = hv;
     s->views[id] = v;
     take.push_back(p);
     vid.push_back(id);
     sel.push_back(nb);
+    nsel.push_back(NewSel());
     status.push_back(IPC_OK);
     touched.push_back(id);
     values += n;
@@ -294,18 +343,35 @@ void admit_and_launch(ipc_server* s) {
   fl.t_launch = Clock::now();
   std::vector<ipc_field*> fs;
   std::vector<void*> outs;
+  std::vector<std::vector<int>> bsel;
+  std::vector<size_t> inc;  // refines of incremental views: through the view
   for (size_t i = 0; i < take.size(); ++i) {
     SView& v = s->views[vid[i]];
     v.busy += 1;
+    if (nsel[i].incremental) {
+      inc.push_back(i);
+      continue;
+    }
     fs.push_back(v.f);
     outs.push_back(v.out);
+    bsel.push_back(sel[i]);
   }
-  int rc;
+  int rc = IPC_OK;
   // a batch of one takes the single-field path (no entry table to upload)
-  if (s->cfg.plain || take.size() == 1) rc = ipc_internal_reconstruct_each(fs, sel, outs, st);
-  else rc = ipc_internal_reconstruct_batch(fs, sel, outs, st, &fl.tabs);
+  if (!fs.empty()) {
+    if (s->cfg.plain || fs.size() == 1) rc = ipc_internal_reconstruct_each(fs, bsel, outs, st);
+    else rc = ipc_internal_reconstruct_batch(fs, bsel, outs, st, &fl.tabs);
+  }
   if (rc)
-    for (auto& x : fl.status) x = rc;
+    for (size_t i = 0; i < take.size(); ++i)
+      if (!nsel[i].incremental) fl.status[i] = rc;
+  for (size_t i : inc) {
+    // the same constrained selection; the increment when its bound allows,
+    // else a reconstruction that records the view's state
+    SView& v = s->views[vid[i]];
+    fl.status[i] = ipc_refine(v.hv, nsel[i].target, v.out, st);
+  }
+  fl.nsel = std::move(nsel);
   cudaEventCreateWithFlags(&fl.done, cudaEventDisableTiming);
   cudaEventRecord(fl.done, st);
   s->batches += 1;
@@ -358,7 +424,8 @@ void worker_main(ipc_server* s) {
 extern "C" {
 
 int ipc_server_create(const ipc_server_cfg* cfg, ipc_server** out) {
-  if (!cfg || !out || cfg->nstreams < 1 || cfg->nstreams > 16 || cfg->max_inflight < 1)
+  if (!cfg || !out || cfg->nstreams < 1 || cfg->nstreams > 16 || cfg->max_inflight < 1 ||
+      (cfg->refine_mode != IPC_REFINE_CANONICAL && cfg->refine_mode != IPC_REFINE_INCREMENTAL))
     return IPC_EINVAL;
   ipc_server* s = new (std::nothrow) ipc_server();
   if (!s) return IPC_ENOMEM;
@@ -420,15 +487,23 @@ int ipc_server_stats(ipc_server* s, uint64_t* batches, uint64_t* requests, uint6
   return IPC_OK;
 }
 
-int ipc_server_destroy(ipc_server* s) {
-  if (!s) return IPC_OK;
-  if (s->tag != kServerTag) return IPC_EINVAL;
+int ipc_server_stop(ipc_server* s) {
+  if (!s || s->tag != kServerTag) return IPC_EINVAL;
   s->stop.store(true);
   s->cv_in.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  return IPC_OK;
+}
+
+int ipc_server_destroy(ipc_server* s) {
+  if (!s) return IPC_OK;
+  if (s->tag != kServerTag) return IPC_EINVAL;
+  ipc_server_stop(s);
   for (auto st : s->streams) cudaStreamSynchronize(st);
-  for (auto& kv : s->views)
+  for (auto& kv : s->views) {
     if (kv.second.out) cudaFreeAsync(kv.second.out, s->streams[0]);
+    if (kv.second.hv) ipc_free(kv.second.hv);
+  }
   for (auto st : s->streams) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);

@@ -26,6 +26,8 @@ IPC_LINEAR, IPC_CUBIC = 0, 1
 IPC_EB_ABS, IPC_EB_REL = 0, 1
 IPC_BOUND_STRICT, IPC_BOUND_PAPER = 0, 1
 IPC_TARGET_EB, IPC_TARGET_BITRATE = 0, 1
+IPC_REFINE_CANONICAL, IPC_REFINE_INCREMENTAL = 0, 1
+IPC_KERNEL_RETRIEVE_LEVEL, IPC_KERNEL_INCREMENT_LEVEL = 2, 6
 
 
 class ipc_target(C.Structure):
@@ -41,7 +43,7 @@ class ipc_batch_item(C.Structure):
 class ipc_server_cfg(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("hbm_reserve", C.c_uint64), ("max_batch", C.c_int),
                 ("max_inflight", C.c_int), ("nstreams", C.c_int), ("plain", C.c_int),
-                ("max_batch_values", C.c_uint64)]
+                ("max_batch_values", C.c_uint64), ("refine_mode", C.c_int)]
 
 
 class ipc_request(C.Structure):
@@ -85,6 +87,9 @@ def lib() -> C.CDLL:
                                C.c_int, vp, C.POINTER(vp)]
     L.ipc_retrieve.argtypes = [vp, ipc_target, vp, vp, C.POINTER(vp)]
     L.ipc_refine.argtypes = [vp, ipc_target, vp, vp]
+    L.ipc_retrieve_ex.argtypes = [vp, ipc_target, vp, vp, C.c_int, C.POINTER(vp)]
+    L.ipc_view_set_refine_mode.argtypes = [vp, C.c_int]
+    L.ipc_refine_info.argtypes = [vp, C.POINTER(C.c_int), u64p]
     L.ipc_autotune_retrieve.argtypes = [vp, ipc_target, vp, vp, C.c_int, C.POINTER(C.c_int)]
     L.ipc_autotune_entry.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p,
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -112,6 +117,7 @@ def lib() -> C.CDLL:
                                   C.c_int]
     L.ipc_server_stats.argtypes = [vp, u64p, u64p, u64p]
     L.ipc_server_destroy.argtypes = [vp]
+    L.ipc_server_stop.argtypes = [vp]
     L.ipc_profile_enable.argtypes = [C.c_int]
     L.ipc_profile_read.argtypes = [C.c_int, u64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.ipc_launch_count.restype = C.c_uint64
@@ -198,6 +204,28 @@ def ipc_autotune_entries():
             return out
         out.append((dt.value, w.value, tuple(M), ns.value, ps.value))
         i += 1
+
+
+def ipc_retrieve_ex(field, kind: int, value: float, out, refine_mode: int, stream=None):
+    """ipc_retrieve whose view refines in `refine_mode` (IPC_REFINE_*)."""
+    _require_cuda(out, "out")
+    v = C.c_void_p()
+    _check(lib().ipc_retrieve_ex(field, ipc_target(int(kind), float(value)),
+                                 C.c_void_p(out.data_ptr()), _stream(stream), int(refine_mode),
+                                 C.byref(v)), "ipc_retrieve_ex")
+    return v
+
+
+def ipc_view_set_refine_mode(view, refine_mode: int) -> None:
+    _check(lib().ipc_view_set_refine_mode(view, int(refine_mode)), "ipc_view_set_refine_mode")
+
+
+def ipc_refine_info(view):
+    """(whether the last refinement added an increment, plane-stream bytes it read)."""
+    inc = C.c_int()
+    by = C.c_uint64()
+    _check(lib().ipc_refine_info(view, C.byref(inc), C.byref(by)), "ipc_refine_info")
+    return bool(inc.value), by.value
 
 
 def ipc_refine(view, kind: int, value: float, out, stream=None) -> None:
@@ -341,9 +369,10 @@ def ipc_plan_launch(plan, stream=None):
 
 
 def ipc_server_create(mem_budget, max_batch=0, max_inflight=2, nstreams=2, plain=False,
-                      hbm_reserve=1 << 30, max_batch_values=0):
+                      hbm_reserve=1 << 30, max_batch_values=0, refine_mode=IPC_REFINE_CANONICAL):
     cfg = ipc_server_cfg(int(mem_budget), int(hbm_reserve), int(max_batch), int(max_inflight),
-                         int(nstreams), 1 if plain else 0, int(max_batch_values))
+                         int(nstreams), 1 if plain else 0, int(max_batch_values),
+                         int(refine_mode))
     h = C.c_void_p()
     _check(lib().ipc_server_create(C.byref(cfg), C.byref(h)), "ipc_server_create")
     return h
@@ -375,6 +404,10 @@ def ipc_server_stats(server):
     return dict(batches=b.value, requests=r.value, mem_used=m.value)
 
 
+def ipc_server_stop(server) -> None:
+    _check(lib().ipc_server_stop(server), "ipc_server_stop")
+
+
 def ipc_server_destroy(server):
     _check(lib().ipc_server_destroy(server), "ipc_server_destroy")
 
@@ -393,7 +426,8 @@ def device_view(ptr, shape, dtype):
     return torch.as_tensor(a, device="cuda")
 
 
-IPC_KERNEL_NAMES = ["range", "compress_level", "retrieve_level", "anchor", "pack", "unpack"]
+IPC_KERNEL_NAMES = ["range", "compress_level", "retrieve_level", "anchor", "pack", "unpack",
+                    "increment_level", "coarse"]
 
 
 def ipc_profile_enable(on: bool) -> None:
@@ -445,11 +479,11 @@ class Field:
             _lib.ipc_free(self.h)
             self.h = None
 
-    def retrieve(self, kind, value, out=None, stream=None):
+    def retrieve(self, kind, value, out=None, stream=None, refine_mode=IPC_REFINE_CANONICAL):
         import torch
         if out is None:
             out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
-        v = ipc_retrieve(self.h, kind, value, out, stream)
+        v = ipc_retrieve_ex(self.h, kind, value, out, refine_mode, stream)
         return out, View(v, self, out)
 
     def export(self) -> bytes:
@@ -476,6 +510,9 @@ class View:
     def refine(self, kind, value, stream=None):
         ipc_refine(self.h, kind, value, self.out, stream)
         return self.out
+
+    def refine_info(self):
+        return ipc_refine_info(self.h)
 
     def selection(self):
         return ipc_selection(self.h)

@@ -36,3 +36,19 @@ def compress_refine_chain(job):
         y = view.refine(oracle.EB, E)
         sels.append(view.selection()[0])
     return _digest(f.export()), sels, _digest(y)
+
+
+def compress_delta_chain(job):
+    """(x, eb, eb_mode, [(kind, value), ...]) -> (container digest, [(selection,
+    incremental, bound, output digest) per step]): retrieve at the first
+    target, then refine incrementally (Algorithm 2) to the others."""
+    x, eb, mode, chain = job
+    f = oracle.compress(x, eb, mode)
+    y, view = f.retrieve(*chain[0])
+    sel, _, bound = view.selection()
+    steps = [(sel, False, bound, _digest(y))]
+    for kind, v in chain[1:]:
+        y, inc = view.refine_delta(kind, v)
+        sel, _, bound = view.selection()
+        steps.append((sel, inc, bound, _digest(y)))
+    return _digest(f.export()), steps

@@ -8,7 +8,8 @@ worker).
 - 8 f64 fields of 384x384x256, rel eb 1e-8: batched compression, then per
   field a retrieval at 1e-2 refined to 1e-4, 1e-6 and 1e-8;
 - a sample of the resident serving fields (k^-5/3, rel eb 1e-6): the three
-  smallest, with eb, bitrate and refine requests."""
+  smallest and the two largest (the 768^3 class that sets the p99), with eb,
+  bitrate and refine requests."""
 import hashlib
 import multiprocessing as mp
 import os
@@ -97,9 +98,11 @@ def test_f64_refine_chain_full_size(pool):
             ipc.ipc_free(h)
 
 
-def test_serving_fields_sample(pool):
+@pytest.mark.parametrize("which", ["smallest", "largest"])
+def test_serving_fields_sample(pool, which):
     edges = synth.serving_edges(nfields=128, hi=768)
-    pick = sorted(range(len(edges)), key=lambda j: edges[j])[:3]
+    order = sorted(range(len(edges)), key=lambda j: edges[j])
+    pick = order[:3] if which == "smallest" else order[-2:]
     xs = [synth.grf_k53((edges[j],) * 3, seed=1500 + j, device="cuda") for j in pick]
     torch.cuda.synchronize()
     targets = [(oracle.EB, 1e-2), (oracle.BITRATE, 6.5), (oracle.EB, 3e-6)]

@@ -137,3 +137,64 @@ def test_memory_admission_and_failures(fields):
         assert drain(srv, 1)[t]["status"] == ipc.IPC_EBOUND
     finally:
         ipc.ipc_server_destroy(srv)
+
+
+def test_incremental_refines_same_alone_and_in_the_mix():
+    """A server whose refines take the incremental form (Algorithm 2): each
+    served refine chain ends bitwise equal to the same chain on a view of
+    its own (a canonical retrieval switched to the incremental form, so the
+    first refine reconstructs and records the state, the later ones add
+    increments), and the selection and bound agree."""
+    shapes = [(40, 48, 36), (33, 70, 21), (96, 80)]
+    xs = [torch.from_numpy(synth.random_field(s, seed=20 + i, dtype=dt)).cuda()
+          for i, s in enumerate(shapes) for dt in (np.float32, np.float64)]
+    fs = [ipc.Field.compress(x, 1e-9 if x.dtype == torch.float64 else 1e-6, ipc.IPC_EB_REL)
+          for x in xs]
+    srv = ipc.ipc_server_create(8 << 30, max_inflight=3, nstreams=3,
+                                refine_mode=ipc.IPC_REFINE_INCREMENTAL)
+    try:
+        ts = [ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, f.h, target=(0, 1e-1))
+              for f in fs]
+        got = drain(srv, len(ts))
+        vids = [got[t]["view_id"] for t in ts]
+        assert all(got[t]["status"] == 0 for t in ts)
+        chain = [(ipc.IPC_TARGET_EB, 1e-2), (ipc.IPC_TARGET_BITRATE, 6.0),
+                 (ipc.IPC_TARGET_EB, 1e-4), (ipc.IPC_TARGET_EB, 1e-5)]
+        reqs = [(ipc.ipc_server_submit(srv, ipc.IPC_REQ_REFINE, view_id=vid, target=tg), i, j)
+                for j, tg in enumerate(chain) for i, vid in enumerate(vids)]
+        got2 = drain(srv, len(reqs))
+        for i, f in enumerate(fs):
+            out = torch.empty_like(xs[i])
+            v = ipc.ipc_retrieve(f.h, 0, 1e-1, out)
+            ipc.ipc_view_set_refine_mode(v, ipc.IPC_REFINE_INCREMENTAL)
+            for tg in chain:
+                ipc.ipc_refine(v, tg[0], tg[1], out)
+            torch.cuda.synchronize()
+            last = [r for r in reqs if r[1] == i][-1]
+            c = got2[last[0]]
+            assert c["status"] == 0
+            served = ipc.device_view(c["d_out"], xs[i].shape, xs[i].dtype).clone()
+            assert torch.equal(served, out), i
+            assert (c["bytes"], c["bound"]) == tuple(ipc.ipc_selection(v)[1:]), i
+            ipc.ipc_free(v)
+        rel = [ipc.ipc_server_submit(srv, ipc.IPC_REQ_RELEASE, view_id=v) for v in vids]
+        assert all(c["status"] == 0 for c in drain(srv, len(rel)).values())
+    finally:
+        ipc.ipc_server_destroy(srv)
+
+
+def test_stop_completes_what_cannot_run_with_ebusy(fields):
+    xs, fs = fields
+    big = fs[1]  # 64^3 f32 = 1 MiB output
+    srv = ipc.ipc_server_create(int(1.5 * (1 << 20)), max_inflight=2, nstreams=2)
+    try:
+        t1 = ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, big.h, target=(0, 1e-2))
+        t2 = ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, big.h, target=(0, 1e-3))
+        assert drain(srv, 1)[t1]["status"] == 0
+        ipc.ipc_server_stop(srv)  # t2 waits for memory that is never released
+        assert drain(srv, 1)[t2]["status"] == ipc.IPC_EBUSY
+        with pytest.raises(ipc.IpcError) as e:
+            ipc.ipc_server_submit(srv, ipc.IPC_REQ_RETRIEVE, big.h, target=(0, 1e-2))
+        assert e.value.rc == ipc.IPC_EBUSY
+    finally:
+        ipc.ipc_server_destroy(srv)
