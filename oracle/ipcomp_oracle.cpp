@@ -118,14 +118,22 @@ bool make_geometry(int ndim, const int64_t* dims, Geometry* g) {
 /* otherwise linear (Eq. 1) if i+s is inside; otherwise the left neighbour   */
 /* is copied. Every rule has infinity-norm <= p (Sec. 5.1, p = 1 or 1.25).   */
 /* Op order (fixed): u = b + c; v = a + d; w = 9u; z = w - v; pred = z/16.   */
+/* interp 2 (cubic with quadratic boundaries, a predictor beyond the paper's */
+/* two): where cubic lacks one outer neighbour, the quadratic through the    */
+/* three points that exist -- (3b + 6c - d)/8 at the left end (i - 3s       */
+/* outside), (-a + 6b + 3c)/8 at the right end -- instead of Eq. 1. Its      */
+/* infinity-norm is (3 + 6 + 1)/8 = 1.25 = p of the cubic mode. Op order:    */
+/* u = 3b; v = 6c; w = u + v; z = w - d; pred = z/8 (left), and u = 6b;      */
+/* v = 3c; w = u + v; z = w - a; pred = z/8 (right).                         */
 /* ------------------------------------------------------------------------ */
 template <class T>
 T predict(const T* xh, int64_t base, int64_t stride, int64_t i, int64_t s,
-          int64_t N, bool cubic) {
+          int64_t N, int interp) {
   T b = xh[base + (i - s) * stride];
   if (i + s > N - 1) return b;
   T c = xh[base + (i + s) * stride];
-  if (cubic && i - 3 * s >= 0 && i + 3 * s <= N - 1) {
+  const bool left = i - 3 * s >= 0, right = i + 3 * s <= N - 1;
+  if (interp >= 1 && left && right) {
     T a = xh[base + (i - 3 * s) * stride];
     T d = xh[base + (i + 3 * s) * stride];
     T u = b + c;
@@ -133,6 +141,22 @@ T predict(const T* xh, int64_t base, int64_t stride, int64_t i, int64_t s,
     T w = (T)9 * u;
     T z = w - v;
     return z * (T)0.0625;
+  }
+  if (interp == 2 && right) {
+    T d = xh[base + (i + 3 * s) * stride];
+    T u = (T)3 * b;
+    T v = (T)6 * c;
+    T w = u + v;
+    T z = w - d;
+    return z * (T)0.125;
+  }
+  if (interp == 2 && left) {
+    T a = xh[base + (i - 3 * s) * stride];
+    T u = (T)6 * b;
+    T v = (T)3 * c;
+    T w = u + v;
+    T z = w - a;
+    return z * (T)0.125;
   }
   T u = b + c;
   return u * (T)0.5;
@@ -350,7 +374,7 @@ int compress_t(const T* x, ipco_field* f) {
   const T twoeb = (T)(2.0 * eq);
   const T ebchk = (T)(eb * Prec<T>::shrink());
   const T R = (T)Prec<T>::radius();
-  const bool cubic = f->interp == 1;
+  const bool cubic = f->interp >= 1;  /* p = 1.25, kappa 24 */
 
   std::vector<T> xh(g.n);
   xh[0] = x[0];
@@ -373,7 +397,7 @@ int compress_t(const T* x, ipco_field* f) {
                           sg.start[2] + c2 * sg.step[2]};
           int64_t idx = i[0] * stride[0] + i[1] * stride[1] + i[2];
           int64_t base = idx - i[d] * stride[d];
-          T pred = predict<T>(xh.data(), base, stride[d], i[d], s, g.N[d], cubic);
+          T pred = predict<T>(xh.data(), base, stride[d], i[d], s, g.N[d], f->interp);
           /* y = x - P xhat; quantize to the nearest multiple of 2eb. */
           T xv = x[idx];
           T diff = xv - pred;
@@ -516,7 +540,7 @@ struct Options {
 void option_tables(const ipco_field* f, double A, Options* o) {
   const Geometry& g = f->g;
   const int K = g.K, S = (int)g.stages.size();
-  const bool cubic = f->interp == 1;
+  const bool cubic = f->interp >= 1;  /* p = 1.25, kappa 24 */
   const double p = cubic ? 1.25 : 1.0;
   std::vector<double> P(std::max(S, K) + 1);
   P[0] = 1.0;
@@ -700,7 +724,7 @@ template <class T>
 int reconstruct_t(const ipco_field* f, const std::vector<int>& bsel, T* out) {
   const Geometry& g = f->g;
   const T twoeb = (T)(2.0 * half_bin(f->eb, f->xmaxabs, f->dtype));
-  const bool cubic = f->interp == 1;
+  const bool cubic = f->interp >= 1;  /* p = 1.25, kappa 24 */
   const int64_t stride[3] = {g.N[1] * g.N[2], g.N[2], 1};
   out[0] = (T)f->anchor;
   std::vector<uint32_t> words;
@@ -737,7 +761,7 @@ int reconstruct_t(const ipco_field* f, const std::vector<int>& bsel, T* out) {
             continue;
           }
           int64_t base = idx - i[d] * stride[d];
-          T pred = predict<T>(out, base, stride[d], i[d], s, g.N[d], cubic);
+          T pred = predict<T>(out, base, stride[d], i[d], s, g.N[d], f->interp);
           uint32_t N = xor_decode(E[ci]) & plane_mask(b);
           int64_t qv = negabinary_inv(N);
           T r = (T)qv * twoeb;
@@ -814,7 +838,7 @@ int delta_t(const ipco_field* f, const std::vector<int>& bold, const std::vector
             std::vector<std::vector<uint32_t>>* N, T* out) {
   const Geometry& g = f->g;
   const T twoeb = (T)(2.0 * half_bin(f->eb, f->xmaxabs, f->dtype));
-  const bool cubic = f->interp == 1;
+  const bool cubic = f->interp >= 1;  /* p = 1.25, kappa 24 */
   const int64_t stride[3] = {g.N[1] * g.N[2], g.N[2], 1};
   std::vector<T> D(g.n, (T)0);  /* Delta; the anchor never changes */
   std::vector<std::vector<uint32_t>> Nn = *N;
@@ -851,7 +875,7 @@ int delta_t(const ipco_field* f, const std::vector<int>& bold, const std::vector
             continue;
           }
           int64_t base = idx - i[d] * stride[d];
-          T pred = predict<T>(D.data(), base, stride[d], i[d], s, g.N[d], cubic);
+          T pred = predict<T>(D.data(), base, stride[d], i[d], s, g.N[d], f->interp);
           uint32_t nd = bn < bo ? decode_window(E[ci], (*N)[t][ci], bn, bo) : 0u;
           int64_t dq = negabinary_inv(nd);  /* value of the new digits */
           T r = (T)dq * twoeb;
@@ -880,7 +904,7 @@ void delta_bound(const ipco_field* f, const ipco_view* v, const std::vector<int>
   if (f->bound != 0) { *Gd = Gnew; *racc = 0; return; }
   const Geometry& g = f->g;
   const int S = (int)g.stages.size();
-  const bool cubic = f->interp == 1;
+  const bool cubic = f->interp >= 1;  /* p = 1.25, kappa 24 */
   int lc = 0;
   for (int l = 1; l <= g.K; ++l)
     if (b[l - 1] < v->b[l - 1]) lc = l;
@@ -918,7 +942,7 @@ int parse(const uint8_t* p, uint64_t len, ipco_field* f) {
   f->eb_user = r.f64(); f->eb = r.f64();
   f->xmin = r.f64(); f->xmax = r.f64(); f->xmaxabs = r.f64(); f->anchor = r.f64();
   uint32_t S = r.u32(); r.u32();
-  if (!r.ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 1 ||
+  if (!r.ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 2 ||
       f->bound < 0 || f->bound > 1 || f->eb_mode < 0 || f->eb_mode > 1)
     return IPCO_ECORRUPT;
   for (int e = 0; e < ndim && e < 3; ++e)
@@ -999,7 +1023,7 @@ extern "C" {
 int ipco_compress(const void* x, int dtype, int ndim, const int64_t* dims,
                   int eb_mode, double eb, int interp, int bound,
                   ipco_field** out) {
-  if (!x || !out || dtype < 0 || dtype > 1 || interp < 0 || interp > 1 ||
+  if (!x || !out || dtype < 0 || dtype > 1 || interp < 0 || interp > 2 ||
       bound < 0 || bound > 1 || eb_mode < 0 || eb_mode > 1 || !std::isfinite(eb) ||
       !(eb > 0))
     return IPCO_EINVAL;

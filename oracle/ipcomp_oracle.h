@@ -31,7 +31,8 @@ typedef struct ipco_view ipco_view;
 
 /* Compress x (dtype 0 = f32, 1 = f64; row-major, last dim fastest).
  * eb_mode 0 = absolute, 1 = relative to (max - min). interp 0 linear,
- * 1 cubic. bound 0 strict, 1 paper. */
+ * 1 cubic, 2 cubic with quadratic boundaries (see the predictor in the
+ * .cpp). bound 0 strict, 1 paper. */
 int ipco_compress(const void* x, int dtype, int ndim, const int64_t* dims,
                   int eb_mode, double eb, int interp, int bound,
                   ipco_field** out);

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 OK, EINVAL, EBOUND, EBUDGET, ENOMEM, ECORRUPT = 0, -1, -2, -3, -4, -5
 F32, F64 = 0, 1
-LINEAR, CUBIC = 0, 1
+LINEAR, CUBIC, CUBIC_QUAD = 0, 1, 2
 ABS, REL = 0, 1
 STRICT, PAPER = 0, 1
 EB, BITRATE = 0, 1

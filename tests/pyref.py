@@ -126,10 +126,17 @@ def _pred(T, xh, N, idx3, d, s, cubic):
     if i + s > N[d] - 1:
         return b
     c = at(i + s)
-    if cubic and i - 3 * s >= 0 and i + 3 * s <= N[d] - 1:
+    left, right = i - 3 * s >= 0, i + 3 * s <= N[d] - 1
+    if cubic and left and right:
         a = at(i - 3 * s)
         dd = at(i + 3 * s)
         return (T.t(9) * (b + c) - (a + dd)) * T.t(0.0625)
+    # mode 2: the quadratic through the three neighbours that exist
+    # (Lagrange weights 3/8, 6/8, -1/8 at distances s, s, 3s)
+    if cubic == 2 and right:
+        return (T.t(3) * b + T.t(6) * c - at(i + 3 * s)) * T.t(0.125)
+    if cubic == 2 and left:
+        return (T.t(6) * b + T.t(3) * c - at(i - 3 * s)) * T.t(0.125)
     return (b + c) * T.t(0.5)
 
 
@@ -195,7 +202,7 @@ def compress(x: np.ndarray, eb_user: float, eb_mode=0, cubic=True, bound=0):
             codes.append(q)
             outl.append(ol)
     # container
-    hdr = struct.pack("<6I", 0x31435049, 1, 0 if T.is32 else 1, 1 if cubic else 0, bound,
+    hdr = struct.pack("<6I", 0x31435049, 1, 0 if T.is32 else 1, int(cubic), bound,
                       x.ndim)
     dims = list(x.shape) + [0] * (3 - x.ndim)
     hdr += struct.pack("<3Q", *dims)

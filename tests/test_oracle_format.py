@@ -12,7 +12,9 @@ CASES = [((7,), np.float32, "smooth", 1e-2, 1), ((40,), np.float64, "noise", 1e-
          ((6, 9), np.float32, "smooth", 1e-4, 1), ((5, 4, 3), np.float32, "spiky", 1e-3, 1),
          ((9, 9), np.float64, "ramp", 1e-5, 0), ((3, 5, 7), np.float32, "noise", 1e-1, 0),
          ((2, 1, 33), np.float32, "smooth", 1e-6, 1), ((1,), np.float32, "smooth", 1e-3, 1),
-         ((66,), np.float32, "smooth", 1e-7, 1)]
+         ((66,), np.float32, "smooth", 1e-7, 1), ((40,), np.float64, "noise", 1e-3, 2),
+         ((6, 9), np.float32, "smooth", 1e-4, 2), ((5, 4, 7), np.float32, "spiky", 1e-3, 2),
+         ((17, 3, 11), np.float64, "smooth", 1e-6, 2)]
 
 
 @pytest.mark.parametrize("shape,dtype,kind,eb,cubic", CASES)
@@ -20,18 +22,18 @@ def test_bytes_equal_independent_restatement(oracle, shape, dtype, kind, eb, cub
     x = synth.random_field(shape, seed=len(shape) * 13 + int(-np.log10(eb)), dtype=dtype, kind=kind)
     for mode in (oracle.ABS, oracle.REL):
         f = oracle.compress(x, eb, mode, cubic)
-        ref, codes = pyref.compress(x, eb, mode, bool(cubic))
+        ref, codes = pyref.compress(x, eb, mode, cubic)
         got = f.export()
         assert got == ref
         for t in range(f.info()["S"]):
             assert f.codes(t).tolist() == codes[t]
 
 
-@pytest.mark.parametrize("shape,dtype,kind,eb,cubic", CASES[:6])
+@pytest.mark.parametrize("shape,dtype,kind,eb,cubic", CASES[:6] + CASES[-3:])
 def test_reconstruction_equals_restatement(oracle, shape, dtype, kind, eb, cubic):
     x = synth.random_field(shape, seed=3, dtype=dtype, kind=kind)
     f = oracle.compress(x, eb, oracle.REL, cubic)
-    _, codes = pyref.compress(x, eb, oracle.REL, bool(cubic))
+    _, codes = pyref.compress(x, eb, oracle.REL, cubic)
     info = f.info()
     K = info["K"]
     st, _ = pyref.stages(shape)
@@ -53,7 +55,7 @@ def test_reconstruction_equals_restatement(oracle, shape, dtype, kind, eb, cubic
     for b in [[0] * K, [32] * K] + [list(rng.integers(0, 33, size=K)) for _ in range(6)]:
         mine = f.reconstruct(b)
         ref = pyref.reconstruct(shape, dtype, codes, outl, float(x.reshape(-1)[0]),
-                                info["eb"], b, bool(cubic), info["xmaxabs"])
+                                info["eb"], b, cubic, info["xmaxabs"])
         assert np.array_equal(mine, ref, equal_nan=True), b
 
 

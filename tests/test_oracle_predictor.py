@@ -10,6 +10,7 @@ import pytest
 
 import pyref
 from helpers import exact_eb
+from paper_2502_04093_gb300 import synth
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 
@@ -125,3 +126,66 @@ def test_separable_cubic_3d(oracle):
                 assert q[c] == 0
                 zeros += 1
     assert zeros > 100
+
+
+@pytest.mark.parametrize("N", [9, 17, 33, 65, 100])
+def test_quadratic_boundaries_exact_on_quadratics(oracle, N):
+    """Mode 2: a quadratic sequence is predicted exactly wherever a target has
+    both near neighbours and at least one of the far ones: by Eq. 2 inside,
+    by the three-point quadratic where one far neighbour is missing. Plain
+    cubic mode falls back to Eq. 1 there, which misses the curvature."""
+    i = np.arange(N, dtype=np.float64)
+    x = (2 * i ** 2 - 9 * i + 4).astype(np.float32)
+    eb = exact_eb(x)
+    fq = oracle.compress(x, eb, oracle.ABS, oracle.CUBIC_QUAD)
+    fc = oracle.compress(x, eb, oracle.ABS, oracle.CUBIC)
+    boundary = 0
+    for t in range(fq.info()["S"]):
+        st = fq.stage(t)
+        q, qc = fq.codes(t), fc.codes(t)
+        s = 1 << (st["level"] - 1)
+        for c, pos in enumerate(_positions_1d(N, st["level"], st["ncodes"])):
+            if pos + s > N - 1:
+                continue  # copy rule
+            left, right = pos - 3 * s >= 0, pos + 3 * s <= N - 1
+            if left or right:
+                assert q[c] == 0, (pos, s)
+            if left != right:
+                boundary += 1
+                assert qc[c] != 0  # Eq. 1 is not exact on a quadratic
+        assert st["noutliers"] == 0
+    assert boundary > 0
+
+
+def test_quadratic_weights_and_norm():
+    """The three-point weights are the Lagrange weights at 0 of the nodes
+    -1, 1, 3 (left end) and -3, -1, 1 (right end), in units of s; their
+    absolute sum is 1.25, the cubic stencil's infinity norm (Sec. 5.1)."""
+    from fractions import Fraction as Fr
+
+    def lagrange_at0(nodes):
+        out = []
+        for j, xj in enumerate(nodes):
+            w = Fr(1)
+            for m, xm in enumerate(nodes):
+                if m != j:
+                    w *= Fr(0 - xm, xj - xm)
+            out.append(w)
+        return out
+    assert lagrange_at0([-1, 1, 3]) == [Fr(3, 8), Fr(6, 8), Fr(-1, 8)]
+    assert lagrange_at0([-3, -1, 1]) == [Fr(-1, 8), Fr(6, 8), Fr(3, 8)]
+    assert sum(abs(w) for w in lagrange_at0([-1, 1, 3])) == Fr(5, 4)
+
+
+def test_quadratic_mode_errors_and_costs(oracle):
+    """Mode 2 keeps the error guarantee (Theorem 1 with the cubic mode's
+    p = 1.25), at the full precision and at every selection; an unknown
+    interpolation mode is refused."""
+    x = synth.random_field((33, 20, 17), seed=4, dtype=np.float32, kind="smooth")
+    f = oracle.compress(x, 1e-5, oracle.REL, oracle.CUBIC_QUAD)
+    y, v = f.retrieve(oracle.EB, 1e-5)
+    assert np.abs(y.astype(np.float64) - x).max() <= f.info()["eb"]
+    for E in (1e-2, 1e-3):
+        y, v = f.retrieve(oracle.EB, E)
+        assert np.abs(y.astype(np.float64) - x).max() <= v.selection()[2]
+    assert oracle.compress_rc(x, 1e-3, interp=3) == oracle.EINVAL
