@@ -67,7 +67,8 @@ def parse():
     return ap.parse_args()
 
 
-KERNEL_SOURCES = ("ipc_device.cuh", "ipc_internal.h", "ipc_level.cu")
+KERNEL_SOURCES = ("ipc_device.cuh", "ipc_internal.h", "ipc_level_body.cuh",
+                  "ipc_level_kernels.cuh", "ipc_level.cu")
 
 
 def kernel_sources_sha256() -> str:

@@ -51,8 +51,12 @@ enum {
 };
 
 typedef enum { IPC_F32 = 0, IPC_F64 = 1 } ipc_dtype;
-/* Eq. 1 (linear, p = 1) or Eq. 2 (cubic, p = 1.25), Sec. 4.1. */
-typedef enum { IPC_LINEAR = 0, IPC_CUBIC = 1 } ipc_interp;
+/* Eq. 1 (linear, p = 1) or Eq. 2 (cubic, p = 1.25), Sec. 4.1; a cubic
+ * target missing one far neighbour takes Eq. 1 (IPC_CUBIC) or the
+ * three-point quadratic through its two near neighbours and the far one
+ * that exists (IPC_CUBIC_QUAD: weights 3/8, 6/8, -1/8, infinity norm 1.25,
+ * so p and the error model are the cubic ones). */
+typedef enum { IPC_LINEAR = 0, IPC_CUBIC = 1, IPC_CUBIC_QUAD = 2 } ipc_interp;
 /* Error bound absolute, or relative to the value range (max - min). */
 typedef enum { IPC_EB_ABS = 0, IPC_EB_REL = 1 } ipc_eb_mode;
 /* Error model of the loader (Sec. 5.1, Theorem 1): STRICT amplifies every

@@ -1,8 +1,9 @@
 // The coarse levels of a reconstruction in one CTA per field (sm_103a).
 //
-// A level's launch in ipc_level.cu costs a dependent chain of global loads
-// per tile (bitmaps, plane words, known points) whatever the level's size,
-// so the small coarse levels take several microseconds each for a few
+// A level's launch of the tile kernels (ipc_level_kernels.cuh) costs a
+// dependent chain of global loads per tile (bitmaps, plane words, known
+// points) whatever the level's size, so the small coarse levels take
+// several microseconds each for a few
 // thousand points. Here one CTA reconstructs levels K .. Lc together in
 // shared memory (Algorithm 1), Lc chosen by the host so that the level-Lc
 // lattice and the codes of every stage of those levels fit:
@@ -11,8 +12,8 @@
 //     top-down, transposed) into a code buffer -- the codes do not depend on
 //     the values, so all of the loads are in flight together;
 //   phase B: the stages in order (coarse to fine, dimension 0..2), each
-//     target predicted from the values of earlier stages (Eq. 1 / Eq. 2 with
-//     the boundary rule, the compressor's operation order), plus its code's
+//     target predicted from the values of earlier stages (pred4: Eq. 1 /
+//     Eq. 2 with the boundary rule, the compressor's operation order), plus its code's
 //     value times 2e_q, or the outlier's exact value;
 //   the level-Lc lattice is then written densely: the known points of level
 //   Lc - 1, or the caller's array when Lc = 1.
@@ -43,21 +44,21 @@ __device__ __forceinline__ void outlier_value(const CoarseStage& S, const uint64
   if (lo < S.out_end && __ldg(idx + lo) == ci) *v = (T)__ldg(val + lo);
 }
 
+// pred4 on the dense level-Lc lattice: idx the target, st the lattice
+// stride of one level-l step along the sweep; a far neighbour is read only
+// where it lies on the lattice and the form uses it.
 template <class T>
 __device__ __forceinline__ T coarse_pred(const T* v, int64_t idx, int64_t st, int i, int M,
-                                         int cubic) {
-  // i: the target's coordinate along the sweep in its level's lattice (odd)
+                                         int interp) {
   const T b = v[idx - st];
   if (i + 1 > M - 1) return b;
   const T c = v[idx + st];
-  if (cubic && i - 3 >= 0 && i + 3 <= M - 1) {
-    const T a = v[idx - 3 * st], d = v[idx + 3 * st];
-    const T u = FP<T>::add(b, c);
-    const T w = FP<T>::add(a, d);
-    const T z = FP<T>::sub(FP<T>::mul((T)9, u), w);
-    return FP<T>::mul(z, (T)0.0625);
-  }
-  return FP<T>::mul(FP<T>::add(b, c), (T)0.5);
+  const bool left = i - 3 >= 0, right = i + 3 <= M - 1;
+  // far neighbours: both for Eq. 2, the one that exists for the quadratic
+  const bool far = interp == 2 || (interp != 0 && left && right);
+  const T a = far && left ? v[idx - 3 * st] : b;
+  const T d = far && right ? v[idx + 3 * st] : b;
+  return pred4<T>(a, b, c, d, i, M, interp);
 }
 
 template <class T>
@@ -144,7 +145,7 @@ __device__ void coarse_body(const CoarseArgs& a, unsigned char* smem) {
       const int64_t p2 = d == 2 ? 2 * (int64_t)c2 + 1 : 2 * (int64_t)c2;
       const int64_t idx = ((p0 << f) * s0) + ((p1 << f) * s1) + (p2 << f);
       const int i = (int)(d == 0 ? p0 : (d == 1 ? p1 : p2));
-      const T pred = coarse_pred<T>(val, idx, sd, i, (int)M, a.cubic);
+      const T pred = coarse_pred<T>(val, idx, sd, i, (int)M, a.interp);
       T v = FP<T>::add(pred, FP<T>::mul(code_value(code[S.code_off + ci], T()), twoeb));
       if (has_out) outlier_value<T>(S, a.oidx, a.oval, ci, &v);
       val[idx] = v;

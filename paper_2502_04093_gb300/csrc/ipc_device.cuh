@@ -58,6 +58,50 @@ static __device__ __noinline__ float code_value_wide(uint32_t n) {
   return __ll2float_rn((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
 }
 // 1 if the code's value needs the wide conversion (|q| >= 2^22 or n >= 2^31).
+// Interpolation along one dimension (Sec. 4.1), for a target at odd lattice
+// coordinate i of extent M whose lattice neighbours at i - 3, i - 1, i + 1,
+// i + 3 are a, b, c, d. interp: 0 linear (Eq. 1), 1 cubic (Eq. 2, Eq. 1
+// where a far neighbour is missing), 2 cubic with the three-point quadratic
+// through b, c and the far neighbour that exists where the other is missing;
+// the last odd point with no right neighbour copies b. a (d) is used only
+// when i - 3 (i + 3) lies on the lattice. Each form keeps one fixed operation
+// order, without contraction: the compressor and every reconstruction round
+// identically.
+template <class T>
+__device__ __forceinline__ T quad3(T a, T b, T c, T d, bool right) {
+  // weights 3/8, 6/8, -1/8 (far neighbour on the right) or mirrored
+  const T u = FP<T>::mul(right ? (T)3 : (T)6, b);
+  const T v = FP<T>::mul(right ? (T)6 : (T)3, c);
+  return FP<T>::mul(FP<T>::sub(FP<T>::add(u, v), right ? d : a), (T)0.125);
+}
+
+// Q = false compiles the quadratic forms out (interp 0 or 1 only).
+template <class T, bool Q = true>
+__device__ __forceinline__ T pred4(T a, T b, T c, T d, int i, int M, int interp) {
+  if (i + 1 > M - 1) return b;
+  if (interp != 0 && i - 3 >= 0 && i + 3 <= M - 1) {
+    const T u = FP<T>::add(b, c);
+    const T v = FP<T>::add(a, d);
+    const T w = FP<T>::mul((T)9, u);
+    const T z = FP<T>::sub(w, v);
+    return FP<T>::mul(z, (T)0.0625);
+  }
+  if (Q && interp == 2 && (i - 3 >= 0 || i + 3 <= M - 1))
+    return quad3<T>(a, b, c, d, i + 3 <= M - 1);
+  return FP<T>::mul(FP<T>::add(b, c), (T)0.5);
+}
+
+// Which form pred4 takes at coordinate i: 0 copy, 1 Eq. 1, 2 Eq. 2,
+// 4 quadratic with d, 5 quadratic with a (bit 2: a quadratic form).
+template <bool Q = true>
+__device__ __forceinline__ uint32_t pred_rule(int i, int M, int interp) {
+  if (i + 1 > M - 1) return 0u;
+  if (interp != 0 && i - 3 >= 0 && i + 3 <= M - 1) return 2u;
+  if (Q && interp == 2 && i + 3 <= M - 1) return 4u;
+  if (Q && interp == 2 && i - 3 >= 0) return 5u;
+  return 1u;
+}
+
 __device__ __forceinline__ unsigned code_wide(uint32_t n, int* q) {
   *q = (int)((n ^ 0xAAAAAAAAu) - 0xAAAAAAAAu);
   return (n >> 31) | ((unsigned)(*q + (1 << 22)) >> 23);

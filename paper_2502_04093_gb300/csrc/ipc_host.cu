@@ -165,7 +165,7 @@ bool build_geo(int ndim, const int64_t* dims, int dtype, Geo* g) {
       sg.ncodes = sg.rows * (uint64_t)sg.m[2];
       sg.wr = ((uint64_t)sg.m[2] + 31) / 32;
       sg.words = sg.rows * sg.wr;
-      // segments = the words of one level-kernel CTA (see ipc_level.cu)
+      // segments = the words of one level-kernel CTA (see ipc_level_kernels.cuh)
       sg.RB = d == 2 ? BR : BR / 2;
       sg.CW = (uint32_t)std::min<uint64_t>(CWD, sg.wr);
       sg.nrb = ((uint64_t)sg.m[1] + sg.RB - 1) / sg.RB;
@@ -428,7 +428,7 @@ LevelArgs level_args(const ipc_field* f, int l) {
   L.stride[1] = g.N[2];
   L.stride[0] = g.N[1] * g.N[2];
   L.s = s;
-  L.cubic = f->interp == IPC_CUBIC;
+  L.interp = f->interp;
   const int BR = level_rows(f->dtype);
   L.nrb = ((uint64_t)L.M[1] + BR - 1) / BR;
   L.nct = ((uint64_t)L.M[2] + kLevelCols - 1) / kLevelCols;
@@ -781,7 +781,9 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
         const CompressEntry& e = ents[lev_off[l]];
         CU(launch_level_compress(dtype, e.L, e.x, e.xh, e.write_xh, e.quant, e.o, e.D, st));
       } else {
-        CU(launch_level_compress_batch(dtype, d_ents + lev_off[l], n_l, lev_ctas[l], st));
+        int quad = 0;  // a field of the level with quadratic boundaries
+        for (int q = 0; q < n_l; ++q) quad |= ents[lev_off[l] + q].L.interp == 2;
+        CU(launch_level_compress_batch(dtype, d_ents + lev_off[l], n_l, lev_ctas[l], quad, st));
       }
       uint64_t nc = 0;
       for (int q = 0; q < n_l; ++q) {
@@ -958,7 +960,7 @@ bool coarse_plan(const ipc_field* f, const std::vector<int>& b, void* out, Coars
   if (g.K < 1) return false;
   std::memset(a, 0, sizeof(*a));
   a->K = g.K;
-  a->cubic = f->interp == IPC_CUBIC;
+  a->interp = f->interp;
   a->esz = f->dtype == 0 ? 4 : 8;
   a->anchor = f->anchor;
   a->twoeb = bin_width(f);
@@ -1198,6 +1200,7 @@ struct BatchTable {
     int w16 = 1;        // 16-bit code rows
     int ns = 1;         // sub-tiles per tile
     int psm = 0;        // CTAs per SM (0: as many as fit)
+    int quad = 0;       // some entry interpolates with quadratic boundaries
   };
   std::vector<Launch> launches;
   uint64_t scratch = 0;      // bytes of the fields' scratch ladders
@@ -1269,6 +1272,7 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       int seen = 0;
       for (size_t i : group[w16]) {
         const LevelArgs La = level_args(fs[i], l);
+        ln.quad |= fs[i]->interp == IPC_CUBIC_QUAD;
         ns = std::min(ns, retrieve_subtiles(La.M[2], w16));
         const ShapeKey k = shape_key(fs[i]->dtype, w16, La);
         if (seen++ && (k < key || key < k)) same = false;
@@ -1342,7 +1346,7 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
     const BatchTable::Launch& ln = T.launches[j];
     const long ph = profile ? prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st) : -1;
     CU(launch_level_retrieve_batch(dtype, d_ents + ln.off, ln.n, ln.ctas, ln.w16, ln.ns, ln.psm,
-                                   st));
+                                   ln.quad, st));
     if (profile) prof_end(ph, st, j + 1 == T.launches.size() ? T.alg_bytes : 0.0);
     ++nl;
   }
@@ -1462,7 +1466,7 @@ int parse_head(const uint8_t* p, uint64_t len, ipc_field* f, uint64_t* pos_out,
   f->anchor = gd();
   const uint32_t S = g32();
   g32();
-  if (!ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 1 || f->bound < 0 ||
+  if (!ok || f->dtype < 0 || f->dtype > 1 || f->interp < 0 || f->interp > 2 || f->bound < 0 ||
       f->bound > 1 || f->eb_mode < 0 || f->eb_mode > 1 || !(f->eb > 0) || !std::isfinite(f->eb)) {
     *why = "bad header fields";
     return IPC_ECORRUPT;
@@ -1512,7 +1516,7 @@ int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims, int
   g_err.clear();
   if (!d_in || !out) return fail(IPC_EINVAL, "null argument");
   if (dtype != IPC_F32 && dtype != IPC_F64) return fail(IPC_EINVAL, "dtype");
-  if (interp != IPC_LINEAR && interp != IPC_CUBIC) return fail(IPC_EINVAL, "interp");
+  if (interp < IPC_LINEAR || interp > IPC_CUBIC_QUAD) return fail(IPC_EINVAL, "interp");
   if (bound != IPC_BOUND_STRICT && bound != IPC_BOUND_PAPER) return fail(IPC_EINVAL, "bound");
   if (eb_mode != IPC_EB_ABS && eb_mode != IPC_EB_REL) return fail(IPC_EINVAL, "eb_mode");
   if (!std::isfinite(eb) || !(eb > 0)) return fail(IPC_EINVAL, "eb must be > 0 and finite");
@@ -2124,7 +2128,7 @@ int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, i
   for (int i = 0; i < nfields; ++i) {
     const ipc_batch_item& it = items[i];
     if (!it.d_in || (it.dtype != IPC_F32 && it.dtype != IPC_F64) ||
-        (it.interp != IPC_LINEAR && it.interp != IPC_CUBIC) ||
+        it.interp < IPC_LINEAR || it.interp > IPC_CUBIC_QUAD ||
         (it.bound != IPC_BOUND_STRICT && it.bound != IPC_BOUND_PAPER) ||
         (it.eb_mode != IPC_EB_ABS && it.eb_mode != IPC_EB_REL) || !std::isfinite(it.eb) ||
         !(it.eb > 0))

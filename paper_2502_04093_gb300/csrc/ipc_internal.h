@@ -69,7 +69,7 @@ struct StagePlanes {
 struct LevelArgs {
   int64_t N[3], stride[3], M[3];  // extents, element strides, lattice extents
   int64_t s;
-  int cubic;
+  int interp;         // 0 linear, 1 cubic, 2 cubic with quadratic boundaries
   int vec;            // output base aligned to two elements (paired stores allowed)
   int stream_out;     // reconstruction: the output is the caller's array, written
                       // with evict-first stores (kept out of L2's way)
@@ -105,7 +105,7 @@ struct CoarseStage {
   uint64_t code_off;       // first code of the stage in the shared code buffer
 };
 struct CoarseArgs {
-  int nst, K, Lc, cubic;
+  int nst, K, Lc, interp;
   int esz;                 // element bytes
   int64_t ML[3];           // level-Lc lattice extents
   double anchor, twoeb;
@@ -237,7 +237,10 @@ cudaError_t launch_range_batch(int dtype, const RangeBatch& rb, int n, uint64_t 
                                cudaStream_t st);
 cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st);
 cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStream_t st);
-// Fused level kernels (ipc_level.cu).
+// Fused level kernels (ipc_level.cu; the variants with the quadratic
+// boundary forms, for interp 2, in ipc_level_quad.cu and
+// ipc_level_delta_quad.cu -- the single-field launchers pick them by
+// L.interp, the batched ones by `quad`: some entry has interp 2).
 cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, void* xh,
                                   int write_xh, const void* quant, const SweepOut& o,
                                   const LevelDescs& d, cudaStream_t st);
@@ -290,11 +293,28 @@ cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, doub
 int level_rows(int dtype);
 // Batched level launches: `ents` (device memory) sorted by cta_begin.
 cudaError_t launch_level_compress_batch(int dtype, const CompressEntry* ents, int n,
-                                        uint64_t ctas, cudaStream_t st);
+                                        uint64_t ctas, int quad, cudaStream_t st);
 // Batched: `tiles` over all entries, each entry's tiles counted with `ns`.
 cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, int n,
-                                        uint64_t tiles, int w16, int ns, int per_sm,
+                                        uint64_t tiles, int w16, int ns, int per_sm, int quad,
                                         cudaStream_t st);
+cudaError_t launch_level_compress_quad(int dtype, const LevelArgs& L, const void* x, void* xh,
+                                       int write_xh, const void* quant, const SweepOut& o,
+                                       const LevelDescs& d, cudaStream_t st);
+cudaError_t launch_level_retrieve_quad(int dtype, const LevelArgs& L, void* out, double twoeb,
+                                       int b, const uint32_t* cap, const uint32_t* bm,
+                                       const uint64_t* oidx, const double* oval, int w16,
+                                       RetrieveShape shape, cudaStream_t st);
+cudaError_t launch_level_compress_batch_quad(int dtype, const CompressEntry* ents, int n,
+                                             uint64_t ctas, cudaStream_t st);
+cudaError_t launch_level_retrieve_batch_quad(int dtype, const RetrieveEntry* ents, int n,
+                                             uint64_t tiles, int w16, int ns, int per_sm,
+                                             cudaStream_t st);
+cudaError_t launch_level_retrieve_mode_quad(int dtype, const LevelArgs& L, void* out,
+                                            double twoeb, int b, const uint32_t* cap,
+                                            const uint32_t* bm, const uint64_t* oidx,
+                                            const double* oval, int w16, RetrieveShape shape,
+                                            int mode, cudaStream_t st);
 // Segmented <-> packed container streams of one stage (export / import).
 // tmp: 2 * 32 * nbm words of scratch; flags[0] = corruption flag,
 // flags[1 + k] = nonzero words found in plane k (import).

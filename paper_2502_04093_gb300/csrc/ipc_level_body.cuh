@@ -1,8 +1,8 @@
 // Reconstruction tile of the fused level kernels of libipcomp (sm_103a),
 // shared by the units that instantiate its kernels (the plain reconstruction
-// in ipc_level.cu, the incremental and state-recording forms in
-// ipc_level_delta.cu). Device code only; see ipc_level.cu for the tile
-// layout.
+// in ipc_level_kernels.cuh, the incremental and state-recording forms
+// below, for ipc_level_delta.cu and ipc_level_delta_quad.cu). See
+// ipc_level_kernels.cuh for the tile layout.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -38,22 +38,6 @@ __device__ __forceinline__ CtaPos cta_pos(const LevelArgs& L, uint64_t cta, int 
   c.pbase = (int64_t)c.P * L.stride[0] * L.s;
   c.rs = L.stride[1] * L.s;
   return c;
-}
-
-
-// Prediction from four lattice neighbours along one dimension (Eq. 1/2 with
-// the boundary rule): i is the target's lattice coordinate, M the extent.
-template <class T>
-__device__ __forceinline__ T pred4(T a, T b, T c, T d, int i, int M, int cubic) {
-  if (i + 1 > M - 1) return b;
-  if (cubic && i - 3 >= 0 && i + 3 <= M - 1) {
-    const T u = FP<T>::add(b, c);
-    const T v = FP<T>::add(a, d);
-    const T w = FP<T>::mul((T)9, u);
-    const T z = FP<T>::sub(w, v);
-    return FP<T>::mul(z, (T)0.0625);
-  }
-  return FP<T>::mul(FP<T>::add(b, c), (T)0.5);
 }
 
 // Quantize x against pred (Sec. 4.2.2); returns the code, writes xhat.
@@ -430,7 +414,8 @@ __device__ __forceinline__ void add_run(T* row, int c2e, int C1, const T (&v)[8]
     if (c2e + i < C1 && v[i] != (T)0) p[i] = FP<T>::add(p[i], v[i]);
 }
 
-template <class T, int BR, int BC, bool W16, int NS, int MODE = kPlain>
+// Q: the quadratic boundary forms of pred4 compiled in (interp 2 possible).
+template <class T, int BR, int BC, bool W16, int NS, int MODE = kPlain, bool Q = false>
 __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, T twoeb, int b,
                                                     const uint32_t* __restrict__ cap,
                                                     const uint32_t* __restrict__ bm,
@@ -462,7 +447,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   auto Q1of = [&](int s) { return Q2of(s) + BR * G::QP; };
   auto Q0of = [&](int s) { return Q1of(s) + G::H1 * G::QP; };
   auto QHof = [&](int s) { return reinterpret_cast<uint32_t*>(Q0of(s) + G::H0 * G::QP); };
-  const int cubic = L.cubic;
+  const int interp = L.interp;
   const int M0 = (int)L.M[0], M1 = (int)L.M[1], M2 = (int)L.M[2];
   const LevelStage &S0 = L.st[0], &S1 = L.st[1], &S2 = L.st[2];
 
@@ -542,14 +527,17 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const T* kin = reinterpret_cast<const T*>(L.kin);
     const int64_t k0 = L.kst0, k1 = L.kst1;
     const bool r1 = c.P + 1 <= M0 - 1;
-    const bool r3 = cubic && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
+    // far planes read: Eq. 2 needs both, the quadratic the one that exists
+    const bool r3 = interp != 0 && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
+    const bool ra = Q && interp == 2 ? r1 && c.P - 3 >= 0 : r3;
+    const bool rd = Q && interp == 2 ? c.P + 3 <= M0 - 1 : r3;
     auto one = [&](const T* p) -> T {
       if (!podd) return __ldg(p);
       const T bb = __ldg(p);
       const T cc = r1 ? __ldg(p + k0) : bb;
-      const T a = r3 ? __ldg(p - k0) : bb;
-      const T d = r3 ? __ldg(p + 2 * k0) : bb;
-      return pred4<T>(a, bb, cc, d, c.P, M0, cubic);
+      const T a = ra ? __ldg(p - k0) : bb;
+      const T d = rd ? __ldg(p + 2 * k0) : bb;
+      return pred4<T, Q>(a, bb, cc, d, c.P, M0, interp);
     };
     const T* kplane = kin + (int64_t)(c.P >> 1) * k0;
     if (pa) {
@@ -575,10 +563,10 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
           } else {
             const V2 bb = __ldg(p2);
             const V2 cc = r1 ? __ldg(reinterpret_cast<const V2*>(p + k0)) : bb;
-            const V2 a = r3 ? __ldg(reinterpret_cast<const V2*>(p - k0)) : bb;
-            const V2 d = r3 ? __ldg(reinterpret_cast<const V2*>(p + 2 * k0)) : bb;
-            v2.x = pred4<T>(a.x, bb.x, cc.x, d.x, c.P, M0, cubic);
-            v2.y = pred4<T>(a.y, bb.y, cc.y, d.y, c.P, M0, cubic);
+            const V2 a = ra ? __ldg(reinterpret_cast<const V2*>(p - k0)) : bb;
+            const V2 d = rd ? __ldg(reinterpret_cast<const V2*>(p + 2 * k0)) : bb;
+            v2.x = pred4<T, Q>(a.x, bb.x, cc.x, d.x, c.P, M0, interp);
+            v2.y = pred4<T, Q>(a.y, bb.y, cc.y, d.y, c.P, M0, interp);
           }
         } else {
           v2.x = one(p);
@@ -840,7 +828,7 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
   {
     const bool has1 = S1.out_end > S1.out_begin;
     auto value = [&](T a, T bb, T cc, T d, int c1, int c2, T cv) {
-      const T pred = pred4<T>(a, bb, cc, d, c1, M1, cubic);
+      const T pred = pred4<T, Q>(a, bb, cc, d, c1, M1, interp);
       T v = FP<T>::add(pred, cv);
       if (has1) {
         const uint64_t ci = ((uint64_t)c.P * S1.m1 + (uint64_t)((c1 - 1) >> 1)) * S1.m2 +
@@ -895,15 +883,14 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     constexpr int NG = G::HC / 4;  // four-column groups per row
     const int g = ltid % NG, rq = ltid / NG;
     const int c2e = c.C0 + 8 * g;  // first (even) lattice column of the run
-    // per odd column k of the run: 2 = cubic, 1 = linear, 0 = copy (the
-    // boundary rule of pred4), two bits each
+    // per odd column k of the run: the form pred4 takes there (pred_rule),
+    // RW bits each
+    constexpr int RW = Q ? 3 : 2;
     uint32_t rule = 0u;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = c2e + 2 * k + 1;
-      const uint32_t r = i + 1 > M2 - 1 ? 0u : ((cubic && i - 3 >= 0 && i + 3 <= M2 - 1) ? 2u : 1u);
-      rule |= r << (2 * k);
-    }
+    for (int k = 0; k < 4; ++k) rule |= pred_rule<Q>(c2e + 2 * k + 1, M2, interp) << (RW * k);
+    // a quadratic boundary form in the run (only runs at the ends of a row)
+    const bool quad = Q && (rule & 04444u) != 0u;
     if (live && c2e < c.C1) {
       for (int lr = rq; lr < BR; lr += 4) {
         const int c1 = c.R0 + lr;
@@ -916,15 +903,25 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           // Eq. 2 and Eq. 1 side by side (same operations as pred4), then
-          // the rule for this column; no lane takes a separate path.
+          // the rule for this column; no lane takes a separate path (the
+          // quadratic forms are redone below).
           const T u = FP<T>::add(w[k + 1], w[k + 2]);
           const T cub = FP<T>::mul(FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])),
                                    (T)0.0625);
           const T lin = FP<T>::mul(u, (T)0.5);
-          const uint32_t r = rule >> (2 * k) & 3u;
+          const uint32_t r = rule >> (RW * k) & ((1u << RW) - 1u);
           const T pred = r == 2u ? cub : (r == 1u ? lin : w[k + 1]);
           v[2 * k] = w[k + 1];
           v[2 * k + 1] = FP<T>::add(pred, cv[k]);
+        }
+        if (quad) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t r = rule >> (RW * k) & 7u;
+            if (r & 4u)
+              v[2 * k + 1] =
+                  FP<T>::add(quad3<T>(w[k], w[k + 1], w[k + 2], w[k + 3], r == 4u), cv[k]);
+          }
         }
         if (has2) {
 #pragma unroll
@@ -980,6 +977,80 @@ inline unsigned persistent_grid(uint64_t tiles, int per_sm) {
 }
 // CTAs per SM of a persistent grid: the shape's, within what fits.
 inline int grid_per_sm(int want, int most) { return want > 0 && want < most ? want : most; }
+
+// ---------------------------------------------------------------------------
+// The recording and incremental forms (single-field launches), instantiated
+// by ipc_level_delta.cu (Q = false) and ipc_level_delta_quad.cu (Q = true).
+template <class T, int BR, int BC, bool W16, int NS, int MODE, bool Q>
+__global__ void __launch_bounds__(256, retrieve_ctas_per_sm<T, BR, W16>()) k_level_retrieve_mode(
+    LevelArgs L, T* out, T twoeb, int b, const uint32_t* __restrict__ cap,
+    const uint32_t* __restrict__ bm, const uint64_t* __restrict__ oidx,
+    const double* __restrict__ oval, uint64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    level_retrieve_body<T, BR, BC, W16, NS, MODE, Q>(L, out, twoeb, b, cap, bm, oidx, oval, t, smem);
+    __syncthreads();  // the next tile reuses shared memory
+  }
+}
+
+template <class T, int BR, int BC, bool W16, int NS, int MODE, bool Q>
+cudaError_t run_mode(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
+                     const uint32_t* bm, const uint64_t* oidx, const double* oval, int per_sm,
+                     cudaStream_t st) {
+  static const cudaError_t setup = cudaFuncSetAttribute(
+      k_level_retrieve_mode<T, BR, BC, W16, NS, MODE, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)smem_retrieve<T, BR, BC, W16, NS>());
+  if (setup != cudaSuccess) return setup;
+  const uint64_t tiles = retrieve_tiles(L, NS);
+  if (tiles == 0) return cudaSuccess;
+  k_level_retrieve_mode<T, BR, BC, W16, NS, MODE, Q>
+      <<<persistent_grid(tiles, grid_per_sm(per_sm, retrieve_ctas_per_sm<T, BR, W16>())), 256,
+         smem_retrieve<T, BR, BC, W16, NS>(), st>>>(L, (T*)out, (T)twoeb, b, cap, bm, oidx, oval,
+                                                    tiles);
+  return cudaGetLastError();
+}
+
+// BR16 / BR32: tile rows with 16-bit code rows / with 32-bit code rows and
+// several planes per tile, as for the plain kernels.
+template <class T, int BR16, int BR32, int BC, int MODE, bool Q>
+cudaError_t dispatch_mode(const LevelArgs& L, void* out, double twoeb, int b, const uint32_t* cap,
+                          const uint32_t* bm, const uint64_t* oidx, const double* oval, int w16,
+                          int ns, int per_sm, cudaStream_t st) {
+#define IPC_RM(R, W, N) \
+  return run_mode<T, R, BC, W, N, MODE, Q>(L, out, twoeb, b, cap, bm, oidx, oval, per_sm, st)
+  if (!w16) {
+    if (ns == 4) IPC_RM(BR32, false, 4);
+    if (ns == 2) IPC_RM(BR32, false, 2);
+    IPC_RM(BR16, false, 1);
+  }
+  if (ns == 4) IPC_RM(BR16, true, 4);
+  if (ns == 2) IPC_RM(BR16, true, 2);
+  IPC_RM(BR16, true, 1);
+#undef IPC_RM
+}
+
+template <bool Q>
+cudaError_t level_retrieve_mode_impl(int dtype, const LevelArgs& L, void* out, double twoeb,
+                                       int b, const uint32_t* cap, const uint32_t* bm,
+                                       const uint64_t* oidx, const double* oval, int w16,
+                                       RetrieveShape shape, int mode, cudaStream_t st) {
+  const int ns = shape.ns ? shape.ns : retrieve_subtiles(L.M[2], w16);
+  if (!retrieve_ns_ok(L.M[2], ns)) return cudaErrorInvalidValue;
+  if (retrieve_tiles(L, ns) >= (1ULL << 32)) return cudaErrorInvalidValue;  // 32-bit tile ids
+  if (mode != kRecord && mode != kDelta) return cudaErrorInvalidValue;
+  if (dtype == 0) {
+    if (mode == kRecord)
+      return dispatch_mode<float, kLevelRowsF32, kLevelRowsF32 / 2, kLevelCols, kRecord, Q>(
+          L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
+    return dispatch_mode<float, kLevelRowsF32, kLevelRowsF32 / 2, kLevelCols, kDelta, Q>(
+        L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
+  }
+  if (mode == kRecord)
+    return dispatch_mode<double, kLevelRowsF64, kLevelRowsF64, kLevelCols, kRecord, Q>(
+        L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
+  return dispatch_mode<double, kLevelRowsF64, kLevelRowsF64, kLevelCols, kDelta, Q>(
+      L, out, twoeb, b, cap, bm, oidx, oval, w16, ns, shape.per_sm, st);
+}
 
 }  // namespace
 }  // namespace ipc

@@ -41,7 +41,7 @@ struct Tables {
 
 void build_tables(const SelInput& in, double A, Tables* T) {
   const int K = in.K, S = (int)in.st.size();
-  const bool cubic = in.interp == IPC_CUBIC, strict = in.bound == IPC_BOUND_STRICT;
+  const bool cubic = in.interp != IPC_LINEAR, strict = in.bound == IPC_BOUND_STRICT;
   const double p = cubic ? 1.25 : 1.0;
   std::vector<double> pw(std::max(S, K) + 1);
   pw[0] = 1.0;
@@ -349,7 +349,7 @@ double incremental_bound(const SelInput& in, const std::vector<int>& bold, doubl
     return Gnew;
   }
   const int S = (int)in.st.size();
-  const bool cubic = in.interp == IPC_CUBIC;
+  const bool cubic = in.interp != IPC_LINEAR;
   int lc = 0;  // coarsest level that loads new planes
   for (int l = 1; l <= in.K; ++l)
     if (bnew[l - 1] < bold[l - 1]) lc = l;

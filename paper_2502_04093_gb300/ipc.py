@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libipcomp.so")
 IPC_OK, IPC_EINVAL, IPC_EBOUND, IPC_EBUDGET = 0, -1, -2, -3
 IPC_ENOMEM, IPC_ECORRUPT, IPC_ECUDA, IPC_ETIMEOUT, IPC_EBUSY = -4, -5, -6, -7, -8
 IPC_F32, IPC_F64 = 0, 1
-IPC_LINEAR, IPC_CUBIC = 0, 1
+IPC_LINEAR, IPC_CUBIC, IPC_CUBIC_QUAD = 0, 1, 2
 IPC_EB_ABS, IPC_EB_REL = 0, 1
 IPC_BOUND_STRICT, IPC_BOUND_PAPER = 0, 1
 IPC_TARGET_EB, IPC_TARGET_BITRATE = 0, 1
@@ -326,7 +326,7 @@ def ipc_compress_batch(xs, ebs, eb_mode=IPC_EB_ABS, interp=IPC_CUBIC, bound=IPC_
             it.dims[e] = int(d)
         it.eb_mode = int(eb_mode[i] if isinstance(eb_mode, (list, tuple)) else eb_mode)
         it.eb = float(ebs[i] if isinstance(ebs, (list, tuple)) else ebs)
-        it.interp = int(interp)
+        it.interp = int(interp[i] if isinstance(interp, (list, tuple)) else interp)
         it.bound = int(bound)
     outs = (C.c_void_p * max(n, 1))()
     _check(lib().ipc_compress_batch(n, items, _stream(stream), outs), "ipc_compress_batch")

@@ -55,6 +55,29 @@ def test_batch_mixed_dtypes_and_modes():
             ipc.ipc_free(h)
 
 
+def test_batch_mixed_interpolation():
+    """One batch whose fields use the three interpolation modes: each field's
+    container and reconstruction are the oracle's for its own mode."""
+    xs = [synth.random_field((40, 33, 70), seed=11), synth.random_field((300, 77), seed=12),
+          synth.random_field((21, 50, 130), seed=13, dtype=np.float64)]
+    modes = [ipc.IPC_CUBIC_QUAD, ipc.IPC_LINEAR, ipc.IPC_CUBIC_QUAD]
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    hs = ipc.ipc_compress_batch(dev, 1e-5, ipc.IPC_EB_REL, modes)
+    try:
+        ofs = [oracle.compress(x, 1e-5, oracle.REL, m) for x, m in zip(xs, modes)]
+        for h, of in zip(hs, ofs):
+            assert ipc.ipc_export(h) == of.export()
+        outs = [torch.empty_like(d) for d in dev]
+        ipc.ipc_retrieve_batch(hs, [(ipc.IPC_TARGET_EB, 1e-3)] * 3, outs)
+        torch.cuda.synchronize()
+        for out, of in zip(outs, ofs):
+            y, _ = of.retrieve(oracle.EB, 1e-3)
+            assert np.array_equal(out.cpu().numpy().view(np.uint8), y.view(np.uint8))
+    finally:
+        for h in hs:
+            ipc.ipc_free(h)
+
+
 def test_batch_retrieve_and_plan_equal_single():
     xs = uneven_fields(n=10)
     dev = [torch.from_numpy(x).cuda() for x in xs]

@@ -60,7 +60,7 @@ SMALL = [
 
 
 @pytest.mark.parametrize("shape,dtype,kind", SMALL)
-@pytest.mark.parametrize("interp", [ipc.IPC_CUBIC, ipc.IPC_LINEAR])
+@pytest.mark.parametrize("interp", [ipc.IPC_CUBIC, ipc.IPC_LINEAR, ipc.IPC_CUBIC_QUAD])
 def test_compress_bytes_and_retrieve_bits(shape, dtype, kind, interp):
     x = synth.random_field(shape, seed=sum(shape) + (7 if kind == "noise" else 0), dtype=dtype,
                            kind=kind)
@@ -179,6 +179,22 @@ def test_large_ragged(dtype):
     """Several tiles per sweep with ragged rows in every dimension."""
     x = synth.random_field((67, 130, 259), seed=8, dtype=dtype)
     g, o = both(x, 1e-6)
+    assert g.export() == o.export()
+    for E in (1e-6, 1e-4, 1e-2):
+        check_retrieve(g, o, oracle.EB, E)
+    check_retrieve(g, o, oracle.BITRATE, 2.0)
+
+
+@pytest.mark.parametrize("shape,dtype", [((67, 130, 259), np.float32), ((67, 130, 259), np.float64),
+                                         ((5, 2049, 7), np.float32), ((2, 33, 1100), np.float32),
+                                         ((1030,), np.float64), ((200, 1000), np.float32)])
+def test_quadratic_boundaries_tiled(shape, dtype):
+    """Cubic interpolation with the three-point quadratic at the boundaries:
+    every sweep of the tiled level kernels and of the coarse-level kernel
+    meets targets that miss one far neighbour (near both ends of every
+    extent, at every level)."""
+    x = synth.random_field(shape, seed=sum(shape) + 5, dtype=dtype)
+    g, o = both(x, 1e-6, interp=ipc.IPC_CUBIC_QUAD)
     assert g.export() == o.export()
     for E in (1e-6, 1e-4, 1e-2):
         check_retrieve(g, o, oracle.EB, E)

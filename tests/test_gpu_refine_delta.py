@@ -92,7 +92,7 @@ def test_eb_chain_matches_oracle(dtype, shape):
         assert incs >= 4
 
 
-@pytest.mark.parametrize("interp", [oracle.LINEAR, oracle.CUBIC])
+@pytest.mark.parametrize("interp", [oracle.LINEAR, oracle.CUBIC, oracle.CUBIC_QUAD])
 def test_bitrate_chain_with_outliers(interp):
     # non-finite values and two spikes far beyond the quantizer's range are
     # outliers (a finite spike of 1e30 would instead inflate max|x|, and with
@@ -106,6 +106,12 @@ def test_bitrate_chain_with_outliers(interp):
     m = of.info()["mandatory"] * 8.0 / of.info()["n"]
     chain = [(BR, m + d) for d in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0)]
     assert run_chain(x, 1e-6, oracle.ABS, chain, interp) >= 4
+
+
+def test_quadratic_boundaries_eb_chain():
+    x = synth.random_field((70, 45, 530), seed=31, dtype=np.float64, kind="smooth")
+    chain = [(EB, 1e-1), (EB, 3e-2), (EB, 1e-3), (EB, 1e-4), (EB, 1e-5), (EB, 1e-10)]
+    assert run_chain(x, 1e-10, oracle.REL, chain, oracle.CUBIC_QUAD) >= 4
 
 
 def test_mixed_targets_and_fallback():
