@@ -346,15 +346,21 @@ std::vector<uint8_t> header_bytes(const ipc_field* f) {
   return h;
 }
 
+// Bytes of header_bytes(f) without building it: 112-byte fixed part, per
+// stage a 32-byte record and 32 plane sizes, 16 bytes per outlier.
+uint64_t header_size(const ipc_field* f) {
+  uint64_t nout = 0;
+  for (const auto& s : f->st) nout += s.out_idx.size();
+  return 112 + 288 * (uint64_t)f->g.stages.size() + 16 * nout;
+}
+
 void dfree(void* p) {
   if (p) cudaFreeAsync(p, cudaStreamLegacy);
 }
 
 void free_field_device(ipc_field* f) {
-  dfree(f->d_cap);
-  dfree(f->d_bm);
-  dfree(f->d_oidx);
-  dfree(f->d_oval);
+  dfree(f->d_cap);  // the bitmaps share its allocation
+  dfree(f->d_oidx);  // the outlier values share its allocation
   f->d_cap = nullptr;
   f->d_bm = nullptr;
   f->d_oidx = nullptr;
@@ -368,6 +374,55 @@ int dalloc(void** p, uint64_t bytes, cudaStream_t st) {
     *p = nullptr;
     return fail(IPC_ENOMEM, "device allocation failed");
   }
+  return IPC_OK;
+}
+
+// Pinned host staging of the tables that batched launches read from device
+// memory (a pageable source makes every upload a staged, blocking copy): a
+// ring of buffers per device, each reused only after the event recorded
+// behind its previous copy has completed. `fill` writes the bytes.
+constexpr int kStageSlots = 4;
+struct StageRing {
+  std::mutex mu;
+  void* buf[kStageSlots] = {};
+  size_t cap[kStageSlots] = {};
+  cudaEvent_t ev[kStageSlots] = {};
+  bool pending[kStageSlots] = {};
+  int next = 0;
+};
+StageRing g_stage[64];
+
+template <class Fill>
+int upload_staged(void* d_dst, size_t bytes, cudaStream_t st, Fill fill) {
+  if (bytes == 0) return IPC_OK;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(IPC_EINVAL, "device index out of range");
+  StageRing& r = g_stage[dev];
+  std::lock_guard<std::mutex> lk(r.mu);
+  const int s = r.next;
+  r.next = (s + 1) % kStageSlots;
+  if (r.pending[s]) {
+    CU(cudaEventSynchronize(r.ev[s]));
+    r.pending[s] = false;
+  }
+  if (!r.ev[s]) CU(cudaEventCreateWithFlags(&r.ev[s], cudaEventDisableTiming));
+  if (r.cap[s] < bytes) {
+    if (r.buf[s]) cudaFreeHost(r.buf[s]);
+    r.buf[s] = nullptr;
+    r.cap[s] = 0;
+    const size_t c = std::max<size_t>(bytes + bytes / 2, 1 << 16);
+    if (cudaMallocHost(&r.buf[s], c) != cudaSuccess) {
+      cudaGetLastError();
+      r.buf[s] = nullptr;
+      return fail(IPC_ENOMEM, "pinned host allocation failed");
+    }
+    r.cap[s] = c;
+  }
+  fill((uint8_t*)r.buf[s]);
+  CU(cudaMemcpyAsync(d_dst, r.buf[s], bytes, cudaMemcpyHostToDevice, st));
+  CU(cudaEventRecord(r.ev[s], st));
+  r.pending[s] = true;
   return IPC_OK;
 }
 
@@ -407,11 +462,13 @@ int plan_field(ipc_field* f, cudaStream_t st) {
   }
   f->cap_words = cw;
   f->bm_words = bw;
-  int rc;
-  if ((rc = dalloc((void**)&f->d_cap, cw * 4, st)) || (rc = dalloc((void**)&f->d_bm, bw * 4, st))) {
+  // capacity arrays and bitmaps in one allocation (bitmaps behind)
+  const int rc = dalloc((void**)&f->d_cap, (cw + bw) * 4, st);
+  if (rc) {
     free_field_device(f);
     return rc;
   }
+  f->d_bm = f->d_cap + cw;
   return IPC_OK;
 }
 
@@ -467,29 +524,31 @@ void retrieve_tiling(LevelArgs* L, int dtype, int w16, int ns) {
 
 // Reconstruction view of level l's plane streams with b_l = b: where plane
 // 0 of each stage lies, the plane strides, and the planes to load.
+// Offsets of the planes of level l's stages: plane k's capacity array at
+// cap0 + k pcap, its bitmap at bm0 + k pbm (words).
+void plane_offsets(const ipc_field* f, int l, LevelArgs* L) {
+  for (int d = 0; d < 3; ++d) {
+    const int t = f->g.level_stage[d][l - 1];
+    if (t < 0) continue;
+    const StageGeo& sg = f->g.stages[t];
+    StagePlanes& S = L->sp[d];
+    S.cap0 = f->desc[t].p[0].cap_off;
+    S.bm0 = f->desc[t].p[0].bm_off;
+    S.pcap = sg.nseg * (uint64_t)sg.RB * sg.CW;
+    S.pbm = sg.nseg * sg.bw;
+  }
+}
+
 void retrieve_planes(const ipc_field* f, int l, int b, LevelArgs* L) {
+  plane_offsets(f, l, L);
   for (int d = 0; d < 3; ++d) {
     const int t = f->g.level_stage[d][l - 1];
     StagePlanes& S = L->sp[d];
     S.kmask = 0;
     if (t < 0) continue;
-    const StageGeo& sg = f->g.stages[t];
-    S.cap0 = f->desc[t].p[0].cap_off;
-    S.bm0 = f->desc[t].p[0].bm_off;
-    S.pcap = sg.nseg * (uint64_t)sg.RB * sg.CW;
-    S.pbm = sg.nseg * sg.bw;
     for (int k = std::max(b, 0); k < 32; ++k)
       if (f->st[t].nnz[k]) S.kmask |= 1u << k;
   }
-}
-
-LevelDescs level_descs(const ipc_field* f, int l) {
-  LevelDescs D{};
-  for (int d = 0; d < 3; ++d) {
-    const int t = f->g.level_stage[d][l - 1];
-    if (t >= 0) D.s[d] = f->desc[t];
-  }
-  return D;
 }
 
 // Container layout from the per-plane nnz: stream sizes and modes, packed
@@ -517,24 +576,22 @@ int finish_field(ipc_field* f, cudaStream_t st) {
     nout += f->st[t].out_idx.size();
   }
   f->out_off[g.stages.size()] = nout;
-  f->mandatory = header_bytes(f).size();
-  int rc;
-  if ((rc = dalloc((void**)&f->d_oidx, nout * 8, st)) || (rc = dalloc((void**)&f->d_oval, nout * 8, st)))
-    return rc;
-  if (nout) {
-    std::vector<uint64_t> idx;
-    std::vector<double> val;
-    idx.reserve(nout);
-    val.reserve(nout);
+  f->mandatory = header_size(f);
+  if (nout == 0) return IPC_OK;  // no outlier arrays (kernels read them only for outliers)
+  // indices, then values, in one allocation, from pinned staging
+  const int rc = dalloc((void**)&f->d_oidx, nout * 16, st);
+  if (rc) return rc;
+  f->d_oval = reinterpret_cast<double*>(f->d_oidx + nout);
+  return upload_staged(f->d_oidx, nout * 16, st, [&](uint8_t* h) {
+    uint64_t* idx = reinterpret_cast<uint64_t*>(h);
+    double* val = reinterpret_cast<double*>(h + nout * 8);
     for (auto& s : f->st) {
-      idx.insert(idx.end(), s.out_idx.begin(), s.out_idx.end());
-      val.insert(val.end(), s.out_val.begin(), s.out_val.end());
+      std::memcpy(idx, s.out_idx.data(), s.out_idx.size() * 8);
+      std::memcpy(val, s.out_val.data(), s.out_val.size() * 8);
+      idx += s.out_idx.size();
+      val += s.out_val.size();
     }
-    CU(cudaMemcpyAsync(f->d_oidx, idx.data(), nout * 8, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(f->d_oval, val.data(), nout * 8, cudaMemcpyHostToDevice, st));
-    CU(cudaStreamSynchronize(st));
-  }
-  return IPC_OK;
+  });
 }
 
 double okey_to_double(unsigned long long k) {
@@ -696,6 +753,8 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
   CU(cudaMemcpyAsync(hacc.data(), acc, 40 * nf, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   std::vector<std::array<unsigned char, 32>> quant(nf);
+  std::vector<AnchorEntry> anch;  // the origin of level K + 1 is x[0], stored exactly
+  anch.reserve(nf);
   for (size_t i = 0; i < nf; ++i) {
     ipc_field* f = fs[i];
     const unsigned long long* a4 = &hacc[4 * i];
@@ -718,10 +777,7 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     if (dtype == 0) quant_args<float>(eb, f->xmaxabs, quant[i].data());
     else quant_args<double>(eb, f->xmaxabs, quant[i].data());
     if ((rc = plan_field(f, st))) return rc;
-    // the anchor is stored exactly: the origin of level K + 1 is x[0]
-    if (f->g.K > 0)
-      CU(cudaMemcpyAsync((uint8_t*)ws.xh + xo[i] + xl[i][f->g.K + 1], ins[i], esz,
-                         cudaMemcpyDeviceToDevice, st));
+    if (f->g.K > 0) anch.push_back(AnchorEntry{(uint8_t*)ws.xh + xo[i] + xl[i][f->g.K + 1], f->anchor});
   }
 
   // entry table of every level (coarsest first)
@@ -740,7 +796,7 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
         CompressEntry e{};
         e.L = level_args(f, l);
         e.L.vec = 1;  // the scratch is allocated aligned
-        e.D = level_descs(f, l);
+        plane_offsets(f, l, &e.L);
         e.o = SweepOut{f->d_cap, f->d_bm, ws.nnz + 32 * so[i], ws.okey, ws.oval, ocount,
                        ws.ocap, ws.stat + 2 * so[i], (uint32_t)i};
         compress_layout(&e.L, (uint8_t*)ws.xh + xo[i] + xl[i][l + 1]);
@@ -757,20 +813,27 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     }
   };
   build_entries();
+  // device table: [entries | anchors]
+  const size_t eby = ents.size() * sizeof(CompressEntry), aby = anch.size() * sizeof(AnchorEntry);
   CompressEntry* d_ents = nullptr;
-  if ((rc = dalloc((void**)&d_ents, ents.size() * sizeof(CompressEntry), st))) return rc;
+  if ((rc = dalloc((void**)&d_ents, eby + aby, st))) return rc;
   struct EntGuard {
     CompressEntry*& p;
     cudaStream_t s;
     ~EntGuard() { if (p) cudaFreeAsync(p, s); }
   } eguard{d_ents, st};
+  AnchorEntry* d_anch = reinterpret_cast<AnchorEntry*>((uint8_t*)d_ents + eby);
 
   std::vector<long> level_prof(Kmax + 1, -1);
   unsigned long long nout = 0;
   std::vector<uint32_t> stat(2 * so[nf]), nnz(32 * so[nf]);
   for (int attempt = 0; attempt < 2; ++attempt) {
-    CU(cudaMemcpyAsync(d_ents, ents.data(), ents.size() * sizeof(CompressEntry),
-                       cudaMemcpyHostToDevice, st));
+    if ((rc = upload_staged(d_ents, eby + aby, st, [&](uint8_t* h) {
+           std::memcpy(h, ents.data(), eby);
+           std::memcpy(h + eby, anch.data(), aby);
+         })))
+      return rc;
+    if (!anch.empty()) CU(launch_set_anchors(dtype, d_anch, (int)anch.size(), st));
     CU(cudaMemsetAsync(ws.stat, 0, 2 * so[nf] * 4, st));
     CU(cudaMemsetAsync(ws.nnz, 0, 32 * so[nf] * 4, st));
     CU(cudaMemsetAsync(ocount, 0, 8, st));
@@ -779,7 +842,7 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
       const long ph = prof_begin(IPC_KERNEL_COMPRESS_LEVEL, st);
       if (n_l == 1) {  // one field: arguments in the parameter space
         const CompressEntry& e = ents[lev_off[l]];
-        CU(launch_level_compress(dtype, e.L, e.x, e.xh, e.write_xh, e.quant, e.o, e.D, st));
+        CU(launch_level_compress(dtype, e.L, e.x, e.xh, e.write_xh, e.quant, e.o, st));
       } else {
         int quad = 0;  // a field of the level with quadratic boundaries
         for (int q = 0; q < n_l; ++q) quad |= ents[lev_off[l] + q].L.interp == 2;
@@ -1367,24 +1430,25 @@ int upload_table(const BatchTable& T, void** tab, cudaStream_t st, bool pooled) 
     return fail(IPC_ENOMEM, "device allocation failed");
   }
   uint8_t* base = (uint8_t*)*tab;
-  std::vector<RetrieveEntry> ents = T.ents;
-  std::vector<AnchorEntry> anch = T.anchors;
-  for (size_t i = 0; i < ents.size(); ++i) {
-    ents[i].L.kin = base + T.kin_off[i];
-    if (T.out_off[i] >= 0) ents[i].out = base + T.out_off[i];
-  }
-  for (size_t i = 0; i < anch.size(); ++i)
-    if (T.anch_off[i] >= 0) anch[i].out = base + T.anch_off[i];
-  std::vector<CoarseArgs> co = T.coarse;
-  for (size_t i = 0; i < co.size(); ++i)
-    if (T.coarse_off[i] >= 0) co[i].out = base + T.coarse_off[i];
-  std::vector<uint8_t> h(bytes);
-  std::memcpy(h.data(), ents.data(), ents.size() * sizeof(RetrieveEntry));
-  std::memcpy(h.data() + ents.size() * sizeof(RetrieveEntry), anch.data(),
-              anch.size() * sizeof(AnchorEntry));
-  if (!co.empty()) std::memcpy(h.data() + eb, co.data(), co.size() * sizeof(CoarseArgs));
-  // pageable source: the copy is staged before the call returns
-  CU(cudaMemcpyAsync(base + sb, h.data(), bytes, cudaMemcpyHostToDevice, st));
+  // the entries with their scratch offsets turned into addresses, written
+  // straight into pinned staging
+  rc = upload_staged(base + sb, bytes, st, [&](uint8_t* h) {
+    RetrieveEntry* ents = reinterpret_cast<RetrieveEntry*>(h);
+    std::memcpy(ents, T.ents.data(), T.ents.size() * sizeof(RetrieveEntry));
+    for (size_t i = 0; i < T.ents.size(); ++i) {
+      ents[i].L.kin = base + T.kin_off[i];
+      if (T.out_off[i] >= 0) ents[i].out = base + T.out_off[i];
+    }
+    AnchorEntry* anch = reinterpret_cast<AnchorEntry*>(h + T.ents.size() * sizeof(RetrieveEntry));
+    std::memcpy(anch, T.anchors.data(), T.anchors.size() * sizeof(AnchorEntry));
+    for (size_t i = 0; i < T.anchors.size(); ++i)
+      if (T.anch_off[i] >= 0) anch[i].out = base + T.anch_off[i];
+    CoarseArgs* co = reinterpret_cast<CoarseArgs*>(h + eb);
+    if (!T.coarse.empty()) std::memcpy(co, T.coarse.data(), T.coarse.size() * sizeof(CoarseArgs));
+    for (size_t i = 0; i < T.coarse.size(); ++i)
+      if (T.coarse_off[i] >= 0) co[i].out = base + T.coarse_off[i];
+  });
+  if (rc) return rc;
   if (!pooled) CU(cudaStreamSynchronize(st));
   return IPC_OK;
 }

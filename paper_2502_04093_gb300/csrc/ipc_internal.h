@@ -176,9 +176,6 @@ struct PlaneDesc {
 struct StageDescs {
   PlaneDesc p[32];
 };
-struct LevelDescs {
-  StageDescs s[3];  // by sweep dimension
-};
 
 // Stream mode and byte size from (nnz, W) (format definition).
 inline uint32_t stream_mode(uint64_t nnz, uint64_t W) {
@@ -195,8 +192,7 @@ inline uint64_t stream_bytes(uint64_t nnz, uint64_t W) {
 
 // One field's share of a batched level launch (device memory).
 struct CompressEntry {
-  LevelArgs L;
-  LevelDescs D;
+  LevelArgs L;  // L.sp: the planes' capacity and bitmap offsets
   SweepOut o;
   const void* x;
   void* xh;
@@ -243,7 +239,7 @@ cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStrea
 // L.interp, the batched ones by `quad`: some entry has interp 2).
 cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, void* xh,
                                   int write_xh, const void* quant, const SweepOut& o,
-                                  const LevelDescs& d, cudaStream_t st);
+                                  cudaStream_t st);
 // Retrieve tiles of a level: levels whose lattice rows hold at most
 // kLevelCols/2 (kLevelCols/4) columns put 2 (4) planes of the same parity
 // side by side in one tile.
@@ -300,7 +296,7 @@ cudaError_t launch_level_retrieve_batch(int dtype, const RetrieveEntry* ents, in
                                         cudaStream_t st);
 cudaError_t launch_level_compress_quad(int dtype, const LevelArgs& L, const void* x, void* xh,
                                        int write_xh, const void* quant, const SweepOut& o,
-                                       const LevelDescs& d, cudaStream_t st);
+                                       cudaStream_t st);
 cudaError_t launch_level_retrieve_quad(int dtype, const LevelArgs& L, void* out, double twoeb,
                                        int b, const uint32_t* cap, const uint32_t* bm,
                                        const uint64_t* oidx, const double* oval, int w16,

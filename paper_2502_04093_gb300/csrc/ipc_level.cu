@@ -9,9 +9,9 @@ int level_rows(int dtype) { return dtype == 0 ? kLevelRowsF32 : kLevelRowsF64; }
 
 cudaError_t launch_level_compress(int dtype, const LevelArgs& L, const void* x, void* xh,
                                   int write_xh, const void* quant, const SweepOut& o,
-                                  const LevelDescs& d, cudaStream_t st) {
-  if (L.interp == 2) return launch_level_compress_quad(dtype, L, x, xh, write_xh, quant, o, d, st);
-  return level_compress_impl<false>(dtype, L, x, xh, write_xh, quant, o, d, st);
+                                  cudaStream_t st) {
+  if (L.interp == 2) return launch_level_compress_quad(dtype, L, x, xh, write_xh, quant, o, st);
+  return level_compress_impl<false>(dtype, L, x, xh, write_xh, quant, o, st);
 }
 
 cudaError_t launch_level_retrieve(int dtype, const LevelArgs& L, void* out, double twoeb, int b,

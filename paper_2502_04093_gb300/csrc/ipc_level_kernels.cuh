@@ -79,7 +79,7 @@ struct CTile {
 template <class T, int BR, int BC, bool Q>
 __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T* __restrict__ x,
                                                     T* xh, int write_xh, const QuantArgs<T>& qa,
-                                                    const SweepOut& o, const LevelDescs& D,
+                                                    const SweepOut& o,
                                                     uint64_t cta, unsigned char* smem) {
   typedef CTile<BR, BC> G;
   typedef typename Vec2<T>::type V2;
@@ -399,7 +399,7 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
   const uint64_t pi = sidx == 0 ? (uint64_t)((c.P - 1) >> 1) : (uint64_t)c.P;
   const uint64_t gseg = active ? seg_id(S, pi, c.rb, c.ct) : 0;
   const uint32_t bwords = (uint32_t)((nwords + 31) / 32);
-  const PlaneDesc* pds = D.s[sidx].p;
+  const StagePlanes& SP = L.sp[sidx];  // plane k: capacity SP.cap0 + k SP.pcap, bitmap alike
   const int wl = li >> 5;  // 32-word group of the segment (one warp)
   const bool wact = active && wl < (int)bwords;
   __shared__ uint32_t scnt[3][32];
@@ -423,10 +423,10 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
     if (k > ktop) break;
     const uint32_t mk = __ballot_sync(~0u, cd[k] != 0u);
     if (lane == k) mybm = mk;
-    if (wact && cd[k]) o.cap[pds[k].cap_off + capg + __popc(mk & lt)] = cd[k];
+    if (wact && cd[k]) o.cap[SP.cap0 + (uint64_t)k * SP.pcap + capg + __popc(mk & lt)] = cd[k];
   }
   if (wact) {
-    o.bm[pds[lane].bm_off + gseg * S.bw + wl] = mybm;
+    o.bm[SP.bm0 + (uint64_t)lane * SP.pbm + gseg * S.bw + wl] = mybm;
     if (mybm) atomicAdd(&scnt[sidx][lane], (uint32_t)__popc(mybm));
   }
   __syncthreads();
@@ -442,9 +442,9 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
 template <class T, int BR, int BC, bool Q>
 __global__ void __launch_bounds__(256, 4) k_level_compress(LevelArgs L, const T* __restrict__ x,
                                                            T* xh, int write_xh, QuantArgs<T> qa,
-                                                           SweepOut o, LevelDescs D) {
+                                                           SweepOut o) {
   extern __shared__ __align__(16) unsigned char smem[];
-  level_compress_body<T, BR, BC, Q>(L, x, xh, write_xh, qa, o, D, blockIdx.x, smem);
+  level_compress_body<T, BR, BC, Q>(L, x, xh, write_xh, qa, o, blockIdx.x, smem);
 }
 
 template <class T, int BR, int BC, bool W16, int NS, bool Q>
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(256, 3) k_level_compress_batch(
   extern __shared__ __align__(16) unsigned char smem[];
   const CompressEntry& e = find_entry(ents, n, blockIdx.x);
   level_compress_body<T, BR, BC, Q>(e.L, (const T*)e.x, (T*)e.xh, e.write_xh,
-                                 *reinterpret_cast<const QuantArgs<T>*>(e.quant), e.o, e.D,
+                                 *reinterpret_cast<const QuantArgs<T>*>(e.quant), e.o,
                                  blockIdx.x - e.cta_begin, smem);
 }
 
@@ -594,7 +594,7 @@ void retrieve_batch_dispatch(const RetrieveEntry* ents, int n, uint64_t tiles, i
 template <bool Q>
 cudaError_t level_compress_impl(int dtype, const LevelArgs& L, const void* x, void* xh,
                                   int write_xh, const void* quant, const SweepOut& o,
-                                  const LevelDescs& d, cudaStream_t st) {
+                                  cudaStream_t st) {
   const uint64_t grid = (uint64_t)L.M[0] * L.nrb * L.nct;
   if (grid == 0) return cudaSuccess;
   if (grid >= (1ULL << 31)) return cudaErrorInvalidValue;  // grid x limit (tile ids are 32-bit)
@@ -603,12 +603,12 @@ cudaError_t level_compress_impl(int dtype, const LevelArgs& L, const void* x, vo
     if ((e = setup_once<float, kLevelRowsF32, kLevelCols, Q>()) != cudaSuccess) return e;
     k_level_compress<float, kLevelRowsF32, kLevelCols, Q>
         <<<(unsigned)grid, 256, smem_compress<float, kLevelRowsF32, kLevelCols>(), st>>>(
-            L, (const float*)x, (float*)xh, write_xh, *(const QuantArgs<float>*)quant, o, d);
+            L, (const float*)x, (float*)xh, write_xh, *(const QuantArgs<float>*)quant, o);
   } else {
     if ((e = setup_once<double, kLevelRowsF64, kLevelCols, Q>()) != cudaSuccess) return e;
     k_level_compress<double, kLevelRowsF64, kLevelCols, Q>
         <<<(unsigned)grid, 256, smem_compress<double, kLevelRowsF64, kLevelCols>(), st>>>(
-            L, (const double*)x, (double*)xh, write_xh, *(const QuantArgs<double>*)quant, o, d);
+            L, (const double*)x, (double*)xh, write_xh, *(const QuantArgs<double>*)quant, o);
   }
   return cudaGetLastError();
 }

@@ -7,8 +7,8 @@ namespace ipc {
 
 cudaError_t launch_level_compress_quad(int dtype, const LevelArgs& L, const void* x, void* xh,
                                        int write_xh, const void* quant, const SweepOut& o,
-                                       const LevelDescs& d, cudaStream_t st) {
-  return level_compress_impl<true>(dtype, L, x, xh, write_xh, quant, o, d, st);
+                                       cudaStream_t st) {
+  return level_compress_impl<true>(dtype, L, x, xh, write_xh, quant, o, st);
 }
 
 cudaError_t launch_level_retrieve_quad(int dtype, const LevelArgs& L, void* out, double twoeb,
