@@ -321,6 +321,11 @@ struct ipco_field {
   std::vector<uint8_t> bytes; /* the whole container */
   uint64_t mandatory;
   std::vector<std::vector<int32_t>> codes; /* kept after compress (tests) */
+  /* Which bound on |q - q'_b| the cost tables use: 0 the closed form of
+   * stage_M (the container's model), 1 the data maximum `mdata` (a study of
+   * the table Sec. 5.1 says can be precomputed; needs `codes`). */
+  int delta_model = 0;
+  std::vector<std::vector<uint64_t>> mdata; /* per stage, b = 0..32 */
 };
 
 struct ipco_view {
@@ -531,6 +536,29 @@ uint64_t stage_M(const StageData& sd, int b) {
   return sd.Q;
 }
 
+/* The data maximum of |q - q'_b| over a stage's codes, b = 0..32. Since a
+ * negabinary value is the sum of its digits' values, q - q'_b is the value
+ * of the b dropped low digits alone: per code, the partial sums of
+ * digit_k * (-2)^k, k < b, and their largest magnitude over the codes. */
+void delta_data(const std::vector<int32_t>& q, std::vector<uint64_t>* out) {
+  out->assign(33, 0);
+  for (int32_t v : q) {
+    const uint32_t n = negabinary(v);
+    int64_t low = 0, w = 1; /* value of digits 0 .. k; w = (-2)^k */
+    for (int k = 0; k < 32; ++k) {
+      if ((n >> k) & 1u) low += w;
+      w *= -2;
+      const uint64_t a = (uint64_t)(low < 0 ? -low : low);
+      if (a > (*out)[k + 1]) (*out)[k + 1] = a;
+    }
+  }
+}
+
+uint64_t stage_M(const ipco_field* f, int t, int b) {
+  if (f->delta_model == 1) return b <= 0 ? 0 : f->mdata[t][b];
+  return stage_M(f->st[t], b);
+}
+
 struct Options {
   std::vector<uint64_t> cost;  /* K x 33 */
   std::vector<uint64_t> bytes; /* K x 33 */
@@ -577,7 +605,7 @@ void option_tables(const ipco_field* f, double A, Options* o) {
       uint64_t mmax = 0;
       for (int t = 0; t < S; ++t) {
         if (g.stages[t].level != l) continue;
-        uint64_t M = stage_M(f->st[t], b);
+        uint64_t M = stage_M(f, t, b);
         if (f->bound == 0) {
           double a = cubic ? P[S - 1 - t] : 1.0;
           c = sat_add(c, ceil_units(a * (double)M * bin * 65536.0));
@@ -1193,6 +1221,25 @@ int ipco_stage_info(const ipco_field* f, int t, int* level, int* dim,
   if (H) *H = f->st[t].H;
   if (Q) *Q = f->st[t].Q;
   if (noutliers) *noutliers = f->st[t].outliers.size();
+  return IPCO_OK;
+}
+
+int ipco_delta_table(const ipco_field* f, int t, uint64_t* out) {
+  if (!f || !out || t < 0 || (size_t)t >= f->codes.size()) return IPCO_EINVAL;
+  std::vector<uint64_t> m;
+  delta_data(f->codes[t], &m);
+  for (int b = 0; b <= 32; ++b) out[b] = m[b];
+  return IPCO_OK;
+}
+
+int ipco_set_delta_model(ipco_field* f, int model) {
+  if (!f || model < 0 || model > 1) return IPCO_EINVAL;
+  if (model == 1) {
+    if (f->codes.size() != f->g.stages.size()) return IPCO_EINVAL; /* imported: no codes */
+    f->mdata.resize(f->codes.size());
+    for (size_t t = 0; t < f->codes.size(); ++t) delta_data(f->codes[t], &f->mdata[t]);
+  }
+  f->delta_model = model;
   return IPCO_OK;
 }
 

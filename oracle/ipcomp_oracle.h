@@ -75,6 +75,13 @@ int ipco_stage_info(const ipco_field* f, int t, int* level, int* dim,
                     uint64_t* noutliers);
 /* The quantized codes of stage t in code order (0 at outliers). */
 int ipco_stage_codes(const ipco_field* f, int t, int32_t* q);
+/* The data maximum of |q - q'_b| over stage t's codes, b = 0..32 (out[33]);
+ * fields compressed here only (the codes are kept). */
+int ipco_delta_table(const ipco_field* f, int t, uint64_t* out);
+/* Bound on |q - q'_b| in the cost tables: 0 the closed form (U(b) up to the
+ * top digit H, then Q; the container's model), 1 the data maximum (a
+ * study: it is not stored in the container). */
+int ipco_set_delta_model(ipco_field* f, int model);
 /* Byte size of stream (t, plane k). */
 int ipco_stream_size(const ipco_field* f, int t, int k, uint64_t* bytes);
 /* For every point (row-major), the stage that produces it (-1 = anchor). */

@@ -67,6 +67,8 @@ def lib() -> C.CDLL:
         L.ipco_stage_info.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       u64p, C.POINTER(C.c_int), C.POINTER(C.c_uint32), u64p]
         L.ipco_stage_codes.argtypes = [vp, C.c_int, vp]
+        L.ipco_delta_table.argtypes = [vp, C.c_int, vp]
+        L.ipco_set_delta_model.argtypes = [vp, C.c_int]
         L.ipco_stream_size.argtypes = [vp, C.c_int, C.c_int, u64p]
         L.ipco_point_stage.argtypes = [C.c_int, i64p, vp]
         L.ipco_option_tables.argtypes = [vp, C.c_double, vp, vp]
@@ -144,6 +146,16 @@ class Field:
         q = np.zeros(nc, dtype=np.int32)
         _check(lib().ipco_stage_codes(self.h, t, q.ctypes.data), "ipco_stage_codes")
         return q
+
+    def delta_table(self, t: int) -> np.ndarray:
+        """Data maximum of |q - q'_b| over stage t's codes, b = 0..32."""
+        m = np.zeros(33, dtype=np.uint64)
+        _check(lib().ipco_delta_table(self.h, t, m.ctypes.data), "ipco_delta_table")
+        return m
+
+    def set_delta_model(self, model: int) -> None:
+        """0: closed-form bound (the container's); 1: data maximum (study)."""
+        _check(lib().ipco_set_delta_model(self.h, model), "ipco_set_delta_model")
 
     def stream_size(self, t: int, k: int) -> int:
         b = C.c_uint64()

@@ -16,6 +16,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ipc.h"
@@ -222,6 +223,7 @@ struct ipc_field {
   double* d_oval;
   std::vector<StageDescs> desc;   // per stage
   std::vector<uint64_t> out_off;  // per stage offset into d_oidx/d_oval
+  SelInput sel;                   // the selector's input, prepared once
 };
 
 struct ipc_view {
@@ -345,6 +347,8 @@ std::vector<uint8_t> header_bytes(const ipc_field* f) {
     }
   return h;
 }
+
+SelInput sel_input(const ipc_field* f);
 
 // Bytes of header_bytes(f) without building it: 112-byte fixed part, per
 // stage a 32-byte record and 32 plane sizes, 16 bytes per outlier.
@@ -577,6 +581,8 @@ int finish_field(ipc_field* f, cudaStream_t st) {
   }
   f->out_off[g.stages.size()] = nout;
   f->mandatory = header_size(f);
+  f->sel = sel_input(f);
+  prepare_selection(&f->sel);
   if (nout == 0) return IPC_OK;  // no outlier arrays (kernels read them only for outliers)
   // indices, then values, in one allocation, from pinned staging
   const int rc = dalloc((void**)&f->d_oidx, nout * 16, st);
@@ -956,7 +962,7 @@ int select(const ipc_field* f, ipc_target tg, const std::vector<int>* upper, std
            uint64_t* bytes, double* bound, uint64_t* rparts = nullptr) {
   const char* why = "";
   const int rc =
-      select_planes(sel_input(f), tg.kind, tg.value, upper, b, bytes, bound, &why, rparts);
+      select_planes(f->sel, tg.kind, tg.value, upper, b, bytes, bound, &why, rparts);
   return rc ? fail(rc, why) : IPC_OK;
 }
 
@@ -1286,6 +1292,10 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   T->coarse_off.clear();
   T->coarse_smem = 0;
   T->alg_bytes = 0;
+  T->ents.reserve(fs.size() * (size_t)T->Kmax);
+  T->kin_off.reserve(fs.size() * (size_t)T->Kmax);
+  T->out_off.reserve(fs.size() * (size_t)T->Kmax);
+  T->coarse.reserve(fs.size());
   // each field's scratch ladder, one after the other
   std::vector<uint64_t> base(nf, 0);
   std::vector<std::vector<uint64_t>> off(nf);
@@ -1333,8 +1343,11 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       bool same = true;
       ShapeKey key{};
       int seen = 0;
+      std::vector<LevelArgs> las;  // the entries' level arguments
+      las.reserve(group[w16].size());
       for (size_t i : group[w16]) {
-        const LevelArgs La = level_args(fs[i], l);
+        las.push_back(level_args(fs[i], l));
+        const LevelArgs& La = las.back();
         ln.quad |= fs[i]->interp == IPC_CUBIC_QUAD;
         ns = std::min(ns, retrieve_subtiles(La.M[2], w16));
         const ShapeKey k = shape_key(fs[i]->dtype, w16, La);
@@ -1348,11 +1361,12 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       }
       ln.ns = ns;
       uint64_t cta = 0;
+      size_t q = 0;
       for (size_t i : group[w16]) {
         ipc_field* f = fs[i];
         const size_t esz = f->dtype == 0 ? 4 : 8;
         RetrieveEntry e{};
-        e.L = level_args(f, l);
+        e.L = las[q++];
         retrieve_layout(&e.L, nullptr);
         retrieve_planes(f, l, bs[i][l - 1], &e.L);
         retrieve_tiling(&e.L, f->dtype, w16, ns);
@@ -1808,7 +1822,7 @@ int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream) {
   if (v->mode == IPC_REFINE_INCREMENTAL && v->state_valid) {
     uint64_t racc = 0;
     const double Gd =
-        incremental_bound(sel_input(f), v->b, v->bound, v->racc, b, bound, rparts, &racc);
+        incremental_bound(f->sel, v->b, v->bound, v->racc, b, bound, rparts, &racc);
     double E = target.value;
     if (f->eb_mode == IPC_EB_REL && f->xmax - f->xmin > 0) E = target.value * (f->xmax - f->xmin);
     if (target.kind == IPC_TARGET_BITRATE || Gd <= E) {
@@ -1940,7 +1954,9 @@ int ipc_select_container(const void* buf, uint64_t len, ipc_target target, int* 
   std::vector<int> b;
   uint64_t y = 0;
   double bound = 0;
-  const int rc = select_planes(sel_input(&f), target.kind, target.value, nullptr, &b, &y, &bound, &why);
+  SelInput in = sel_input(&f);
+  prepare_selection(&in);  // the tables as a device-resident field keeps them
+  const int rc = select_planes(in, target.kind, target.value, nullptr, &b, &y, &bound, &why);
   if (rc) return fail(rc, why);
   if (nlevels) *nlevels = (int)b.size();
   if (b_per_level)
@@ -2235,12 +2251,32 @@ int batch_select(int n, ipc_field* const* fields, const ipc_target* targets, voi
   bs->assign(n, {});
   bytes->assign(n, 0);
   bounds->assign(n, 0.0);
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < n; ++i)
     if (!fields[i] || fields[i]->tag != kFieldTag || !d_outs[i])
       return fail(IPC_EINVAL, "invalid field or output");
-    const int rc = select(fields[i], targets[i], nullptr, &(*bs)[i], &(*bytes)[i], &(*bounds)[i]);
-    if (rc) return rc;
+  // the fields' selections are independent: large batches spread them over
+  // a few host threads (the first failure in field order is reported)
+  std::vector<int> rcs(n, IPC_OK);
+  std::vector<const char*> why(n, "");
+  auto work = [&](int i0, int step) {
+    for (int i = i0; i < n; i += step)
+      rcs[i] = select_planes(fields[i]->sel, targets[i].kind, targets[i].value, nullptr,
+                             &(*bs)[i], &(*bytes)[i], &(*bounds)[i], &why[i]);
+  };
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int nt = n >= 16 ? (int)std::min<unsigned>(8, std::max(1u, hc / 2)) : 1;
+  std::vector<std::thread> th;
+  for (int k = 1; k < nt; ++k) {
+    try {
+      th.emplace_back(work, k, nt);
+    } catch (...) {  // no thread: this one takes the stride
+      work(k, nt);
+    }
   }
+  work(0, nt);
+  for (auto& t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (rcs[i]) return fail(rcs[i], why[i]);
   return IPC_OK;
 }
 }  // namespace

@@ -39,42 +39,78 @@ struct Tables {
   std::vector<uint64_t> rho;  // per level: the rounding margin inside cost(l, b > 0)
 };
 
-void build_tables(const SelInput& in, double A, Tables* T) {
+// The target-independent parts of the tables: base[l-1][b] (strict: the sum
+// of the stage terms; paper: the whole cost), ybytes[l-1][b], asum[l-1].
+void prepare_tables(const SelInput& in, std::vector<uint64_t>* base, std::vector<uint64_t>* ybytes,
+                    std::vector<double>* asum_out) {
   const int K = in.K, S = (int)in.st.size();
   const bool cubic = in.interp != IPC_LINEAR, strict = in.bound == IPC_BOUND_STRICT;
   const double p = cubic ? 1.25 : 1.0;
   std::vector<double> pw(std::max(S, K) + 1);
   pw[0] = 1.0;
   for (size_t i = 1; i < pw.size(); ++i) pw[i] = pw[i - 1] * p;
-  const double u = in.dtype == IPC_F32 ? 1.0 / 16777216.0 : 1.0 / 9007199254740992.0;
-  const double kappa = cubic ? 24.0 : 12.0;
-  T->K = K;
-  T->cost.assign((size_t)K * 33, 0);
-  T->bytes.assign((size_t)K * 33, 0);
-  T->rho.assign((size_t)K, 0);
+  base->assign((size_t)K * 33, 0);
+  ybytes->assign((size_t)K * 33, 0);
+  asum_out->assign((size_t)K, 0.0);
+  // the stages of each level (stage order), and the bytes of planes >= b of
+  // each stage (suffix sums), so a level's options cost O(33 x its stages)
+  std::vector<int> by_level(S), first(K + 2, 0);
+  for (int t = 0; t < S; ++t) ++first[in.st[t].level + 1];
+  for (int l = 1; l <= K + 1; ++l) first[l] += first[l - 1];
+  {
+    std::vector<int> fill(first.begin(), first.end());
+    for (int t = 0; t < S; ++t) by_level[fill[in.st[t].level]++] = t;
+  }
+  std::vector<uint64_t> ysuf((size_t)S * 33);
+  for (int t = 0; t < S; ++t) {
+    ysuf[(size_t)t * 33 + 32] = 0;
+    for (int k = 31; k >= 0; --k) ysuf[(size_t)t * 33 + k] = ysuf[(size_t)t * 33 + k + 1] + in.st[t].size[k];
+  }
   for (int l = 1; l <= K; ++l) {
-    double asum = 0;
+    double asum = 0;  // a_t over the stages of levels <= l, in stage order
     for (int t = 0; t < S; ++t)
       if (in.st[t].level <= l) asum += (strict && cubic) ? pw[S - 1 - t] : 1.0;
-    const uint64_t rho = units(kappa * u * (A / in.eb) * 65536.0 * asum);
-    T->rho[l - 1] = strict ? rho : 0;
+    (*asum_out)[l - 1] = asum;
     for (int b = 0; b <= 32; ++b) {
       uint64_t c = 0, y = 0, mmax = 0;
-      for (int t = 0; t < S; ++t) {
+      for (int j = first[l]; j < first[l + 1]; ++j) {
+        const int t = by_level[j];
         const SelStage& s = in.st[t];
-        if (s.level != l) continue;
         const uint64_t M = b <= 0 ? 0 : (b <= s.H ? uncert(b) : (uint64_t)s.Q);
         if (strict) c = sadd(c, units((cubic ? pw[S - 1 - t] : 1.0) * (double)M * in.bin * 65536.0));
         else mmax = std::max(mmax, M);
-        for (int k = b; k < 32; ++k) y += s.size[k];
+        y += ysuf[(size_t)t * 33 + b];
       }
-      if (strict) {
-        if (b > 0) c = sadd(c, rho);
-      } else {
-        c = units(pw[l - 1] * (double)mmax * in.bin * 65536.0);
-      }
-      T->cost[(size_t)(l - 1) * 33 + b] = c;
-      T->bytes[(size_t)(l - 1) * 33 + b] = y;
+      if (!strict) c = units(pw[l - 1] * (double)mmax * in.bin * 65536.0);
+      (*base)[(size_t)(l - 1) * 33 + b] = c;
+      (*ybytes)[(size_t)(l - 1) * 33 + b] = y;
+    }
+  }
+}
+
+// Option tables for the magnitude bound A (strict: rho_l from A, added to
+// every b > 0).
+void build_tables(const SelInput& in, double A, Tables* T) {
+  std::vector<uint64_t> lb, ly;
+  std::vector<double> la;
+  const bool prepared = !in.base.empty();
+  if (!prepared) prepare_tables(in, &lb, &ly, &la);
+  const std::vector<uint64_t>& base = prepared ? in.base : lb;
+  const std::vector<double>& asum = prepared ? in.asum : la;
+  const int K = in.K;
+  const bool cubic = in.interp != IPC_LINEAR, strict = in.bound == IPC_BOUND_STRICT;
+  const double u = in.dtype == IPC_F32 ? 1.0 / 16777216.0 : 1.0 / 9007199254740992.0;
+  const double kappa = cubic ? 24.0 : 12.0;
+  T->K = K;
+  T->bytes = prepared ? in.ybytes : ly;
+  T->cost.assign((size_t)K * 33, 0);
+  T->rho.assign((size_t)K, 0);
+  for (int l = 1; l <= K; ++l) {
+    const uint64_t rho = units(kappa * u * (A / in.eb) * 65536.0 * asum[l - 1]);
+    T->rho[l - 1] = strict ? rho : 0;
+    for (int b = 0; b <= 32; ++b) {
+      const uint64_t c = base[(size_t)(l - 1) * 33 + b];
+      T->cost[(size_t)(l - 1) * 33 + b] = strict && b > 0 ? sadd(c, rho) : c;
     }
   }
 }
@@ -98,32 +134,53 @@ uint64_t greedy_bound(const Tables& T, int kind, uint64_t limit, const std::vect
     y += T.bytes[(size_t)l * 33 + b[l]];
   }
   if ((kind == 0 && c > limit) || (kind == 1 && y > limit)) return ~uint64_t(0);
+  // Each step takes the move of best ratio over all levels. A level's best
+  // move depends only on its own b and on the slack left (cost in eb mode,
+  // bytes in bitrate mode), and the slack only shrinks: so a level's best is
+  // recomputed only after it moved, or when the slack no longer admits it
+  // (the best of a subset that still holds the old best is the old best).
+  auto level_best = [&](int l, int* v_out) -> double {
+    const uint64_t c0 = T.cost[(size_t)l * 33 + b[l]], y0 = T.bytes[(size_t)l * 33 + b[l]];
+    double best = 0;
+    *v_out = -1;
+    if (kind == 0) {  // drop more planes: fewer bytes for more cost
+      const int bmax = upper ? (*upper)[l] : 32;
+      for (int v = b[l] + 1; v <= bmax; ++v) {
+        const uint64_t c1 = T.cost[(size_t)l * 33 + v], y1 = T.bytes[(size_t)l * 33 + v];
+        if (c1 < c0 || sadd(c - c0, c1) > limit || y1 >= y0) continue;
+        const double r = (double)(y0 - y1) / (double)(c1 - c0 + 1);
+        if (r > best) { best = r; *v_out = v; }
+      }
+    } else {  // load more planes: less cost for more bytes
+      for (int v = b[l] - 1; v >= 0; --v) {
+        const uint64_t c1 = T.cost[(size_t)l * 33 + v], y1 = T.bytes[(size_t)l * 33 + v];
+        if (c1 >= c0 || y - y0 + y1 > limit) continue;
+        const double r = (double)(c0 - c1) / (double)(y1 - y0 + 1);
+        if (r > best) { best = r; *v_out = v; }
+      }
+    }
+    return best;
+  };
+  auto fits = [&](int l, int v) {
+    const uint64_t c0 = T.cost[(size_t)l * 33 + b[l]], y0 = T.bytes[(size_t)l * 33 + b[l]];
+    const uint64_t c1 = T.cost[(size_t)l * 33 + v], y1 = T.bytes[(size_t)l * 33 + v];
+    return kind == 0 ? sadd(c - c0, c1) <= limit : y - y0 + y1 <= limit;
+  };
+  std::vector<double> lr(K);
+  std::vector<int> lv(K);
+  for (int l = 0; l < K; ++l) lr[l] = level_best(l, &lv[l]);
   for (;;) {
     int bl = -1, bb = -1;
     double best = 0;
     for (int l = 0; l < K; ++l) {
-      const uint64_t c0 = T.cost[(size_t)l * 33 + b[l]], y0 = T.bytes[(size_t)l * 33 + b[l]];
-      if (kind == 0) {  // drop more planes: fewer bytes for more cost
-        const int bmax = upper ? (*upper)[l] : 32;
-        for (int v = b[l] + 1; v <= bmax; ++v) {
-          const uint64_t c1 = T.cost[(size_t)l * 33 + v], y1 = T.bytes[(size_t)l * 33 + v];
-          if (c1 < c0 || sadd(c - c0, c1) > limit || y1 >= y0) continue;
-          const double r = (double)(y0 - y1) / (double)(c1 - c0 + 1);
-          if (r > best) { best = r; bl = l; bb = v; }
-        }
-      } else {  // load more planes: less cost for more bytes
-        for (int v = b[l] - 1; v >= 0; --v) {
-          const uint64_t c1 = T.cost[(size_t)l * 33 + v], y1 = T.bytes[(size_t)l * 33 + v];
-          if (c1 >= c0 || y - y0 + y1 > limit) continue;
-          const double r = (double)(c0 - c1) / (double)(y1 - y0 + 1);
-          if (r > best) { best = r; bl = l; bb = v; }
-        }
-      }
+      if (lv[l] >= 0 && !fits(l, lv[l])) lr[l] = level_best(l, &lv[l]);
+      if (lv[l] >= 0 && lr[l] > best) { best = lr[l]; bl = l; bb = lv[l]; }
     }
     if (bl < 0) break;
     c = sadd(c - T.cost[(size_t)bl * 33 + b[bl]], T.cost[(size_t)bl * 33 + bb]);
     y = y - T.bytes[(size_t)bl * 33 + b[bl]] + T.bytes[(size_t)bl * 33 + bb];
     b[bl] = bb;
+    lr[bl] = level_best(bl, &lv[bl]);
   }
   return kind == 0 ? y : c;
 }
@@ -167,21 +224,73 @@ void half_frontier(const Tables& T, int l0, int l1, int kind, uint64_t limit, ui
         best = c;
       }
     }
-    G.clear();
-    G.reserve(F.size() * nopt);
-    for (const Part& e : F)
-      for (int i = 0; i < nopt; ++i) {
-        const int b = opt[i];
-        const uint64_t c = sadd(e.c, T.cost[(size_t)l * 33 + b]);
-        const uint64_t y = e.y + T.bytes[(size_t)l * 33 + b];
-        if (kind == 0 ? (c > limit || y > gbound) : (y > limit || c > gbound)) continue;
-        G.push_back(Part{c, y, key_put(e.key, l - l0, b)});
-      }
-    std::sort(G.begin(), G.end(), [](const Part& x, const Part& z) {
+    // F extended by option i is F shifted by a constant: still sorted (but
+    // where saturated costs tie). The nopt runs are merged (heap on their
+    // heads) in the order of `before`; should a run not be sorted, the merge
+    // is sorted after all. Then the Pareto filter.
+    auto before = [](const Part& x, const Part& z) {
       if (x.c != z.c) return x.c < z.c;
       if (x.y != z.y) return x.y < z.y;
       return x.key > z.key;
-    });
+    };
+    auto entry = [&](int i, size_t j, Part* out) {  // run i, position j; false: pruned
+      const int b = opt[i];
+      const Part& e = F[j];
+      const uint64_t c = sadd(e.c, T.cost[(size_t)l * 33 + b]);
+      const uint64_t y = e.y + T.bytes[(size_t)l * 33 + b];
+      if (kind == 0 ? (c > limit || y > gbound) : (y > limit || c > gbound)) return false;
+      *out = Part{c, y, key_put(e.key, l - l0, b)};
+      return true;
+    };
+    struct Head {
+      Part p;
+      int run;
+      size_t pos;
+    };
+    Head heap[33];
+    int nh = 0;
+    auto push = [&](const Head& h) {  // binary min-heap on `before`
+      int i = nh++;
+      while (i > 0 && before(h.p, heap[(i - 1) / 2].p)) {
+        heap[i] = heap[(i - 1) / 2];
+        i = (i - 1) / 2;
+      }
+      heap[i] = h;
+    };
+    auto pop = [&]() {
+      const Head top = heap[0];
+      const Head last = heap[--nh];
+      int i = 0;
+      for (;;) {
+        int c = 2 * i + 1;
+        if (c >= nh) break;
+        if (c + 1 < nh && before(heap[c + 1].p, heap[c].p)) ++c;
+        if (!before(heap[c].p, last.p)) break;
+        heap[i] = heap[c];
+        i = c;
+      }
+      if (nh > 0) heap[i] = last;
+      return top;
+    };
+    // next unpruned entry of run i at or after position j
+    auto advance = [&](int i, size_t j) {
+      Part p;
+      for (; j < F.size(); ++j)
+        if (entry(i, j, &p)) {
+          push(Head{p, i, j});
+          return;
+        }
+    };
+    for (int i = 0; i < nopt; ++i) advance(i, 0);
+    G.clear();
+    bool sorted = true;
+    while (nh > 0) {
+      const Head h = pop();
+      if (!G.empty() && before(h.p, G.back())) sorted = false;
+      G.push_back(h.p);
+      advance(h.run, h.pos + 1);
+    }
+    if (!sorted) std::sort(G.begin(), G.end(), before);
     F.clear();
     for (const Part& e : G)
       if (F.empty() || e.y < F.back().y) F.push_back(e);
@@ -275,6 +384,8 @@ uint64_t loaded(const SelInput& in, const std::vector<int>& b) {
 }
 
 }  // namespace
+
+void prepare_selection(SelInput* in) { prepare_tables(*in, &in->base, &in->ybytes, &in->asum); }
 
 int select_planes(const SelInput& in, int kind, double value, const std::vector<int>* upper,
                   std::vector<int>* b, uint64_t* bytes, double* bound, const char** why,

@@ -25,7 +25,16 @@ struct SelInput {
   uint64_t n;          // values
   uint64_t mandatory;  // container bytes always loaded (header, tables, outliers)
   std::vector<SelStage> st;
+  // Optional, filled by prepare_selection: the parts of the option tables
+  // that do not depend on the target (per level l and b: the cost terms of
+  // the stages, the loaded stream bytes; per level: the sum of a_t over the
+  // stages of levels <= l). Without them every selection computes them.
+  std::vector<uint64_t> base, ybytes;
+  std::vector<double> asum;
 };
+
+// Fills in.base, in.ybytes and in.asum (for inputs selected many times).
+void prepare_selection(SelInput* in);
 
 // Selection for a target (kind 0: error bound in the field's eb mode, kind 1:
 // bitrate in bits/value). upper (optional) bounds b_l from above (refine).

@@ -28,6 +28,8 @@ CASES = [
     ((90, 180), np.float32, "zonal", 1e-4, oracle.REL, oracle.LINEAR, oracle.STRICT),
     ((1000,), np.float32, "noise", 1e-3, oracle.ABS, oracle.CUBIC, oracle.STRICT),
     ((20, 30, 40), np.float32, "spiky", 1e-4, oracle.ABS, oracle.CUBIC, oracle.STRICT),
+    ((33, 50, 70), np.float32, "smooth", 1e-6, oracle.ABS, oracle.CUBIC_QUAD, oracle.STRICT),
+    ((400, 700), np.float32, "zonal", 1e-5, oracle.REL, oracle.CUBIC, oracle.STRICT),
 ]
 
 
