@@ -365,6 +365,11 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if not args.no_systems:
         extra["refine_chain"] = measure_refine_chain(ipc, x, out)
+        # the host-side lossless stage on this field's container (untimed leg)
+        f_l = ipc.Field.compress(x, EB)
+        extra["lossless"] = measure_codec(ipc, f_l.export(), nbytes)
+        extra["lossless"]["container_bytes"] = f_l.size()
+        del f_l
     del out, outs_br
     if not args.no_systems:
         del x
@@ -997,10 +1002,32 @@ def _zstd():
     return None
 
 
+def measure_codec(ipc, blob, raw):
+    """The library's lossless stage on a container: size, and host GB/s of
+    encoding and decoding (all host threads, best of three)."""
+    enc, dec = [], []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        coded = ipc.ipc_encode_container(blob)
+        t1 = time.perf_counter()
+        back = ipc.ipc_decode_container(coded)
+        t2 = time.perf_counter()
+        enc.append(t1 - t0)
+        dec.append(t2 - t1)
+    assert back == blob
+    return {"coder": "ipc rANS (order 0, 1 MiB blocks, host threads)", "bytes": len(coded),
+            "ratio": round(raw / len(coded), 3),
+            "container_ratio_gain": round(len(blob) / len(coded), 4),
+            "encode_GBps": round(len(blob) / min(enc) / 1e9, 2),
+            "decode_GBps": round(len(blob) / min(dec) / 1e9, 2),
+            "host_threads": os.cpu_count()}
+
+
 def entropy_study(args):
-    """How much a host-side lossless coder would add to the container of the
-    bench field (the paper runs zstd over its plane streams; this build's
-    GPU format stops at zero-word compaction). One JSON line."""
+    """What the host-side lossless stage adds to the container of the bench
+    field (the paper runs zstd over its plane streams): the library's rANS
+    coder (ipc_encode_container), against zlib and, where libzstd loads,
+    zstd. One JSON line."""
     import ctypes
     import zlib
 
@@ -1016,6 +1043,7 @@ def entropy_study(args):
     res = {"workload": "grf_k53 %d^3 f32, eb 1e-6 abs, cubic, strict" % args.edge,
            "field_bytes": raw, "container_bytes": len(blob),
            "container_ratio": round(raw / len(blob), 3), "coders": []}
+    res["coders"].append(measure_codec(ipc, blob, raw))
     for lvl in (1, 6):
         t0 = time.perf_counter()
         n = len(zlib.compress(blob, lvl))

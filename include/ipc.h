@@ -203,6 +203,34 @@ int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len);
 int ipc_import(const void* host_buf, uint64_t len, void* stream,
                ipc_field** out);
 
+/* ---- lossless backend (host) --------------------------------------------- */
+/* ipc_encode_container -- the lossless stage after predictive coding (Sec.
+ * 6.2.1, where the paper runs zstd over the plane streams): a byte string,
+ * normally an exported container, cut into blocks of 2^block_log2 bytes
+ * (0: 2^20; 12..26), each coded by an order-0 range asymmetric numeral
+ * system (rANS, 12-bit symbol frequencies, 32-bit state) or stored when
+ * coding does not shrink it. Host memory only; blocks run on up to
+ * `nthreads` host threads (0: the host's cores, at most 16). The coded
+ * form: u32 magic "IPCZ", u32 version 1, u64 raw length, u32 block_log2,
+ * u32 block count, u32 record size per block, the records (u8 mode 0 +
+ * raw bytes, or u8 mode 1 + 256 u16 frequencies + the rANS bytes, final
+ * encoder state first); little-endian. Deterministic: equal inputs give
+ * equal bytes on every host.
+ * out == NULL: *out_len receives an upper bound of the coded size.
+ * Otherwise *out_len is the capacity on entry and the size on return.
+ * Errors: IPC_EINVAL (null pointer, block size, capacity too small). */
+int ipc_encode_container(const void* raw, uint64_t raw_len, int block_log2, void* out,
+                         uint64_t* out_len, int nthreads);
+
+/* ipc_decode_container -- inverse of ipc_encode_container. out == NULL:
+ * *out_len receives the decoded size (read from the header). Otherwise
+ * *out_len is the capacity on entry and the size on return. Errors:
+ * IPC_ECORRUPT (magic, version, block table, or a block that does not
+ * decode to exactly its length), IPC_EINVAL. ipc_import also accepts the
+ * coded form and decodes it first. */
+int ipc_decode_container(const void* coded, uint64_t coded_len, void* out, uint64_t* out_len,
+                         int nthreads);
+
 /* ---- batches (uneven fields in one launch per level) --------------------- */
 /* One field of a batched compression; the fields are the same as ipc_compress
  * arguments. dims[] holds ndim extents. */

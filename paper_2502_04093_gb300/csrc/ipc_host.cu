@@ -350,6 +350,10 @@ std::vector<uint8_t> header_bytes(const ipc_field* f) {
 
 SelInput sel_input(const ipc_field* f);
 
+uint32_t get32le(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
 // Bytes of header_bytes(f) without building it: 112-byte fixed part, per
 // stage a 32-byte record and 32 plane sizes, 16 bytes per outlier.
 uint64_t header_size(const ipc_field* f) {
@@ -2030,6 +2034,20 @@ int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len) {
 int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out) {
   g_err.clear();
   if (!out || (!host_buf && len)) return fail(IPC_EINVAL, "null argument");
+  if (len >= 4 && get32le((const uint8_t*)host_buf) == 0x5A435049u) {  // coded form: decode first
+    uint64_t raw = 0;
+    int rc = ipc_decode_container(host_buf, len, nullptr, &raw, 0);
+    if (rc) return rc;
+    std::vector<uint8_t> dec;
+    try {
+      dec.resize(raw);
+    } catch (...) {
+      return fail(IPC_ENOMEM, "host allocation");
+    }
+    if ((rc = ipc_decode_container(host_buf, len, dec.data(), &raw, 0))) return rc;
+    if (raw >= 4 && get32le(dec.data()) == 0x5A435049u) return fail(IPC_ECORRUPT, "nested coding");
+    return ipc_import(dec.data(), raw, stream, out);
+  }
   const uint8_t* p = (const uint8_t*)host_buf;
   ipc_field* f = new (std::nothrow) ipc_field();
   if (!f) return fail(IPC_ENOMEM, "host allocation");

@@ -101,6 +101,8 @@ def lib() -> C.CDLL:
     L.ipc_compressed_size.argtypes = [vp, u64p]
     L.ipc_export.argtypes = [vp, vp, u64p]
     L.ipc_import.argtypes = [vp, C.c_uint64, vp, C.POINTER(vp)]
+    L.ipc_encode_container.argtypes = [C.c_char_p, C.c_uint64, C.c_int, vp, u64p, C.c_int]
+    L.ipc_decode_container.argtypes = [C.c_char_p, C.c_uint64, vp, u64p, C.c_int]
     L.ipc_field_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p,
                                  C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -273,6 +275,31 @@ def ipc_export_size(field) -> int:
     n = C.c_uint64()
     _check(lib().ipc_export(field, None, C.byref(n)), "ipc_export")
     return n.value
+
+
+def ipc_encode_container(raw: bytes, block_log2: int = 0, nthreads: int = 0) -> bytes:
+    """The lossless stage (host): `raw` (normally an exported container) as
+    an rANS-coded container."""
+    raw = bytes(raw)
+    n = C.c_uint64()
+    _check(lib().ipc_encode_container(raw, len(raw), block_log2, None, C.byref(n), nthreads),
+           "ipc_encode_container")
+    out = C.create_string_buffer(max(n.value, 1))
+    _check(lib().ipc_encode_container(raw, len(raw), block_log2, out, C.byref(n), nthreads),
+           "ipc_encode_container")
+    return out.raw[:n.value]
+
+
+def ipc_decode_container(coded: bytes, nthreads: int = 0) -> bytes:
+    """Inverse of ipc_encode_container."""
+    coded = bytes(coded)
+    n = C.c_uint64()
+    _check(lib().ipc_decode_container(coded, len(coded), None, C.byref(n), nthreads),
+           "ipc_decode_container")
+    out = C.create_string_buffer(max(n.value, 1))
+    _check(lib().ipc_decode_container(coded, len(coded), out, C.byref(n), nthreads),
+           "ipc_decode_container")
+    return out.raw[:n.value]
 
 
 def ipc_export(field, out=None):

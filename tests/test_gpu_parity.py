@@ -154,6 +154,26 @@ def test_import_from_oracle_bytes():
         assert e.value.rc == ipc.IPC_ECORRUPT
 
 
+def test_import_coded_container():
+    """ipc_import also takes the lossless stage's coded form (decoded on the
+    host first): the same field, container and reconstructions; coded bytes
+    that do not decode, or a coded container inside another, are refused."""
+    from oracle import rans_oracle
+    x = synth.random_field((40, 33, 70), seed=17)
+    g, o = both(x, 1e-5, ipc.IPC_EB_ABS)
+    raw = g.export()
+    for coded in (ipc.ipc_encode_container(raw), rans_oracle.encode(raw, block_log2=14)):
+        h = ipc.Field.from_bytes(coded, x.shape, torch.float32)
+        assert h.export() == raw == o.export()
+        for E in (1e-5, 1e-3):
+            check_retrieve(h, o, oracle.EB, E)
+    coded = ipc.ipc_encode_container(raw)
+    for b in (coded[:-1], ipc.ipc_encode_container(coded)):
+        with pytest.raises(ipc.IpcError) as e:
+            ipc.ipc_import(b)
+        assert e.value.rc == ipc.IPC_ECORRUPT
+
+
 def test_errors():
     x = torch.ones(8, 8, device="cuda")
     with pytest.raises(ipc.IpcError) as e:
