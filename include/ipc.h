@@ -203,6 +203,45 @@ int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len);
 int ipc_import(const void* host_buf, uint64_t len, void* stream,
                ipc_field** out);
 
+/* ---- progressive loading (Sec. 5: only the selected bitplanes are read) --- */
+/* ipc_container_ranges -- the byte ranges of a container that hold, for
+ * each level l, the streams of planes b_new[l-1] <= k < b_old[l-1] of its
+ * stages, and, when b_old == NULL (nothing loaded yet), the leading tables
+ * and the planes k >= b_new[l-1]. Computed from the container's leading
+ * bytes (as ipc_select_container: header, stage records, plane sizes).
+ * Streams are stored stage by stage, planes 31 .. 0, so each stage gives
+ * one run; adjacent runs are merged. ranges: (offset, length) pairs;
+ * *nranges: capacity on entry (pairs), count on return (ranges == NULL:
+ * count only). Errors: IPC_ECORRUPT (tables), IPC_EINVAL (nlevels != the
+ * container's level count, bounds outside 0 <= b_new <= b_old <= 32,
+ * capacity). */
+int ipc_container_ranges(const void* head, uint64_t head_len, const int* b_new, const int* b_old,
+                         int nlevels, uint64_t* ranges, int* nranges);
+
+/* ipc_import_partial -- a device-resident field from the bytes of those
+ * ranges for b_old == NULL, concatenated in order: it holds the planes
+ * k >= b_per_level[l-1] of each level. Every retrieval and refinement of it
+ * selects among the planes it holds (Sec. 5.2 / 5.3 with b_l >= the
+ * resident bound): a target those planes cannot meet fails with IPC_EBOUND
+ * (IPC_EBUDGET for a bitrate). ipc_export refuses such a field (IPC_EINVAL)
+ * until every plane is loaded. Errors as ipc_import. */
+int ipc_import_partial(const void* parts, uint64_t len, const int* b_per_level, int nlevels,
+                       void* stream, ipc_field** out);
+
+/* ipc_field_load_planes -- adds the planes b_new[l-1] <= k < resident[l-1]
+ * of each level to a partially loaded field, from the bytes of
+ * ipc_container_ranges(b_new, resident) concatenated in order. b_new <=
+ * resident per level. Synchronises `stream`; views of the field keep their
+ * selections (the new planes serve later retrievals and refinements).
+ * Errors: IPC_EINVAL, IPC_ECORRUPT (the streams do not match the tables),
+ * IPC_ENOMEM, IPC_ECUDA. */
+int ipc_field_load_planes(ipc_field* f, const void* parts, uint64_t len, const int* b_new,
+                          int nlevels, void* stream);
+
+/* ipc_field_resident -- per level, the lowest plane the field holds (all 0
+ * for a field with every plane); *nlevels = K. */
+int ipc_field_resident(const ipc_field* f, int* b_per_level, int* nlevels);
+
 /* ---- lossless backend (host) --------------------------------------------- */
 /* ipc_encode_container -- the lossless stage after predictive coding (Sec.
  * 6.2.1, where the paper runs zstd over the plane streams): a byte string,

@@ -12,11 +12,30 @@ namespace dev {
 // Element-type arithmetic (round-to-nearest, no contraction).
 // ---------------------------------------------------------------------------
 template <class T> struct FP;
+// Exact double of an integer |q| < 2^53 built in integer arithmetic: GB300
+// runs FP64 instructions (conversions included) at about 1/70 of its FP32
+// rate, so the f64 kernels keep them for the operations that round.
+__device__ __forceinline__ double exact_double(long long q) {
+  if (q == 0) return 0.0;
+  const unsigned long long s = (unsigned long long)q & 0x8000000000000000ull;
+  const unsigned long long m = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+  const int lz = __clzll((long long)m);  // >= 11
+  const unsigned long long frac = ((m << lz) << 1) >> 12;  // the bits below the leading one
+  return __longlong_as_double((long long)(s | ((unsigned long long)(1086 - lz) << 52) | frac));
+}
+
 template <> struct FP<float> {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float fabs_(float a) { return fabsf(a); }
+  // |a| <= lim (lim >= 0, not NaN); false for NaN a
+  static __device__ __forceinline__ bool abs_le(float a, float lim) { return fabsf(a) <= lim; }
+  // a * 2^K (K < 0)
+  template <int K>
+  static __device__ __forceinline__ float mul_pow2(float a) {
+    return __fmul_rn(a, 1.0f / (float)(1 << -K));
+  }
   // Round-to-nearest-even of |t| <= 2^21 by adding 1.5*2^23: the sum lies in
   // [2^23, 2^24) where the spacing is 1, so the addition itself rounds. The
   // integer is the distance of the bit patterns; the sign of a zero result
@@ -42,13 +61,30 @@ template <> struct FP<double> {
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double fabs_(double a) { return fabs(a); }
+  // |a| <= lim (lim >= 0, not NaN) on the bit patterns: non-negative doubles
+  // order as their patterns, and a NaN's pattern lies above every number's
+  static __device__ __forceinline__ bool abs_le(double a, double lim) {
+    return (unsigned long long)(__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll) <=
+           (unsigned long long)__double_as_longlong(lim);
+  }
+  // a * 2^K (K < 0), the product the multiplication gives: for a normal
+  // result only the exponent field changes (integer ops); zeros, results
+  // that would be subnormal, infinities and NaNs take the multiplication.
+  template <int K>
+  static __device__ __forceinline__ double mul_pow2(double a) {
+    const long long b = __double_as_longlong(a);
+    const int e = (int)((unsigned long long)b >> 52) & 0x7FF;
+    if (e > -K && e != 0x7FF) return __longlong_as_double(b - ((long long)(-K) << 52));
+    return __dmul_rn(a, 1.0 / (double)(1 << -K));
+  }
   static __device__ __forceinline__ double rint_(double t, int32_t* qi) {
     const double magic = 6755399441055744.0;  // 1.5 * 2^52
     double y = __dadd_rn(t, magic);
     *qi = (int32_t)(__double_as_longlong(y) - 0x4338000000000000LL);
-    return copysign(__dsub_rn(y, magic), t);
+    // y - magic is the integer itself (the same sign as t unless zero)
+    return *qi == 0 ? copysign(0.0, t) : exact_double(*qi);
   }
-  static __device__ __forceinline__ double from_code(int64_t q) { return __ll2double_rn(q); }
+  static __device__ __forceinline__ double from_code(int64_t q) { return exact_double(q); }
 };
 
 // Value of a (possibly truncated) negabinary code in the element type,
@@ -72,7 +108,7 @@ __device__ __forceinline__ T quad3(T a, T b, T c, T d, bool right) {
   // weights 3/8, 6/8, -1/8 (far neighbour on the right) or mirrored
   const T u = FP<T>::mul(right ? (T)3 : (T)6, b);
   const T v = FP<T>::mul(right ? (T)6 : (T)3, c);
-  return FP<T>::mul(FP<T>::sub(FP<T>::add(u, v), right ? d : a), (T)0.125);
+  return FP<T>::template mul_pow2<-3>(FP<T>::sub(FP<T>::add(u, v), right ? d : a));
 }
 
 // Q = false compiles the quadratic forms out (interp 0 or 1 only).
@@ -84,11 +120,11 @@ __device__ __forceinline__ T pred4(T a, T b, T c, T d, int i, int M, int interp)
     const T v = FP<T>::add(a, d);
     const T w = FP<T>::mul((T)9, u);
     const T z = FP<T>::sub(w, v);
-    return FP<T>::mul(z, (T)0.0625);
+    return FP<T>::template mul_pow2<-4>(z);
   }
   if (Q && interp == 2 && (i - 3 >= 0 || i + 3 <= M - 1))
     return quad3<T>(a, b, c, d, i + 3 <= M - 1);
-  return FP<T>::mul(FP<T>::add(b, c), (T)0.5);
+  return FP<T>::template mul_pow2<-1>(FP<T>::add(b, c));
 }
 
 // Which form pred4 takes at coordinate i: 0 copy, 1 Eq. 1, 2 Eq. 2,
@@ -115,7 +151,7 @@ __device__ __forceinline__ float code_value(uint32_t n, float) {
   return code_value_wide(n);
 }
 __device__ __forceinline__ double code_value(uint32_t n, double) {
-  return __ll2double_rn((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
+  return exact_double((int64_t)(n ^ 0xAAAAAAAAu) - (int64_t)0xAAAAAAAAu);
 }
 
 __device__ __forceinline__ uint32_t negabinary(int32_t q) {

@@ -224,6 +224,9 @@ struct ipc_field {
   std::vector<StageDescs> desc;   // per stage
   std::vector<uint64_t> out_off;  // per stage offset into d_oidx/d_oval
   SelInput sel;                   // the selector's input, prepared once
+  // Planes held on the device: per level, planes k >= rb[l-1] (a field
+  // imported from part of a container); empty: every plane.
+  std::vector<int> rb;
 };
 
 struct ipc_view {
@@ -1989,6 +1992,7 @@ int ipc_compressed_size(const ipc_field* f, uint64_t* bytes) {
 
 int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len) {
   if (!f || f->tag != kFieldTag || !len) return fail(IPC_EINVAL, "invalid argument");
+  if (!f->rb.empty()) return fail(IPC_EINVAL, "the field holds only some of its planes");
   const uint64_t total = f->mandatory + f->stream_bytes;
   if (!host_buf) {
     *len = total;
@@ -2031,24 +2035,81 @@ int ipc_export(const ipc_field* f, void* host_buf, uint64_t* len) {
   return IPC_OK;
 }
 
-int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out) {
-  g_err.clear();
-  if (!out || (!host_buf && len)) return fail(IPC_EINVAL, "null argument");
-  if (len >= 4 && get32le((const uint8_t*)host_buf) == 0x5A435049u) {  // coded form: decode first
-    uint64_t raw = 0;
-    int rc = ipc_decode_container(host_buf, len, nullptr, &raw, 0);
-    if (rc) return rc;
-    std::vector<uint8_t> dec;
-    try {
-      dec.resize(raw);
-    } catch (...) {
-      return fail(IPC_ENOMEM, "host allocation");
-    }
-    if ((rc = ipc_decode_container(host_buf, len, dec.data(), &raw, 0))) return rc;
-    if (raw >= 4 && get32le(dec.data()) == 0x5A435049u) return fail(IPC_ECORRUPT, "nested coding");
-    return ipc_import(dec.data(), raw, stream, out);
+}  // extern "C"
+
+namespace {
+
+// nnz of a stream from its size alone (a plane whose stream is not loaded):
+// exact for empty and sparse streams; a dense one is known only to have
+// nonzero words (W stands in until the stream is loaded).
+uint64_t nnz_from_size(uint64_t z, uint64_t W) {
+  const uint64_t nbm = (W + 31) / 32;
+  if (z == 4) return 0;
+  if (z == 4 + 4 * W) return W;
+  return (z - 4) / 4 - nbm;
+}
+
+// Uploads `len` bytes of streams (stage order, planes descending within a
+// stage, the planes of stage t at level l being [lo_l, hi_l)) and unpacks
+// them into the field's segmented layout; `nzs` holds their nnz (read from
+// the streams by the caller). Synchronises.
+int unpack_streams(ipc_field* f, const uint8_t* p, uint64_t len, const std::vector<int>& lo,
+                   const std::vector<int>& hi, const std::vector<uint32_t>& nzs, cudaStream_t st) {
+  uint32_t *blob = nullptr, *tmp = nullptr;
+  unsigned int* flags = nullptr;  // [0] corruption flag
+  uint64_t tw = 0;
+  for (auto& sg : f->g.stages) tw = std::max<uint64_t>(tw, 2 * 32 * ((sg.words + 31) / 32));
+  int rc;
+  if ((rc = dalloc((void**)&blob, std::max<uint64_t>(len, 4), st)) ||
+      (rc = dalloc((void**)&tmp, tw * 4, st)) || (rc = dalloc((void**)&flags, 4, st))) {
+    dfree(blob);
+    dfree(tmp);
+    return rc;
   }
-  const uint8_t* p = (const uint8_t*)host_buf;
+  cudaError_t e = cudaSuccess;
+  if (len) e = cudaMemcpyAsync(blob, p, len, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 4, st);
+  uint64_t word = 0;  // word offset of the next stream in the blob
+  size_t j = 0;
+  const uint32_t S = (uint32_t)f->g.stages.size();
+  for (uint32_t t = 0; t < S && e == cudaSuccess; ++t) {
+    const int l = f->g.stages[t].level;
+    const uint64_t W = f->g.stages[t].words;
+    StageDescs d = f->desc[t];
+    uint32_t kmask = 0;
+    for (int k = 31; k >= 0; --k) {
+      PlaneDesc& pd = d.p[k];
+      if (k >= lo[l - 1] && k < hi[l - 1]) {
+        pd.nnz = nzs[j++];
+        pd.mode = stream_mode(pd.nnz, W);
+        pd.pk_off = word;
+        word += stream_bytes(pd.nnz, W) / 4;
+        kmask |= 1u << k;
+      } else {
+        pd.mode = 0;  // not in this upload: left as it is
+      }
+    }
+    if (!kmask) continue;
+    const long ph = prof_begin(IPC_KERNEL_UNPACK, st);
+    e = launch_unpack(stage_args(f->g.stages[t]), d, f->g.stages[t].nseg, blob, tmp, f->d_cap,
+                      f->d_bm, flags, kmask, st);
+    prof_end(ph, st, 0);
+  }
+  unsigned int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, flags, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(blob, st);
+  cudaFreeAsync(tmp, st);
+  cudaFreeAsync(flags, st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream upload");
+  if (hbad) return fail(IPC_ECORRUPT, "stream contents disagree with their nnz / bitmap");
+  return IPC_OK;
+}
+
+// A device field from container bytes: the leading tables, then for each
+// stage the streams of its planes k >= res_l (every plane when res is null).
+int import_core(const uint8_t* p, uint64_t len, const int* res, int nres, cudaStream_t st,
+                ipc_field** out) {
   ipc_field* f = new (std::nothrow) ipc_field();
   if (!f) return fail(IPC_ENOMEM, "host allocation");
   f->tag = kFieldTag;
@@ -2058,12 +2119,21 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
     free_field_device(f);
     f->tag = kDeadTag;
     delete f;
-    return code == IPC_ECUDA ? code : fail(code, why);
+    return code == IPC_ECUDA || !why ? code : fail(code, why);
   };
   uint64_t pos = 0;
   std::vector<uint64_t> nout, size;
   const char* why = "";
   if (parse_head(p, len, f, &pos, &nout, &size, &why)) return drop(IPC_ECORRUPT, why);
+  const int K = f->g.K;
+  std::vector<int> lo(K, 0), hi(K, 32);
+  if (res) {
+    if (nres != K) return drop(IPC_EINVAL, "resident planes: one entry per level");
+    for (int l = 0; l < K; ++l) {
+      if (res[l] < 0 || res[l] > 32) return drop(IPC_EINVAL, "resident planes out of range");
+      lo[l] = res[l];
+    }
+  }
   const uint32_t S = (uint32_t)f->g.stages.size();
   for (uint32_t t = 0; t < S; ++t) {
     if (pos + nout[t] * 16 > len) return drop(IPC_ECORRUPT, "truncated outliers");
@@ -2081,59 +2151,185 @@ int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out
   }
   const uint64_t mand = pos;
   uint64_t spos = pos;
+  std::vector<uint32_t> nzs;
   for (uint32_t t = 0; t < S; ++t) {
     const uint64_t W = f->g.stages[t].words;
+    const int l = f->g.stages[t].level;
     for (int k = 31; k >= 0; --k) {
+      const uint64_t z = size[32 * t + k];
+      if (k < lo[l - 1]) {  // not loaded: what the size tells
+        if (z < 4 || stream_bytes(nnz_from_size(z, W), W) != z) return drop(IPC_ECORRUPT, "bad stream size");
+        f->st[t].nnz[k] = nnz_from_size(z, W);
+        continue;
+      }
       if (spos + 4 > len) return drop(IPC_ECORRUPT, "truncated streams");
       uint32_t nz = 0;
       for (int i = 0; i < 4; ++i) nz |= uint32_t(p[spos + i]) << (8 * i);
-      if (nz > W || size[32 * t + k] != stream_bytes(nz, W)) return drop(IPC_ECORRUPT, "bad stream size");
+      if (nz > W || z != stream_bytes(nz, W)) return drop(IPC_ECORRUPT, "bad stream size");
       f->st[t].nnz[k] = nz;
-      spos += size[32 * t + k];
+      nzs.push_back(nz);
+      spos += z;
       if (spos > len) return drop(IPC_ECORRUPT, "truncated streams");
     }
   }
   if (spos != len) return drop(IPC_ECORRUPT, "trailing bytes");
   DeviceGuard dg(f->device);
-  cudaStream_t st = (cudaStream_t)stream;
   int rc = plan_field(f, st);
   if (rc) return drop(rc, "allocation");
   rc = finish_field(f, st);
   if (rc) return drop(rc, "allocation");
   if (f->mandatory != mand) return drop(IPC_ECORRUPT, "table size mismatch");
-  // streams -> device, then unpack into the segmented layout
-  uint32_t *blob = nullptr, *tmp = nullptr;
-  unsigned int* flags = nullptr;  // [0] corruption flag
-  uint64_t tw = 0;
-  for (auto& sg : f->g.stages) tw = std::max<uint64_t>(tw, 2 * 32 * ((sg.words + 31) / 32));
-  if ((rc = dalloc((void**)&blob, f->stream_bytes, st)) || (rc = dalloc((void**)&tmp, tw * 4, st)) ||
-      (rc = dalloc((void**)&flags, 4, st))) {
-    dfree(blob);
-    dfree(tmp);
-    return drop(rc, "allocation");
+  if (res) {
+    bool any = false;
+    for (int l = 0; l < K; ++l) any |= lo[l] > 0;
+    if (any) {
+      f->rb = lo;
+      f->sel.lower = lo;
+    }
   }
-  cudaError_t e = cudaSuccess;
-  if (f->stream_bytes)
-    e = cudaMemcpyAsync(blob, p + mand, f->stream_bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 4, st);
-  for (uint32_t t = 0; t < S && e == cudaSuccess; ++t) {
-    const long ph = prof_begin(IPC_KERNEL_UNPACK, st);
-    e = launch_unpack(stage_args(f->g.stages[t]), f->desc[t], f->g.stages[t].nseg, blob, tmp,
-                      f->d_cap, f->d_bm, flags, st);
-    prof_end(ph, st, 0);
-  }
-  unsigned int hbad = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, flags, 4, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFreeAsync(blob, st);
-  cudaFreeAsync(tmp, st);
-  cudaFreeAsync(flags, st);
-  if (e != cudaSuccess) {
-    cuda_fail(e, "import");
-    return drop(IPC_ECUDA, "");
-  }
-  if (hbad) return drop(IPC_ECORRUPT, "stream contents disagree with their nnz / bitmap");
+  rc = unpack_streams(f, p + mand, spos - mand, lo, hi, nzs, st);
+  if (rc) return drop(rc, nullptr);
   *out = f;
+  return IPC_OK;
+}
+
+// The streams of planes [lo_l, hi_l) of every stage: byte ranges of the
+// container (stage order, planes descending: each stage's span is one run).
+void stream_ranges(const ipc_field& f, uint64_t mand, const std::vector<uint64_t>& size,
+                   const int* lo, const int* hi, std::vector<std::pair<uint64_t, uint64_t>>* r) {
+  uint64_t pos = mand;
+  for (size_t t = 0; t < f.g.stages.size(); ++t) {
+    const int l = f.g.stages[t].level;
+    uint64_t a = pos, b = pos;
+    for (int k = 31; k >= 0; --k) {
+      const uint64_t z = size[32 * t + k];
+      if (k >= hi[l - 1]) a += z;
+      if (k >= lo[l - 1]) b += z;
+      pos += z;
+    }
+    if (b > a) {
+      if (!r->empty() && r->back().first + r->back().second == a) r->back().second += b - a;
+      else r->push_back({a, b - a});
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out) {
+  g_err.clear();
+  if (!out || (!host_buf && len)) return fail(IPC_EINVAL, "null argument");
+  if (len >= 4 && get32le((const uint8_t*)host_buf) == 0x5A435049u) {  // coded form: decode first
+    uint64_t raw = 0;
+    int rc = ipc_decode_container(host_buf, len, nullptr, &raw, 0);
+    if (rc) return rc;
+    std::vector<uint8_t> dec;
+    try {
+      dec.resize(raw);
+    } catch (...) {
+      return fail(IPC_ENOMEM, "host allocation");
+    }
+    if ((rc = ipc_decode_container(host_buf, len, dec.data(), &raw, 0))) return rc;
+    if (raw >= 4 && get32le(dec.data()) == 0x5A435049u) return fail(IPC_ECORRUPT, "nested coding");
+    return ipc_import(dec.data(), raw, stream, out);
+  }
+  return import_core((const uint8_t*)host_buf, len, nullptr, 0, (cudaStream_t)stream, out);
+}
+
+int ipc_container_ranges(const void* head, uint64_t head_len, const int* b_new, const int* b_old,
+                         int nlevels, uint64_t* ranges, int* nranges) {
+  g_err.clear();
+  if (!head || !b_new || !nranges) return fail(IPC_EINVAL, "null argument");
+  ipc_field f{};
+  uint64_t pos = 0;
+  std::vector<uint64_t> nout, size;
+  const char* why = "";
+  if (parse_head((const uint8_t*)head, head_len, &f, &pos, &nout, &size, &why))
+    return fail(IPC_ECORRUPT, why);
+  const int K = f.g.K;
+  if (nlevels != K) return fail(IPC_EINVAL, "one entry per level");
+  std::vector<int> hi(K, 32);
+  for (int l = 0; l < K; ++l) {
+    if (b_old) hi[l] = b_old[l];
+    if (b_new[l] < 0 || hi[l] > 32 || b_new[l] > hi[l]) return fail(IPC_EINVAL, "plane bounds");
+  }
+  uint64_t mand = pos;
+  for (uint64_t n : nout) mand += 16 * n;
+  std::vector<std::pair<uint64_t, uint64_t>> r;
+  if (!b_old) r.push_back({0, mand});
+  stream_ranges(f, mand, size, b_new, hi.data(), &r);
+  const int cap = *nranges;
+  *nranges = (int)r.size();
+  if (!ranges) return IPC_OK;
+  if ((int)r.size() > cap) return fail(IPC_EINVAL, "range capacity too small");
+  for (size_t i = 0; i < r.size(); ++i) {
+    ranges[2 * i] = r[i].first;
+    ranges[2 * i + 1] = r[i].second;
+  }
+  return IPC_OK;
+}
+
+int ipc_import_partial(const void* parts, uint64_t len, const int* b_per_level, int nlevels,
+                       void* stream, ipc_field** out) {
+  g_err.clear();
+  if (!out || !parts || !b_per_level) return fail(IPC_EINVAL, "null argument");
+  return import_core((const uint8_t*)parts, len, b_per_level, nlevels, (cudaStream_t)stream, out);
+}
+
+int ipc_field_load_planes(ipc_field* f, const void* parts, uint64_t len, const int* b_new,
+                          int nlevels, void* stream) {
+  g_err.clear();
+  if (!f || f->tag != kFieldTag || !b_new || (!parts && len)) return fail(IPC_EINVAL, "invalid argument");
+  const int K = f->g.K;
+  if (nlevels != K) return fail(IPC_EINVAL, "one entry per level");
+  if (f->rb.empty()) return len ? fail(IPC_EINVAL, "the field holds every plane") : IPC_OK;
+  std::vector<int> lo(K), hi = f->rb;
+  for (int l = 0; l < K; ++l) {
+    if (b_new[l] < 0 || b_new[l] > f->rb[l]) return fail(IPC_EINVAL, "plane bounds");
+    lo[l] = b_new[l];
+  }
+  const uint8_t* p = (const uint8_t*)parts;
+  uint64_t pos = 0;
+  std::vector<uint32_t> nzs;
+  std::vector<std::pair<int, int>> at;  // (stage, plane) of each stream
+  for (size_t t = 0; t < f->g.stages.size(); ++t) {
+    const int l = f->g.stages[t].level;
+    const uint64_t W = f->g.stages[t].words;
+    for (int k = hi[l - 1] - 1; k >= lo[l - 1]; --k) {
+      const uint64_t z = f->st[t].size[k];
+      if (pos + 4 > len) return fail(IPC_ECORRUPT, "truncated streams");
+      uint32_t nz = 0;
+      for (int i = 0; i < 4; ++i) nz |= uint32_t(p[pos + i]) << (8 * i);
+      if (nz > W || z != stream_bytes(nz, W)) return fail(IPC_ECORRUPT, "bad stream size");
+      nzs.push_back(nz);
+      at.push_back({(int)t, k});
+      pos += z;
+      if (pos > len) return fail(IPC_ECORRUPT, "truncated streams");
+    }
+  }
+  if (pos != len) return fail(IPC_ECORRUPT, "trailing bytes");
+  DeviceGuard dg(f->device);
+  const int rc = unpack_streams(f, p, len, lo, hi, nzs, (cudaStream_t)stream);
+  if (rc) return rc;
+  for (size_t i = 0; i < at.size(); ++i) {
+    const int t = at[i].first, k = at[i].second;
+    f->st[t].nnz[k] = nzs[i];
+    f->desc[t].p[k].nnz = nzs[i];
+  }
+  bool any = false;
+  for (int l = 0; l < K; ++l) any |= lo[l] > 0;
+  f->rb = any ? lo : std::vector<int>();
+  f->sel.lower = f->rb;
+  return IPC_OK;
+}
+
+int ipc_field_resident(const ipc_field* f, int* b_per_level, int* nlevels) {
+  if (!f || f->tag != kFieldTag) return fail(IPC_EINVAL, "invalid field");
+  if (nlevels) *nlevels = f->g.K;
+  if (b_per_level)
+    for (int l = 0; l < f->g.K; ++l) b_per_level[l] = f->rb.empty() ? 0 : f->rb[l];
   return IPC_OK;
 }
 

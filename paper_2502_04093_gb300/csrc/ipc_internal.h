@@ -316,9 +316,10 @@ cudaError_t launch_level_retrieve_mode_quad(int dtype, const LevelArgs& L, void*
 // flags[1 + k] = nonzero words found in plane k (import).
 cudaError_t launch_pack(const StageArgs& a, const StageDescs& d, const uint32_t* cap,
                         const uint32_t* bm, uint32_t* tmp, uint32_t* blob, cudaStream_t st);
+// kmask: the planes this upload writes (the others keep their words).
 cudaError_t launch_unpack(const StageArgs& a, const StageDescs& d, uint64_t nseg,
                           const uint32_t* blob, uint32_t* tmp, uint32_t* cap, uint32_t* bm,
-                          unsigned int* flags, cudaStream_t st);
+                          unsigned int* flags, uint32_t kmask, cudaStream_t st);
 
 // Sets the message ipc_last_error() returns on the calling thread.
 void set_last_error(const char* what);

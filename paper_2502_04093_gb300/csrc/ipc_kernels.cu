@@ -291,8 +291,10 @@ __global__ void k_unpack_bits(StageArgs a, StageDescs ds, const uint32_t* __rest
 
 // Import step 2: segment bitmaps. grid = (ceil(nseg * bw / 256), 32).
 __global__ void k_unpack_segbits(StageArgs a, StageDescs ds, uint64_t nseg,
-                                 const uint32_t* __restrict__ bits, uint32_t* __restrict__ bm) {
+                                 const uint32_t* __restrict__ bits, uint32_t* __restrict__ bm,
+                                 uint32_t kmask) {
   const int k = blockIdx.y;
+  if (!((kmask >> k) & 1u)) return;  // a plane this upload leaves as it is
   const PlaneDesc pd = ds.p[k];
   const uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (u >= nseg * a.bw) return;
@@ -405,13 +407,13 @@ cudaError_t launch_pack(const StageArgs& a, const StageDescs& d, const uint32_t*
 
 cudaError_t launch_unpack(const StageArgs& a, const StageDescs& d, uint64_t nseg,
                           const uint32_t* blob, uint32_t* tmp, uint32_t* cap, uint32_t* bm,
-                          unsigned int* flags, cudaStream_t st) {
+                          unsigned int* flags, uint32_t kmask, cudaStream_t st) {
   uint32_t* bits = tmp;
   uint32_t* rank = tmp + 32 * a.nbm;
   k_unpack_bits<<<dim3(grid_for(a.nbm, 256, 1u << 30), 32), 256, 0, st>>>(a, d, blob, bits, flags);
   k_scan_bits<<<32, 1024, 0, st>>>(a, d, bits, rank, flags);
   k_unpack_segbits<<<dim3(grid_for(nseg * a.bw, 256, 1u << 30), 32), 256, 0, st>>>(a, d, nseg, bits,
-                                                                                   bm);
+                                                                                   bm, kmask);
   k_unpack_words<<<dim3(grid_for(a.W, 256, 1u << 30), 32), 256, 0, st>>>(a, d, blob, bits, rank, bm,
                                                                           cap, flags);
   return cudaGetLastError();

@@ -45,13 +45,13 @@ template <class T>
 __device__ __forceinline__ int32_t quantize(T xv, T pred, const QuantArgs<T>& qa, T* rec,
                                             bool* outlier) {
   const T t = FP<T>::mul(FP<T>::sub(xv, pred), qa.inv2eb);
-  *outlier = !(FP<T>::fabs_(t) <= qa.R);
+  *outlier = !FP<T>::abs_le(t, qa.R);
   *rec = xv;
   if (*outlier) return 0;
   int32_t qi;
   const T qf = FP<T>::rint_(t, &qi);
   const T rc = FP<T>::add(pred, FP<T>::mul(qf, qa.twoeb));
-  if (FP<T>::fabs_(FP<T>::sub(xv, rc)) <= qa.ebchk) {
+  if (FP<T>::abs_le(FP<T>::sub(xv, rc), qa.ebchk)) {
     *rec = rc;
     return qi;
   }
@@ -238,6 +238,16 @@ __device__ __forceinline__ void scaled_word(uint32_t x, const CodeScale<T>& cs, 
   const float z1 = __fsub_rn(__int_as_float(__byte_perm(t, 0x4B40u, 0x5432)), cs.zbias);
   v[0] = FP<T>::mul((T)z0, cs.tw);
   v[1] = FP<T>::mul((T)z1, cs.tw);
+}
+// double: z in integer arithmetic and its exact double built the same way
+// (no conversion instruction on the FP64 pipe)
+template <>
+__device__ __forceinline__ void scaled_word<double>(uint32_t x, const CodeScale<double>& cs,
+                                                    double* v) {
+  const uint32_t t = x ^ cs.zmask;
+  const int m = (int)(cs.zmask & 0xFFFFu);
+  v[0] = FP<double>::mul(exact_double((int)(t & 0xFFFFu) - m), cs.tw);
+  v[1] = FP<double>::mul(exact_double((int)(t >> 16) - m), cs.tw);
 }
 template <class T>
 __device__ __forceinline__ void scaled_pair(const uint16_t* p, const CodeScale<T>& cs, T (&v)[2]) {
@@ -906,9 +916,9 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
           // the rule for this column; no lane takes a separate path (the
           // quadratic forms are redone below).
           const T u = FP<T>::add(w[k + 1], w[k + 2]);
-          const T cub = FP<T>::mul(FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])),
-                                   (T)0.0625);
-          const T lin = FP<T>::mul(u, (T)0.5);
+          const T cub = FP<T>::template mul_pow2<-4>(
+              FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])));
+          const T lin = FP<T>::template mul_pow2<-1>(u);
           const uint32_t r = rule >> (RW * k) & ((1u << RW) - 1u);
           const T pred = r == 2u ? cub : (r == 1u ? lin : w[k + 1]);
           v[2 * k] = w[k + 1];

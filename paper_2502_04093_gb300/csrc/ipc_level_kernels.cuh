@@ -320,9 +320,9 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
         for (int k = 0; k < 4; ++k) {
           const int c2o = c2e + 2 * k + 1;
           const T u = FP<T>::add(w[k + 1], w[k + 2]);
-          const T cub = FP<T>::mul(FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])),
-                                   (T)0.0625);
-          const T lin = FP<T>::mul(u, (T)0.5);
+          const T cub = FP<T>::template mul_pow2<-4>(
+              FP<T>::sub(FP<T>::mul((T)9, u), FP<T>::add(w[k], w[k + 3])));
+          const T lin = FP<T>::template mul_pow2<-1>(u);
           const uint32_t r = rule >> (RW * k) & ((1u << RW) - 1u);
           T pred = r == 2u ? cub : (r == 1u ? lin : w[k + 1]);
           if (quad && (r & 4u)) pred = quad3<T>(w[k], w[k + 1], w[k + 2], w[k + 3], r == 4u);

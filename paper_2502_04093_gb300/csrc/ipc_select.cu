@@ -37,6 +37,7 @@ struct Tables {
   int K;
   std::vector<uint64_t> cost, bytes;
   std::vector<uint64_t> rho;  // per level: the rounding margin inside cost(l, b > 0)
+  std::vector<int> lo;        // per level: the smallest b allowed
 };
 
 // The target-independent parts of the tables: base[l-1][b] (strict: the sum
@@ -103,6 +104,8 @@ void build_tables(const SelInput& in, double A, Tables* T) {
   const double kappa = cubic ? 24.0 : 12.0;
   T->K = K;
   T->bytes = prepared ? in.ybytes : ly;
+  T->lo.assign((size_t)K, 0);
+  if (in.lower.size() == (size_t)K) T->lo = in.lower;
   T->cost.assign((size_t)K * 33, 0);
   T->rho.assign((size_t)K, 0);
   for (int l = 1; l <= K; ++l) {
@@ -129,7 +132,8 @@ uint64_t greedy_bound(const Tables& T, int kind, uint64_t limit, const std::vect
   std::vector<int> b(K);
   uint64_t c = 0, y = 0;
   for (int l = 0; l < K; ++l) {
-    b[l] = kind == 0 ? 0 : (upper ? (*upper)[l] : 32);
+    b[l] = kind == 0 ? T.lo[l] : (upper ? (*upper)[l] : 32);
+    if (b[l] < T.lo[l] || (upper && b[l] > (*upper)[l])) return ~uint64_t(0);  // no option
     c = sadd(c, T.cost[(size_t)l * 33 + b[l]]);
     y += T.bytes[(size_t)l * 33 + b[l]];
   }
@@ -152,7 +156,7 @@ uint64_t greedy_bound(const Tables& T, int kind, uint64_t limit, const std::vect
         if (r > best) { best = r; *v_out = v; }
       }
     } else {  // load more planes: less cost for more bytes
-      for (int v = b[l] - 1; v >= 0; --v) {
+      for (int v = b[l] - 1; v >= T.lo[l]; --v) {
         const uint64_t c1 = T.cost[(size_t)l * 33 + v], y1 = T.bytes[(size_t)l * 33 + v];
         if (c1 >= c0 || y - y0 + y1 > limit) continue;
         const double r = (double)(c0 - c1) / (double)(y1 - y0 + 1);
@@ -217,7 +221,7 @@ void half_frontier(const Tables& T, int l0, int l1, int kind, uint64_t limit, ui
     int opt[33];
     int nopt = 0;
     uint64_t best = ~uint64_t(0);
-    for (int b = bmax; b >= 0; --b) {  // staircase: keep b only if strictly cheaper
+    for (int b = bmax; b >= T.lo[l]; --b) {  // staircase: keep b only if strictly cheaper
       const uint64_t c = T.cost[(size_t)l * 33 + b];
       if (c < best) {
         opt[nopt++] = b;

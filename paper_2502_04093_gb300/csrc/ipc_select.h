@@ -31,6 +31,9 @@ struct SelInput {
   // stages of levels <= l). Without them every selection computes them.
   std::vector<uint64_t> base, ybytes;
   std::vector<double> asum;
+  // Optional lower bounds on b_l (a field that holds only the planes
+  // k >= lower_l of each level); empty: none.
+  std::vector<int> lower;
 };
 
 // Fills in.base, in.ybytes and in.asum (for inputs selected many times).

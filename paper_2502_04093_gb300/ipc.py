@@ -102,6 +102,13 @@ def lib() -> C.CDLL:
     L.ipc_export.argtypes = [vp, vp, u64p]
     L.ipc_import.argtypes = [vp, C.c_uint64, vp, C.POINTER(vp)]
     L.ipc_encode_container.argtypes = [C.c_char_p, C.c_uint64, C.c_int, vp, u64p, C.c_int]
+    L.ipc_container_ranges.argtypes = [C.c_char_p, C.c_uint64, C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.c_int, u64p, C.POINTER(C.c_int)]
+    L.ipc_import_partial.argtypes = [C.c_char_p, C.c_uint64, C.POINTER(C.c_int), C.c_int, vp,
+                                     C.POINTER(vp)]
+    L.ipc_field_load_planes.argtypes = [vp, C.c_char_p, C.c_uint64, C.POINTER(C.c_int), C.c_int,
+                                        vp]
+    L.ipc_field_resident.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.ipc_decode_container.argtypes = [C.c_char_p, C.c_uint64, vp, u64p, C.c_int]
     L.ipc_field_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p,
                                  C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -275,6 +282,52 @@ def ipc_export_size(field) -> int:
     n = C.c_uint64()
     _check(lib().ipc_export(field, None, C.byref(n)), "ipc_export")
     return n.value
+
+
+def _ints(v):
+    return (C.c_int * max(len(v), 1))(*[int(x) for x in v])
+
+
+def ipc_container_ranges(head: bytes, b_new, b_old=None):
+    """(offset, length) byte ranges of a container holding the planes
+    b_new <= k < b_old of each level (b_old None: the leading tables and the
+    planes k >= b_new), from the container's leading bytes."""
+    head = bytes(head)
+    n = C.c_int(0)
+    bo = _ints(b_old) if b_old is not None else None
+    _check(lib().ipc_container_ranges(head, len(head), _ints(b_new), bo, len(b_new), None,
+                                      C.byref(n)), "ipc_container_ranges")
+    r = (C.c_uint64 * max(2 * n.value, 1))()
+    _check(lib().ipc_container_ranges(head, len(head), _ints(b_new), bo, len(b_new), r,
+                                      C.byref(n)), "ipc_container_ranges")
+    return [(r[2 * i], r[2 * i + 1]) for i in range(n.value)]
+
+
+def ipc_import_partial(parts: bytes, b_per_level, stream=None) -> C.c_void_p:
+    """A device field holding the planes k >= b_per_level[l-1] of each level,
+    from the bytes of ipc_container_ranges(head, b_per_level) in order."""
+    parts = bytes(parts)
+    h = C.c_void_p()
+    _check(lib().ipc_import_partial(parts, len(parts), _ints(b_per_level), len(b_per_level),
+                                    _stream(stream), C.byref(h)), "ipc_import_partial")
+    return h
+
+
+def ipc_field_load_planes(field, parts: bytes, b_new, stream=None) -> None:
+    """Adds planes b_new <= k < resident of each level (bytes of
+    ipc_container_ranges(head, b_new, resident) in order)."""
+    parts = bytes(parts)
+    h = field.h if hasattr(field, "h") else field
+    _check(lib().ipc_field_load_planes(h, parts, len(parts), _ints(b_new), len(b_new),
+                                       _stream(stream)), "ipc_field_load_planes")
+
+
+def ipc_field_resident(field):
+    h = field.h if hasattr(field, "h") else field
+    b = (C.c_int * 64)()
+    n = C.c_int()
+    _check(lib().ipc_field_resident(h, b, C.byref(n)), "ipc_field_resident")
+    return list(b)[:n.value]
 
 
 def ipc_encode_container(raw: bytes, block_log2: int = 0, nthreads: int = 0) -> bytes:
