@@ -752,15 +752,17 @@ def measure_refine_chain(ipc, x, out):
 def serve_stream(ipc, fields, reqs, plain, rate, live_cap=8, seed=77):
     """Feeds one request stream (Poisson arrivals at `rate` per second) to a
     server; returns latencies (us), wall time and output bytes. The served
-    form refines incrementally (a refinement decodes only its new planes
-    into the view's resident reconstruction, Algorithm 2); the plain one
-    reconstructs each request from scratch, one launch sequence at a time."""
+    form refines in IPC_REFINE_AUTO (incrementally for f64 fields, where a
+    refinement then decodes only its new planes into the view's resident
+    reconstruction; these f32 fields reconstruct, the increment's margin
+    missing their targets); the plain one reconstructs each request from
+    scratch, one launch sequence at a time."""
     import numpy as np
     srv = ipc.ipc_server_create(48 << 30, max_batch=1 if plain else 0,
                                 max_inflight=1 if plain else 3, nstreams=1 if plain else 3,
                                 plain=plain, max_batch_values=0 if plain else 1 << 26,
                                 refine_mode=ipc.IPC_REFINE_CANONICAL if plain
-                                else ipc.IPC_REFINE_INCREMENTAL)
+                                else ipc.IPC_REFINE_AUTO)
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
     live = []  # (view_id, field index, current E)
@@ -876,8 +878,8 @@ def measure_serving(ipc, synth, torch, full=False):
         ipc.ipc_free(f)
     return {"workload": "%d resident k^-5/3 f32 fields, edges %d..%d (log-uniform, step 32), "
                         "rel eb 1e-6; %d Poisson requests x 3 arrival sequences (median "
-                        "reported); served: continuous batching, incremental refines; plain: "
-                        "one request at a time, refines reconstructed" % (nf, 128, hi, nreq),
+                        "reported); served: continuous batching, refines in the automatic form; "
+                        "plain: one request at a time" % (nf, 128, hi, nreq),
             "plain_capacity_rps": round(cap, 1), "offered_rps": round(rate, 1), **res}
 
 

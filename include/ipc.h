@@ -135,7 +135,12 @@ int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* pe
  *      guaranteed bound adds the increment's worst-case rounding to the
  *      canonical one; when that bound misses an error target, the refinement
  *      runs in the canonical form instead (ipc_refine_info tells which). */
-enum { IPC_REFINE_CANONICAL = 0, IPC_REFINE_INCREMENTAL = 1 };
+/*  IPC_REFINE_AUTO        : incremental for f64 fields, canonical for f32 ones.
+ *      In f32 the increment's rounding margin (u = 2^-24) misses most error
+ *      targets past the first few planes, so the refinement would fall back
+ *      to a reconstruction and the recorded state would cost without use;
+ *      in f64 the increment nearly always applies. */
+enum { IPC_REFINE_CANONICAL = 0, IPC_REFINE_INCREMENTAL = 1, IPC_REFINE_AUTO = 2 };
 
 /* ipc_refine -- Algorithm 2. The new selection only adds planes (b'_l <= b_l
  * at every level) and minimises the added bytes. d_out: device array of

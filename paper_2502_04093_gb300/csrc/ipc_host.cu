@@ -1639,8 +1639,9 @@ int ipc_retrieve_ex(ipc_field* f, ipc_target target, void* d_out, void* stream, 
                     ipc_view** out) {
   g_err.clear();
   if (!f || f->tag != kFieldTag || !d_out) return fail(IPC_EINVAL, "null or invalid argument");
-  if (refine_mode != IPC_REFINE_CANONICAL && refine_mode != IPC_REFINE_INCREMENTAL)
+  if (refine_mode < IPC_REFINE_CANONICAL || refine_mode > IPC_REFINE_AUTO)
     return fail(IPC_EINVAL, "unknown refine mode");
+  refine_mode = ipc_internal_refine_mode(f, refine_mode);
   DeviceGuard dg(f->device);
   std::vector<int> b;
   uint64_t bytes = 0;
@@ -1880,8 +1881,9 @@ int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream) {
 int ipc_view_set_refine_mode(ipc_view* v, int refine_mode) {
   g_err.clear();
   if (!v || v->tag != kViewTag) return fail(IPC_EINVAL, "null or invalid view");
-  if (refine_mode != IPC_REFINE_CANONICAL && refine_mode != IPC_REFINE_INCREMENTAL)
+  if (refine_mode < IPC_REFINE_CANONICAL || refine_mode > IPC_REFINE_AUTO)
     return fail(IPC_EINVAL, "unknown refine mode");
+  refine_mode = ipc_internal_refine_mode(v->f, refine_mode);
   if (refine_mode != v->mode) v->state_valid = false;
   v->mode = refine_mode;
   return IPC_OK;
@@ -2336,6 +2338,11 @@ int ipc_field_resident(const ipc_field* f, int* b_per_level, int* nlevels) {
 }  // extern "C"
 
 // ---- hooks of the serving loop (ipc_serve.cu) ---------------------------------
+int ipc_internal_refine_mode(const ipc_field* f, int mode) {
+  if (mode != IPC_REFINE_AUTO) return mode;
+  return f->dtype == IPC_F64 ? IPC_REFINE_INCREMENTAL : IPC_REFINE_CANONICAL;
+}
+
 int ipc_internal_select(ipc_field* f, ipc_target tg, const std::vector<int>* upper,
                         std::vector<int>* b, uint64_t* bytes, double* bound, uint64_t* rparts) {
   return select(f, tg, upper, b, bytes, bound, rparts);

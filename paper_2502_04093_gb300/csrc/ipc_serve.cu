@@ -119,12 +119,17 @@ void complete(ipc_server* s, const Pending& p, int status, uint64_t view, const 
   s->cv_out.notify_all();
 }
 
-// Harvests finished batches.
+// Harvests finished batches, each as soon as it is done (batches on
+// different streams finish out of launch order: a small batch behind a large
+// one on another stream completes first).
 void reap(ipc_server* s) {
-  while (!s->flights.empty()) {
-    Flight& fl = s->flights.front();
+  for (auto fit = s->flights.begin(); fit != s->flights.end();) {
+    Flight& fl = *fit;
     const cudaError_t q = cudaEventQuery(fl.done);
-    if (q == cudaErrorNotReady) break;
+    if (q == cudaErrorNotReady) {
+      ++fit;
+      continue;
+    }
     const Clock::time_point now = Clock::now();
     for (size_t i = 0; i < fl.reqs.size(); ++i) {
       auto it = s->views.find(fl.views[i]);
@@ -152,8 +157,22 @@ void reap(ipc_server* s) {
     }
     for (void* t : fl.tabs) cudaFreeAsync(t, s->streams[fl.stream]);
     cudaEventDestroy(fl.done);
-    s->flights.pop_front();
+    fit = s->flights.erase(fit);
   }
+}
+
+// The stream of the next batch: one with no batch in flight, the round-robin
+// one first (a batch queued behind another on the same stream would wait
+// for it); the round-robin one when every stream is busy.
+int pick_stream(const ipc_server* s) {
+  const int n = (int)s->streams.size();
+  for (int k = 0; k < n; ++k) {
+    const int c = (s->next_stream + k) % n;
+    bool busy = false;
+    for (const Flight& fl : s->flights) busy |= fl.stream == c;
+    if (!busy) return c;
+  }
+  return s->next_stream;
 }
 
 // Admits pending requests (arrival order) and launches one batch.
@@ -171,6 +190,7 @@ void admit_and_launch(ipc_server* s) {
   uint64_t values = 0;  // output elements of the batch so far
   const uint64_t maxv = s->cfg.max_batch_values;
   std::vector<uint64_t> touched;
+  const int sidx = pick_stream(s);  // output buffers are allocated on the batch's stream
   size_t free_hbm = 0, total_hbm = 0;
   cudaMemGetInfo(&free_hbm, &total_hbm);
   while (!s->pending.empty()) {
@@ -294,7 +314,7 @@ void admit_and_launch(ipc_server* s) {
       continue;
     }
     ipc_view* hv = nullptr;
-    if (s->cfg.refine_mode == IPC_REFINE_INCREMENTAL) {
+    if (ipc_internal_refine_mode(r.field, s->cfg.refine_mode) == IPC_REFINE_INCREMENTAL) {
       hv = ipc_internal_view_make(r.field, nb, nbytes, nbound, rparts[0], IPC_REFINE_INCREMENTAL);
       if (!hv) {
         complete(s, p, IPC_ENOMEM, 0, nullptr, now, now);
@@ -302,7 +322,6 @@ void admit_and_launch(ipc_server* s) {
       }
     }
     void* out = nullptr;
-    const int sidx = s->next_stream;
     if (cudaMallocAsync(&out, need, s->streams[sidx]) != cudaSuccess) {
       cudaGetLastError();
       if (hv) ipc_free(hv);
@@ -332,8 +351,7 @@ void admit_and_launch(ipc_server* s) {
   }
   s->pending = std::move(keep);
   if (take.empty()) return;
-  const int sidx = s->next_stream;
-  s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
+  s->next_stream = (sidx + 1) % (int)s->streams.size();
   cudaStream_t st = s->streams[sidx];
   Flight fl;
   fl.stream = sidx;
@@ -425,7 +443,7 @@ extern "C" {
 
 int ipc_server_create(const ipc_server_cfg* cfg, ipc_server** out) {
   if (!cfg || !out || cfg->nstreams < 1 || cfg->nstreams > 16 || cfg->max_inflight < 1 ||
-      (cfg->refine_mode != IPC_REFINE_CANONICAL && cfg->refine_mode != IPC_REFINE_INCREMENTAL))
+      cfg->refine_mode < IPC_REFINE_CANONICAL || cfg->refine_mode > IPC_REFINE_AUTO)
     return IPC_EINVAL;
   ipc_server* s = new (std::nothrow) ipc_server();
   if (!s) return IPC_ENOMEM;

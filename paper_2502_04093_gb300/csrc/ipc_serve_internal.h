@@ -19,6 +19,9 @@ ipc_view* ipc_internal_view_make(ipc_field* f, const std::vector<int>& b, uint64
 // The selection of a host view.
 void ipc_internal_view_selection(const ipc_view* v, std::vector<int>* b, uint64_t* bytes,
                                  double* bound);
+// The refinement form a view of f takes for `mode` (IPC_REFINE_AUTO
+// resolved by the element type).
+int ipc_internal_refine_mode(const ipc_field* f, int mode);
 // Element count and dtype of a field.
 void ipc_internal_field_shape(const ipc_field* f, uint64_t* n, int* dtype);
 // One reconstruction per field with the single-field kernels.

@@ -26,7 +26,7 @@ IPC_LINEAR, IPC_CUBIC, IPC_CUBIC_QUAD = 0, 1, 2
 IPC_EB_ABS, IPC_EB_REL = 0, 1
 IPC_BOUND_STRICT, IPC_BOUND_PAPER = 0, 1
 IPC_TARGET_EB, IPC_TARGET_BITRATE = 0, 1
-IPC_REFINE_CANONICAL, IPC_REFINE_INCREMENTAL = 0, 1
+IPC_REFINE_CANONICAL, IPC_REFINE_INCREMENTAL, IPC_REFINE_AUTO = 0, 1, 2
 IPC_KERNEL_RETRIEVE_LEVEL, IPC_KERNEL_INCREMENT_LEVEL = 2, 6
 
 

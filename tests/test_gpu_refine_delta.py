@@ -114,6 +114,28 @@ def test_quadratic_boundaries_eb_chain():
     assert run_chain(x, 1e-10, oracle.REL, chain, oracle.CUBIC_QUAD) >= 4
 
 
+def test_auto_mode_follows_element_type():
+    """IPC_REFINE_AUTO: an f64 view refines incrementally (as the oracle's
+    increment), an f32 view reconstructs (as a fresh retrieval)."""
+    for dtype, eb, incremental in ((np.float64, 1e-10, True), (np.float32, 1e-6, False)):
+        x = synth.random_field((40, 33, 70), seed=5, dtype=dtype, kind="smooth")
+        of = oracle.compress(x, eb, oracle.REL)
+        g = ipc.Field.compress(torch.from_numpy(x).cuda(), eb, ipc.IPC_EB_REL)
+        yo, vo = of.retrieve(EB, 1e-2)
+        yg, vg = g.retrieve(EB, 1e-2, refine_mode=ipc.IPC_REFINE_AUTO)
+        for E in (1e-3, 1e-4):
+            if incremental:
+                vo.refine_delta(EB, E)
+            else:
+                yo = vo.refine(EB, E)
+            vg.refine(EB, E)
+            torch.cuda.synchronize()
+            assert vg.selection() == vo.selection()
+            inc, _ = vg.refine_info()
+            assert bool(inc) == incremental
+            assert np.array_equal(yg.cpu().numpy().view(np.uint8), yo.view(np.uint8))
+
+
 def test_mixed_targets_and_fallback():
     # f32, tight eb: the first refinements change coarse levels, whose
     # increment's rounding margin misses the target (reconstruction), the
