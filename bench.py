@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="tune the reconstruction's launch shapes before the warm-up "
                          "(measured no faster than the defaults on this workload)")
+    ap.add_argument("--nvtx", action="store_true",
+                    help="NVTX ranges around the library's calls and level launches "
+                         "(for a profiler's range filters)")
     ap.add_argument("--serving-small", action="store_true",
                     help="serving with 40 fields up to 448^3 and 400 requests (quick)")
     return ap.parse_args()
@@ -246,6 +249,8 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    if args.nvtx:
+        ipc.ipc_nvtx_enable(True)
     edge = args.edge
     x = synth.grf_k53((edge, edge, edge), seed=SEED + rank, device=dev)
     out = torch.empty_like(x)

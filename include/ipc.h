@@ -430,6 +430,12 @@ enum {
 /* ipc_profile_enable -- when on, every later launch is bracketed by CUDA
  * events recorded on its stream. */
 int ipc_profile_enable(int on);
+/* ipc_nvtx_enable -- when on, the library pushes NVTX ranges (host
+ * timeline) around its calls ("ipc compress", "ipc retrieve", "ipc refine",
+ * "ipc compress batch", "ipc retrieve batch", "ipc import", ...) and around
+ * each level's launches inside them ("level <l>", "launch <j>" for a batch),
+ * so that a profiler can select one level's kernels. Off by default. */
+int ipc_nvtx_enable(int on);
 /* ipc_profile_read -- waits for the recorded events and returns, for one
  * kernel kind, the number of timed launches, their summed device time (ms)
  * and their summed algorithmic bytes (compress level: input values of its

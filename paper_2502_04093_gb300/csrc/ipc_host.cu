@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
 #include <atomic>
@@ -78,6 +80,30 @@ cudaEvent_t prof_event() {
   return e;
 }
 // Returns a handle for prof_end (or -1 when the profiler is off).
+// NVTX ranges (host timeline) around the library's calls and level launches,
+// while enabled (ipc_nvtx_enable): a profiler can then select the kernels of
+// one level (`ncu --nvtx --nvtx-include "ipc retrieve/level 1/"`). The header-only
+// NVTX costs a relaxed load per range when no tool is attached.
+std::atomic<bool> g_nvtx{false};
+struct Nvtx {
+  bool on;
+  explicit Nvtx(const char* name) : on(g_nvtx.load(std::memory_order_relaxed)) {
+    if (on) nvtxRangePushA(name);
+  }
+  Nvtx(const char* fmt, int a) : on(g_nvtx.load(std::memory_order_relaxed)) {
+    if (on) {
+      char b[48];
+      std::snprintf(b, sizeof b, fmt, a);
+      nvtxRangePushA(b);
+    }
+  }
+  ~Nvtx() {
+    if (on) nvtxRangePop();
+  }
+  Nvtx(const Nvtx&) = delete;
+  Nvtx& operator=(const Nvtx&) = delete;
+};
+
 long prof_begin(int kind, cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -851,6 +877,7 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     CU(cudaMemsetAsync(ws.nnz, 0, 32 * so[nf] * 4, st));
     CU(cudaMemsetAsync(ocount, 0, 8, st));
     for (int l = Kmax; l >= 1; --l) {
+      Nvtx nv("level %d", l);
       const int n_l = (int)((l > 1 ? lev_off[l - 1] : ents.size()) - lev_off[l]);
       const long ph = prof_begin(IPC_KERNEL_COMPRESS_LEVEL, st);
       if (n_l == 1) {  // one field: arguments in the parameter space
@@ -1138,6 +1165,7 @@ int reconstruct(ipc_field* f, const std::vector<int>& b, void* d_out, cudaStream
   }
   const double twoeb = bin_width(f);
   for (int l = ltop; l >= 1; --l) {
+    Nvtx nv("level %d", l);
     LevelArgs L = level_args(f, l);
     retrieve_layout(&L, scr + off[l + 1]);
     retrieve_planes(f, l, b[l - 1], &L);
@@ -1213,6 +1241,7 @@ int reconstruct_increment(ipc_field* f, const std::vector<int>& bo, const std::v
   const double twoeb = bin_width(f);
   const double lim = f->dtype == 0 ? (double)FLT_MAX : DBL_MAX;
   for (int l = lc; l >= 1; --l) {
+    Nvtx nv("level %d", l);
     const int b0 = bo[l - 1], b1 = bn[l - 1];
     LevelArgs L = level_args(f, l);
     retrieve_layout(&L, scr + off[l + 1]);
@@ -1427,6 +1456,7 @@ int launch_retrieve_table(int dtype, const BatchTable& T, void* tab, cudaStream_
   }
   // the algorithmic bytes of the whole batch are reported with its last launch
   for (size_t j = 0; j < T.launches.size(); ++j) {
+    Nvtx nv("launch %d", (int)j);
     const BatchTable::Launch& ln = T.launches[j];
     const long ph = profile ? prof_begin(IPC_KERNEL_RETRIEVE_LEVEL, st) : -1;
     CU(launch_level_retrieve_batch(dtype, d_ents + ln.off, ln.n, ln.ctas, ln.w16, ln.ns, ln.psm,
@@ -1599,6 +1629,7 @@ const char* ipc_last_error(void) { return g_err.c_str(); }
 int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims, int eb_mode,
                  double eb, int interp, int bound, void* stream, ipc_field** out) {
   g_err.clear();
+  Nvtx nv_call("ipc compress");
   if (!d_in || !out) return fail(IPC_EINVAL, "null argument");
   if (dtype != IPC_F32 && dtype != IPC_F64) return fail(IPC_EINVAL, "dtype");
   if (interp < IPC_LINEAR || interp > IPC_CUBIC_QUAD) return fail(IPC_EINVAL, "interp");
@@ -1638,6 +1669,7 @@ int ipc_retrieve(ipc_field* f, ipc_target target, void* d_out, void* stream, ipc
 int ipc_retrieve_ex(ipc_field* f, ipc_target target, void* d_out, void* stream, int refine_mode,
                     ipc_view** out) {
   g_err.clear();
+  Nvtx nv_call("ipc retrieve");
   if (!f || f->tag != kFieldTag || !d_out) return fail(IPC_EINVAL, "null or invalid argument");
   if (refine_mode < IPC_REFINE_CANONICAL || refine_mode > IPC_REFINE_AUTO)
     return fail(IPC_EINVAL, "unknown refine mode");
@@ -1812,6 +1844,7 @@ int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* pe
 
 int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream) {
   g_err.clear();
+  Nvtx nv_call("ipc refine");
   if (!v || v->tag != kViewTag || !d_out) return fail(IPC_EINVAL, "null or invalid argument");
   ipc_field* f = v->f;
   DeviceGuard dg(f->device);
@@ -2222,6 +2255,7 @@ extern "C" {
 
 int ipc_import(const void* host_buf, uint64_t len, void* stream, ipc_field** out) {
   g_err.clear();
+  Nvtx nv_call("ipc import");
   if (!out || (!host_buf && len)) return fail(IPC_EINVAL, "null argument");
   if (len >= 4 && get32le((const uint8_t*)host_buf) == 0x5A435049u) {  // coded form: decode first
     uint64_t raw = 0;
@@ -2276,6 +2310,7 @@ int ipc_container_ranges(const void* head, uint64_t head_len, const int* b_new, 
 int ipc_import_partial(const void* parts, uint64_t len, const int* b_per_level, int nlevels,
                        void* stream, ipc_field** out) {
   g_err.clear();
+  Nvtx nv_call("ipc import partial");
   if (!out || !parts || !b_per_level) return fail(IPC_EINVAL, "null argument");
   return import_core((const uint8_t*)parts, len, b_per_level, nlevels, (cudaStream_t)stream, out);
 }
@@ -2283,6 +2318,7 @@ int ipc_import_partial(const void* parts, uint64_t len, const int* b_per_level, 
 int ipc_field_load_planes(ipc_field* f, const void* parts, uint64_t len, const int* b_new,
                           int nlevels, void* stream) {
   g_err.clear();
+  Nvtx nv_call("ipc load planes");
   if (!f || f->tag != kFieldTag || !b_new || (!parts && len)) return fail(IPC_EINVAL, "invalid argument");
   const int K = f->g.K;
   if (nlevels != K) return fail(IPC_EINVAL, "one entry per level");
@@ -2415,6 +2451,7 @@ extern "C" {
 
 int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, ipc_field** outs) {
   g_err.clear();
+  Nvtx nv_call("ipc compress batch");
   if (nfields < 0 || (nfields > 0 && (!items || !outs))) return fail(IPC_EINVAL, "null argument");
   std::vector<ipc_field*> all(nfields, nullptr);
   auto cleanup = [&](int rc) {
@@ -2505,6 +2542,7 @@ int batch_select(int n, ipc_field* const* fields, const ipc_target* targets, voi
 int ipc_retrieve_batch(int n, ipc_field* const* fields, const ipc_target* targets,
                        void* const* d_outs, void* stream, ipc_view** outs) {
   g_err.clear();
+  Nvtx nv_call("ipc retrieve batch");
   std::vector<std::vector<int>> bs;
   std::vector<uint64_t> bytes;
   std::vector<double> bounds;
@@ -2605,6 +2643,11 @@ int ipc_plan_launch(ipc_plan* p, void* stream) {
   if (!p || p->tag != kPlanTag) return fail(IPC_EINVAL, "invalid plan");
   CU(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
   g_launches.fetch_add(p->launches, std::memory_order_relaxed);
+  return IPC_OK;
+}
+
+int ipc_nvtx_enable(int on) {
+  g_nvtx.store(on != 0, std::memory_order_relaxed);
   return IPC_OK;
 }
 

@@ -101,6 +101,7 @@ def lib() -> C.CDLL:
     L.ipc_compressed_size.argtypes = [vp, u64p]
     L.ipc_export.argtypes = [vp, vp, u64p]
     L.ipc_import.argtypes = [vp, C.c_uint64, vp, C.POINTER(vp)]
+    L.ipc_nvtx_enable.argtypes = [C.c_int]
     L.ipc_encode_container.argtypes = [C.c_char_p, C.c_uint64, C.c_int, vp, u64p, C.c_int]
     L.ipc_container_ranges.argtypes = [C.c_char_p, C.c_uint64, C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.c_int, u64p, C.POINTER(C.c_int)]
@@ -328,6 +329,11 @@ def ipc_field_resident(field):
     n = C.c_int()
     _check(lib().ipc_field_resident(h, b, C.byref(n)), "ipc_field_resident")
     return list(b)[:n.value]
+
+
+def ipc_nvtx_enable(on: bool = True) -> None:
+    """NVTX ranges around the library's calls and level launches."""
+    _check(lib().ipc_nvtx_enable(1 if on else 0), "ipc_nvtx_enable")
 
 
 def ipc_encode_container(raw: bytes, block_log2: int = 0, nthreads: int = 0) -> bytes:
