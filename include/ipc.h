@@ -436,6 +436,16 @@ int ipc_profile_enable(int on);
  * each level's launches inside them ("level <l>", "launch <j>" for a batch),
  * so that a profiler can select one level's kernels. Off by default. */
 int ipc_nvtx_enable(int on);
+/* ipc_debug_bounds -- in the bounds-checking build (compiled with
+ * -DIPC_DEBUG_BOUNDS, libipcomp_bounds.so), every global access of the level
+ * kernels (plane words, bitmaps, known points, outputs, the input, the
+ * written streams) is tested against its array's extent; an access outside
+ * it is skipped and the first one recorded. rec[4] receives (count, site,
+ * index, limit) after a device synchronisation; reset clears the record.
+ * Sites: 1 staged plane words, 2 staged bitmaps, 3 plane word, 4 known
+ * point, 5 output, 6 input, 7 written plane word, 8 written bitmap, 9 level
+ * values of a compression. The regular build returns IPC_EINVAL. */
+int ipc_debug_bounds(uint64_t* rec, int reset);
 /* ipc_profile_read -- waits for the recorded events and returns, for one
  * kernel kind, the number of timed launches, their summed device time (ms)
  * and their summed algorithmic bytes (compress level: input values of its

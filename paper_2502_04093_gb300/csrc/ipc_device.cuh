@@ -12,6 +12,31 @@ namespace dev {
 // Element-type arithmetic (round-to-nearest, no contraction).
 // ---------------------------------------------------------------------------
 template <class T> struct FP;
+// Bounds-checking build (-DIPC_DEBUG_BOUNDS): IPC_IN(L, i, n, site) is
+// false, and records the first such access (site, index, limit), when the
+// index i of a global access lies outside [0, n); the access is then
+// skipped. The regular build compiles every check to `true`.
+#ifdef IPC_DEBUG_BOUNDS
+__device__ __forceinline__ bool bounds_ok(unsigned long long* rec, uint64_t i, uint64_t n,
+                                          int site) {
+  if (i < n) return true;
+  if (atomicAdd(rec, 1ull) == 0ull) {
+    rec[1] = (unsigned long long)site;
+    rec[2] = i;
+    rec[3] = n;
+  }
+  return false;
+}
+#define IPC_IN(L, i, n, site) \
+  (::ipc::dev::bounds_ok((L).bounds, (uint64_t)(i), (uint64_t)(n), (site)))
+#else
+#define IPC_IN(L, i, n, site) true
+#endif
+enum BoundsSite {
+  kSiteStageCap = 1, kSiteStageBm = 2, kSitePlaneWord = 3, kSiteKnown = 4, kSiteOut = 5,
+  kSiteX = 6, kSiteCapStore = 7, kSiteBmStore = 8, kSiteXh = 9
+};
+
 // Exact double of an integer |q| < 2^53 built in integer arithmetic: GB300
 // runs FP64 instructions (conversions included) at about 1/70 of its FP32
 // rate, so the f64 kernels keep them for the operations that round.

@@ -379,6 +379,21 @@ std::vector<uint8_t> header_bytes(const ipc_field* f) {
 
 SelInput sel_input(const ipc_field* f);
 
+#ifdef IPC_DEBUG_BOUNDS
+// Bounds-checking build: the device record of the first out-of-bounds
+// access, one per device ([0] count, [1] site, [2] index, [3] limit).
+std::mutex g_bounds_mu;
+unsigned long long* g_bounds_rec[64] = {};
+unsigned long long* bounds_record() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_bounds_mu);
+  if (!g_bounds_rec[dev] && cudaMalloc((void**)&g_bounds_rec[dev], 32) == cudaSuccess)
+    cudaMemset(g_bounds_rec[dev], 0, 32);
+  return g_bounds_rec[dev];
+}
+#endif
+
 uint32_t get32le(const uint8_t* p) {
   return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
 }
@@ -548,6 +563,12 @@ LevelArgs level_args(const ipc_field* f, int l) {
       S.out_end = f->out_off[t + 1];
     }
   }
+#ifdef IPC_DEBUG_BOUNDS
+  L.lim_cap = f->cap_words;
+  L.lim_bm = f->bm_words;
+  L.lim_x = (uint64_t)g.N[0] * g.N[1] * g.N[2];
+  L.bounds = bounds_record();
+#endif
   return L;
 }
 
@@ -701,6 +722,10 @@ void retrieve_layout(LevelArgs* L, const void* kin) {
   L->kin = kin;
   L->kst1 = ((L->M[2] - 1) >> 1) + 1;
   L->kst0 = (((L->M[1] - 1) >> 1) + 1) * L->kst1;
+#ifdef IPC_DEBUG_BOUNDS
+  L->lim_kin = (uint64_t)(((L->M[0] - 1) >> 1) + 1) * L->kst0;
+  L->lim_out = (uint64_t)L->M[0] * L->M[1] * L->M[2];
+#endif
 }
 
 // Level l's layout in a compression: x is read in its natural layout, the
@@ -712,6 +737,10 @@ void compress_layout(LevelArgs* L, const void* kin) {
   L->kst0 = (((L->M[1] - 1) >> 1) + 1) * L->kst1;
   L->ost1 = L->M[2];
   L->ost0 = L->M[1] * L->M[2];
+#ifdef IPC_DEBUG_BOUNDS
+  L->lim_kin = (uint64_t)(((L->M[0] - 1) >> 1) + 1) * L->kst0;
+  L->lim_out = (uint64_t)L->M[0] * L->M[1] * L->M[2];
+#endif
 }
 
 int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>& ins,
@@ -2644,6 +2673,24 @@ int ipc_plan_launch(ipc_plan* p, void* stream) {
   CU(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
   g_launches.fetch_add(p->launches, std::memory_order_relaxed);
   return IPC_OK;
+}
+
+int ipc_debug_bounds(uint64_t* rec, int reset) {
+#ifdef IPC_DEBUG_BOUNDS
+  if (!rec) return fail(IPC_EINVAL, "null argument");
+  unsigned long long* d = bounds_record();
+  if (!d) return fail(IPC_ENOMEM, "bounds record");
+  CU(cudaDeviceSynchronize());
+  unsigned long long h[4];
+  CU(cudaMemcpy(h, d, 32, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) rec[i] = h[i];
+  if (reset) CU(cudaMemset(d, 0, 32));
+  return IPC_OK;
+#else
+  (void)rec;
+  (void)reset;
+  return fail(IPC_EINVAL, "not a bounds-checking build");
+#endif
 }
 
 int ipc_nvtx_enable(int on) {

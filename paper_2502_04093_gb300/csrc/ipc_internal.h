@@ -83,8 +83,15 @@ struct LevelArgs {
   // compression: plane and row strides of the level's own dense lattice
   // (its reconstructed values, the next finer level's known points)
   int64_t ost0, ost1;
-  StagePlanes sp[3];  // reconstruction only
+  StagePlanes sp[3];  // plane offsets (both); the planes to load and the state (reconstruction)
   int bo;             // incremental reconstruction: planes >= bo are loaded already
+#ifdef IPC_DEBUG_BOUNDS
+  // Bounds-checking build: the extents (elements / words) the level's
+  // accesses must stay within, and the device record of the first access
+  // outside them ([0] count, [1] site, [2] index, [3] limit).
+  uint64_t lim_cap, lim_bm, lim_kin, lim_out, lim_x;
+  unsigned long long* bounds;
+#endif
 };
 
 // The coarse levels K .. Lc of a reconstruction in one CTA (ipc_coarse.cu):

@@ -509,9 +509,16 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const uint64_t pi = sx == 0 ? (uint64_t)((Ps - 1) >> 1) : (uint64_t)Ps;
     const uint64_t g = seg_id(S, pi, (uint64_t)rbs, (uint64_t)cts);
     const StagePlanes& SQ = L.sp[sx];
-    SP[s][sl][i] = cap + SQ.cap0 + (uint64_t)k * SQ.pcap + g * (uint64_t)S.RB * S.CW;
-    const uint32_t* bp = bm + SQ.bm0 + (uint64_t)k * SQ.pbm + g * S.bw;
-    for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[s][sl][i][v], bp + v);
+    const uint64_t cofs = SQ.cap0 + (uint64_t)k * SQ.pcap + g * (uint64_t)S.RB * S.CW;
+    const uint64_t bofs = SQ.bm0 + (uint64_t)k * SQ.pbm + g * S.bw;
+    SP[s][sl][i] = cap + cofs;
+    const uint32_t* bp = bm + bofs;
+    if (IPC_IN(L, cofs + (uint64_t)S.RB * S.CW - 1, L.lim_cap, kSiteStageCap) &&
+        IPC_IN(L, bofs + S.bw - 1, L.lim_bm, kSiteStageBm)) {
+      for (int v = 0; v < (int)S.bw; ++v) cp_async4(&SB[s][sl][i][v], bp + v);
+    } else {
+      for (int v = 0; v < (int)S.bw; ++v) SB[s][sl][i][v] = 0u;  // (checked build) nothing read
+    }
   }
 
   // Phase 1a: even value rows -- the sweep-0 predictions of an odd plane
@@ -541,12 +548,20 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
     const bool r3 = interp != 0 && c.P - 3 >= 0 && c.P + 3 <= M0 - 1;
     const bool ra = Q && interp == 2 ? r1 && c.P - 3 >= 0 : r3;
     const bool rd = Q && interp == 2 ? c.P + 3 <= M0 - 1 : r3;
+    // known-point loads (the checked build tests each against the lattice)
+    auto kload = [&](const T* q) -> T {
+      return IPC_IN(L, q - kin, L.lim_kin, kSiteKnown) ? __ldg(q) : (T)0;
+    };
+    auto kload2 = [&](const T* q) -> V2 {
+      return IPC_IN(L, q + 1 - kin, L.lim_kin, kSiteKnown) ? __ldg(reinterpret_cast<const V2*>(q))
+                                                           : V2{};
+    };
     auto one = [&](const T* p) -> T {
-      if (!podd) return __ldg(p);
-      const T bb = __ldg(p);
-      const T cc = r1 ? __ldg(p + k0) : bb;
-      const T a = ra ? __ldg(p - k0) : bb;
-      const T d = rd ? __ldg(p + 2 * k0) : bb;
+      if (!podd) return kload(p);
+      const T bb = kload(p);
+      const T cc = r1 ? kload(p + k0) : bb;
+      const T a = ra ? kload(p - k0) : bb;
+      const T d = rd ? kload(p + 2 * k0) : bb;
       return pred4<T, Q>(a, bb, cc, d, c.P, M0, interp);
     };
     const T* kplane = kin + (int64_t)(c.P >> 1) * k0;
@@ -567,14 +582,13 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
         const T* p = colp + (int64_t)(c1 >> 1) * k1;
         V2 v2;
         if (vec) {
-          const V2* p2 = reinterpret_cast<const V2*>(p);
           if (!podd) {
-            v2 = __ldg(p2);
+            v2 = kload2(p);
           } else {
-            const V2 bb = __ldg(p2);
-            const V2 cc = r1 ? __ldg(reinterpret_cast<const V2*>(p + k0)) : bb;
-            const V2 a = ra ? __ldg(reinterpret_cast<const V2*>(p - k0)) : bb;
-            const V2 d = rd ? __ldg(reinterpret_cast<const V2*>(p + 2 * k0)) : bb;
+            const V2 bb = kload2(p);
+            const V2 cc = r1 ? kload2(p + k0) : bb;
+            const V2 a = ra ? kload2(p - k0) : bb;
+            const V2 d = rd ? kload2(p + 2 * k0) : bb;
             v2.x = pred4<T, Q>(a.x, bb.x, cc.x, d.x, c.P, M0, interp);
             v2.y = pred4<T, Q>(a.y, bb.y, cc.y, d.y, c.P, M0, interp);
           }
@@ -662,7 +676,9 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
       uint32_t w = 0u;
       if ((kmw >> i2) & 1u) {
         const uint32_t m = sb[i2 * BWS];
-        if (m & bit) w = __ldcs(sp[i2] + off + __popc(m & below));  // read once: evict-first
+        if ((m & bit) && IPC_IN(L, (uint64_t)(sp[i2] - cap) + off + __popc(m & below), L.lim_cap,
+                                 kSitePlaneWord))
+          w = __ldcs(sp[i2] + off + __popc(m & below));  // read once: evict-first
       }
       a[i2] = w;
       any |= w;
@@ -944,6 +960,9 @@ __device__ __forceinline__ void level_retrieve_body(const LevelArgs& L, T* out, 
             }
           }
         }
+        if (!IPC_IN(L, c.pbase + (int64_t)c1 * c.rs + (int64_t)(min(c.C1, c2e + 8) - 1) * L.s,
+                    L.lim_out, kSiteOut))
+          continue;
         if (MODE == kDelta && L.stream_out)
           add_run<T>(out + c.pbase + (int64_t)c1 * c.rs, c2e, c.C1, v);  // level 1: x^ += Delta
         else

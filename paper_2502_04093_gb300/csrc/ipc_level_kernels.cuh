@@ -101,6 +101,14 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
     qmx[st] = max(qmx[st], (uint32_t)(q < 0 ? -q : q));
   };
 
+  // x loads (the checked build tests each index against the field)
+  auto xld = [&](int64_t e) -> T { return IPC_IN(L, e, L.lim_x, kSiteX) ? __ldg(x + e) : (T)0; };
+  auto xld4 = [&](int64_t e) -> float4 {
+    return IPC_IN(L, e + 3, L.lim_x, kSiteX)
+               ? __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e))
+               : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+
   // codes outside the grid (edge tiles) must read as zero in phase 4
   if (c.R1 - c.R0 < BR || c.C1 - c.C0 < BC)
     for (int i = tid; i < (BR + G::H1 + BR / 2) * G::QP; i += 256) E2[i] = 0;
@@ -157,7 +165,7 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
       const T d = rd ? __ldg(p + 2 * k0) : bb;
       T v;
       point(pred4<T, Q>(a, bb, cc, d, c.P, M0, interp),
-            __ldg(x + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s), c1, c2, own, &v);
+            xld(c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s), c1, c2, own, &v);
       return v;
     };
     if (pa) {
@@ -186,12 +194,12 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
             const int64_t e = c.pbase + (int64_t)c1 * c.rs + (int64_t)c2p * L.s;
             T xa, xb;
             if (vec) {
-              const float4 xv = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e));
+              const float4 xv = xld4(e);
               xa = (T)xv.x;
               xb = (T)xv.z;
             } else {
-              xa = __ldg(x + e);
-              xb = __ldg(x + e + 2 * L.s);
+              xa = xld(e);
+              xb = xld(e + 2 * L.s);
             }
             point(pred4<T, Q>(a.x, bb.x, cc.x, d.x, c.P, M0, interp), xa, c1, c2p, ownr, &va);
             point(pred4<T, Q>(a.y, bb.y, cc.y, d.y, c.P, M0, interp), xb, c1, c2p + 2, ownr, &vb);
@@ -250,12 +258,12 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
         const int64_t e = c.pbase + (int64_t)c1 * c.rs + (int64_t)c2p * L.s;
         T xa, xb;
         if (vec) {
-          const float4 xv = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e));
+          const float4 xv = xld4(e);
           xa = (T)xv.x;
           xb = (T)xv.z;
         } else {
-          xa = __ldg(x + e);
-          xb = pb ? __ldg(x + e + 2 * L.s) : xa;
+          xa = xld(e);
+          xb = pb ? xld(e + 2 * L.s) : xa;
         }
         V2 v;
         v.x = point(a.x, bb.x, cc.x, d.x, c1, c2p, true, xa);
@@ -275,7 +283,7 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
         VE[G::odd_row(jr) + G::V0 + js] =
             point(col[G::even_row(jr)], col[G::even_row(jr + 1)], col[G::even_row(jr + 2)],
                   col[G::even_row(jr + 3)], c1, c2, false,
-                  __ldg(x + c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s));
+                  xld(c.pbase + (int64_t)c1 * c.rs + (int64_t)c2 * L.s));
       }
     }
   }
@@ -301,8 +309,7 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
         const int64_t e = c.pbase + (int64_t)c1 * c.rs;
         T xo[4];
         if (vec8) {
-          const float4* xp = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(x) + e + c2e);
-          const float4 u = __ldg(xp), v = __ldg(xp + 1);
+          const float4 u = xld4(e + c2e), v = xld4(e + c2e + 4);
           xo[0] = (T)u.y;
           xo[1] = (T)u.w;
           xo[2] = (T)v.y;
@@ -311,7 +318,7 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int c2o = c2e + 2 * k + 1;
-            xo[k] = c2o < c.C1 ? __ldg(x + e + (int64_t)c2o * L.s) : (T)0;
+            xo[k] = c2o < c.C1 ? xld(e + (int64_t)c2o * L.s) : (T)0;
           }
         }
         T v[8];
@@ -342,7 +349,9 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
           }
         }
         *reinterpret_cast<uint4*>(E2 + lr * G::QP + qoff<false>(4 * g)) = make_uint4(n[0], n[1], n[2], n[3]);
-        if (write_xh) store_run<T>(xh + (int64_t)c.P * L.ost0 + (int64_t)c1 * L.ost1, 1, 0, c2e, c.C1, v);
+        if (write_xh && IPC_IN(L, (int64_t)c.P * L.ost0 + (int64_t)c1 * L.ost1 + min(c.C1, c2e + 8) - 1,
+                               L.lim_out, kSiteXh))
+          store_run<T>(xh + (int64_t)c.P * L.ost0 + (int64_t)c1 * L.ost1, 1, 0, c2e, c.C1, v);
       }
     }
   }
@@ -423,10 +432,13 @@ __device__ __forceinline__ void level_compress_body(const LevelArgs& L, const T*
     if (k > ktop) break;
     const uint32_t mk = __ballot_sync(~0u, cd[k] != 0u);
     if (lane == k) mybm = mk;
-    if (wact && cd[k]) o.cap[SP.cap0 + (uint64_t)k * SP.pcap + capg + __popc(mk & lt)] = cd[k];
+    if (wact && cd[k] &&
+        IPC_IN(L, SP.cap0 + (uint64_t)k * SP.pcap + capg + __popc(mk & lt), L.lim_cap, kSiteCapStore))
+      o.cap[SP.cap0 + (uint64_t)k * SP.pcap + capg + __popc(mk & lt)] = cd[k];
   }
   if (wact) {
-    o.bm[SP.bm0 + (uint64_t)lane * SP.pbm + gseg * S.bw + wl] = mybm;
+    if (IPC_IN(L, SP.bm0 + (uint64_t)lane * SP.pbm + gseg * S.bw + wl, L.lim_bm, kSiteBmStore))
+      o.bm[SP.bm0 + (uint64_t)lane * SP.pbm + gseg * S.bw + wl] = mybm;
     if (mybm) atomicAdd(&scnt[sidx][lane], (uint32_t)__popc(mybm));
   }
   __syncthreads();

@@ -18,6 +18,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libipcomp.so")
+# IPC_BOUNDS_CHECK=1 loads the bounds-checking build instead (device-side
+# index checks on the level kernels' global accesses; see ipc_debug_bounds)
+BOUNDS_LIB_PATH = os.path.join(HERE, "libipcomp_bounds.so")
 
 IPC_OK, IPC_EINVAL, IPC_EBOUND, IPC_EBUDGET = 0, -1, -2, -3
 IPC_ENOMEM, IPC_ECORRUPT, IPC_ECUDA, IPC_ETIMEOUT, IPC_EBUSY = -4, -5, -6, -7, -8
@@ -78,9 +81,11 @@ def lib() -> C.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise LibraryMissing("libipcomp.so is not built: run paper_2502_04093_gb300.build.build()")
-    L = C.CDLL(LIB_PATH)
+    path = BOUNDS_LIB_PATH if os.environ.get("IPC_BOUNDS_CHECK") == "1" else LIB_PATH
+    if not os.path.exists(path):
+        raise LibraryMissing("%s is not built: run paper_2502_04093_gb300.build.build(%s)" %
+                             (os.path.basename(path), "bounds=True" if path != LIB_PATH else ""))
+    L = C.CDLL(path)
     vp, u64p = C.c_void_p, C.POINTER(C.c_uint64)
     i64p = C.POINTER(C.c_int64)
     L.ipc_compress.argtypes = [vp, C.c_int, C.c_int, i64p, C.c_int, C.c_double, C.c_int,
@@ -102,6 +107,7 @@ def lib() -> C.CDLL:
     L.ipc_export.argtypes = [vp, vp, u64p]
     L.ipc_import.argtypes = [vp, C.c_uint64, vp, C.POINTER(vp)]
     L.ipc_nvtx_enable.argtypes = [C.c_int]
+    L.ipc_debug_bounds.argtypes = [u64p, C.c_int]
     L.ipc_encode_container.argtypes = [C.c_char_p, C.c_uint64, C.c_int, vp, u64p, C.c_int]
     L.ipc_container_ranges.argtypes = [C.c_char_p, C.c_uint64, C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.c_int, u64p, C.POINTER(C.c_int)]
@@ -329,6 +335,14 @@ def ipc_field_resident(field):
     n = C.c_int()
     _check(lib().ipc_field_resident(h, b, C.byref(n)), "ipc_field_resident")
     return list(b)[:n.value]
+
+
+def ipc_debug_bounds(reset: bool = False):
+    """Bounds-checking build only: (count, site, index, limit) of the first
+    out-of-bounds global access of the level kernels since the last reset."""
+    r = (C.c_uint64 * 4)()
+    _check(lib().ipc_debug_bounds(r, 1 if reset else 0), "ipc_debug_bounds")
+    return tuple(r)
 
 
 def ipc_nvtx_enable(on: bool = True) -> None:
