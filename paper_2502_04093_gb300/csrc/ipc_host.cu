@@ -8,10 +8,14 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <unistd.h>
+
 #include <array>
 #include <atomic>
 #include <cfloat>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -1342,6 +1346,133 @@ struct BatchTable {
   double alg_bytes = 0;
 };
 
+// Persistent host worker threads for the per-field work of large batches
+// (selection, launch-table preparation): run(n, fn) calls fn(i) for every i
+// in [0, n) on the calling thread and the workers that join in, and returns
+// when all calls have finished. One job at a time; the caller claims indices
+// too, so a job completes even if no worker ever wakes (after a fork, say).
+class HostPool {
+ public:
+  static HostPool& get() {
+    static std::mutex mu;
+    static HostPool* p = nullptr;
+    static pid_t owner = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!p || owner != getpid()) {  // a forked child starts a pool of its own
+      p = new HostPool();           // never freed: its workers outlive main
+      owner = getpid();
+    }
+    return *p;
+  }
+  void run(int n, const std::function<void(int)>& fn) {
+    std::lock_guard<std::mutex> one(job_mu_);
+    start_workers();
+    std::atomic<int> next{0};
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      n_ = n;
+      next_ = &next;
+      ++gen_;
+    }
+    cv_.notify_all();
+    claim(fn, n, next);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return active_ == 0; });
+    fn_ = nullptr;  // a worker that wakes late finds no job
+    next_ = nullptr;
+  }
+
+ private:
+  static void claim(const std::function<void(int)>& fn, int n, std::atomic<int>& next) {
+    for (int i; (i = next.fetch_add(1, std::memory_order_relaxed)) < n;) fn(i);
+  }
+  void start_workers() {
+    if (started_) return;
+    started_ = true;
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nw = (int)std::min<unsigned>(8, std::max(1u, hc / 2)) - 1;
+    for (int k = 0; k < nw; ++k) {
+      try {
+        std::thread([this] { loop(); }).detach();
+      } catch (...) {
+        break;  // fewer workers: the caller takes the rest
+      }
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return gen_ != seen && fn_; });
+      seen = gen_;
+      const std::function<void(int)>* fn = fn_;
+      std::atomic<int>* next = next_;
+      const int n = n_;
+      ++active_;
+      lk.unlock();
+      claim(*fn, n, *next);
+      lk.lock();
+      if (--active_ == 0) done_.notify_all();
+    }
+  }
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  std::atomic<int>* next_ = nullptr;
+  int n_ = 0, active_ = 0;
+  uint64_t gen_ = 0;
+  bool started_ = false;
+};
+
+// What a batched reconstruction needs of one field, independent of the
+// other fields: its scratch ladder, its coarse-level plan, and per level
+// it runs in the level kernels the kernel arguments (layout and planes;
+// the row tiling waits for the launch's sub-tile count) and the code width.
+struct FieldPrep {
+  uint64_t scratch = 0;
+  std::vector<uint64_t> off;  // ladder offsets per level
+  bool coarse = false;
+  CoarseArgs ca;
+  int ltop = 0;                  // the finest level the level kernels start at
+  std::vector<LevelArgs> las;    // index l - 1, levels 1..ltop
+  std::vector<uint8_t> w16;      // index l - 1
+  std::vector<double> lbytes;    // algorithmic bytes per level, index l - 1
+  double coarse_bytes = 0;
+};
+
+void prepare_field(const ipc_field* f, const std::vector<int>& b, FieldPrep* P) {
+  const Geo& g = f->g;
+  const size_t esz = f->dtype == 0 ? 4 : 8;
+  P->scratch = g.K > 0 ? ladder(g, esz, &P->off) : 0;
+  P->coarse = coarse_plan(f, b, nullptr, &P->ca);
+  P->ltop = P->coarse ? P->ca.Lc - 1 : g.K;
+  if (P->coarse)
+    for (int j = 0; j < P->ca.nst; ++j) {
+      const int t = g.level_stage[P->ca.st[j].dim][P->ca.st[j].level - 1];
+      P->coarse_bytes += (double)(g.stages[t].ncodes * esz);
+      for (int k = P->ca.st[j].b; k < 32; ++k) P->coarse_bytes += (double)f->st[t].size[k];
+    }
+  P->las.resize(P->ltop);
+  P->w16.resize(P->ltop);
+  P->lbytes.assign(P->ltop, 0.0);
+  for (int l = 1; l <= P->ltop; ++l) {
+    const int bl = b[l - 1];
+    LevelArgs& L = P->las[l - 1];
+    L = level_args(f, l);
+    retrieve_layout(&L, nullptr);
+    retrieve_planes(f, l, bl, &L);
+    L.stream_out = l == 1;
+    P->w16[l - 1] = level_w16(f, l, bl) ? 1 : 0;
+    for (int d = 0; d < 3; ++d) {
+      const int t = g.level_stage[d][l - 1];
+      if (t < 0) continue;
+      P->lbytes[l - 1] += (double)(g.stages[t].ncodes * esz);
+      for (int k = bl; k < 32; ++k) P->lbytes[l - 1] += (double)f->st[t].size[k];
+    }
+  }
+}
+
 void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<std::vector<int>>& bs,
                           const std::vector<void*>& outs, BatchTable* T) {
   const size_t nf = fs.size();
@@ -1361,41 +1492,40 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
   T->kin_off.reserve(fs.size() * (size_t)T->Kmax);
   T->out_off.reserve(fs.size() * (size_t)T->Kmax);
   T->coarse.reserve(fs.size());
+  // the fields' own preparation is independent: large batches spread it
+  // over the host pool
+  std::vector<FieldPrep> P(nf);
+  if (nf >= 8)
+    HostPool::get().run((int)nf, [&](int i) { prepare_field(fs[i], bs[i], &P[i]); });
+  else
+    for (size_t i = 0; i < nf; ++i) prepare_field(fs[i], bs[i], &P[i]);
   // each field's scratch ladder, one after the other
   std::vector<uint64_t> base(nf, 0);
-  std::vector<std::vector<uint64_t>> off(nf);
   T->scratch = 0;
   for (size_t i = 0; i < nf; ++i) {
-    const size_t esz = fs[i]->dtype == 0 ? 4 : 8;
     base[i] = T->scratch;
-    if (fs[i]->g.K > 0) T->scratch += ladder(fs[i]->g, esz, &off[i]);
+    T->scratch += P[i].scratch;
   }
-  std::vector<int> ltop(nf);  // per field the finest level the level kernels start at
   for (size_t i = 0; i < nf; ++i) {
     const int K = fs[i]->g.K;
-    CoarseArgs ca;
-    if (coarse_plan(fs[i], bs[i], nullptr, &ca)) {
-      ltop[i] = ca.Lc - 1;
+    if (P[i].coarse) {
+      const CoarseArgs& ca = P[i].ca;
       T->coarse.push_back(ca);
-      T->coarse_off.push_back(ca.Lc == 1 ? -1 : (int64_t)(base[i] + off[i][ca.Lc]));
+      T->coarse_off.push_back(ca.Lc == 1 ? -1 : (int64_t)(base[i] + P[i].off[ca.Lc]));
       if (ca.Lc == 1) T->coarse.back().out = outs[i];
       T->coarse_smem = std::max(T->coarse_smem, coarse_smem(ca));
-      const size_t esz = fs[i]->dtype == 0 ? 4 : 8;
-      for (int j = 0; j < ca.nst; ++j) {
-        const int t = fs[i]->g.level_stage[ca.st[j].dim][ca.st[j].level - 1];
-        T->alg_bytes += (double)(fs[i]->g.stages[t].ncodes * esz);
-        for (int k = ca.st[j].b; k < 32; ++k) T->alg_bytes += (double)fs[i]->st[t].size[k];
-      }
+      T->alg_bytes += P[i].coarse_bytes;
       continue;
     }
-    ltop[i] = K;
     T->anchors.push_back(AnchorEntry{outs[i], fs[i]->anchor});
-    T->anch_off.push_back(K > 0 ? (int64_t)(base[i] + off[i][K + 1]) : -1);
+    T->anch_off.push_back(K > 0 ? (int64_t)(base[i] + P[i].off[K + 1]) : -1);
   }
+  std::vector<size_t> group[2];  // a level's fields by code width (index: w16)
   for (int l = T->Kmax; l >= 1; --l) {
-    std::vector<size_t> group[2];  // the level's fields by code width (index: w16)
+    group[0].clear();
+    group[1].clear();
     for (size_t i = 0; i < nf; ++i)
-      if (l <= ltop[i]) group[level_w16(fs[i], l, bs[i][l - 1]) ? 1 : 0].push_back(i);
+      if (l <= P[i].ltop) group[P[i].w16[l - 1]].push_back(i);
     for (int w16 : {1, 0}) {
       if (group[w16].empty()) continue;
       BatchTable::Launch ln;
@@ -1408,11 +1538,8 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       bool same = true;
       ShapeKey key{};
       int seen = 0;
-      std::vector<LevelArgs> las;  // the entries' level arguments
-      las.reserve(group[w16].size());
       for (size_t i : group[w16]) {
-        las.push_back(level_args(fs[i], l));
-        const LevelArgs& La = las.back();
+        const LevelArgs& La = P[i].las[l - 1];
         ln.quad |= fs[i]->interp == IPC_CUBIC_QUAD;
         ns = std::min(ns, retrieve_subtiles(La.M[2], w16));
         const ShapeKey k = shape_key(fs[i]->dtype, w16, La);
@@ -1426,16 +1553,11 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
       }
       ln.ns = ns;
       uint64_t cta = 0;
-      size_t q = 0;
       for (size_t i : group[w16]) {
         ipc_field* f = fs[i];
-        const size_t esz = f->dtype == 0 ? 4 : 8;
         RetrieveEntry e{};
-        e.L = las[q++];
-        retrieve_layout(&e.L, nullptr);
-        retrieve_planes(f, l, bs[i][l - 1], &e.L);
+        e.L = P[i].las[l - 1];
         retrieve_tiling(&e.L, f->dtype, w16, ns);
-        e.L.stream_out = l == 1;
         e.out = outs[i];
         e.cap = f->d_cap;
         e.bm = f->d_bm;
@@ -1446,14 +1568,9 @@ void build_retrieve_table(const std::vector<ipc_field*>& fs, const std::vector<s
         e.cta_begin = cta;
         cta += retrieve_tiles(e.L, ns);
         T->ents.push_back(e);
-        T->kin_off.push_back((int64_t)(base[i] + off[i][l + 1]));
-        T->out_off.push_back(l == 1 ? -1 : (int64_t)(base[i] + off[i][l]));
-        for (int d = 0; d < 3; ++d) {
-          const int t = f->g.level_stage[d][l - 1];
-          if (t < 0) continue;
-          T->alg_bytes += (double)(f->g.stages[t].ncodes * esz);
-          for (int k = e.b; k < 32; ++k) T->alg_bytes += (double)f->st[t].size[k];
-        }
+        T->kin_off.push_back((int64_t)(base[i] + P[i].off[l + 1]));
+        T->out_off.push_back(l == 1 ? -1 : (int64_t)(base[i] + P[i].off[l]));
+        T->alg_bytes += P[i].lbytes[l - 1];
       }
       ln.ctas = cta;
       T->launches.push_back(ln);
@@ -2542,26 +2659,22 @@ int batch_select(int n, ipc_field* const* fields, const ipc_target* targets, voi
     if (!fields[i] || fields[i]->tag != kFieldTag || !d_outs[i])
       return fail(IPC_EINVAL, "invalid field or output");
   // the fields' selections are independent: large batches spread them over
-  // a few host threads (the first failure in field order is reported)
+  // the host pool (the first failure in field order is reported)
   std::vector<int> rcs(n, IPC_OK);
   std::vector<const char*> why(n, "");
-  auto work = [&](int i0, int step) {
-    for (int i = i0; i < n; i += step)
+  auto one = [&](int i) {
+    try {
       rcs[i] = select_planes(fields[i]->sel, targets[i].kind, targets[i].value, nullptr,
                              &(*bs)[i], &(*bytes)[i], &(*bounds)[i], &why[i]);
-  };
-  const unsigned hc = std::thread::hardware_concurrency();
-  const int nt = n >= 16 ? (int)std::min<unsigned>(8, std::max(1u, hc / 2)) : 1;
-  std::vector<std::thread> th;
-  for (int k = 1; k < nt; ++k) {
-    try {
-      th.emplace_back(work, k, nt);
-    } catch (...) {  // no thread: this one takes the stride
-      work(k, nt);
+    } catch (const std::bad_alloc&) {
+      rcs[i] = IPC_ENOMEM;
+      why[i] = "host allocation";
     }
-  }
-  work(0, nt);
-  for (auto& t : th) t.join();
+  };
+  if (n >= 16)
+    HostPool::get().run(n, one);
+  else
+    for (int i = 0; i < n; ++i) one(i);
   for (int i = 0; i < n; ++i)
     if (rcs[i]) return fail(rcs[i], why[i]);
   return IPC_OK;
