@@ -290,11 +290,13 @@ typedef struct {
 } ipc_batch_item;
 
 /* ipc_compress_batch -- compresses nfields fields of any shapes (Sec. 4.1-4.4
- * applied to each). Per element type: one range launch per field and one
- * host sync, then ONE kernel launch per interpolation level covering that
- * level's work of every field, and one sync for the statistics. The output
- * of field i is byte-identical to ipc_compress of that field alone.
+ * applied to each). Per element type: one range launch over every field and
+ * one host sync, then ONE kernel launch per interpolation level covering
+ * that level's work of every field, and one sync for the statistics. The
+ * output of field i is byte-identical to ipc_compress of that field alone.
  * outs: host array of nfields handles. On error nothing is returned.
+ * A batch of 8 or more fields keeps its fields' plane streams in one device
+ * allocation, released when the last of those handles is freed.
  * Synchronises `stream`. */
 int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream,
                        ipc_field** outs);

@@ -236,6 +236,12 @@ struct StageTab {
   uint64_t nnz[32], size[32];  // by plane
 };
 
+// One device allocation shared by several fields' plane streams.
+struct SharedStreams {
+  void* p;
+  std::atomic<int> refs;
+};
+
 struct ipc_field {
   uint32_t tag;
   int device;
@@ -248,6 +254,9 @@ struct ipc_field {
   // device: segmented plane streams, outliers
   uint32_t* d_cap;
   uint32_t* d_bm;
+  // the fields of a large compressed batch hold their streams in one
+  // allocation, freed with the last of them (null: d_cap is its own)
+  struct SharedStreams* shared = nullptr;
   uint64_t cap_words, bm_words;
   uint64_t* d_oidx;       // outliers: code indices, per stage contiguous
   double* d_oval;
@@ -291,6 +300,95 @@ struct ipc_plan {
 };
 
 namespace {
+
+// Persistent host worker threads for the per-field work of large batches
+// (selection, launch-table preparation): run(n, fn) calls fn(i) for every i
+// in [0, n) on the calling thread and the workers that join in, and returns
+// when all calls have finished. One job at a time; the caller claims indices
+// too, so a job completes even if no worker ever wakes (after a fork, say).
+class HostPool {
+ public:
+  static HostPool& get() {
+    static std::mutex mu;
+    static HostPool* p = nullptr;
+    static pid_t owner = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!p || owner != getpid()) {  // a forked child starts a pool of its own
+      p = new HostPool();           // never freed: its workers outlive main
+      owner = getpid();
+    }
+    return *p;
+  }
+  void run(int n, const std::function<void(int)>& fn) {
+    if (in_job()) {  // a job's own calls run serially (no nested jobs)
+      for (int i = 0; i < n; ++i) fn(i);
+      return;
+    }
+    std::lock_guard<std::mutex> one(job_mu_);
+    start_workers();
+    std::atomic<int> next{0};
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      n_ = n;
+      next_ = &next;
+      ++gen_;
+    }
+    cv_.notify_all();
+    claim(fn, n, next);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return active_ == 0; });
+    fn_ = nullptr;  // a worker that wakes late finds no job
+    next_ = nullptr;
+  }
+
+ private:
+  static bool& in_job() {
+    thread_local bool b = false;
+    return b;
+  }
+  static void claim(const std::function<void(int)>& fn, int n, std::atomic<int>& next) {
+    in_job() = true;
+    for (int i; (i = next.fetch_add(1, std::memory_order_relaxed)) < n;) fn(i);
+    in_job() = false;
+  }
+  void start_workers() {
+    if (started_) return;
+    started_ = true;
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nw = (int)std::min<unsigned>(8, std::max(1u, hc / 2)) - 1;
+    for (int k = 0; k < nw; ++k) {
+      try {
+        std::thread([this] { loop(); }).detach();
+      } catch (...) {
+        break;  // fewer workers: the caller takes the rest
+      }
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> lk(mu_);
+    for (;;) {
+      cv_.wait(lk, [&] { return gen_ != seen && fn_; });
+      seen = gen_;
+      const std::function<void(int)>* fn = fn_;
+      std::atomic<int>* next = next_;
+      const int n = n_;
+      ++active_;
+      lk.unlock();
+      claim(*fn, n, *next);
+      lk.lock();
+      if (--active_ == 0) done_.notify_all();
+    }
+  }
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* fn_ = nullptr;
+  std::atomic<int>* next_ = nullptr;
+  int n_ = 0, active_ = 0;
+  uint64_t gen_ = 0;
+  bool started_ = false;
+};
 
 // ---------------------------------------------------------------------------
 // Workspace: scratch of compression, one per device, grown on demand.
@@ -415,7 +513,15 @@ void dfree(void* p) {
 }
 
 void free_field_device(ipc_field* f) {
-  dfree(f->d_cap);  // the bitmaps share its allocation
+  if (f->shared) {  // the batch's allocation goes with its last field
+    if (f->shared->refs.fetch_sub(1) == 1) {
+      dfree(f->shared->p);
+      delete f->shared;
+    }
+    f->shared = nullptr;
+  } else {
+    dfree(f->d_cap);  // the bitmaps share its allocation
+  }
   dfree(f->d_oidx);  // the outlier values share its allocation
   f->d_cap = nullptr;
   f->d_bm = nullptr;
@@ -501,7 +607,7 @@ void keep_pool(int dev) {
 // stage and plane, nseg segments of RB*CW capacity words and bw bitmap words.
 // The planes of a stage follow one another at a fixed stride (the level
 // kernels address plane k from plane 0 and that stride).
-int plan_field(ipc_field* f, cudaStream_t st) {
+void stream_layout(ipc_field* f) {
   const Geo& g = f->g;
   f->desc.assign(g.stages.size(), StageDescs{});
   uint64_t cw = 0, bw = 0;
@@ -518,13 +624,45 @@ int plan_field(ipc_field* f, cudaStream_t st) {
   }
   f->cap_words = cw;
   f->bm_words = bw;
+}
+
+int plan_field(ipc_field* f, cudaStream_t st) {
+  stream_layout(f);
   // capacity arrays and bitmaps in one allocation (bitmaps behind)
-  const int rc = dalloc((void**)&f->d_cap, (cw + bw) * 4, st);
+  const int rc = dalloc((void**)&f->d_cap, (f->cap_words + f->bm_words) * 4, st);
   if (rc) {
     free_field_device(f);
     return rc;
   }
-  f->d_bm = f->d_cap + cw;
+  f->d_bm = f->d_cap + f->cap_words;
+  return IPC_OK;
+}
+
+// The streams of a batch's fields in one allocation (each field's at a
+// 256-byte boundary).
+int plan_fields_shared(const std::vector<ipc_field*>& fs, cudaStream_t st) {
+  uint64_t words = 0;
+  std::vector<uint64_t> at(fs.size());
+  for (size_t i = 0; i < fs.size(); ++i) {
+    stream_layout(fs[i]);
+    at[i] = words;
+    words += (fs[i]->cap_words + fs[i]->bm_words + 63) & ~uint64_t(63);
+  }
+  SharedStreams* sh = new (std::nothrow) SharedStreams();
+  if (!sh) return fail(IPC_ENOMEM, "host allocation");
+  uint32_t* p = nullptr;
+  const int rc = dalloc((void**)&p, words * 4, st);
+  if (rc) {
+    delete sh;
+    return rc;
+  }
+  sh->p = p;
+  sh->refs.store((int)fs.size());
+  for (size_t i = 0; i < fs.size(); ++i) {
+    fs[i]->shared = sh;
+    fs[i]->d_cap = p + at[i];
+    fs[i]->d_bm = fs[i]->d_cap + fs[i]->cap_words;
+  }
   return IPC_OK;
 }
 
@@ -614,8 +752,9 @@ void retrieve_planes(const ipc_field* f, int l, int b, LevelArgs* L) {
 }
 
 // Container layout from the per-plane nnz: stream sizes and modes, packed
-// offsets (stage-major, plane 31..0), mandatory bytes; uploads outliers.
-int finish_field(ipc_field* f, cudaStream_t st) {
+// offsets (stage-major, plane 31..0), mandatory bytes, the selector's tables
+// (host only).
+void finish_layout(ipc_field* f) {
   const Geo& g = f->g;
   uint64_t word = 0;
   for (size_t t = 0; t < g.stages.size(); ++t) {
@@ -641,6 +780,11 @@ int finish_field(ipc_field* f, cudaStream_t st) {
   f->mandatory = header_size(f);
   f->sel = sel_input(f);
   prepare_selection(&f->sel);
+}
+
+// The field's outlier arrays to the device.
+int upload_outliers(ipc_field* f, cudaStream_t st) {
+  const uint64_t nout = f->out_off.empty() ? 0 : f->out_off.back();
   if (nout == 0) return IPC_OK;  // no outlier arrays (kernels read them only for outliers)
   // indices, then values, in one allocation, from pinned staging
   const int rc = dalloc((void**)&f->d_oidx, nout * 16, st);
@@ -656,6 +800,11 @@ int finish_field(ipc_field* f, cudaStream_t st) {
       val += s.out_val.size();
     }
   });
+}
+
+int finish_field(ipc_field* f, cudaStream_t st) {
+  finish_layout(f);
+  return upload_outliers(f, st);
 }
 
 double okey_to_double(unsigned long long k) {
@@ -794,37 +943,123 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
   unsigned long long* x0d = ws.small + 4 * nf;  // f64 bits of each field's first value
   unsigned long long* ocount = ws.small + 5 * nf;
 
-  // a0: range over finite values, and the anchor
-  {
-    std::vector<unsigned long long> init(4 * nf);
-    for (size_t i = 0; i < nf; ++i) {
-      init[4 * i] = ~0ULL;
-      init[4 * i + 1] = init[4 * i + 2] = init[4 * i + 3] = 0ULL;
-    }
-    CU(cudaMemcpyAsync(acc, init.data(), 32 * nf, cudaMemcpyHostToDevice, st));
-  }
-  // one range launch per kRangeBatch fields, one read-back of the results
+  // a0: range over finite values, and the anchor: one launch per
+  // kRangeBatch fields, accumulators initialised from pinned staging
+  if ((rc = upload_staged(acc, 32 * nf, st, [&](uint8_t* h) {
+         unsigned long long* a = reinterpret_cast<unsigned long long*>(h);
+         for (size_t i = 0; i < nf; ++i) {
+           a[4 * i] = ~0ULL;
+           a[4 * i + 1] = a[4 * i + 2] = a[4 * i + 3] = 0ULL;
+         }
+       })))
+    return rc;
   for (size_t i0 = 0; i0 < nf; i0 += kRangeBatch) {
     const int nb = (int)std::min<size_t>(kRangeBatch, nf - i0);
     RangeBatch rb{};
-    uint64_t nmax = 0;
     double by = 0;
     for (int j = 0; j < nb; ++j) {
       rb.x[j] = ins[i0 + j];
       rb.n[j] = fs[i0 + j]->g.n;
-      nmax = std::max(nmax, rb.n[j]);
       by += (double)(rb.n[j] * esz);
     }
     rb.acc = acc + 4 * i0;
     rb.x0 = x0d + i0;
     const long ph = prof_begin(IPC_KERNEL_RANGE, st);
-    CU(launch_range_batch(dtype, rb, nb, nmax, st));
+    CU(launch_range_batch(dtype, rb, nb, st));
     prof_end(ph, st, by);
   }
+  // While the range runs: the fields' device streams, and the entry table
+  // of every level (coarsest first), uploaded without the quantizer
+  // arguments, which wait for the range.
+  if (nf >= 8) {
+    if ((rc = plan_fields_shared(fs, st))) return rc;
+  } else {
+    for (size_t i = 0; i < nf; ++i)
+      if ((rc = plan_field(fs[i], st))) return rc;
+  }
+  std::vector<std::array<unsigned char, 32>> quant(nf);
+  for (auto& q : quant) q.fill(0);
+  std::vector<uint64_t> lev_off(Kmax + 1, 0), lev_ctas(Kmax + 1, 0);
+  std::vector<CompressEntry> ents;
+  std::vector<std::pair<size_t, int>> who;  // (field, level) of each entry
+  bool table = false;  // some level has several fields (the batched kernel)
+  // entry positions: level-major (coarsest first), fields in order within
+  // a level; the entries themselves are filled per field (large batches on
+  // the host pool), the CTA offsets then per level
+  std::vector<size_t> pos(nf * (size_t)(Kmax + 1), 0);
+  size_t ne = 0;
+  for (int l = Kmax; l >= 1; --l) {
+    lev_off[l] = ne;
+    for (size_t i = 0; i < nf; ++i)
+      if (l <= fs[i]->g.K) pos[i * (Kmax + 1) + l] = ne++;
+    if (ne - lev_off[l] > 1) table = true;
+  }
+  ents.resize(ne);
+  who.resize(ne);
+  auto field_entries = [&](int i) {
+    ipc_field* f = fs[i];
+    for (int l = 1; l <= f->g.K; ++l) {
+      const size_t q = pos[i * (Kmax + 1) + l];
+      CompressEntry& e = ents[q];
+      e = CompressEntry{};
+      e.L = level_args(f, l);
+      e.L.vec = 1;  // the scratch is allocated aligned
+      plane_offsets(f, l, &e.L);
+      e.o = SweepOut{f->d_cap, f->d_bm, ws.nnz + 32 * so[i], ws.okey, ws.oval, ocount,
+                     ws.ocap, ws.stat + 2 * so[i], (uint32_t)i};
+      compress_layout(&e.L, (uint8_t*)ws.xh + xo[i] + xl[i][l + 1]);
+      e.x = ins[i];
+      e.xh = l > 1 ? (uint8_t*)ws.xh + xo[i] + xl[i][l] : nullptr;
+      std::memcpy(e.quant, quant[i].data(), 32);
+      e.write_xh = l > 1;  // the finest level's values are never read again
+      who[q] = {(size_t)i, l};
+    }
+  };
+  auto build_entries = [&]() {
+    if (nf >= 8)
+      HostPool::get().run((int)nf, field_entries);
+    else
+      for (size_t i = 0; i < nf; ++i) field_entries((int)i);
+    for (int l = Kmax; l >= 1; --l) {
+      uint64_t cta = 0;
+      const size_t end = l > 1 ? lev_off[l - 1] : ne;
+      for (size_t q = lev_off[l]; q < end; ++q) {
+        ents[q].cta_begin = cta;
+        cta += (uint64_t)ents[q].L.M[0] * ents[q].L.nrb * ents[q].L.nct;
+      }
+      lev_ctas[l] = cta;
+    }
+  };
+  build_entries();
+  // device table: [entries | anchors | quantizer arguments per field]
+  const size_t eby = ents.size() * sizeof(CompressEntry), aby = nf * sizeof(AnchorEntry);
+  CompressEntry* d_ents = nullptr;
+  if ((rc = dalloc((void**)&d_ents, eby + aby + 32 * nf, st))) return rc;
+  struct EntGuard {
+    CompressEntry*& p;
+    cudaStream_t s;
+    ~EntGuard() { if (p) cudaFreeAsync(p, s); }
+  } eguard{d_ents, st};
+  AnchorEntry* d_anch = reinterpret_cast<AnchorEntry*>((uint8_t*)d_ents + eby);
+  unsigned char* d_quant = (uint8_t*)d_ents + eby + aby;
+  auto upload_entries = [&]() {
+    return upload_staged(d_ents, eby, st, [&](uint8_t* h) {
+      const size_t chunk = 64 << 10, nc = (eby + chunk - 1) / chunk;
+      auto part = [&](int c) {
+        const size_t o = c * chunk;
+        std::memcpy(h + o, (const uint8_t*)ents.data() + o, std::min(chunk, eby - o));
+      };
+      if (nc >= 4)
+        HostPool::get().run((int)nc, part);
+      else
+        for (size_t c = 0; c < nc; ++c) part((int)c);
+    });
+  };
+  if (table && (rc = upload_entries())) return rc;
+
   std::vector<unsigned long long> hacc(5 * nf);
   CU(cudaMemcpyAsync(hacc.data(), acc, 40 * nf, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  std::vector<std::array<unsigned char, 32>> quant(nf);
   std::vector<AnchorEntry> anch;  // the origin of level K + 1 is x[0], stored exactly
   anch.reserve(nf);
   for (size_t i = 0; i < nf; ++i) {
@@ -845,67 +1080,26 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     if (!(eb > 0) || !std::isfinite(eb)) return fail(IPC_EINVAL, "error bound must be > 0 and finite");
     f->eb = eb;
     std::memcpy(&f->anchor, &hacc[4 * nf + i], 8);
-    quant[i].fill(0);
     if (dtype == 0) quant_args<float>(eb, f->xmaxabs, quant[i].data());
     else quant_args<double>(eb, f->xmaxabs, quant[i].data());
-    if ((rc = plan_field(f, st))) return rc;
     if (f->g.K > 0) anch.push_back(AnchorEntry{(uint8_t*)ws.xh + xo[i] + xl[i][f->g.K + 1], f->anchor});
   }
-
-  // entry table of every level (coarsest first)
-  std::vector<uint64_t> lev_off(Kmax + 1, 0), lev_ctas(Kmax + 1, 0);
-  std::vector<CompressEntry> ents;
-  std::vector<std::pair<size_t, int>> who;  // (field, level) of each entry
-  auto build_entries = [&]() {
-    ents.clear();
-    who.clear();
-    for (int l = Kmax; l >= 1; --l) {
-      lev_off[l] = ents.size();
-      uint64_t cta = 0;
-      for (size_t i = 0; i < nf; ++i) {
-        ipc_field* f = fs[i];
-        if (l > f->g.K) continue;
-        CompressEntry e{};
-        e.L = level_args(f, l);
-        e.L.vec = 1;  // the scratch is allocated aligned
-        plane_offsets(f, l, &e.L);
-        e.o = SweepOut{f->d_cap, f->d_bm, ws.nnz + 32 * so[i], ws.okey, ws.oval, ocount,
-                       ws.ocap, ws.stat + 2 * so[i], (uint32_t)i};
-        compress_layout(&e.L, (uint8_t*)ws.xh + xo[i] + xl[i][l + 1]);
-        e.x = ins[i];
-        e.xh = l > 1 ? (uint8_t*)ws.xh + xo[i] + xl[i][l] : nullptr;
-        std::memcpy(e.quant, quant[i].data(), 32);
-        e.write_xh = l > 1;  // the finest level's values are never read again
-        e.cta_begin = cta;
-        cta += (uint64_t)e.L.M[0] * e.L.nrb * e.L.nct;
-        ents.push_back(e);
-        who.push_back({i, l});
-      }
-      lev_ctas[l] = cta;
-    }
-  };
-  build_entries();
-  // device table: [entries | anchors]
-  const size_t eby = ents.size() * sizeof(CompressEntry), aby = anch.size() * sizeof(AnchorEntry);
-  CompressEntry* d_ents = nullptr;
-  if ((rc = dalloc((void**)&d_ents, eby + aby, st))) return rc;
-  struct EntGuard {
-    CompressEntry*& p;
-    cudaStream_t s;
-    ~EntGuard() { if (p) cudaFreeAsync(p, s); }
-  } eguard{d_ents, st};
-  AnchorEntry* d_anch = reinterpret_cast<AnchorEntry*>((uint8_t*)d_ents + eby);
+  // the host's entries take the quantizer arguments too (single-field
+  // launches pass theirs by value, a retry uploads them whole)
+  for (size_t q = 0; q < ents.size(); ++q) std::memcpy(ents[q].quant, quant[who[q].first].data(), 32);
+  if ((rc = upload_staged(d_anch, aby + 32 * nf, st, [&](uint8_t* h) {
+         std::memcpy(h, anch.data(), anch.size() * sizeof(AnchorEntry));
+         for (size_t i = 0; i < nf; ++i) std::memcpy(h + aby + 32 * i, quant[i].data(), 32);
+       })))
+    return rc;
 
   std::vector<long> level_prof(Kmax + 1, -1);
   unsigned long long nout = 0;
   std::vector<uint32_t> stat(2 * so[nf]), nnz(32 * so[nf]);
   for (int attempt = 0; attempt < 2; ++attempt) {
-    if ((rc = upload_staged(d_ents, eby + aby, st, [&](uint8_t* h) {
-           std::memcpy(h, ents.data(), eby);
-           std::memcpy(h + eby, anch.data(), aby);
-         })))
-      return rc;
+    if (attempt > 0 && table && (rc = upload_entries())) return rc;
     if (!anch.empty()) CU(launch_set_anchors(dtype, d_anch, (int)anch.size(), st));
+    if (table) CU(launch_set_quant(d_ents, (int)ents.size(), d_quant, st));
     CU(cudaMemsetAsync(ws.stat, 0, 2 * so[nf] * 4, st));
     CU(cudaMemsetAsync(ws.nnz, 0, 32 * so[nf] * 4, st));
     CU(cudaMemsetAsync(ocount, 0, 8, st));
@@ -948,7 +1142,27 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     build_entries();
   }
 
-  for (size_t i = 0; i < nf; ++i) {
+  // outliers sorted by key: (field, stage, code index), so each field's are
+  // one run, its stages in order
+  std::vector<unsigned long long> key(nout);
+  std::vector<double> val(nout);
+  std::vector<uint64_t> order(nout), obeg(nf + 1, nout);
+  if (nout) {
+    CU(cudaMemcpyAsync(key.data(), ws.okey, nout * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(val.data(), ws.oval, nout * 8, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (uint64_t i = 0; i < nout; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return key[a] < key[b]; });
+    for (uint64_t q = nout; q-- > 0;) {
+      const size_t fi = (size_t)(key[order[q]] >> 48);
+      if (fi >= nf) return fail(IPC_ECUDA, "outlier of an unknown field");
+      obeg[fi] = q;
+    }
+    for (size_t i = nf; i-- > 0;) obeg[i] = std::min(obeg[i], obeg[i + 1]);
+  }
+  // per field (large batches on the host pool): the stage statistics, its
+  // outliers, then the container layout and the selector's tables
+  auto finish = [&](int i) {
     ipc_field* f = fs[i];
     const size_t S = f->g.stages.size();
     f->st.assign(S, StageTab{});
@@ -960,24 +1174,20 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
       f->st[t].Q = stat[2 * (so[i] + t) + 1];
       for (int k = 0; k < 32; ++k) f->st[t].nnz[k] = nnz[32 * (so[i] + t) + k];
     }
-  }
-  if (nout) {
-    std::vector<unsigned long long> key(nout);
-    std::vector<double> val(nout);
-    CU(cudaMemcpyAsync(key.data(), ws.okey, nout * 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(val.data(), ws.oval, nout * 8, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    std::vector<uint64_t> order(nout);
-    for (uint64_t i = 0; i < nout; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) { return key[a] < key[b]; });
-    for (uint64_t i : order) {
-      const size_t fi = (size_t)(key[i] >> 48), t = (size_t)((key[i] >> 40) & 0xFF);
-      fs[fi]->st[t].out_idx.push_back(key[i] & ((1ULL << 40) - 1));
-      fs[fi]->st[t].out_val.push_back(val[i]);
+    for (uint64_t q = obeg[i]; q < obeg[i + 1]; ++q) {
+      const uint64_t j = order[q];
+      const size_t t = (size_t)((key[j] >> 40) & 0xFF);
+      f->st[t].out_idx.push_back(key[j] & ((1ULL << 40) - 1));
+      f->st[t].out_val.push_back(val[j]);
     }
-  }
+    finish_layout(f);
+  };
+  if (nf >= 8)
+    HostPool::get().run((int)nf, finish);
+  else
+    for (size_t i = 0; i < nf; ++i) finish((int)i);
   for (size_t i = 0; i < nf; ++i)
-    if ((rc = finish_field(fs[i], st))) return rc;
+    if ((rc = upload_outliers(fs[i], st))) return rc;
   // algorithmic bytes of each level launch: input values + produced streams
   for (int l = 1; l <= Kmax; ++l) {
     double by = 0;
@@ -1344,85 +1554,6 @@ struct BatchTable {
   uint64_t scratch = 0;      // bytes of the fields' scratch ladders
   int Kmax = 0;
   double alg_bytes = 0;
-};
-
-// Persistent host worker threads for the per-field work of large batches
-// (selection, launch-table preparation): run(n, fn) calls fn(i) for every i
-// in [0, n) on the calling thread and the workers that join in, and returns
-// when all calls have finished. One job at a time; the caller claims indices
-// too, so a job completes even if no worker ever wakes (after a fork, say).
-class HostPool {
- public:
-  static HostPool& get() {
-    static std::mutex mu;
-    static HostPool* p = nullptr;
-    static pid_t owner = 0;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!p || owner != getpid()) {  // a forked child starts a pool of its own
-      p = new HostPool();           // never freed: its workers outlive main
-      owner = getpid();
-    }
-    return *p;
-  }
-  void run(int n, const std::function<void(int)>& fn) {
-    std::lock_guard<std::mutex> one(job_mu_);
-    start_workers();
-    std::atomic<int> next{0};
-    {
-      std::lock_guard<std::mutex> lk(mu_);
-      fn_ = &fn;
-      n_ = n;
-      next_ = &next;
-      ++gen_;
-    }
-    cv_.notify_all();
-    claim(fn, n, next);
-    std::unique_lock<std::mutex> lk(mu_);
-    done_.wait(lk, [&] { return active_ == 0; });
-    fn_ = nullptr;  // a worker that wakes late finds no job
-    next_ = nullptr;
-  }
-
- private:
-  static void claim(const std::function<void(int)>& fn, int n, std::atomic<int>& next) {
-    for (int i; (i = next.fetch_add(1, std::memory_order_relaxed)) < n;) fn(i);
-  }
-  void start_workers() {
-    if (started_) return;
-    started_ = true;
-    const unsigned hc = std::thread::hardware_concurrency();
-    const int nw = (int)std::min<unsigned>(8, std::max(1u, hc / 2)) - 1;
-    for (int k = 0; k < nw; ++k) {
-      try {
-        std::thread([this] { loop(); }).detach();
-      } catch (...) {
-        break;  // fewer workers: the caller takes the rest
-      }
-    }
-  }
-  void loop() {
-    uint64_t seen = 0;
-    std::unique_lock<std::mutex> lk(mu_);
-    for (;;) {
-      cv_.wait(lk, [&] { return gen_ != seen && fn_; });
-      seen = gen_;
-      const std::function<void(int)>* fn = fn_;
-      std::atomic<int>* next = next_;
-      const int n = n_;
-      ++active_;
-      lk.unlock();
-      claim(*fn, n, *next);
-      lk.lock();
-      if (--active_ == 0) done_.notify_all();
-    }
-  }
-  std::mutex job_mu_, mu_;
-  std::condition_variable cv_, done_;
-  const std::function<void(int)>* fn_ = nullptr;
-  std::atomic<int>* next_ = nullptr;
-  int n_ = 0, active_ = 0;
-  uint64_t gen_ = 0;
-  bool started_ = false;
 };
 
 // What a batched reconstruction needs of one field, independent of the
@@ -2600,6 +2731,8 @@ int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, i
   Nvtx nv_call("ipc compress batch");
   if (nfields < 0 || (nfields > 0 && (!items || !outs))) return fail(IPC_EINVAL, "null argument");
   std::vector<ipc_field*> all(nfields, nullptr);
+  int dev = 0;
+  cudaGetDevice(&dev);
   auto cleanup = [&](int rc) {
     for (auto* f : all)
       if (f) {
@@ -2621,14 +2754,28 @@ int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, i
     if (!f) return cleanup(fail(IPC_ENOMEM, "host allocation"));
     all[i] = f;
     f->tag = kFieldTag;
-    if (!build_geo(it.ndim, it.dims, it.dtype, &f->g)) return cleanup(fail(IPC_EINVAL, "shape"));
-    cudaGetDevice(&f->device);
+    f->device = dev;
     f->dtype = it.dtype;
     f->interp = it.interp;
     f->bound = it.bound;
     f->eb_mode = it.eb_mode;
     f->eb_user = it.eb;
   }
+  // the fields' geometries (large batches on the host pool)
+  std::vector<char> geo_ok(nfields, 0);
+  auto geo = [&](int i) {
+    try {
+      geo_ok[i] = build_geo(items[i].ndim, items[i].dims, items[i].dtype, &all[i]->g) ? 1 : 0;
+    } catch (const std::bad_alloc&) {
+      geo_ok[i] = 0;
+    }
+  };
+  if (nfields >= 8)
+    HostPool::get().run(nfields, geo);
+  else
+    for (int i = 0; i < nfields; ++i) geo(i);
+  for (int i = 0; i < nfields; ++i)
+    if (!geo_ok[i]) return cleanup(fail(IPC_EINVAL, "shape"));
   for (int dt = 0; dt < 2; ++dt) {
     std::vector<ipc_field*> fs;
     std::vector<const void*> ins;

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "ipc_device.cuh"
 #include "ipc_internal.h"
 
@@ -87,22 +89,30 @@ __global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, uint64_t
   }
 }
 
-// The range of up to kRangeBatch arrays in one launch: blockIdx.y picks the
-// array; its blocks reduce it as k_range does, and block 0 also copies the
-// array's first value (the anchor) as f64 bits into x0[j].
+// The range of up to kRangeBatch arrays in one launch: the array of a block
+// is the j with blk[j] <= blockIdx.x < blk[j + 1]; its blocks reduce it as
+// k_range does, and its first block also copies the array's first value (the
+// anchor) as f64 bits into x0[j].
 template <class T>
-__global__ void __launch_bounds__(256) k_range_batch(RangeBatch rb) {
-  const int j = blockIdx.y;
+__global__ void __launch_bounds__(256) k_range_batch(RangeBatch rb, int narr) {
+  int lo = 0, hi = narr - 1;  // the last j with blk[j] <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rb.blk[mid] <= blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const int j = lo;
+  const uint32_t b0 = rb.blk[j], nb = rb.blk[j + 1] - b0;
   const T* __restrict__ x = (const T*)rb.x[j];
   const uint64_t n = rb.n[j];
   unsigned long long* acc = rb.acc + 4 * j;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && n)
+  if (blockIdx.x == b0 && threadIdx.x == 0 && n)
     rb.x0[j] = (unsigned long long)__double_as_longlong((double)__ldg(x));
   typedef typename Vec16<T>::type V;
   constexpr int VN = Vec16<T>::n;
   RangeAcc<T> r{(T)0, (T)0, (T)0, 0ULL};
-  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (blockIdx.x - b0) * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t nth = (uint64_t)nb * blockDim.x;
   const uint64_t mis = ((uintptr_t)x & 15) / sizeof(T);
   const uint64_t head = mis ? ((uint64_t)VN - mis < n ? (uint64_t)VN - mis : n) : 0;
   if (tid < head) r.add(__ldg(x + tid));
@@ -141,6 +151,15 @@ template <class T>
 __global__ void k_anchors(const AnchorEntry* __restrict__ a, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) ((T*)a[i].out)[0] = (T)a[i].v;
+}
+
+__global__ void k_set_quant(CompressEntry* __restrict__ e, int n, const uint4* __restrict__ q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t f = e[i].o.field;
+  uint4* d = reinterpret_cast<uint4*>(e[i].quant);
+  d[0] = q[2 * f];
+  d[1] = q[2 * f + 1];
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim = 1024).
@@ -365,18 +384,24 @@ cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long lon
   return cudaGetLastError();
 }
 
-cudaError_t launch_range_batch(int dtype, const RangeBatch& rb, int n, uint64_t nmax,
-                               cudaStream_t st) {
+cudaError_t launch_range_batch(int dtype, RangeBatch& rb, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (n > kRangeBatch) return cudaErrorInvalidValue;
-  // about 152 * 8 blocks over the batch, at least one per array
-  uint64_t per = (152 * 8 + n - 1) / n;
-  const uint64_t need = (nmax / 4 + 255) / 256;
-  if (per > need) per = need;
-  if (per < 1) per = 1;
-  const dim3 grid((unsigned)per, (unsigned)n);
-  if (dtype == 0) k_range_batch<float><<<grid, 256, 0, st>>>(rb);
-  else k_range_batch<double><<<grid, 256, 0, st>>>(rb);
+  // about 152 * 8 blocks over the batch in proportion to the arrays' sizes,
+  // each array at least one and at most one per 1024 values
+  uint64_t tot = 0;
+  for (int j = 0; j < n; ++j) tot += rb.n[j];
+  const uint64_t target = 152 * 8;
+  uint64_t b = 0;
+  for (int j = 0; j < n; ++j) {
+    rb.blk[j] = (uint32_t)b;
+    uint64_t per = tot ? (rb.n[j] * target + tot - 1) / tot : 1;
+    per = std::min<uint64_t>(per, (rb.n[j] + 1023) / 1024);
+    b += std::max<uint64_t>(per, 1);
+  }
+  rb.blk[n] = (uint32_t)b;
+  if (dtype == 0) k_range_batch<float><<<(unsigned)b, 256, 0, st>>>(rb, n);
+  else k_range_batch<double><<<(unsigned)b, 256, 0, st>>>(rb, n);
   return cudaGetLastError();
 }
 
@@ -391,6 +416,12 @@ cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStrea
   const unsigned grid = (unsigned)((n + 127) / 128);
   if (dtype == 0) k_anchors<float><<<grid, 128, 0, st>>>(a, n);
   else k_anchors<double><<<grid, 128, 0, st>>>(a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_quant(CompressEntry* e, int n, const unsigned char* q, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_set_quant<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(e, n, reinterpret_cast<const uint4*>(q));
   return cudaGetLastError();
 }
 
