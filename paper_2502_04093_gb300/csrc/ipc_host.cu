@@ -29,6 +29,7 @@
 #include "ipc_internal.h"
 #include "ipc_select.h"
 #include "ipc_serve_internal.h"
+#include "ipc_table_kernels.h"
 
 using namespace ipc;
 
@@ -965,7 +966,7 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
     rb.acc = acc + 4 * i0;
     rb.x0 = x0d + i0;
     const long ph = prof_begin(IPC_KERNEL_RANGE, st);
-    CU(launch_range_batch(dtype, rb, nb, st));
+    CU(launch_range_batch(dtype, rb, nb, 0, st));
     prof_end(ph, st, by);
   }
   // While the range runs: the fields' device streams, and the entry table

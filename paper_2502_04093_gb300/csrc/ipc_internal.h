@@ -229,22 +229,17 @@ cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long lon
                          cudaStream_t st);
 // The range of up to kRangeBatch arrays in one launch (arguments by value):
 // acc[4 j ..] as launch_range, x0[j] = the f64 bits of array j's first value.
-// Array j takes blocks blk[j] .. blk[j + 1] - 1 of a one-dimensional grid
-// (filled by launch_range_batch, in proportion to the arrays' sizes).
 constexpr int kRangeBatch = 128;
 struct RangeBatch {
   const void* x[kRangeBatch];
   uint64_t n[kRangeBatch];
-  uint32_t blk[kRangeBatch + 1];
   unsigned long long* acc;
   unsigned long long* x0;
 };
-cudaError_t launch_range_batch(int dtype, RangeBatch& rb, int n, cudaStream_t st);
+cudaError_t launch_range_batch(int dtype, const RangeBatch& rb, int n, uint64_t nmax,
+                               cudaStream_t st);
 cudaError_t launch_set_anchor(int dtype, void* out, double v, cudaStream_t st);
 cudaError_t launch_set_anchors(int dtype, const AnchorEntry* a, int n, cudaStream_t st);
-// Entry i of a compression table takes the quantizer arguments of its field:
-// the 32 bytes at q + 32 * e[i].o.field (q 16-byte aligned).
-cudaError_t launch_set_quant(CompressEntry* e, int n, const unsigned char* q, cudaStream_t st);
 // Fused level kernels (ipc_level.cu; the variants with the quadratic
 // boundary forms, for interp 2, in ipc_level_quad.cu and
 // ipc_level_delta_quad.cu -- the single-field launchers pick them by

@@ -13,6 +13,7 @@
 
 #include "ipc_device.cuh"
 #include "ipc_internal.h"
+#include "ipc_table_kernels.h"
 
 namespace ipc {
 namespace {
@@ -89,20 +90,24 @@ __global__ void __launch_bounds__(256) k_range(const T* __restrict__ x, uint64_t
   }
 }
 
-// The range of up to kRangeBatch arrays in one launch: the array of a block
-// is the j with blk[j] <= blockIdx.x < blk[j + 1]; its blocks reduce it as
-// k_range does, and its first block also copies the array's first value (the
-// anchor) as f64 bits into x0[j].
+// The range of up to kRangeBatch arrays in one launch: array j takes blocks
+// blk[j] .. blk[j + 1] - 1 of a one-dimensional grid, in proportion to the
+// arrays' sizes; its blocks reduce it as k_range does, and its first block
+// also copies the array's first value (the anchor) as f64 bits into x0[j].
+struct RangeBlocks {
+  uint32_t blk[kRangeBatch + 1];
+};
+
 template <class T>
-__global__ void __launch_bounds__(256) k_range_batch(RangeBatch rb, int narr) {
+__global__ void __launch_bounds__(256) k_range_batch(RangeBatch rb, RangeBlocks bl, int narr) {
   int lo = 0, hi = narr - 1;  // the last j with blk[j] <= blockIdx.x
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (rb.blk[mid] <= blockIdx.x) lo = mid;
+    if (bl.blk[mid] <= blockIdx.x) lo = mid;
     else hi = mid - 1;
   }
   const int j = lo;
-  const uint32_t b0 = rb.blk[j], nb = rb.blk[j + 1] - b0;
+  const uint32_t b0 = bl.blk[j], nb = bl.blk[j + 1] - b0;
   const T* __restrict__ x = (const T*)rb.x[j];
   const uint64_t n = rb.n[j];
   unsigned long long* acc = rb.acc + 4 * j;
@@ -384,24 +389,27 @@ cudaError_t launch_range(int dtype, const void* x, uint64_t n, unsigned long lon
   return cudaGetLastError();
 }
 
-cudaError_t launch_range_batch(int dtype, RangeBatch& rb, int n, cudaStream_t st) {
+// nmax is not needed: the blocks follow every array's own size.
+cudaError_t launch_range_batch(int dtype, const RangeBatch& rb, int n, uint64_t /*nmax*/,
+                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (n > kRangeBatch) return cudaErrorInvalidValue;
   // about 152 * 8 blocks over the batch in proportion to the arrays' sizes,
   // each array at least one and at most one per 1024 values
+  RangeBlocks bl{};
   uint64_t tot = 0;
   for (int j = 0; j < n; ++j) tot += rb.n[j];
   const uint64_t target = 152 * 8;
   uint64_t b = 0;
   for (int j = 0; j < n; ++j) {
-    rb.blk[j] = (uint32_t)b;
+    bl.blk[j] = (uint32_t)b;
     uint64_t per = tot ? (rb.n[j] * target + tot - 1) / tot : 1;
     per = std::min<uint64_t>(per, (rb.n[j] + 1023) / 1024);
     b += std::max<uint64_t>(per, 1);
   }
-  rb.blk[n] = (uint32_t)b;
-  if (dtype == 0) k_range_batch<float><<<(unsigned)b, 256, 0, st>>>(rb, n);
-  else k_range_batch<double><<<(unsigned)b, 256, 0, st>>>(rb, n);
+  bl.blk[n] = (uint32_t)b;
+  if (dtype == 0) k_range_batch<float><<<(unsigned)b, 256, 0, st>>>(rb, bl, n);
+  else k_range_batch<double><<<(unsigned)b, 256, 0, st>>>(rb, bl, n);
   return cudaGetLastError();
 }
 
