@@ -61,8 +61,19 @@ uint64_t get64(const uint8_t* p) {
 }
 
 void normalise(const uint8_t* src, uint64_t n, uint32_t f[256]) {
-  uint64_t c[256] = {};
-  for (uint64_t i = 0; i < n; ++i) ++c[src[i]];
+  // four interleaved counter tables: runs of one byte value do not chain
+  // every increment on the same counter
+  uint64_t c4[4][256] = {};
+  uint64_t i = 0;
+  for (; i + 4 <= n; i += 4) {
+    ++c4[0][src[i]];
+    ++c4[1][src[i + 1]];
+    ++c4[2][src[i + 2]];
+    ++c4[3][src[i + 3]];
+  }
+  for (; i < n; ++i) ++c4[0][src[i]];
+  uint64_t c[256];
+  for (int s = 0; s < 256; ++s) c[s] = c4[0][s] + c4[1][s] + c4[2][s] + c4[3][s];
   int64_t sum = 0;
   for (int s = 0; s < 256; ++s) {
     f[s] = c[s] == 0 ? 0 : (uint32_t)std::max<uint64_t>(1, c[s] * kTotal / n);
@@ -84,31 +95,55 @@ void normalise(const uint8_t* src, uint64_t n, uint32_t f[256]) {
   }
 }
 
+// Division of a state x < 2^31 by a frequency 1 <= f <= 4096 as a multiply
+// and shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 f) and m = ceil(2^(31+l) / f),
+// floor(x / f) = floor(x m / 2^(31+l)) for every x < 2^31, and x m < 2^64.
+struct Recip {
+  uint64_t m;
+  uint32_t shift;
+};
+Recip recip(uint32_t f) {
+  uint32_t l = 0;
+  while ((1u << l) < f) ++l;
+  const uint64_t num = uint64_t(1) << (31 + l);
+  return Recip{(num + f - 1) / f, 31 + l};
+}
+
 // Codes one block of n bytes into `rec` (capacity 1 + n: a record is never
 // larger than the stored form); returns the record's size.
 uint64_t encode_block(const uint8_t* src, uint64_t n, uint8_t* rec, std::vector<uint8_t>* tmp) {
-  uint32_t f[256], start[256];
+  uint32_t f[256], start[256], xmax[256];
+  Recip rc[256];
   normalise(src, n, f);
   uint32_t acc = 0;
   for (int s = 0; s < 256; ++s) {
     start[s] = acc;
     acc += f[s];
+    xmax[s] = ((kLow >> kScale) << 8) * f[s];
+    rc[s] = f[s] ? recip(f[s]) : Recip{0, 0};
   }
   // the rANS bytes are written backwards from the end of a scratch buffer:
   // at most 2 bytes per symbol (a frequency >= 1 of 4096 adds at most 12
   // bits of state) plus the final state
   tmp->resize(2 * n + 8);
-  uint8_t* end = tmp->data() + tmp->size();
+  uint8_t* const end = tmp->data() + tmp->size();
   uint8_t* p = end;
   uint32_t x = kLow;
   for (uint64_t i = n; i-- > 0;) {
-    const uint32_t s = src[i], fs = f[s];
-    const uint32_t xmax = ((kLow >> kScale) << 8) * fs;
-    while (x >= xmax) {
-      *--p = (uint8_t)(x & 0xFF);
-      x >>= 8;
-    }
-    x = ((x / fs) << kScale) + (x % fs) + start[s];
+    const uint32_t s = src[i];
+    // shift out low bytes while x >= xmax_s: with x < 2^31 and
+    // xmax_s >= 2^19 that is at most two, decided without a branch (the
+    // count is data-dependent); both candidate bytes are stored, p moves by
+    // the count (the space below p is unused so far: p >= end - 2 i)
+    const uint32_t nb = (uint32_t)(x >= xmax[s]) + (uint32_t)((uint64_t)x >= ((uint64_t)xmax[s] << 8));
+    p[-1] = (uint8_t)(x & 0xFF);
+    p[-2] = (uint8_t)((x >> 8) & 0xFF);
+    p -= nb;
+    x >>= 8 * nb;
+    // x < 2^31 here (x < xmax <= 2^31); q = floor(x / f_s)
+    const uint32_t q = (uint32_t)(((uint64_t)x * rc[s].m) >> rc[s].shift);
+    x = (q << kScale) + (x - q * f[s]) + start[s];
   }
   p -= 4;
   put32(p, x);
@@ -128,9 +163,11 @@ uint64_t encode_block(const uint8_t* src, uint64_t n, uint8_t* rec, std::vector<
 }
 
 // Decodes one record into n bytes; false when it is not a valid coding of n
-// bytes.
+// bytes. The slot table holds, per slot of [0, 4096), its symbol, the
+// symbol's frequency and the slot's offset in the symbol's range, so that a
+// step is one table load.
 bool decode_block(const uint8_t* rec, uint64_t len, uint8_t* dst, uint64_t n,
-                  std::vector<uint8_t>* sym) {
+                  std::vector<uint32_t>* slots) {
   if (len < 1) return false;
   if (rec[0] == 0) {
     if (len != 1 + n) return false;
@@ -138,28 +175,39 @@ bool decode_block(const uint8_t* rec, uint64_t len, uint8_t* dst, uint64_t n,
     return true;
   }
   if (rec[0] != 1 || len < 1 + kTable + 4) return false;
-  uint32_t f[256], start[256], acc = 0;
+  uint32_t f[256], acc = 0;
   for (int s = 0; s < 256; ++s) {
     f[s] = (uint32_t)rec[1 + 2 * s] | ((uint32_t)rec[2 + 2 * s] << 8);
-    start[s] = acc;
     acc += f[s];
   }
   if (acc != kTotal) return false;
-  sym->resize(kTotal);
-  for (int s = 0; s < 256; ++s)
-    for (uint32_t k = 0; k < f[s]; ++k) (*sym)[start[s] + k] = (uint8_t)s;
+  slots->resize(kTotal);
+  uint32_t* const tab = slots->data();
+  // entry: symbol (bits 0-7), frequency - 1 (bits 8-19), offset in the
+  // symbol's range (bits 20-31)
+  for (uint32_t s = 0, slot = 0; s < 256; ++s)
+    for (uint32_t k = 0; k < f[s]; ++k, ++slot) tab[slot] = s | ((f[s] - 1) << 8) | (k << 20);
   const uint8_t* p = rec + 1 + kTable;
-  const uint8_t* end = rec + len;
+  const uint8_t* const end = rec + len;
   uint32_t x = get32(p);
   p += 4;
   for (uint64_t i = 0; i < n; ++i) {
-    const uint32_t slot = x & (kTotal - 1);
-    const uint8_t s = (*sym)[slot];
-    dst[i] = s;
-    x = f[s] * (x >> kScale) + slot - start[s];
-    while (x < kLow) {
-      if (p >= end) return false;
-      x = (x << 8) | *p++;
+    const uint32_t e = tab[x & (kTotal - 1)];
+    dst[i] = (uint8_t)e;
+    x = (((e >> 8) & 0xFFF) + 1) * (x >> kScale) + (e >> 20);
+    // x >= f (2^23 >> 12) >= 2^11 now: at most two bytes bring it back to
+    // [2^23, 2^31); the count is taken without a branch while two bytes are
+    // left to read, byte by byte near the end of the stream
+    if (end - p >= 2) {
+      const uint32_t nb = (uint32_t)(x < kLow) + (uint32_t)(x < (kLow >> 8));
+      const uint32_t two = ((uint32_t)p[0] << 8) | p[1];
+      x = (x << (8 * nb)) | (two >> (8 * (2 - nb)));
+      p += nb;
+    } else {
+      while (x < kLow) {
+        if (p >= end) return false;
+        x = (x << 8) | *p++;
+      }
     }
   }
   // the encoder started from the state kLow and used every byte
@@ -265,9 +313,9 @@ int ipc_decode_container(const void* coded, uint64_t coded_len, void* out, uint6
   std::atomic<int> bad{0};
   uint8_t* o = (uint8_t*)out;
   parallel_blocks(nb, threads_for(nthreads, nb), [&](uint64_t i) {
-    thread_local std::vector<uint8_t> sym;
+    thread_local std::vector<uint32_t> slots;
     const uint64_t n = std::min(bs, raw_len - i * bs);
-    if (!decode_block(c + off[i], off[i + 1] - off[i], o + i * bs, n, &sym)) bad.store(1);
+    if (!decode_block(c + off[i], off[i + 1] - off[i], o + i * bs, n, &slots)) bad.store(1);
   });
   if (bad.load()) return err(IPC_ECORRUPT, "a block does not decode to its length");
   *out_len = raw_len;
