@@ -18,6 +18,7 @@
 #include <functional>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <mutex>
 #include <new>
@@ -307,6 +308,8 @@ namespace {
 // in [0, n) on the calling thread and the workers that join in, and returns
 // when all calls have finished. One job at a time; the caller claims indices
 // too, so a job completes even if no worker ever wakes (after a fork, say).
+// An exception thrown by a call (on any thread) stops the job's remaining
+// calls and is rethrown on the calling thread, as a serial loop would.
 class HostPool {
  public:
   static HostPool& get() {
@@ -337,10 +340,15 @@ class HostPool {
     }
     cv_.notify_all();
     claim(fn, n, next);
-    std::unique_lock<std::mutex> lk(mu_);
-    done_.wait(lk, [&] { return active_ == 0; });
-    fn_ = nullptr;  // a worker that wakes late finds no job
-    next_ = nullptr;
+    std::exception_ptr err;
+    {
+      std::unique_lock<std::mutex> lk(mu_);
+      done_.wait(lk, [&] { return active_ == 0; });
+      fn_ = nullptr;  // a worker that wakes late finds no job
+      next_ = nullptr;
+      std::swap(err, err_);
+    }
+    if (err) std::rethrow_exception(err);
   }
 
  private:
@@ -348,9 +356,15 @@ class HostPool {
     thread_local bool b = false;
     return b;
   }
-  static void claim(const std::function<void(int)>& fn, int n, std::atomic<int>& next) {
+  void claim(const std::function<void(int)>& fn, int n, std::atomic<int>& next) {
     in_job() = true;
-    for (int i; (i = next.fetch_add(1, std::memory_order_relaxed)) < n;) fn(i);
+    try {
+      for (int i; (i = next.fetch_add(1, std::memory_order_relaxed)) < n;) fn(i);
+    } catch (...) {
+      next.store(n);  // the others stop claiming
+      std::lock_guard<std::mutex> lk(mu_);
+      if (!err_) err_ = std::current_exception();
+    }
     in_job() = false;
   }
   void start_workers() {
@@ -386,6 +400,7 @@ class HostPool {
   std::condition_variable cv_, done_;
   const std::function<void(int)>* fn_ = nullptr;
   std::atomic<int>* next_ = nullptr;
+  std::exception_ptr err_;  // the job's first exception
   int n_ = 0, active_ = 0;
   uint64_t gen_ = 0;
   bool started_ = false;
