@@ -8,10 +8,15 @@ choice could reach: the sum over levels of the smallest of the three
 modes' stream bytes for that level (plus the smallest mandatory part). The
 estimate treats levels as independent, which they nearly are: a level's
 codes depend on the coarser levels only through reconstructions that
-differ by at most the error bound. Oracle only (test infrastructure):
+differ by at most the error bound. The second table covers the order in which a level sweeps its
+dimensions: compressing a transposed copy of a field sweeps its axes in the
+permuted order, so each permutation (with each mode) is compressed and the
+best is compared with the natural order's best. Oracle only (test
+infrastructure):
 
     python -m oracle.interp_study
 """
+import itertools
 import time
 
 import numpy as np
@@ -69,6 +74,24 @@ def main():
               % (name, tot[0], tot[1], tot[2], est, 100.0 * (best - est) / best, pick, E,
                  ret[0], ret[1], ret[2]))
         print("<!-- %s: %.1f s -->" % (name, time.perf_counter() - t0))
+    print()
+    print("| workload | best (order, mode) by container | container below the natural order's best "
+          "| retrieval at E below the natural order's best |")
+    print("|---|---|---|---|")
+    for name, x, eb, mode, E in workloads():
+        rows = []
+        for perm in itertools.permutations(range(x.ndim)):
+            xp = np.ascontiguousarray(x.transpose(perm))
+            for m in MODES:
+                f = oracle.compress(xp, eb, mode, interp=m)
+                rows.append((perm, m, len(f.export()), f.retrieve(oracle.EB, E)[1].selection()[1]))
+        nat = [r for r in rows if r[0] == tuple(range(x.ndim))]
+        c0, c1 = min(r[2] for r in nat), min(r[2] for r in rows)
+        r0, r1 = min(r[3] for r in nat), min(r[3] for r in rows)
+        best = min(rows, key=lambda r: r[2])
+        print("| %s | %s, %s | %.2f %% | %g: %.2f %% |" % (name, best[0], "LCQ"[best[1]],
+                                                          100.0 * (c0 - c1) / c0, E,
+                                                          100.0 * (r0 - r1) / r0))
 
 
 if __name__ == "__main__":
