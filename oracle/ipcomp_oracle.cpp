@@ -1046,15 +1046,95 @@ int parse(const uint8_t* p, uint64_t len, ipco_field* f) {
 /* ======================================================================== */
 /* C API                                                                     */
 /* ======================================================================== */
+namespace {
+
+/* Per-field choice of the interpolation (interp 3): the mode whose container
+ * is smallest on a sample of the field. This build's reading of the
+ * per-field form of the interpolation tuning that the QoZ line of
+ * compressors applies (the paper fixes cubic, Sec. 4.1): the sample is the
+ * centred block of extents min(N_d, c) with c = 2^20, 1024, 128 for 1, 2, 3
+ * dimensions (first index floor((N_d - e_d) / 2)); each mode compresses it
+ * with the absolute error bound of the whole field (a relative bound times
+ * the whole field's finite range); the smallest container wins, the lower
+ * mode on a tie. */
+template <class T>
+int auto_mode_t(const T* x, int ndim, const int64_t* dims, int eb_mode, double eb, int bound,
+                int* mode) {
+  uint64_t n = 1;
+  for (int d = 0; d < ndim; ++d) n *= (uint64_t)dims[d];
+  double eb_abs = eb;
+  if (eb_mode == 1) {
+    double mn = 0, mx = 0;
+    bool any = false;
+    for (uint64_t i = 0; i < n; ++i) {
+      const double v = (double)x[i];
+      if (!std::isfinite(v)) continue;
+      if (!any) { mn = mx = v; any = true; }
+      mn = std::min(mn, v);
+      mx = std::max(mx, v);
+    }
+    if (!any) return IPCO_EINVAL;
+    const double range = mx - mn;
+    eb_abs = range > 0 ? eb * range : eb;
+  }
+  if (!(eb_abs > 0) || !std::isfinite(eb_abs)) return IPCO_EINVAL;
+  const int64_t cap = ndim == 1 ? (int64_t)1 << 20 : ndim == 2 ? 1024 : 128;
+  int64_t N[3] = {1, 1, 1}, e[3] = {1, 1, 1}, o[3] = {0, 0, 0};
+  for (int d = 0; d < ndim; ++d) {
+    N[3 - ndim + d] = dims[d];
+    e[3 - ndim + d] = std::min<int64_t>(dims[d], cap);
+    o[3 - ndim + d] = (dims[d] - e[3 - ndim + d]) / 2;
+  }
+  std::vector<T> sample((size_t)(e[0] * e[1] * e[2]));
+  size_t k = 0;
+  for (int64_t i0 = 0; i0 < e[0]; ++i0)
+    for (int64_t i1 = 0; i1 < e[1]; ++i1)
+      for (int64_t i2 = 0; i2 < e[2]; ++i2)
+        sample[k++] = x[((o[0] + i0) * N[1] + (o[1] + i1)) * N[2] + (o[2] + i2)];
+  int64_t sd[3];
+  for (int d = 0; d < ndim; ++d) sd[d] = e[3 - ndim + d];
+  uint64_t best = 0;
+  for (int m = 0; m < 3; ++m) {
+    ipco_field* f = nullptr;
+    const int rc = ipco_compress(sample.data(), sizeof(T) == 4 ? 0 : 1, ndim, sd, 0, eb_abs, m,
+                                 bound, &f);
+    if (rc) return rc;
+    const uint64_t bytes = f->bytes.size();
+    ipco_free_field(f);
+    if (m == 0 || bytes < best) {
+      best = bytes;
+      *mode = m;
+    }
+  }
+  return IPCO_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int ipco_auto_interp(const void* x, int dtype, int ndim, const int64_t* dims, int eb_mode,
+                     double eb, int bound, int* mode) {
+  if (!x || !mode || !dims || ndim < 1 || ndim > 3 || dtype < 0 || dtype > 1 || bound < 0 ||
+      bound > 1 || eb_mode < 0 || eb_mode > 1 || !std::isfinite(eb) || !(eb > 0))
+    return IPCO_EINVAL;
+  for (int d = 0; d < ndim; ++d)
+    if (dims[d] < 1) return IPCO_EINVAL;
+  return dtype == 0 ? auto_mode_t((const float*)x, ndim, dims, eb_mode, eb, bound, mode)
+                    : auto_mode_t((const double*)x, ndim, dims, eb_mode, eb, bound, mode);
+}
 
 int ipco_compress(const void* x, int dtype, int ndim, const int64_t* dims,
                   int eb_mode, double eb, int interp, int bound,
                   ipco_field** out) {
-  if (!x || !out || dtype < 0 || dtype > 1 || interp < 0 || interp > 2 ||
+  if (!x || !out || dtype < 0 || dtype > 1 || interp < 0 || interp > 3 ||
       bound < 0 || bound > 1 || eb_mode < 0 || eb_mode > 1 || !std::isfinite(eb) ||
       !(eb > 0))
     return IPCO_EINVAL;
+  if (interp == 3) {  /* the per-field choice, then that mode's container */
+    const int rc = ipco_auto_interp(x, dtype, ndim, dims, eb_mode, eb, bound, &interp);
+    if (rc) return rc;
+  }
   ipco_field* f = new (std::nothrow) ipco_field();
   if (!f) return IPCO_ENOMEM;
   if (!make_geometry(ndim, dims, &f->g)) { delete f; return IPCO_EINVAL; }

@@ -32,10 +32,17 @@ typedef struct ipco_view ipco_view;
 /* Compress x (dtype 0 = f32, 1 = f64; row-major, last dim fastest).
  * eb_mode 0 = absolute, 1 = relative to (max - min). interp 0 linear,
  * 1 cubic, 2 cubic with quadratic boundaries (see the predictor in the
- * .cpp). bound 0 strict, 1 paper. */
+ * .cpp), 3 the per-field choice of ipco_auto_interp (the container records
+ * the chosen mode). bound 0 strict, 1 paper. */
 int ipco_compress(const void* x, int dtype, int ndim, const int64_t* dims,
                   int eb_mode, double eb, int interp, int bound,
                   ipco_field** out);
+/* The interpolation mode (0..2) whose container is smallest on a centred
+ * sample of the field (extents min(N_d, c), c = 2^20 / 1024 / 128 for 1 / 2
+ * / 3 dimensions), compressed with the whole field's absolute error bound;
+ * the lower mode on a tie. */
+int ipco_auto_interp(const void* x, int dtype, int ndim, const int64_t* dims, int eb_mode,
+                     double eb, int bound, int* mode);
 /* Container bytes: len query when buf == NULL. */
 int ipco_export(const ipco_field* f, void* buf, uint64_t* len);
 int ipco_import(const void* buf, uint64_t len, ipco_field** out);

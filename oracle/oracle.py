@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 OK, EINVAL, EBOUND, EBUDGET, ENOMEM, ECORRUPT = 0, -1, -2, -3, -4, -5
 F32, F64 = 0, 1
-LINEAR, CUBIC, CUBIC_QUAD = 0, 1, 2
+LINEAR, CUBIC, CUBIC_QUAD, AUTO = 0, 1, 2, 3
 ABS, REL = 0, 1
 STRICT, PAPER = 0, 1
 EB, BITRATE = 0, 1
@@ -49,6 +49,8 @@ def lib() -> C.CDLL:
         vp, i64p, u64p = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
         L.ipco_compress.argtypes = [vp, C.c_int, C.c_int, i64p, C.c_int, C.c_double,
                                     C.c_int, C.c_int, C.POINTER(vp)]
+        L.ipco_auto_interp.argtypes = [vp, C.c_int, C.c_int, i64p, C.c_int, C.c_double, C.c_int,
+                                       C.POINTER(C.c_int)]
         L.ipco_export.argtypes = [vp, vp, u64p]
         L.ipco_import.argtypes = [vp, C.c_uint64, C.POINTER(vp)]
         L.ipco_free_field.argtypes = [vp]
@@ -233,6 +235,16 @@ def compress(x: np.ndarray, eb: float, eb_mode: int = ABS, interp: int = CUBIC,
     _check(lib().ipco_compress(x.ctypes.data, dt, x.ndim, _dims(x.shape), eb_mode,
                                float(eb), interp, bound, C.byref(h)), "ipco_compress")
     return Field(h.value, x.shape, x.dtype)
+
+
+def auto_interp(x: np.ndarray, eb: float, eb_mode: int = ABS, bound: int = STRICT) -> int:
+    """The interpolation mode compress(..., interp=AUTO) takes for x."""
+    x = np.ascontiguousarray(x)
+    dt = F32 if x.dtype == np.float32 else F64
+    m = C.c_int(-1)
+    _check(lib().ipco_auto_interp(x.ctypes.data, dt, x.ndim, _dims(x.shape), eb_mode, float(eb),
+                                  bound, C.byref(m)), "ipco_auto_interp")
+    return m.value
 
 
 def compress_rc(x: np.ndarray, eb: float, eb_mode: int = ABS, interp: int = CUBIC,

@@ -188,4 +188,4 @@ def test_quadratic_mode_errors_and_costs(oracle):
     for E in (1e-2, 1e-3):
         y, v = f.retrieve(oracle.EB, E)
         assert np.abs(y.astype(np.float64) - x).max() <= v.selection()[2]
-    assert oracle.compress_rc(x, 1e-3, interp=3) == oracle.EINVAL
+    assert oracle.compress_rc(x, 1e-3, interp=4) == oracle.EINVAL  # 3 is the per-field choice
