@@ -55,8 +55,14 @@ typedef enum { IPC_F32 = 0, IPC_F64 = 1 } ipc_dtype;
  * target missing one far neighbour takes Eq. 1 (IPC_CUBIC) or the
  * three-point quadratic through its two near neighbours and the far one
  * that exists (IPC_CUBIC_QUAD: weights 3/8, 6/8, -1/8, infinity norm 1.25,
- * so p and the error model are the cubic ones). */
-typedef enum { IPC_LINEAR = 0, IPC_CUBIC = 1, IPC_CUBIC_QUAD = 2 } ipc_interp;
+ * so p and the error model are the cubic ones).
+ * IPC_INTERP_AUTO (compression only) chooses one of the three per field:
+ * the mode whose container is smallest on the centred block of extents
+ * min(N_d, c), c = 2^20 / 1024 / 128 for 1 / 2 / 3 dimensions (first index
+ * floor((N_d - e_d) / 2)), compressed with the whole field's absolute error
+ * bound; the lower mode on a tie. The container records the chosen mode. It
+ * costs a range pass (relative bounds) and three compressions of the block. */
+typedef enum { IPC_LINEAR = 0, IPC_CUBIC = 1, IPC_CUBIC_QUAD = 2, IPC_INTERP_AUTO = 3 } ipc_interp;
 /* Error bound absolute, or relative to the value range (max - min). */
 typedef enum { IPC_EB_ABS = 0, IPC_EB_REL = 1 } ipc_eb_mode;
 /* Error model of the loader (Sec. 5.1, Theorem 1): STRICT amplifies every

@@ -1222,6 +1222,177 @@ int compress_fields(std::vector<ipc_field*>& fs, const std::vector<const void*>&
   return IPC_OK;
 }
 
+// Per-field choice of the interpolation (IPC_INTERP_AUTO): the mode whose
+// container is smallest on the centred block of extents min(N_d, c),
+// c = 2^20 / 1024 / 128 for 1 / 2 / 3 dimensions (first index
+// floor((N_d - e_d) / 2)), compressed with the whole field's absolute error
+// bound; the lower mode on a tie. The whole fields' ranges (relative
+// bounds) take one range launch per element type, the blocks are copied
+// out with strided copies, and every block's three trial compressions run
+// as one batch per element type.
+struct AutoItem {
+  const void* d_in;
+  int dtype, ndim;
+  int64_t dims[3];
+  int eb_mode, bound;
+  double eb;
+  int mode;  // out: the chosen interpolation
+};
+
+int resolve_auto(std::vector<AutoItem>& v, cudaStream_t st) {
+  const size_t na = v.size();
+  if (na == 0) return IPC_OK;
+  int rc;
+  struct DevFree {
+    void* p = nullptr;
+    cudaStream_t s;
+    ~DevFree() { if (p) cudaFreeAsync(p, s); }
+  };
+  // the absolute bound of every field
+  std::vector<double> eb_abs(na);
+  std::vector<size_t> order;  // relative-bound fields, by element type
+  for (int dt = 0; dt < 2; ++dt)
+    for (size_t i = 0; i < na; ++i)
+      if (v[i].dtype == dt && v[i].eb_mode == IPC_EB_REL) order.push_back(i);
+  for (size_t i = 0; i < na; ++i)
+    if (v[i].eb_mode != IPC_EB_REL) eb_abs[i] = v[i].eb;
+  if (!order.empty()) {
+    const size_t nr = order.size();
+    DevFree acc{nullptr, st};
+    if ((rc = dalloc(&acc.p, 40 * nr, st))) return rc;
+    unsigned long long* a = (unsigned long long*)acc.p;  // [4 per field | first value per field]
+    if ((rc = upload_staged(a, 32 * nr, st, [&](uint8_t* h) {
+           unsigned long long* w = reinterpret_cast<unsigned long long*>(h);
+           for (size_t k = 0; k < nr; ++k) {
+             w[4 * k] = ~0ULL;
+             w[4 * k + 1] = w[4 * k + 2] = w[4 * k + 3] = 0ULL;
+           }
+         })))
+      return rc;
+    for (size_t k0 = 0; k0 < nr;) {
+      const int dt = v[order[k0]].dtype;
+      RangeBatch rb{};
+      int nb = 0;
+      while (k0 + nb < nr && nb < kRangeBatch && v[order[k0 + nb]].dtype == dt) {
+        const AutoItem& it = v[order[k0 + nb]];
+        rb.x[nb] = it.d_in;
+        rb.n[nb] = (uint64_t)it.dims[0] * (uint64_t)(it.ndim > 1 ? it.dims[1] : 1) *
+                   (uint64_t)(it.ndim > 2 ? it.dims[2] : 1);
+        ++nb;
+      }
+      rb.acc = a + 4 * k0;
+      rb.x0 = a + 4 * nr + k0;
+      CU(launch_range_batch(dt, rb, nb, 0, st));
+      k0 += nb;
+    }
+    std::vector<unsigned long long> h(4 * nr);
+    CU(cudaMemcpyAsync(h.data(), a, 32 * nr, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < nr; ++k) {
+      if (h[4 * k + 3] == 0)
+        return fail(IPC_EINVAL, "relative error bound on a field without finite values");
+      const double r = okey_to_double(h[4 * k + 1]) - okey_to_double(h[4 * k]);
+      const size_t i = order[k];
+      eb_abs[i] = r > 0 ? v[i].eb * r : v[i].eb;
+    }
+  }
+  for (size_t i = 0; i < na; ++i)
+    if (!(eb_abs[i] > 0) || !std::isfinite(eb_abs[i]))
+      return fail(IPC_EINVAL, "error bound must be > 0 and finite");
+  // the blocks, one after another in one allocation
+  std::vector<std::array<int64_t, 3>> ext(na);
+  std::vector<uint64_t> boff(na);
+  uint64_t tot = 0;
+  for (size_t i = 0; i < na; ++i) {
+    const AutoItem& it = v[i];
+    const int64_t cap = it.ndim == 1 ? (int64_t)1 << 20 : it.ndim == 2 ? 1024 : 128;
+    uint64_t n = it.dtype == IPC_F32 ? 4 : 8;
+    for (int d = 0; d < it.ndim; ++d) {
+      ext[i][d] = std::min<int64_t>(it.dims[d], cap);
+      n *= (uint64_t)ext[i][d];
+    }
+    boff[i] = tot;
+    tot += (n + 255) & ~uint64_t(255);
+  }
+  DevFree blocks{nullptr, st};
+  if ((rc = dalloc(&blocks.p, tot, st))) return rc;
+  for (size_t i = 0; i < na; ++i) {
+    const AutoItem& it = v[i];
+    const size_t esz = it.dtype == IPC_F32 ? 4 : 8;
+    int64_t N[3] = {1, 1, 1}, e[3] = {1, 1, 1}, o[3] = {0, 0, 0};
+    for (int d = 0; d < it.ndim; ++d) {
+      N[3 - it.ndim + d] = it.dims[d];
+      e[3 - it.ndim + d] = ext[i][d];
+      o[3 - it.ndim + d] = (it.dims[d] - ext[i][d]) / 2;
+    }
+    const uint8_t* src = (const uint8_t*)it.d_in;
+    uint8_t* dst = (uint8_t*)blocks.p + boff[i];
+    if (e[0] == 1 && e[1] == 1) {  // one row (a 1-D field): a plain copy
+      CU(cudaMemcpyAsync(dst, src + (size_t)((o[0] * N[1] + o[1]) * N[2] + o[2]) * esz,
+                         (size_t)e[2] * esz, cudaMemcpyDeviceToDevice, st));
+      continue;
+    }
+    for (int64_t i0 = 0; i0 < e[0]; ++i0)
+      CU(cudaMemcpy2DAsync(dst + (size_t)(i0 * e[1] * e[2]) * esz, (size_t)e[2] * esz,
+                           src + (size_t)(((o[0] + i0) * N[1] + o[1]) * N[2] + o[2]) * esz,
+                           (size_t)N[2] * esz, (size_t)e[2] * esz, (size_t)e[1],
+                           cudaMemcpyDeviceToDevice, st));
+  }
+  // three trial compressions per block, one batch per element type
+  std::vector<ipc_field*> trial(3 * na, nullptr);
+  struct TrialFree {
+    std::vector<ipc_field*>& t;
+    ~TrialFree() {
+      for (auto* f : t)
+        if (f) {
+          free_field_device(f);
+          f->tag = kDeadTag;
+          delete f;
+        }
+    }
+  } tguard{trial};
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  for (size_t i = 0; i < na; ++i)
+    for (int m = 0; m < 3; ++m) {
+      ipc_field* f = new (std::nothrow) ipc_field();
+      if (!f) return fail(IPC_ENOMEM, "host allocation");
+      trial[3 * i + m] = f;
+      f->tag = kFieldTag;
+      if (!build_geo(v[i].ndim, ext[i].data(), v[i].dtype, &f->g)) return fail(IPC_EINVAL, "shape");
+      f->device = dev;
+      f->dtype = v[i].dtype;
+      f->interp = m;
+      f->bound = v[i].bound;
+      f->eb_mode = IPC_EB_ABS;
+      f->eb_user = eb_abs[i];
+    }
+  for (int dt = 0; dt < 2; ++dt) {
+    std::vector<ipc_field*> fs;
+    std::vector<const void*> ins;
+    for (size_t i = 0; i < na; ++i)
+      if (v[i].dtype == dt)
+        for (int m = 0; m < 3; ++m) {
+          fs.push_back(trial[3 * i + m]);
+          ins.push_back((const uint8_t*)blocks.p + boff[i]);
+        }
+    if (!fs.empty() && (rc = compress_fields(fs, ins, st))) return rc;
+  }
+  for (size_t i = 0; i < na; ++i) {
+    v[i].mode = 0;
+    uint64_t best = 0;
+    for (int m = 0; m < 3; ++m) {
+      const ipc_field* f = trial[3 * i + m];
+      const uint64_t bytes = f->mandatory + f->stream_bytes;
+      if (m == 0 || bytes < best) {
+        best = bytes;
+        v[i].mode = m;
+      }
+    }
+  }
+  return IPC_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Optimized loader (Sec. 5.2 / 5.3): the field's stage statistics and plane
 // sizes go to the host selector (ipc_select.cu).
@@ -1925,7 +2096,7 @@ int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims, int
   Nvtx nv_call("ipc compress");
   if (!d_in || !out) return fail(IPC_EINVAL, "null argument");
   if (dtype != IPC_F32 && dtype != IPC_F64) return fail(IPC_EINVAL, "dtype");
-  if (interp < IPC_LINEAR || interp > IPC_CUBIC_QUAD) return fail(IPC_EINVAL, "interp");
+  if (interp < IPC_LINEAR || interp > IPC_INTERP_AUTO) return fail(IPC_EINVAL, "interp");
   if (bound != IPC_BOUND_STRICT && bound != IPC_BOUND_PAPER) return fail(IPC_EINVAL, "bound");
   if (eb_mode != IPC_EB_ABS && eb_mode != IPC_EB_REL) return fail(IPC_EINVAL, "eb_mode");
   if (!std::isfinite(eb) || !(eb > 0)) return fail(IPC_EINVAL, "eb must be > 0 and finite");
@@ -1935,6 +2106,16 @@ int ipc_compress(const void* d_in, int dtype, int ndim, const int64_t* dims, int
   if (!build_geo(ndim, dims, dtype, &f->g)) {
     delete f;
     return fail(IPC_EINVAL, "shape");
+  }
+  if (interp == IPC_INTERP_AUTO) {
+    std::vector<AutoItem> a(1, AutoItem{d_in, dtype, ndim, {1, 1, 1}, eb_mode, bound, eb, -1});
+    for (int d = 0; d < ndim; ++d) a[0].dims[d] = dims[d];
+    const int rc = resolve_auto(a, (cudaStream_t)stream);
+    if (rc) {
+      delete f;
+      return rc;
+    }
+    interp = a[0].mode;
   }
   cudaGetDevice(&f->device);
   f->dtype = dtype;
@@ -2761,7 +2942,7 @@ int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, i
   for (int i = 0; i < nfields; ++i) {
     const ipc_batch_item& it = items[i];
     if (!it.d_in || (it.dtype != IPC_F32 && it.dtype != IPC_F64) ||
-        it.interp < IPC_LINEAR || it.interp > IPC_CUBIC_QUAD ||
+        it.interp < IPC_LINEAR || it.interp > IPC_INTERP_AUTO ||
         (it.bound != IPC_BOUND_STRICT && it.bound != IPC_BOUND_PAPER) ||
         (it.eb_mode != IPC_EB_ABS && it.eb_mode != IPC_EB_REL) || !std::isfinite(it.eb) ||
         !(it.eb > 0))
@@ -2792,6 +2973,21 @@ int ipc_compress_batch(int nfields, const ipc_batch_item* items, void* stream, i
     for (int i = 0; i < nfields; ++i) geo(i);
   for (int i = 0; i < nfields; ++i)
     if (!geo_ok[i]) return cleanup(fail(IPC_EINVAL, "shape"));
+  // the per-field interpolation choices, all in one pass
+  {
+    std::vector<AutoItem> a;
+    std::vector<int> who;
+    for (int i = 0; i < nfields; ++i)
+      if (items[i].interp == IPC_INTERP_AUTO) {
+        const ipc_batch_item& it = items[i];
+        a.push_back(AutoItem{it.d_in, it.dtype, it.ndim, {1, 1, 1}, it.eb_mode, it.bound, it.eb, -1});
+        for (int d = 0; d < it.ndim; ++d) a.back().dims[d] = it.dims[d];
+        who.push_back(i);
+      }
+    const int rc = resolve_auto(a, (cudaStream_t)stream);
+    if (rc) return cleanup(rc);
+    for (size_t k = 0; k < a.size(); ++k) all[who[k]]->interp = a[k].mode;
+  }
   for (int dt = 0; dt < 2; ++dt) {
     std::vector<ipc_field*> fs;
     std::vector<const void*> ins;

@@ -25,7 +25,7 @@ BOUNDS_LIB_PATH = os.path.join(HERE, "libipcomp_bounds.so")
 IPC_OK, IPC_EINVAL, IPC_EBOUND, IPC_EBUDGET = 0, -1, -2, -3
 IPC_ENOMEM, IPC_ECORRUPT, IPC_ECUDA, IPC_ETIMEOUT, IPC_EBUSY = -4, -5, -6, -7, -8
 IPC_F32, IPC_F64 = 0, 1
-IPC_LINEAR, IPC_CUBIC, IPC_CUBIC_QUAD = 0, 1, 2
+IPC_LINEAR, IPC_CUBIC, IPC_CUBIC_QUAD, IPC_INTERP_AUTO = 0, 1, 2, 3
 IPC_EB_ABS, IPC_EB_REL = 0, 1
 IPC_BOUND_STRICT, IPC_BOUND_PAPER = 0, 1
 IPC_TARGET_EB, IPC_TARGET_BITRATE = 0, 1
