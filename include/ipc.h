@@ -128,6 +128,14 @@ int ipc_autotune_clear(void);
  * CTAs per SM (0, 0: the default shape measured fastest). IPC_EINVAL when i
  * is out of range. Any output pointer may be NULL. */
 int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* per_sm);
+/* ipc_autotune_set -- records a shape in the table as ipc_autotune_retrieve
+ * would (replacing the entry of the same key), so that a table saved from
+ * ipc_autotune_entry can be restored in another process. Accepted shapes are
+ * those the tuner can record: (ns, per_sm) = (0, 0), or ns in {1, 2, 4} with
+ * ns = 2 only for M[2] <= 256 and ns = 4 only for M[2] <= 128, and
+ * 1 <= per_sm <= 4 (16-bit codes, or f32 with ns > 1) or 3 (otherwise).
+ * Host only. Errors: IPC_EINVAL (null M, dtype, w16, extents < 1, shape). */
+int ipc_autotune_set(int dtype, int w16, const int64_t* M, int ns, int per_sm);
 
 /* Refinement forms of a view (Algorithm 2, Sec. 4.3).
  *  IPC_REFINE_CANONICAL   : a refinement reconstructs from the union of the

@@ -2316,6 +2316,21 @@ int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* pe
   return IPC_OK;
 }
 
+int ipc_autotune_set(int dtype, int w16, const int64_t* M, int ns, int per_sm) {
+  g_err.clear();
+  if (!M) return fail(IPC_EINVAL, "null argument");
+  if ((dtype != IPC_F32 && dtype != IPC_F64) || (w16 != 0 && w16 != 1))
+    return fail(IPC_EINVAL, "dtype or code width");
+  if (M[0] < 1 || M[1] < 1 || M[2] < 1) return fail(IPC_EINVAL, "extents");
+  const bool dflt = ns == 0 && per_sm == 0;
+  if (!dflt && ((ns != 1 && ns != 2 && ns != 4) || !retrieve_ns_ok(M[2], ns) || per_sm < 1 ||
+                per_sm > retrieve_max_per_sm(dtype, w16, ns)))
+    return fail(IPC_EINVAL, "not a shape the tuner records");
+  std::lock_guard<std::mutex> lk(g_shape_mu);
+  g_shapes[ShapeKey{dtype, w16, M[0], M[1], M[2]}] = RetrieveShape{ns, per_sm};
+  return IPC_OK;
+}
+
 int ipc_refine(ipc_view* v, ipc_target target, void* d_out, void* stream) {
   g_err.clear();
   Nvtx nv_call("ipc refine");

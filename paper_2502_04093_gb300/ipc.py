@@ -98,6 +98,7 @@ def lib() -> C.CDLL:
     L.ipc_autotune_retrieve.argtypes = [vp, ipc_target, vp, vp, C.c_int, C.POINTER(C.c_int)]
     L.ipc_autotune_entry.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p,
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.ipc_autotune_set.argtypes = [C.c_int, C.c_int, i64p, C.c_int, C.c_int]
     L.ipc_free.argtypes = [vp]
     L.ipc_selection.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
                                 C.POINTER(C.c_double)]
@@ -220,6 +221,34 @@ def ipc_autotune_entries():
             return out
         out.append((dt.value, w.value, tuple(M), ns.value, ps.value))
         i += 1
+
+
+def ipc_autotune_set(dtype: int, w16: int, M, ns: int, per_sm: int) -> None:
+    """Record one shape in the table (as ipc_autotune_entries lists them)."""
+    arr = (C.c_int64 * 3)(*[int(m) for m in M])
+    _check(lib().ipc_autotune_set(int(dtype), int(w16), arr, int(ns), int(per_sm)),
+           "ipc_autotune_set")
+
+
+def ipc_autotune_save(path: str) -> int:
+    """Write the table to a JSON file; returns the number of entries."""
+    import json
+    ents = [{"dtype": d, "w16": w, "M": list(M), "ns": ns, "per_sm": ps}
+            for d, w, M, ns, ps in ipc_autotune_entries()]
+    with open(path, "w") as fh:
+        json.dump({"launch_shapes": ents}, fh, indent=1)
+    return len(ents)
+
+
+def ipc_autotune_load(path: str) -> int:
+    """Add the entries of a file written by ipc_autotune_save to the table
+    (each checked by ipc_autotune_set); returns their number."""
+    import json
+    with open(path) as fh:
+        ents = json.load(fh)["launch_shapes"]
+    for e in ents:
+        ipc_autotune_set(e["dtype"], e["w16"], e["M"], e["ns"], e["per_sm"])
+    return len(ents)
 
 
 def ipc_retrieve_ex(field, kind: int, value: float, out, refine_mode: int, stream=None):

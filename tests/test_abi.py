@@ -74,3 +74,40 @@ def test_autotune_table_without_gpu(libipc):
     n = ctypes.c_int()
     rc = libipc.ipc_autotune_retrieve(None, Target(0, 1e-3), None, None, 3, ctypes.byref(n))
     assert rc == -1
+
+
+def test_autotune_table_save_and_restore(tmp_path):
+    """The shape table round-trips through a file (host only): the shapes
+    the tuner can record are accepted and listed back in key order, others
+    are refused, and a restored table equals the saved one."""
+    from paper_2502_04093_gb300 import build, ipc
+    build.build()
+    ipc.ipc_autotune_clear()
+    good = [(0, 1, (257, 257, 129), 2, 4), (0, 0, (129, 129, 65), 4, 4),
+            (1, 0, (513, 513, 513), 1, 3), (1, 1, (65, 65, 33), 0, 0)]
+    for d, w, M, ns, ps in good:
+        ipc.ipc_autotune_set(d, w, M, ns, ps)
+    ipc.ipc_autotune_set(0, 1, (257, 257, 129), 1, 2)  # same key: replaced
+    want = sorted([(0, 1, (257, 257, 129), 1, 2)] + good[1:])
+    assert ipc.ipc_autotune_entries() == want
+    bad = [(2, 0, (9, 9, 9), 1, 1),       # element type
+           (0, 2, (9, 9, 9), 1, 1),       # code width
+           (0, 0, (0, 9, 9), 1, 1),       # extents
+           (0, 0, (9, 9, 300), 2, 1),     # two planes need rows of at most 256
+           (0, 0, (9, 9, 200), 4, 1),     # four need at most 128
+           (0, 0, (9, 9, 9), 3, 1),       # planes per tile
+           (1, 0, (9, 9, 9), 1, 4),       # f64, 32-bit codes: at most 3 per SM
+           (0, 0, (9, 9, 9), 1, 0),       # a tuned shape has CTAs per SM
+           (0, 0, (9, 9, 9), 0, 2)]
+    for d, w, M, ns, ps in bad:
+        with pytest.raises(ipc.IpcError) as e:
+            ipc.ipc_autotune_set(d, w, M, ns, ps)
+        assert e.value.rc == ipc.IPC_EINVAL
+    assert ipc.ipc_autotune_entries() == want
+    p = str(tmp_path / "shapes.json")
+    assert ipc.ipc_autotune_save(p) == 4
+    ipc.ipc_autotune_clear()
+    assert ipc.ipc_autotune_entries() == []
+    assert ipc.ipc_autotune_load(p) == 4
+    assert ipc.ipc_autotune_entries() == want
+    ipc.ipc_autotune_clear()
