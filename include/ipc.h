@@ -289,6 +289,27 @@ int ipc_encode_container(const void* raw, uint64_t raw_len, int block_log2, void
 int ipc_decode_container(const void* coded, uint64_t coded_len, void* out, uint64_t* out_len,
                          int nthreads);
 
+/* ---- error metrics (Sec. 3.1.1 definitions; host, FP64) ------------------- */
+/* Deviation of a reconstruction y from the original x (n host values of
+ * `dtype`, compared in FP64). Over the positions where x is finite:
+ * max_abs_err = max |x - y| (the L-inf error), mse = mean (x - y)^2 over
+ * those where y is finite too (0 when there are none),
+ * range = max(x) - min(x), psnr = 20 log10(range / sqrt(mse)) (+inf when
+ * mse = 0, -inf when range = 0 < mse). A non-finite y there counts in
+ * `nonfinite_mismatch` and leaves the sums (max_abs_err is then +inf).
+ * Where x is not finite, y must hold the same class (NaN, +Inf, -Inf) --
+ * the container stores those values exactly -- else it counts in
+ * `nonfinite_mismatch`. `finite` = the finite positions of x. Sums run in
+ * fixed chunks combined in order, so the result does not depend on the
+ * number of host threads. Errors: IPC_EINVAL (null pointer with n > 0,
+ * dtype). */
+typedef struct {
+  double max_abs_err, mse, psnr, range;
+  uint64_t finite, nonfinite_mismatch;
+} ipc_error_metrics;
+int ipc_error_metrics_host(const void* x, const void* y, int dtype, uint64_t n,
+                           ipc_error_metrics* out);
+
 /* ---- batches (uneven fields in one launch per level) --------------------- */
 /* One field of a batched compression; the fields are the same as ipc_compress
  * arguments. dims[] holds ndim extents. */

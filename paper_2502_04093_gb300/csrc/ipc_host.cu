@@ -2316,6 +2316,72 @@ int ipc_autotune_entry(int i, int* dtype, int* w16, int64_t* M, int* ns, int* pe
   return IPC_OK;
 }
 
+int ipc_error_metrics_host(const void* x, const void* y, int dtype, uint64_t n,
+                           ipc_error_metrics* out) {
+  g_err.clear();
+  if (!out || (n && (!x || !y))) return fail(IPC_EINVAL, "null argument");
+  if (dtype != IPC_F32 && dtype != IPC_F64) return fail(IPC_EINVAL, "dtype");
+  struct Part {
+    double maxe = 0, sse = 0, mn = 0, mx = 0;
+    uint64_t fin = 0, bad = 0, cnt = 0;  // cnt: pairs in the sums
+  };
+  constexpr uint64_t kChunk = uint64_t(1) << 16;
+  const uint64_t nc = (n + kChunk - 1) / kChunk;
+  std::vector<Part> part(nc);
+  auto chunk = [&](int c) {
+    Part p;
+    const uint64_t a = (uint64_t)c * kChunk, b = std::min(n, a + kChunk);
+    for (uint64_t i = a; i < b; ++i) {
+      const double xv = dtype == IPC_F32 ? (double)((const float*)x)[i] : ((const double*)x)[i];
+      const double yv = dtype == IPC_F32 ? (double)((const float*)y)[i] : ((const double*)y)[i];
+      if (!std::isfinite(xv)) {
+        const bool same = std::isnan(xv) ? std::isnan(yv) : yv == xv;
+        if (!same) ++p.bad;
+        continue;
+      }
+      if (p.fin == 0) p.mn = p.mx = xv;
+      p.mn = std::min(p.mn, xv);
+      p.mx = std::max(p.mx, xv);
+      ++p.fin;
+      if (!std::isfinite(yv)) {
+        ++p.bad;
+        p.maxe = HUGE_VAL;
+        continue;
+      }
+      const double d = xv - yv;
+      p.maxe = std::max(p.maxe, std::fabs(d));
+      p.sse += d * d;
+      ++p.cnt;
+    }
+    part[c] = p;
+  };
+  if (nc >= 8)
+    HostPool::get().run((int)nc, chunk);
+  else
+    for (uint64_t c = 0; c < nc; ++c) chunk((int)c);
+  Part t;
+  for (const Part& p : part) {  // in chunk order
+    if (p.fin) {
+      t.mn = t.fin ? std::min(t.mn, p.mn) : p.mn;
+      t.mx = t.fin ? std::max(t.mx, p.mx) : p.mx;
+    }
+    t.fin += p.fin;
+    t.bad += p.bad;
+    t.cnt += p.cnt;
+    t.maxe = std::max(t.maxe, p.maxe);
+    t.sse += p.sse;
+  }
+  out->finite = t.fin;
+  out->nonfinite_mismatch = t.bad;
+  out->max_abs_err = t.maxe;
+  out->range = t.fin ? t.mx - t.mn : 0.0;
+  out->mse = t.cnt ? t.sse / (double)t.cnt : 0.0;
+  if (out->mse == 0.0) out->psnr = HUGE_VAL;
+  else if (out->range == 0.0) out->psnr = -HUGE_VAL;
+  else out->psnr = 20.0 * std::log10(out->range / std::sqrt(out->mse));
+  return IPC_OK;
+}
+
 int ipc_autotune_set(int dtype, int w16, const int64_t* M, int ns, int per_sm) {
   g_err.clear();
   if (!M) return fail(IPC_EINVAL, "null argument");

@@ -43,6 +43,11 @@ class ipc_batch_item(C.Structure):
                 ("interp", C.c_int), ("bound", C.c_int)]
 
 
+class ipc_error_metrics(C.Structure):
+    _fields_ = [("max_abs_err", C.c_double), ("mse", C.c_double), ("psnr", C.c_double),
+                ("range", C.c_double), ("finite", C.c_uint64), ("nonfinite_mismatch", C.c_uint64)]
+
+
 class ipc_server_cfg(C.Structure):
     _fields_ = [("mem_budget", C.c_uint64), ("hbm_reserve", C.c_uint64), ("max_batch", C.c_int),
                 ("max_inflight", C.c_int), ("nstreams", C.c_int), ("plain", C.c_int),
@@ -99,6 +104,7 @@ def lib() -> C.CDLL:
     L.ipc_autotune_entry.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), i64p,
                                      C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.ipc_autotune_set.argtypes = [C.c_int, C.c_int, i64p, C.c_int, C.c_int]
+    L.ipc_error_metrics_host.argtypes = [vp, vp, C.c_int, C.c_uint64, C.POINTER(ipc_error_metrics)]
     L.ipc_free.argtypes = [vp]
     L.ipc_selection.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
                                 C.POINTER(C.c_double)]
@@ -221,6 +227,23 @@ def ipc_autotune_entries():
             return out
         out.append((dt.value, w.value, tuple(M), ns.value, ps.value))
         i += 1
+
+
+def ipc_error_metrics_host(x, y) -> dict:
+    """L-inf error, MSE, value range and PSNR of y against x (host arrays of
+    one float type, compared in FP64; Sec. 3.1.1 definitions)."""
+    import numpy as np
+    x = np.ascontiguousarray(x)
+    y = np.ascontiguousarray(y)
+    if x.shape != y.shape or x.dtype != y.dtype or x.dtype not in (np.float32, np.float64):
+        raise IpcError(IPC_EINVAL, "ipc_error_metrics_host",
+                       "x and y must be float32 or float64 arrays of one shape and type")
+    m = ipc_error_metrics()
+    _check(lib().ipc_error_metrics_host(x.ctypes.data, y.ctypes.data,
+                                        IPC_F32 if x.dtype == np.float32 else IPC_F64, x.size,
+                                        C.byref(m)), "ipc_error_metrics_host")
+    return {"max_abs_err": m.max_abs_err, "mse": m.mse, "psnr": m.psnr, "range": m.range,
+            "finite": m.finite, "nonfinite_mismatch": m.nonfinite_mismatch}
 
 
 def ipc_autotune_set(dtype: int, w16: int, M, ns: int, per_sm: int) -> None:
