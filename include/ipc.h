@@ -269,18 +269,20 @@ int ipc_field_resident(const ipc_field* f, int* b_per_level, int* nlevels);
  * system (rANS, 12-bit symbol frequencies, 32-bit state) or stored when
  * coding does not shrink it. Host memory only; blocks run on up to
  * `nthreads` host threads (0: the host's cores, at most 16). The coded
- * form: u32 magic "IPCZ", u32 version 1, u64 raw length, u32 block_log2,
+ * form: u32 magic "IPCZ", u32 version 2, u64 raw length, u32 block_log2,
  * u32 block count, u32 record size per block, the records (u8 mode 0 +
- * raw bytes, or u8 mode 1 + 256 u16 frequencies + the rANS bytes, final
- * encoder state first); little-endian. Deterministic: equal inputs give
- * equal bytes on every host.
+ * raw bytes, or u8 mode 2 + 256 u16 frequencies + the bytes of two rANS
+ * states that code the symbols in turn -- symbol i with state i mod 2 --
+ * over one stream, the two final encoder states first); little-endian.
+ * Deterministic: equal inputs give equal bytes on every host.
  * out == NULL: *out_len receives an upper bound of the coded size.
  * Otherwise *out_len is the capacity on entry and the size on return.
  * Errors: IPC_EINVAL (null pointer, block size, capacity too small). */
 int ipc_encode_container(const void* raw, uint64_t raw_len, int block_log2, void* out,
                          uint64_t* out_len, int nthreads);
 
-/* ipc_decode_container -- inverse of ipc_encode_container. out == NULL:
+/* ipc_decode_container -- inverse of ipc_encode_container; version 1
+ * containers (mode 1 records: one state) are read too. out == NULL:
  * *out_len receives the decoded size (read from the header). Otherwise
  * *out_len is the capacity on entry and the size on return. Errors:
  * IPC_ECORRUPT (magic, version, block table, or a block that does not

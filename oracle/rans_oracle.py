@@ -15,9 +15,17 @@ shifting out low bytes of x while x >= 2^15 f_s (so that x' < 2^31); the
 decoder inverts it: s is the symbol whose range holds x mod M, x =
 f_s * floor(x / M) + (x mod M) - c_s, then bytes are shifted in while
 x < L. Symbols are coded last to first, so they decode first to last.
+
+Version 2 records (mode 2) run two such states that take the symbols in
+turn, symbol i with state i mod 2, over one shared byte stream
+(interleaved rANS, Giesen 2014): the encoder walks the symbols backwards,
+each step shifting bytes out of its own state; the stream starts with the
+final states 0 and 1, and the decoder, walking forwards, reads each
+symbol's bytes into the state that decoded it. Version 1 records (mode 1)
+have one state; both versions are read.
 """
 MAGIC = 0x5A435049  # "IPCZ"
-VERSION = 1
+VERSION = 2
 SCALE = 12
 M = 1 << SCALE
 L = 1 << 23
@@ -48,23 +56,25 @@ def frequencies(block: bytes):
     return f
 
 
-def encode_block(block: bytes) -> bytes:
+def encode_block(block: bytes, nstates: int = 2) -> bytes:
     f = frequencies(block)
     cum = [0] * 256
     for s in range(1, 256):
         cum[s] = cum[s - 1] + f[s - 1]
     out = bytearray()  # emitted bytes, in emission order (reversed below)
-    x = L
-    for v in reversed(block):
-        while x >= ((L >> SCALE) << 8) * f[v]:
-            out.append(x & 0xFF)
-            x >>= 8
-        x = (x // f[v]) * M + (x % f[v]) + cum[v]
-    stream = x.to_bytes(4, "little") + bytes(reversed(out))
+    x = [L] * nstates
+    for i in range(len(block) - 1, -1, -1):
+        v = block[i]
+        j = i % nstates
+        while x[j] >= ((L >> SCALE) << 8) * f[v]:
+            out.append(x[j] & 0xFF)
+            x[j] >>= 8
+        x[j] = (x[j] // f[v]) * M + (x[j] % f[v]) + cum[v]
+    stream = b"".join(xj.to_bytes(4, "little") for xj in x) + bytes(reversed(out))
     if 1 + 512 + len(stream) >= 1 + len(block):
         return b"\x00" + bytes(block)
     table = b"".join(fs.to_bytes(2, "little") for fs in f)
-    return b"\x01" + table + stream
+    return bytes([nstates]) + table + stream
 
 
 def decode_block(rec: bytes, n: int) -> bytes:
@@ -74,7 +84,8 @@ def decode_block(rec: bytes, n: int) -> bytes:
         if len(rec) != 1 + n:
             raise CodecError("stored record size")
         return bytes(rec[1:])
-    if rec[0] != 1 or len(rec) < 1 + 512 + 4:
+    nstates = rec[0]
+    if nstates not in (1, 2) or len(rec) < 1 + 512 + 4 * nstates:
         raise CodecError("record mode")
     f = [int.from_bytes(rec[1 + 2 * s:3 + 2 * s], "little") for s in range(256)]
     if sum(f) != M:
@@ -86,29 +97,32 @@ def decode_block(rec: bytes, n: int) -> bytes:
     for s in range(256):
         sym += [s] * f[s]
     p = 1 + 512
-    x = int.from_bytes(rec[p:p + 4], "little")
-    p += 4
+    x = [int.from_bytes(rec[p + 4 * j:p + 4 * j + 4], "little") for j in range(nstates)]
+    p += 4 * nstates
     out = bytearray()
-    for _ in range(n):
-        slot = x % M
+    for i in range(n):
+        j = i % nstates
+        slot = x[j] % M
         s = sym[slot]
         out.append(s)
-        x = f[s] * (x // M) + slot - cum[s]
-        while x < L:
+        x[j] = f[s] * (x[j] // M) + slot - cum[s]
+        while x[j] < L:
             if p >= len(rec):
                 raise CodecError("stream overrun")
-            x = (x << 8) | rec[p]
+            x[j] = (x[j] << 8) | rec[p]
             p += 1
-    if p != len(rec) or x != L:
-        raise CodecError("stream does not end in the initial state")
+    if p != len(rec) or any(xj != L for xj in x):
+        raise CodecError("stream does not end in the initial states")
     return bytes(out)
 
 
-def encode(raw: bytes, block_log2: int = 20) -> bytes:
+def encode(raw: bytes, block_log2: int = 20, version: int = VERSION) -> bytes:
+    """Version 2 (two states per record), or version 1 (one state) as
+    earlier containers hold."""
     bs = 1 << block_log2
     blocks = [raw[i:i + bs] for i in range(0, len(raw), bs)]
-    recs = [encode_block(b) for b in blocks]
-    head = (MAGIC.to_bytes(4, "little") + VERSION.to_bytes(4, "little") +
+    recs = [encode_block(b, nstates=2 if version == 2 else 1) for b in blocks]
+    head = (MAGIC.to_bytes(4, "little") + version.to_bytes(4, "little") +
             len(raw).to_bytes(8, "little") + block_log2.to_bytes(4, "little") +
             len(blocks).to_bytes(4, "little"))
     return head + b"".join(len(r).to_bytes(4, "little") for r in recs) + b"".join(recs)
@@ -116,7 +130,7 @@ def encode(raw: bytes, block_log2: int = 20) -> bytes:
 
 def decode(coded: bytes) -> bytes:
     if len(coded) < 24 or int.from_bytes(coded[0:4], "little") != MAGIC or \
-            int.from_bytes(coded[4:8], "little") != VERSION:
+            int.from_bytes(coded[4:8], "little") not in (1, 2):
         raise CodecError("header")
     n = int.from_bytes(coded[8:16], "little")
     lg = int.from_bytes(coded[16:20], "little")

@@ -4,14 +4,20 @@
 // turns its bytes (or any byte string) into a coded container and back.
 //
 // Coded container (little-endian):
-//   u32 magic "IPCZ", u32 version 1, u64 raw length, u32 log2 of the block
-//   size, u32 block count, then one u32 per block (its record's bytes),
-//   then the block records. A block is the next 2^log2 raw bytes (the last
-//   one shorter). Record: u8 mode; mode 0 holds the raw bytes; mode 1 holds
-//   256 u16 symbol frequencies (summing to 4096) and an order-0 rANS byte
-//   stream (range asymmetric numeral systems, Duda 2013; 32-bit state kept
-//   in [2^23, 2^31), byte-wise renormalisation) whose first four bytes are
-//   the encoder's final state.
+//   u32 magic "IPCZ", u32 version (2; version 1 is still read), u64 raw
+//   length, u32 log2 of the block size, u32 block count, then one u32 per
+//   block (its record's bytes), then the block records. A block is the next
+//   2^log2 raw bytes (the last one shorter). Record: u8 mode; mode 0 holds
+//   the raw bytes; modes 1 and 2 hold 256 u16 symbol frequencies (summing to
+//   4096) and an order-0 rANS byte stream (range asymmetric numeral
+//   systems, Duda 2013; 32-bit states kept in [2^23, 2^31), byte-wise
+//   renormalisation). Mode 1 (written by version 1) has one state, whose
+//   final value leads the stream. Mode 2 (written now) has two states that
+//   take the symbols in turn -- symbol i uses state i mod 2 -- and share the
+//   byte stream (interleaved rANS, Giesen 2014): the stream leads with the
+//   final values of states 0 and 1, and each symbol's renormalisation bytes
+//   follow in symbol order. Two states let the decoder work on two
+//   independent dependency chains.
 // Frequencies: f_s = 0 for absent bytes, else max(1, floor(c_s 4096 / n));
 // the difference to 4096 is then settled one unit at a time on the symbol
 // of largest frequency (lowest byte value on ties; never below 1). A block
@@ -31,7 +37,7 @@
 namespace {
 
 constexpr uint32_t kMagicZ = 0x5A435049u;  // "IPCZ"
-constexpr uint32_t kVersionZ = 1;
+constexpr uint32_t kVersionZ = 2;  // written; 1 and 2 are read
 constexpr int kScale = 12;
 constexpr uint32_t kTotal = 1u << kScale;
 constexpr uint32_t kLow = 1u << 23;  // lower end of the normalised state interval
@@ -125,13 +131,14 @@ uint64_t encode_block(const uint8_t* src, uint64_t n, uint8_t* rec, std::vector<
   }
   // the rANS bytes are written backwards from the end of a scratch buffer:
   // at most 2 bytes per symbol (a frequency >= 1 of 4096 adds at most 12
-  // bits of state) plus the final state
-  tmp->resize(2 * n + 8);
+  // bits of state) plus the two final states
+  tmp->resize(2 * n + 12);
   uint8_t* const end = tmp->data() + tmp->size();
   uint8_t* p = end;
-  uint32_t x = kLow;
+  uint32_t xs[2] = {kLow, kLow};
   for (uint64_t i = n; i-- > 0;) {
     const uint32_t s = src[i];
+    uint32_t& x = xs[i & 1];
     // shift out low bytes while x >= xmax_s: with x < 2^31 and
     // xmax_s >= 2^19 that is at most two, decided without a branch (the
     // count is data-dependent); both candidate bytes are stored, p moves by
@@ -146,14 +153,16 @@ uint64_t encode_block(const uint8_t* src, uint64_t n, uint8_t* rec, std::vector<
     x = (q << kScale) + (x - q * f[s]) + start[s];
   }
   p -= 4;
-  put32(p, x);
+  put32(p, xs[1]);
+  p -= 4;
+  put32(p, xs[0]);
   const uint64_t coded = (uint64_t)(end - p);
   if (1 + kTable + coded >= 1 + n) {  // no gain: stored
     rec[0] = 0;
     std::memcpy(rec + 1, src, n);
     return 1 + n;
   }
-  rec[0] = 1;
+  rec[0] = 2;
   for (int s = 0; s < 256; ++s) {
     rec[1 + 2 * s] = (uint8_t)(f[s] & 0xFF);
     rec[2 + 2 * s] = (uint8_t)(f[s] >> 8);
@@ -174,7 +183,8 @@ bool decode_block(const uint8_t* rec, uint64_t len, uint8_t* dst, uint64_t n,
     std::memcpy(dst, rec + 1, n);
     return true;
   }
-  if (rec[0] != 1 || len < 1 + kTable + 4) return false;
+  const int nstates = rec[0];
+  if ((nstates != 1 && nstates != 2) || len < 1 + kTable + 4 * (uint64_t)nstates) return false;
   uint32_t f[256], acc = 0;
   for (int s = 0; s < 256; ++s) {
     f[s] = (uint32_t)rec[1 + 2 * s] | ((uint32_t)rec[2 + 2 * s] << 8);
@@ -189,15 +199,17 @@ bool decode_block(const uint8_t* rec, uint64_t len, uint8_t* dst, uint64_t n,
     for (uint32_t k = 0; k < f[s]; ++k, ++slot) tab[slot] = s | ((f[s] - 1) << 8) | (k << 20);
   const uint8_t* p = rec + 1 + kTable;
   const uint8_t* const end = rec + len;
-  uint32_t x = get32(p);
-  p += 4;
-  for (uint64_t i = 0; i < n; ++i) {
+  uint32_t xs[2] = {get32(p), nstates == 2 ? get32(p + 4) : kLow};
+  p += 4 * nstates;
+  bool ok = true;
+  // one symbol from state x, then its renormalisation: x >= f (2^23 >> 12)
+  // >= 2^11 after the step, so at most two bytes bring it back to
+  // [2^23, 2^31); the count is taken without a branch while two bytes are
+  // left to read, byte by byte near the end of the stream
+  auto step = [&](uint32_t& x, uint8_t* out) {
     const uint32_t e = tab[x & (kTotal - 1)];
-    dst[i] = (uint8_t)e;
+    *out = (uint8_t)e;
     x = (((e >> 8) & 0xFFF) + 1) * (x >> kScale) + (e >> 20);
-    // x >= f (2^23 >> 12) >= 2^11 now: at most two bytes bring it back to
-    // [2^23, 2^31); the count is taken without a branch while two bytes are
-    // left to read, byte by byte near the end of the stream
     if (end - p >= 2) {
       const uint32_t nb = (uint32_t)(x < kLow) + (uint32_t)(x < (kLow >> 8));
       const uint32_t two = ((uint32_t)p[0] << 8) | p[1];
@@ -205,13 +217,27 @@ bool decode_block(const uint8_t* rec, uint64_t len, uint8_t* dst, uint64_t n,
       p += nb;
     } else {
       while (x < kLow) {
-        if (p >= end) return false;
+        if (p >= end) {
+          ok = false;
+          x = kLow;  // ends the loop; the record is refused
+          break;
+        }
         x = (x << 8) | *p++;
       }
     }
+  };
+  if (nstates == 1) {
+    for (uint64_t i = 0; i < n && ok; ++i) step(xs[0], dst + i);
+  } else {
+    uint64_t i = 0;
+    for (; i + 1 < n && ok; i += 2) {
+      step(xs[0], dst + i);
+      step(xs[1], dst + i + 1);
+    }
+    if (i < n && ok) step(xs[0], dst + i);
   }
-  // the encoder started from the state kLow and used every byte
-  return p == end && x == kLow;
+  // the encoder started every state from kLow and used every byte
+  return ok && p == end && xs[0] == kLow && xs[1] == kLow;
 }
 
 int threads_for(int nthreads, uint64_t nblocks) {
@@ -292,7 +318,7 @@ int ipc_decode_container(const void* coded, uint64_t coded_len, void* out, uint6
   ipc::set_last_error("");
   if (!coded || !out_len) return err(IPC_EINVAL, "null argument");
   const uint8_t* c = (const uint8_t*)coded;
-  if (coded_len < kHead || get32(c) != kMagicZ || get32(c + 4) != kVersionZ)
+  if (coded_len < kHead || get32(c) != kMagicZ || (get32(c + 4) != 1 && get32(c + 4) != 2))
     return err(IPC_ECORRUPT, "not a coded container");
   const uint64_t raw_len = get64(c + 8);
   const uint32_t lg = get32(c + 16);

@@ -69,21 +69,26 @@ def test_stored_and_single_symbol_records():
     c = ipc.ipc_encode_container(raw, block_log2=12)
     assert len(c) == 24 + 4 + 1 + 4096 and c[28] == 0
     c = ipc.ipc_encode_container(b"\x42" * 4096, block_log2=12)
-    # one symbol of frequency 4096: the state never moves, no byte is emitted
-    assert len(c) == 24 + 4 + 1 + 512 + 4 and c[28] == 1
+    # one symbol of frequency 4096: the states never move, no byte is
+    # emitted; the record holds the two final states
+    assert len(c) == 24 + 4 + 1 + 512 + 8 and c[28] == 2
 
 
 def test_corrupt_inputs_rejected():
     raw = np.random.default_rng(2).geometric(0.3, 10000).astype(np.uint8).tobytes()
     c = ipc.ipc_encode_container(raw, block_log2=12)
-    bad = [b"XPCZ" + c[4:], c[:4] + b"\x02" + c[5:], c[:-1], c + b"\x00", c[:20]]
+    bad = [b"XPCZ" + c[4:], c[:4] + b"\x03" + c[5:], c[:-1], c + b"\x00", c[:20]]
     tab = bytearray(c)
     off = 24 + 4 * 3 + 1  # first record's frequency table (3 blocks)
     tab[off] ^= 1  # frequencies no longer sum to 4096
     bad.append(bytes(tab))
-    st = bytearray(c)
-    st[off + 512 + 2] ^= 0x40  # the first record's final state
-    bad.append(bytes(st))
+    for k in (2, 6):  # the first record's final states 0 and 1
+        st = bytearray(c)
+        st[off + 512 + k] ^= 0x40
+        bad.append(bytes(st))
+    md = bytearray(c)
+    md[off - 1] = 3  # the first record's mode
+    bad.append(bytes(md))
     for b in bad:
         with pytest.raises(ipc.IpcError) as e:
             ipc.ipc_decode_container(b)
@@ -102,3 +107,17 @@ def test_oracle_container_shrinks():
     assert ipc.ipc_decode_container(c) == raw
     assert len(c) < len(raw)
     assert math.isfinite(len(raw) / len(c))
+
+
+def test_version_1_containers_still_decode():
+    """Containers of version 1 (one rANS state per record), as the
+    restatement still writes them, decode in the library and in the
+    restatement; version 2 records are one state pair per record."""
+    rng = np.random.default_rng(8)
+    for raw in (rng.geometric(0.2, 20000).clip(0, 255).astype(np.uint8).tobytes(), b"\x05" * 5000,
+                bytes(range(256)) * 40):
+        v1 = ro.encode(raw, block_log2=12, version=1)
+        assert v1[4] == 1 and ro.decode(v1) == raw
+        assert ipc.ipc_decode_container(v1) == raw
+        v2 = ro.encode(raw, block_log2=12)
+        assert v2[4] == 2 and v2 == ipc.ipc_encode_container(raw, block_log2=12)
