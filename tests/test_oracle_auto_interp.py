@@ -92,3 +92,13 @@ def test_invalid_arguments(oracle):
         oracle.auto_interp(x, 1e-3, oracle.REL)
     assert oracle.compress_rc(np.zeros(8, np.float32), 1e-3, oracle.ABS, interp=4) != 0
     assert oracle.compress_rc(np.zeros(8, np.float32), 1e-3, oracle.ABS, interp=oracle.AUTO) == 0
+
+
+def test_ties_take_the_lower_mode(oracle):
+    """A constant field codes to the same container under every mode (every
+    prediction is exact), and a field of two points has no interpolated
+    target: both ties go to linear."""
+    for x in (np.full((9, 10, 11), 3.5, dtype=np.float32), np.array([1.0, 2.0], dtype=np.float64)):
+        m, sizes = expected_mode(oracle, x, 1e-3, oracle.ABS)
+        assert sizes[0] == sizes[1] == sizes[2]
+        assert m == 0 and oracle.auto_interp(x, 1e-3, oracle.ABS) == oracle.LINEAR
