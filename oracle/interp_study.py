@@ -8,7 +8,9 @@ choice could reach: the sum over levels of the smallest of the three
 modes' stream bytes for that level (plus the smallest mandatory part). The
 estimate treats levels as independent, which they nearly are: a level's
 codes depend on the coarser levels only through reconstructions that
-differ by at most the error bound. The second table covers the order in which a level sweeps its
+differ by at most the error bound. The second table compares the per-field choice (interp 3: the mode with
+the smallest container on a sample) with the fixed cubic mode. The third
+covers the order in which a level sweeps its
 dimensions: compressing a transposed copy of a field sweeps its axes in the
 permuted order, so each permutation (with each mode) is compressed and the
 best is compared with the natural order's best. Oracle only (test
@@ -74,6 +76,18 @@ def main():
               % (name, tot[0], tot[1], tot[2], est, 100.0 * (best - est) / best, pick, E,
                  ret[0], ret[1], ret[2]))
         print("<!-- %s: %.1f s -->" % (name, time.perf_counter() - t0))
+    print()
+    print("| workload | mode chosen on the sample | container vs cubic | retrieval at E vs cubic |")
+    print("|---|---|---|---|")
+    for name, x, eb, mode, E in workloads():
+        m = oracle.auto_interp(x, eb, mode)
+        fa = oracle.compress(x, eb, mode, interp=oracle.AUTO)
+        fc = oracle.compress(x, eb, mode, interp=oracle.CUBIC)
+        ca, cc = len(fa.export()), len(fc.export())
+        ra = fa.retrieve(oracle.EB, E)[1].selection()[1]
+        rc = fc.retrieve(oracle.EB, E)[1].selection()[1]
+        print("| %s | %s | %+.2f %% | %g: %+.2f %% |" % (name, "LCQ"[m], 100.0 * (ca - cc) / cc, E,
+                                                        100.0 * (ra - rc) / rc))
     print()
     print("| workload | best (order, mode) by container | container below the natural order's best "
           "| retrieval at E below the natural order's best |")
