@@ -30,6 +30,9 @@ CASES = [
     ((20, 30, 40), np.float32, "spiky", 1e-4, oracle.ABS, oracle.CUBIC, oracle.STRICT),
     ((33, 50, 70), np.float32, "smooth", 1e-6, oracle.ABS, oracle.CUBIC_QUAD, oracle.STRICT),
     ((400, 700), np.float32, "zonal", 1e-5, oracle.REL, oracle.CUBIC, oracle.STRICT),
+    # the per-field choice: the container carries the chosen mode
+    ((24, 26, 28), np.float64, "spiky", 1e-7, oracle.REL, oracle.AUTO, oracle.STRICT),
+    ((30, 29, 31), np.float32, "smooth", 1e-5, oracle.ABS, oracle.AUTO, oracle.PAPER),
 ]
 
 
