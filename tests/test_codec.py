@@ -30,6 +30,9 @@ def inputs():
     yield "two symbols", rng.choice([3, 250], 7000, p=[0.99, 0.01]).astype(np.uint8).tobytes()
     yield "all 256 + tail", bytes(range(256)) * 3 + b"\x01" * 5000
     yield "block boundary", rng.geometric(0.5, 8192).astype(np.uint8).tobytes()
+    # odd block lengths: the last symbol of a coded block falls to state 0 alone
+    yield "odd last block", rng.geometric(0.3, 4096 + 1001).clip(0, 255).astype(np.uint8).tobytes()
+    yield "odd short block", rng.geometric(0.6, 4096 + 1023).clip(0, 255).astype(np.uint8).tobytes()
 
 
 @pytest.mark.parametrize("name,raw", list(inputs()), ids=[n for n, _ in inputs()])
@@ -121,3 +124,14 @@ def test_version_1_containers_still_decode():
         assert ipc.ipc_decode_container(v1) == raw
         v2 = ro.encode(raw, block_log2=12)
         assert v2[4] == 2 and v2 == ipc.ipc_encode_container(raw, block_log2=12)
+
+
+@pytest.mark.parametrize("n", [4097, 4099, 6001, 8191])
+def test_odd_length_coded_blocks(n):
+    """One coded block of odd length (block size 2^13): both states finish
+    in their initial value only if the odd symbol was coded by state 0."""
+    raw = np.random.default_rng(n).geometric(0.4, n).clip(0, 255).astype(np.uint8).tobytes()
+    c = ipc.ipc_encode_container(raw, block_log2=13)
+    assert c[28] == 2  # coded, not stored
+    assert c == ro.encode(raw, block_log2=13)
+    assert ipc.ipc_decode_container(c) == raw and ro.decode(c) == raw
